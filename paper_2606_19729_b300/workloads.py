@@ -1,0 +1,155 @@
+"""Seeded synthetic inputs for the rollout and belief-update workloads.
+
+This module only draws inputs (weights, particles, action sequences) from
+numpy's PCG64 generator and rounds them to the storage precision of a form.
+It holds none of the method's arithmetic, so both the CUDA path and the CPU
+oracle can be fed from it.
+
+The paper's robot tasks (FloorPositioning, LeggedNavigation, TargetFinding,
+Sec. 5.1) need simulators, datasets and trained weights that are not
+available; these workloads stand in for them with random-init MLPs shaped
+like the paper's models (Sec. 5.2 architecture paragraph) and the sizes of
+the five workload configurations:
+
+* ``small_fp32``  d_s=4, d_a=2, d_o=4, d_omega=4, MLPs 2x64 tanh, N=256, K=64, H=10
+* ``mid_bf16``    d_s=8, d_a=2, d_o=6, d_omega=8, MLPs 3x256 SiLU, N=4096, K=1024, H=20
+* ``sweep``       d_s=12, d_a=3, d_omega=16, generator 4x512 SiLU, N=16384, K=2048, H=25
+* ``distill``     teacher 3x512 + 64-d step embedding, student 3x256, B=65536
+* ``batched``     64 planners sharing the mid-size MLPs, uneven N, K, H
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional
+
+import numpy as np
+
+ACT_IDENTITY, ACT_TANH, ACT_SILU = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
+
+
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """Round FP64 values to the nearest bfloat16 (ties to even), returned as FP64."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    u = x.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    u = (u + np.uint64(0x7FFF) + lsb) & np.uint64(0xFFFF0000)
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def round_to(x: np.ndarray, prec: int) -> np.ndarray:
+    """Storage rounding of a weight tensor for precision form `prec`."""
+    if prec == PREC_BF16:
+        return round_bf16(x)
+    return np.asarray(x, np.float32).astype(np.float64)
+
+
+@dataclass
+class MLPSpec:
+    """Weights W[l] [out, in] and biases b[l] [out] as FP64 arrays, already rounded
+    to what the device stores (FP32 or BF16 weights; FP32 biases)."""
+    W: List[np.ndarray]
+    b: List[np.ndarray]
+    act: int
+    prec: int = PREC_FP32
+
+    @property
+    def dims(self) -> List[int]:
+        return [self.W[0].shape[1]] + [w.shape[0] for w in self.W]
+
+
+def xavier_mlp(rng: np.random.Generator, dims: List[int], act: int, prec: int,
+               bias_scale: float = 0.1) -> MLPSpec:
+    """Xavier-uniform weights U(+-sqrt(6/(fan_in+fan_out))) (Glorot and Bengio, 2010).
+
+    Biases are drawn U(+-bias_scale) rather than left at zero so that every
+    bias path is exercised.
+    """
+    W, b = [], []
+    for din, dout in zip(dims[:-1], dims[1:]):
+        a = math.sqrt(6.0 / (din + dout))
+        W.append(round_to(rng.uniform(-a, a, size=(dout, din)), prec))
+        b.append(round_to(rng.uniform(-bias_scale, bias_scale, size=(dout,)), PREC_FP32))
+    return MLPSpec(W, b, act, prec)
+
+
+@dataclass
+class Workload:
+    name: str
+    d_s: int
+    d_a: int
+    d_o: int
+    d_omega: int
+    N: int
+    K: int
+    H: int
+    gamma: float
+    seed: int
+    prec: int
+    g_T: MLPSpec
+    g_Z: Optional[MLPSpec]
+    ell: Optional[MLPSpec]
+    reward_mlp: Optional[MLPSpec]
+    goal: Optional[np.ndarray]
+    particles: np.ndarray          # [N, d_s]
+    actions: np.ndarray            # [K, H, d_a]
+    lam: float = 1.0
+    extra: Dict = field(default_factory=dict)
+
+
+def small_fp32(seed: int = 0, N: int = 256, K: int = 64, H: int = 10) -> Workload:
+    """Plain FP32 workload: 2x64 tanh MLPs, particles ~N(0, 0.5^2 I), actions U[-1,1]^2."""
+    rng = np.random.default_rng(seed)
+    d_s, d_a, d_o, d_w = 4, 2, 4, 4
+    g_T = xavier_mlp(rng, [d_s + d_a + d_w, 64, 64, d_s], ACT_TANH, PREC_FP32)
+    g_Z = xavier_mlp(rng, [d_s + d_a + d_w, 64, 64, d_o], ACT_TANH, PREC_FP32)
+    ell = xavier_mlp(rng, [d_s + d_a + d_o, 64, 64, 1], ACT_TANH, PREC_FP32)
+    rew = xavier_mlp(rng, [d_s + d_a, 64, 64, 1], ACT_TANH, PREC_FP32)
+    particles = round_to(rng.normal(0.0, 0.5, size=(N, d_s)), PREC_FP32)
+    actions = round_to(rng.uniform(-1.0, 1.0, size=(K, H, d_a)), PREC_FP32)
+    return Workload("small_fp32", d_s, d_a, d_o, d_w, N, K, H, 0.95, seed, PREC_FP32,
+                    g_T, g_Z, ell, rew, np.array([1.0, 1.0]), particles, actions)
+
+
+def mid_bf16(seed: int = 1, N: int = 4096, K: int = 1024, H: int = 20,
+             prec: int = PREC_BF16) -> Workload:
+    """Mid-size planning step: 3x256 SiLU MLPs, particles ~N(0, I), actions U[-1,1]^2."""
+    rng = np.random.default_rng(seed)
+    d_s, d_a, d_o, d_w = 8, 2, 6, 8
+    g_T = xavier_mlp(rng, [d_s + d_a + d_w, 256, 256, 256, d_s], ACT_SILU, prec)
+    g_Z = xavier_mlp(rng, [d_s + d_a + d_w, 256, 256, 256, d_o], ACT_SILU, prec)
+    ell = xavier_mlp(rng, [d_s + d_a + d_o, 256, 256, 256, 1], ACT_SILU, prec)
+    rew = xavier_mlp(rng, [d_s + d_a, 256, 256, 256, 1], ACT_SILU, prec)
+    particles = round_to(rng.normal(0.0, 1.0, size=(N, d_s)), PREC_FP32)
+    actions = round_to(rng.uniform(-1.0, 1.0, size=(K, H, d_a)), PREC_FP32)
+    return Workload("mid_bf16", d_s, d_a, d_o, d_w, N, K, H, 0.98, seed, prec,
+                    g_T, g_Z, ell, rew, None, particles, actions)
+
+
+def sweep(seed: int = 2, N: int = 16384, K: int = 2048, H: int = 25,
+          prec: int = PREC_BF16) -> Workload:
+    """Precision-sweep rollout: 4x512 SiLU generator, GOAL reward at (1, 1)."""
+    rng = np.random.default_rng(seed)
+    d_s, d_a, d_w = 12, 3, 16
+    g_T = xavier_mlp(rng, [d_s + d_a + d_w, 512, 512, 512, 512, d_s], ACT_SILU, prec)
+    particles = round_to(rng.normal(0.0, 1.0, size=(N, d_s)), PREC_FP32)
+    actions = round_to(rng.uniform(-1.0, 1.0, size=(K, H, d_a)), PREC_FP32)
+    return Workload("sweep", d_s, d_a, 0, d_w, N, K, H, 0.98, seed, prec,
+                    g_T, None, None, None, np.array([1.0, 1.0]), particles, actions)
+
+
+def true_state(rng_seed: int, d_s: int, scale: float) -> np.ndarray:
+    """The synthetic episode's true state, drawn from the particle prior."""
+    rng = np.random.default_rng(rng_seed + 1000)
+    return round_to(rng.normal(0.0, scale, size=(d_s,)), PREC_FP32)
+
+
+def batched_planners(seed: int = 4, P: int = 64):
+    """Per-planner (N_p, K_p, H_p): N log-uniform in [512, 16384], K uniform in
+    {128..1024}, H uniform in {5..30}."""
+    rng = np.random.default_rng(seed)
+    N = np.rint(np.exp(rng.uniform(math.log(512), math.log(16384), size=P))).astype(int)
+    K = rng.integers(128, 1025, size=P)
+    H = rng.integers(5, 31, size=P)
+    return N, K, H

@@ -1,0 +1,365 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each test ties one oracle function to an independent source: another
+implementation of the same published algorithm, a library routine, a closed
+form, a mathematical invariant or brute force on tiny inputs.
+"""
+import json
+import math
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+import scipy.special
+import scipy.stats
+import torch
+
+from oracle import voila_oracle as O
+from paper_2606_19729_b300 import workloads as WL
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10 against Triton's independent Python implementation, run in
+# Triton's CPU interpreter (a separate process so the interpreter switch
+# cannot leak into other tests).
+# --------------------------------------------------------------------------
+_TRITON_SCRIPT = textwrap.dedent(
+    """
+    import os, sys, json
+    os.environ["TRITON_INTERPRET"] = "1"
+    import torch, triton, triton.language as tl
+
+    @triton.jit
+    def kern(out_ptr, c_ptr, seed, n, BLOCK: tl.constexpr):
+        i = tl.arange(0, BLOCK)
+        m = i < n
+        c0 = tl.load(c_ptr + 4 * i + 0, mask=m).to(tl.uint32)
+        c1 = tl.load(c_ptr + 4 * i + 1, mask=m).to(tl.uint32)
+        c2 = tl.load(c_ptr + 4 * i + 2, mask=m).to(tl.uint32)
+        c3 = tl.load(c_ptr + 4 * i + 3, mask=m).to(tl.uint32)
+        a, b, c, d = tl.philox(seed, c0, c1, c2, c3)
+        tl.store(out_ptr + 4 * i + 0, a.to(tl.int64), mask=m)
+        tl.store(out_ptr + 4 * i + 1, b.to(tl.int64), mask=m)
+        tl.store(out_ptr + 4 * i + 2, c.to(tl.int64), mask=m)
+        tl.store(out_ptr + 4 * i + 3, d.to(tl.int64), mask=m)
+
+    cases = json.loads(sys.stdin.read())
+    res = []
+    for seed, ctrs in cases:
+        c = torch.tensor(ctrs, dtype=torch.int64).reshape(-1)
+        out = torch.zeros_like(c)
+        kern[(1,)](out, c, seed, len(ctrs), BLOCK=64)
+        res.append([int(v) & 0xFFFFFFFF for v in out.tolist()])
+    print(json.dumps(res))
+    """
+)
+
+
+def test_philox_matches_independent_implementation():
+    rng = np.random.default_rng(123)
+    cases = []
+    seeds = [0, 1, 0xFFFFFFFF, 0x123456789ABCDEF, 2 ** 64 - 1, int(rng.integers(0, 2 ** 63))]
+    for seed in seeds:
+        ctrs = rng.integers(0, 2 ** 32, size=(64, 4), dtype=np.uint64)
+        ctrs[0] = [0, 0, 0, 0]
+        ctrs[1] = [0xFFFFFFFF] * 4
+        cases.append([seed, ctrs.tolist()])
+    proc = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=json.dumps(cases),
+                          capture_output=True, text=True, timeout=600)
+    if proc.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + proc.stderr[-300:])
+    ref = json.loads(proc.stdout.strip().splitlines()[-1])
+    for (seed, ctrs), want in zip(cases, ref):
+        c = np.array(ctrs, dtype=np.uint64)
+        k0, k1 = O.seed_key(seed)
+        got = np.stack(O.philox4x32_10(c[:, 0], c[:, 1], c[:, 2], c[:, 3], k0, k1), axis=1)
+        assert got.reshape(-1).tolist() == want
+
+
+def test_philox_rounds_are_a_bijection_sample():
+    # Distinct counters must give distinct outputs (Philox is a bijection of the counter space).
+    n = np.arange(1 << 16, dtype=np.uint64)
+    w = O.philox4x32_10(n, 0, 0, 0, 7, 9)
+    packed = {(int(a), int(b), int(c), int(d)) for a, b, c, d in zip(*w)}
+    assert len(packed) == n.size
+
+
+def test_uniform24_range_and_exactness():
+    x = np.array([0, 1, 511, 512, 0x7FFFFFFF, 0xFFFFFFFF], dtype=np.uint64)
+    u = O.uniform24(x)
+    assert u[0] == 2.0 ** -24 and u[1] == 2.0 ** -24 and u[2] == 2.0 ** -24
+    assert u[3] == 3 * 2.0 ** -24
+    assert u[-1] == 1.0 - 2.0 ** -24
+    assert np.all(u.astype(np.float32).astype(np.float64) == u)   # exact in FP32
+    assert np.all((u > 0) & (u < 1))
+
+
+def test_uniform53_range():
+    assert O.uniform53(0, 0) == 0.0
+    assert O.uniform53(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    assert O.uniform53(0, 1 << 11) == 2.0 ** -53
+
+
+def test_box_muller_invariants():
+    rng = np.random.default_rng(5)
+    ua = rng.uniform(1e-9, 1.0, 1000)
+    ub = rng.uniform(0.0, 1.0, 1000)
+    z0, z1 = O.box_muller(ua, ub)
+    np.testing.assert_allclose(z0 * z0 + z1 * z1, -2.0 * np.log(ua), rtol=1e-12, atol=1e-14)
+    ang = np.mod(np.arctan2(z1, z0), 2 * math.pi)
+    d = np.abs(ang - 2 * math.pi * ub)
+    d = np.minimum(d, 2 * math.pi - d)
+    assert np.max(d[np.abs(ua - 1) > 1e-6]) < 1e-9
+
+
+def test_normals_are_standard_normal():
+    z = O.normals(42, np.arange(1 << 14), 3, 5, O.STREAM_ROLLOUT_OMEGA, 0, 8)
+    assert z.shape == (1 << 14, 8)
+    flat = z.reshape(-1)
+    assert abs(flat.mean()) < 0.01 and abs(flat.var() - 1.0) < 0.02
+    assert scipy.stats.kstest(flat, "norm").pvalue > 1e-4
+    # Columns from different Philox words and blocks are uncorrelated.
+    c = np.corrcoef(z.T)
+    assert np.max(np.abs(c - np.eye(8))) < 0.05
+    # Different streams give different numbers for the same counter.
+    z2 = O.normals(42, np.arange(16), 3, 5, O.STREAM_BELIEF_OMEGA, 0, 8)
+    assert not np.allclose(z2, z[:16])
+
+
+# --------------------------------------------------------------------------
+# MLP forward/backward against torch (float64) and finite differences.
+# --------------------------------------------------------------------------
+def _torch_mlp(spec, x):
+    h = torch.tensor(x, dtype=torch.float64)
+    for l, (W, b) in enumerate(zip(spec.W, spec.b)):
+        h = torch.nn.functional.linear(h, torch.tensor(W), torch.tensor(b))
+        if l < len(spec.W) - 1:
+            h = {O.ACT_TANH: torch.tanh, O.ACT_SILU: torch.nn.functional.silu,
+                 O.ACT_IDENTITY: lambda v: v}[spec.act](h)
+    return h
+
+
+@pytest.mark.parametrize("act", [O.ACT_TANH, O.ACT_SILU, O.ACT_IDENTITY])
+def test_mlp_forward_matches_torch(act):
+    rng = np.random.default_rng(1)
+    spec = WL.xavier_mlp(rng, [10, 64, 32, 4], act, WL.PREC_FP32)
+    x = rng.normal(size=(37, 10)) * 3
+    got = O.mlp_forward(O.MLP(spec.W, spec.b, act), x)
+    want = _torch_mlp(spec, x).numpy()
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("act", [O.ACT_TANH, O.ACT_SILU])
+def test_mlp_backward_matches_autograd_and_fd(act):
+    rng = np.random.default_rng(2)
+    spec = WL.xavier_mlp(rng, [6, 16, 16, 3], act, WL.PREC_FP32)
+    m = O.MLP(spec.W, spec.b, act)
+    x = rng.normal(size=(16, 6))
+    dY = rng.normal(size=(16, 3))
+    dX, dW, db = O.mlp_backward(m, x, dY)
+    # autograd
+    xt = torch.tensor(x, requires_grad=True)
+    Ws = [torch.tensor(W, requires_grad=True) for W in spec.W]
+    bs = [torch.tensor(b, requires_grad=True) for b in spec.b]
+    h = xt
+    for l in range(3):
+        h = torch.nn.functional.linear(h, Ws[l], bs[l])
+        if l < 2:
+            h = torch.tanh(h) if act == O.ACT_TANH else torch.nn.functional.silu(h)
+    (h * torch.tensor(dY)).sum().backward()
+    np.testing.assert_allclose(dX, xt.grad.numpy(), rtol=1e-12, atol=1e-12)
+    for l in range(3):
+        np.testing.assert_allclose(dW[l], Ws[l].grad.numpy(), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(db[l], bs[l].grad.numpy(), rtol=1e-12, atol=1e-12)
+    # central differences on a few weight entries, h = 1e-6
+    def loss(mm):
+        return float(np.sum(O.mlp_forward(mm, x) * dY))
+    for l, (i, j) in [(0, (3, 2)), (1, (5, 7)), (2, (1, 9))]:
+        Wp = [w.copy() for w in spec.W]
+        Wm = [w.copy() for w in spec.W]
+        Wp[l][i, j] += 1e-6
+        Wm[l][i, j] -= 1e-6
+        fd = (loss(O.MLP(Wp, spec.b, act)) - loss(O.MLP(Wm, spec.b, act))) / 2e-6
+        assert abs(fd - dW[l][i, j]) < 1e-6 * max(1.0, abs(fd))
+
+
+# --------------------------------------------------------------------------
+# Rollout closed forms.
+# --------------------------------------------------------------------------
+def _linear_generator(d_s, d_a, d_w, sigma, two_layer=False):
+    """s' = s + P a + sigma * omega, P = first d_a coordinates."""
+    W = np.zeros((d_s, d_s + d_a + d_w))
+    W[:, :d_s] = np.eye(d_s)
+    for i in range(min(d_a, d_s)):
+        W[i, d_s + i] = 1.0
+    for i in range(min(d_w, d_s)):
+        W[i, d_s + d_a + i] = sigma
+    b = np.zeros(d_s)
+    if two_layer:
+        return O.MLP([W, np.eye(d_s)], [b, np.zeros(d_s)], O.ACT_IDENTITY)
+    return O.MLP([W], [b], O.ACT_IDENTITY)
+
+
+@pytest.mark.parametrize("sigma,two_layer", [(0.0, False), (0.0, True), (0.3, False), (0.3, True)])
+def test_rollout_linear_closed_form(sigma, two_layer):
+    rng = np.random.default_rng(3)
+    N, K, H, d_s, d_a, d_w = 5, 3, 7, 4, 2, 4
+    gamma, seed = 0.9, 11
+    particles = rng.normal(size=(N, d_s))
+    actions = rng.uniform(-1, 1, size=(K, H, d_a))
+    goal = np.array([1.0, -0.5])
+    g = _linear_generator(d_s, d_a, d_w, sigma, two_layer)
+    J, G = O.rollout(g, O.Reward(O.REWARD_GOAL, goal), particles, actions, d_w, gamma, seed)
+    # closed form: s_t = s_0 + P cumsum(a) + sigma cumsum(omega)
+    G_ref = np.zeros((K, N))
+    for k in range(K):
+        for n in range(N):
+            s = particles[n].copy()
+            for t in range(H):
+                s[:d_a] += actions[k, t]
+                if sigma:
+                    s[:d_w] += sigma * O.normals(seed, n, k, t, O.STREAM_ROLLOUT_OMEGA, 0, d_w)
+                G_ref[k, n] += gamma ** t * -np.sum((s[:2] - goal) ** 2)
+    np.testing.assert_allclose(G, G_ref, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(J, G_ref.mean(axis=1), rtol=1e-12, atol=1e-12)
+
+
+def test_rollout_constant_reward_geometric_series():
+    # Identity generator, zero actions: r_t is constant, G = r (1 - gamma^H) / (1 - gamma).
+    N, K, H, d_s, d_a = 3, 2, 12, 2, 2
+    g = _linear_generator(d_s, d_a, 0, 0.0)
+    particles = np.array([[0.0, 0.0], [1.0, 1.0], [2.0, 0.0]])
+    actions = np.zeros((K, H, d_a))
+    goal = np.array([1.0, 1.0])
+    gamma = 0.95
+    J, G = O.rollout(g, O.Reward(O.REWARD_GOAL, goal), particles, actions, 0, gamma, 0)
+    r = -np.array([2.0, 0.0, 2.0])
+    np.testing.assert_allclose(G, np.tile(r * (1 - gamma ** H) / (1 - gamma), (K, 1)), rtol=1e-14)
+
+
+def test_rollout_weights_and_subset():
+    wl = WL.small_fp32(N=9, K=5, H=3)
+    g = O.MLP(wl.g_T.W, wl.g_T.b, wl.g_T.act)
+    R = O.Reward(O.REWARD_GOAL, wl.goal)
+    w = np.random.default_rng(0).dirichlet(np.ones(9))
+    J, G = O.rollout(g, R, wl.particles, wl.actions, wl.d_omega, wl.gamma, wl.seed, w=w)
+    np.testing.assert_allclose(J, G @ w, rtol=1e-14)
+    # evaluating a subset of sequences reproduces the same rows (noise keyed by global k)
+    Js, Gs = O.rollout(g, R, wl.particles, wl.actions, wl.d_omega, wl.gamma, wl.seed, w=w, k_index=[4, 1])
+    np.testing.assert_allclose(Gs, G[[4, 1]], rtol=1e-14)  # BLAS blocking may differ by an ulp
+
+
+def test_best_sequence_lowest_index_on_ties():
+    assert O.best_sequence(np.array([1.0, 3.0, 3.0, 2.0])) == 1
+    assert O.best_sequence(np.array([-5.0])) == 0
+
+
+# --------------------------------------------------------------------------
+# Weights, log-sum-exp and systematic resampling.
+# --------------------------------------------------------------------------
+def test_log_normalise_matches_brute_force_and_scipy():
+    rng = np.random.default_rng(4)
+    for N in range(1, 9):
+        lw = rng.normal(size=N) * 30
+        w, logZ = O.log_normalise(lw)
+        brute = math.log(math.fsum(math.exp(v) for v in lw))
+        assert abs(logZ - brute) < 1e-12 * max(1, abs(brute))
+        assert abs(logZ - scipy.special.logsumexp(lw)) < 1e-12 * max(1, abs(brute))
+        np.testing.assert_allclose(w, [math.exp(v - brute) for v in lw], rtol=1e-12)
+    with pytest.raises(O.DegenerateWeights):
+        O.log_normalise(np.full(4, -np.inf))
+    with pytest.raises(O.NonFiniteWeights):
+        O.log_normalise(np.array([0.0, np.nan]))
+
+
+def test_gaussian_likelihood_gives_analytic_weights():
+    rng = np.random.default_rng(6)
+    N, d_s, d_o, sigma = 200, 4, 3, 0.7
+    s = rng.normal(size=(N, d_s))
+    o = rng.normal(size=d_o)
+    ell = O.likelihood(O.Likelihood(O.LIK_GAUSSIAN, sigma=sigma), s, np.zeros(2), o)
+    w, _ = O.log_normalise(ell)
+    dens = np.array([scipy.stats.multivariate_normal(mean=s[i, :d_o], cov=sigma ** 2 * np.eye(d_o)).pdf(o)
+                     for i in range(N)])
+    np.testing.assert_allclose(w, dens / dens.sum(), rtol=1e-10)
+
+
+def test_quantised_weights_sum_to_one_and_prefix_is_order_free():
+    rng = np.random.default_rng(7)
+    for N in [1, 2, 7, 256, 4096, 16384]:
+        w, _ = O.log_normalise(rng.normal(size=N) * 5)
+        q = O.quantise_weights(w)
+        assert abs(np.sum(q) - 1.0) <= N * 2.0 ** -52
+        assert np.all(q * 2.0 ** 52 == np.rint(q * 2.0 ** 52))
+        fwd = math.fsum(q)
+        acc = 0.0
+        for v in q[::-1]:
+            acc += v
+        pair = q.copy()
+        while pair.size > 1:
+            if pair.size % 2:
+                pair = np.append(pair, 0.0)
+            pair = pair[0::2] + pair[1::2]
+        assert acc == fwd == pair[0] == np.cumsum(q)[-1]
+
+
+def _brute_systematic(q, u0):
+    N = len(q)
+    C = []
+    acc = 0.0
+    for v in q:
+        acc += v
+        C.append(acc)
+    out = []
+    for j in range(N):
+        p = ((u0 + j) * C[-1]) / N
+        i = 0
+        while i < N and not (C[i] > p):
+            i += 1
+        out.append(min(i, N - 1))
+    return out
+
+
+def test_systematic_resampling_brute_force_and_properties():
+    rng = np.random.default_rng(8)
+    for N in [1, 2, 3, 5, 8, 13]:
+        for _ in range(20):
+            w, _ = O.log_normalise(rng.normal(size=N) * 2)
+            q = O.quantise_weights(w)
+            u0 = float(rng.uniform())
+            idx = O.systematic_resample(q, u0)
+            assert idx.tolist() == _brute_systematic(q, u0)
+            # each particle is drawn floor(N q_i) or ceil(N q_i) times
+            counts = np.bincount(idx, minlength=N)
+            assert np.all(counts >= np.floor(N * q - 1e-9)) and np.all(counts <= np.ceil(N * q + 1e-9))
+            assert np.all(np.diff(idx) >= 0)
+    # uniform weights -> identity; one-hot -> all equal
+    for N in [4, 64, 1024]:
+        q = O.quantise_weights(np.full(N, 1.0 / N))
+        assert O.systematic_resample(q, 0.37).tolist() == list(range(N))
+        oh = np.zeros(N)
+        oh[N // 3] = 1.0
+        assert set(O.systematic_resample(oh, 0.9).tolist()) == {N // 3}
+
+
+def test_belief_update_identity_proposal_gaussian():
+    # Identity proposal (no noise): weights are the analytic Gaussian posterior over particles.
+    rng = np.random.default_rng(9)
+    N, d_s, d_a, d_o = 64, 3, 2, 2
+    g = _linear_generator(d_s, d_a, 0, 0.0)
+    s = rng.normal(size=(N, d_s))
+    a = np.zeros(d_a)
+    o = np.array([0.2, -0.1])
+    res = O.belief_update(g, O.Likelihood(O.LIK_GAUSSIAN, sigma=0.5), s, a, o, 0, 1.0, 5, 2)
+    dens = np.exp(-np.sum((s[:, :d_o] - o) ** 2, axis=1) / (2 * 0.25))
+    np.testing.assert_allclose(res.w, dens / dens.sum(), rtol=1e-9, atol=1e-15)
+    np.testing.assert_array_equal(res.particles_out, s[res.idx])
+    assert abs(res.ess - 1.0 / np.sum((dens / dens.sum()) ** 2)) < 1e-9 * res.ess
+    # temperature lambda flattens: lambda -> large gives ESS -> N
+    res2 = O.belief_update(g, O.Likelihood(O.LIK_GAUSSIAN, sigma=0.5), s, a, o, 0, 1e6, 5, 2)
+    assert res2.ess > N * 0.999
