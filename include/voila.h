@@ -1,0 +1,233 @@
+/*
+ * voila.h - C-ABI of the VOiLA planning-loop hot path on B300 (sm_103a).
+ *
+ * VOiLA (Vectorized Online planning wIth Learned diffusion model for POMDP
+ * Agents) plans with a distilled feed-forward transition generator
+ * s' = f_T(s, a, omega_T) (Eq. 2), an observation sampler z = f_Z(s', a, omega_Z)
+ * (Eq. 5) and an unnormalised likelihood l(s', a, o) whose tempered
+ * exponential exp(l / lambda) weights particles (Sec. 4.2.3). This library
+ * runs the data-parallel part of that loop:
+ *
+ *   voila_rollout        Monte-Carlo rollout of N particles x K action
+ *                        sequences x H steps and the per-sequence return
+ *                        reduction (value definition of Sec. 2.1; the
+ *                        Monte-Carlo estimate of R(b, a) in Eq. 1, Sec. 2.2).
+ *   voila_belief_update  one SIR particle-filter step: propose with f_T,
+ *                        weight with l, normalise, resample systematically
+ *                        (Sec. 3, belief operator of Sec. 2.1).
+ *   voila_generator_fwd  batched forward of a generator MLP (Eq. 2 / Eq. 5).
+ *   voila_philox_fill    raw Philox4x32-10 words, for checking the noise stream.
+ *
+ * Conventions shared by every call:
+ *  - Every array argument is DEVICE memory owned by the caller unless the
+ *    comment says "host". The library never allocates on these paths: it uses
+ *    the caller's workspace, whose size the *_workspace_size calls return.
+ *  - Calls are asynchronous on `stream`. The returned status reports argument
+ *    validation and kernel launch only. Conditions found on the device
+ *    (non-finite or all-zero weights, a wait that timed out) are written to a
+ *    status word inside the workspace; voila_workspace_status() reads it.
+ *  - Outputs are undefined when a call or its device status is not VOILA_OK.
+ *  - Calls with distinct workspaces may run concurrently.
+ *  - Layouts are row-major and densely packed.
+ *
+ * Random numbers: omega is drawn in-kernel by Philox4x32-10 (Salmon et al.,
+ * SC'11) with key = (seed & 0xffffffff, seed >> 32) and counter
+ * (c0, c1, c2, c3) = (n, k, t, stream << 28 | planner << 12 | block); each
+ * block gives four uniforms u = (2 * (x >> 9) + 1) * 2^-24 and four normals
+ * by Box-Muller, (r cos 2 pi u1, r sin 2 pi u1), r = sqrt(-2 ln u0), then
+ * (r' cos 2 pi u3, r' sin 2 pi u3), r' = sqrt(-2 ln u2).
+ * Streams: 0 rollout omega_T(n, k, t); 1 belief-update omega_T(i, 0, step);
+ * 2 resampling offset (0, 0, step); 3 observation omega_Z.
+ */
+#ifndef VOILA_H_
+#define VOILA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* voila_stream_t;
+
+typedef enum {
+  VOILA_OK = 0,
+  VOILA_ERR_ARG = -1,          /* null pointer, bad enum, negative size */
+  VOILA_ERR_SHAPE = -2,        /* inconsistent dimensions between arguments */
+  VOILA_ERR_CUDA = -3,         /* a CUDA runtime call or launch failed */
+  VOILA_ERR_NONFINITE = -4,    /* device status: a log-weight was NaN or +inf */
+  VOILA_ERR_DEGENERATE = -5,   /* device status: every log-weight was -inf */
+  VOILA_ERR_TIMEOUT = -6,      /* device status: a bounded wait ran out */
+  VOILA_ERR_UNSUPPORTED = -7,  /* valid request this build has no kernel for */
+  VOILA_ERR_WORKSPACE = -8     /* workspace missing, misaligned or too small */
+} voila_status;
+
+enum { VOILA_ACT_IDENTITY = 0, VOILA_ACT_TANH = 1, VOILA_ACT_SILU = 2 };
+enum { VOILA_FP32 = 0, VOILA_BF16 = 1, VOILA_FP8E4M3 = 2 };
+enum { VOILA_REWARD_GOAL = 0, VOILA_REWARD_MLP = 1 };
+enum { VOILA_LIK_MLP = 0, VOILA_LIK_GAUSSIAN = 1 };
+enum {
+  VOILA_STREAM_ROLLOUT_OMEGA = 0,
+  VOILA_STREAM_BELIEF_OMEGA = 1,
+  VOILA_STREAM_RESAMPLE = 2,
+  VOILA_STREAM_OBS_OMEGA = 3
+};
+
+#define VOILA_MAX_LAYERS 8
+#define VOILA_MAX_WIDTH 512
+#define VOILA_MAX_GOAL 4
+
+/*
+ * A feed-forward MLP y = L_n(act(... act(L_1(x)))), L_l(h) = h W_l^T + b_l,
+ * with a linear last layer: the distilled generator form of Eq. 2 and the
+ * model shapes of Sec. 5.2 (widths up to VOILA_MAX_WIDTH).
+ *   W[l]  device, row-major [dims[l+1]][dims[l]] ("[out][in]"), element type
+ *         float for VOILA_FP32, __nv_bfloat16 for VOILA_BF16.
+ *   b[l]  device, float [dims[l+1]].
+ *   w_scale[l]  FP8 form only (per-output-channel scales); NULL otherwise.
+ * The struct itself is read on the host during the call and may be freed
+ * after the call returns.
+ */
+typedef struct {
+  int32_t n_layers;                       /* 1 .. VOILA_MAX_LAYERS */
+  int32_t dims[VOILA_MAX_LAYERS + 1];     /* dims[0] input width, dims[n_layers] output width */
+  int32_t act;                            /* VOILA_ACT_*, applied after every layer but the last */
+  int32_t prec;                           /* VOILA_FP32 or VOILA_BF16 */
+  const void* W[VOILA_MAX_LAYERS];
+  const float* b[VOILA_MAX_LAYERS];
+  const float* w_scale[VOILA_MAX_LAYERS];
+} voila_mlp;
+
+/*
+ * Reward head R(s_{t+1}, a_t) (reward function of the POMDP tuple, Sec. 2.1;
+ * the post-transition state is the one scored).
+ *   GOAL: r = -sum_{d < goal_dims} (s[d] - goal[d])^2, goal given on the host.
+ *   MLP:  r = R([s; a]) with mlp->dims[0] == d_s + d_a and a scalar output.
+ */
+typedef struct {
+  int32_t kind;
+  int32_t goal_dims;
+  float goal[VOILA_MAX_GOAL];
+  const voila_mlp* mlp;
+} voila_reward;
+
+/*
+ * Likelihood l(s', a, o) (Sec. 4.2.3).
+ *   MLP:      l = mlp([s'; a; o]), mlp->dims[0] == d_s + d_a + d_o, scalar output.
+ *   GAUSSIAN: l = -||o - s'[:d_o]||^2 / (2 sigma^2), an analytic test kind.
+ */
+typedef struct {
+  int32_t kind;
+  float sigma;
+  const voila_mlp* mlp;
+} voila_likelihood;
+
+/* Status word written by kernels into a workspace; blocks on `stream`. */
+voila_status voila_workspace_status(const void* workspace, voila_stream_t stream);
+
+/* Human-readable name of a status code (static string). */
+const char* voila_status_string(voila_status s);
+
+/*
+ * Workspace bytes for voila_rollout with these sizes (host call, no device work).
+ */
+voila_status voila_rollout_workspace_size(const voila_mlp* g_T, const voila_reward* R,
+                                          int32_t N, int32_t K, int32_t H, size_t* bytes);
+
+/*
+ * Batched Monte-Carlo rollout (value definition, Sec. 2.1; R(b, a) estimate
+ * of Eq. 1, Sec. 2.2; generator of Eq. 2).
+ * For every particle n < N and action sequence k < K:
+ *   s_0 = particles[n];  for t < H:
+ *     s_{t+1} = g_T([s_t; actions[k][t]; omega_T(n, k, t)])
+ *     G[k][n] += gamma^t * R(s_{t+1}, actions[k][t])
+ *   J[k] = sum_n w[n] * G[k][n]   (w = 1/N when w == NULL)
+ *   best_k = argmax_k J[k], lowest index on ties.
+ * Arguments:
+ *   particles [N][d_s] float; w [N] double or NULL; actions [K][H][d_a] float;
+ *   g_T->dims[0] == d_s + d_a + d_omega, g_T output width == d_s;
+ *   J [K] double (required); G [K][N] double or NULL; best_k [1] int32 or NULL.
+ *   planner_id < 65536 selects an independent noise stream per planner.
+ * Precision forms: VOILA_FP32 runs on CUDA cores in FP32; VOILA_BF16 runs on
+ * the tcgen05 tensor cores (BF16 operands, FP32 accumulation in TMEM).
+ * Returns are accumulated in FP64 in both forms.
+ * N == 0 or K == 0 is a no-op; H == 0 gives zero returns.
+ */
+voila_status voila_rollout(const voila_mlp* g_T, const voila_reward* R,
+                           const float* particles, const double* w, int32_t N, int32_t d_s,
+                           const float* actions, int32_t K, int32_t H, int32_t d_a,
+                           int32_t d_omega, double gamma, uint64_t seed, uint32_t planner_id,
+                           double* J, double* G, int32_t* best_k,
+                           void* workspace, size_t ws_bytes, voila_stream_t stream);
+
+/* Workspace bytes for voila_belief_update. */
+voila_status voila_belief_update_workspace_size(const voila_mlp* g_T, const voila_likelihood* ell,
+                                                int32_t N, size_t* bytes);
+
+/*
+ * One SIR particle-filter step (Sec. 3; belief operator of Sec. 2.1; weights
+ * exp(l / lambda), Sec. 4.2.3):
+ *   s'_i = g_T([particles_in[i]; action; omega_T(i, 0, step)])
+ *   lw_i = logw_in[i] + l(s'_i, action, obs) / lambda    (logw_in NULL = 0)
+ *   w_i  = exp(lw_i - max lw) / sum_j exp(lw_j - max lw)
+ *   q_i  = rn(w_i * 2^52) * 2^-52; C = inclusive FP64 prefix sum of q (exact)
+ *   u0   = 53-bit uniform from stream 2 at counter (0, 0, step)
+ *   idx_j = min{i : C_i > ((u0 + j) * C_{N-1}) / N}, or N-1 if none
+ *   particles_out[j] = s'_{idx_j}
+ * Arguments: particles_in [N][d_s] float; logw_in [N] double or NULL;
+ *   action [d_a] and obs [d_o] float (device); particles_out [N][d_s] float;
+ *   idx_out [N] int32 or NULL; w_out [N] double (the q_i) or NULL;
+ *   logZ_out [1] double = log sum_i exp(lw_i), or NULL; ess_out [1] double =
+ *   1 / sum_i q_i^2, or NULL. particles_out must not alias particles_in.
+ * Device status: VOILA_ERR_NONFINITE if some lw_i is NaN or +inf,
+ * VOILA_ERR_DEGENERATE if all are -inf. N <= 262144.
+ */
+voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* ell,
+                                 const float* particles_in, const double* logw_in,
+                                 int32_t N, int32_t d_s, const float* action, const float* obs,
+                                 int32_t d_a, int32_t d_o, int32_t d_omega, float lambda,
+                                 uint64_t seed, uint32_t step, uint32_t planner_id,
+                                 float* particles_out, int32_t* idx_out, double* w_out,
+                                 double* logZ_out, double* ess_out,
+                                 void* workspace, size_t ws_bytes, voila_stream_t stream);
+
+/*
+ * Batched MLP forward Y = mlp(X) (Eq. 2 / Eq. 5 generator form).
+ *   X [B][dims[0]] float, Y [B][dims[n_layers]] float. No workspace.
+ */
+voila_status voila_generator_fwd(const voila_mlp* mlp, const float* X, int32_t B, float* Y,
+                                 voila_stream_t stream);
+
+/*
+ * Seeded sampler form of Eq. 2 / Eq. 5: Y[i] = mlp([S[i]; A[i]; omega(i, 0, step)])
+ * with omega from Philox stream `stream_id`. S [B][d_s], A [B][d_a] float;
+ * A may have row stride 0 (a_stride = 0: one action for every row).
+ */
+voila_status voila_generator_fwd_seeded(const voila_mlp* mlp, const float* S, const float* A,
+                                        int32_t a_stride, int32_t B, int32_t d_s, int32_t d_a,
+                                        int32_t d_omega, uint64_t seed, uint32_t stream_id,
+                                        uint32_t step, uint32_t planner_id, float* Y,
+                                        voila_stream_t stream);
+
+/*
+ * Raw Philox4x32-10 words: out[4 i + j] = word j of counter (i, c1, c2, c3),
+ * i < n. out holds 4 n uint32 (device).
+ */
+voila_status voila_philox_fill(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3,
+                               uint32_t* out, int64_t n, voila_stream_t stream);
+
+/*
+ * The normals the kernels draw: out[i][d] = component d of the noise vector
+ * at counter (i, c1, c2) of stream `stream_id`, i < n, d < dim (float, device).
+ */
+voila_status voila_normal_fill(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t stream_id,
+                               uint32_t planner_id, int32_t dim, float* out, int64_t n,
+                               voila_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VOILA_H_ */

@@ -1,0 +1,361 @@
+// C-ABI entry points (include/voila.h): argument validation, workspace
+// layout and kernel dispatch. No entry point allocates device memory.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/voila.h"
+#include "kernels.h"
+#include "tc.h"
+
+using namespace voila;
+
+namespace {
+
+constexpr size_t kHeaderBytes = 256;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
+
+bool valid_mlp(const voila_mlp* m) {
+  if (!m) return false;
+  if (m->n_layers < 1 || m->n_layers > VOILA_MAX_LAYERS) return false;
+  if (m->act < VOILA_ACT_IDENTITY || m->act > VOILA_ACT_SILU) return false;
+  if (m->prec != VOILA_FP32 && m->prec != VOILA_BF16 && m->prec != VOILA_FP8E4M3) return false;
+  for (int l = 0; l <= m->n_layers; ++l)
+    if (m->dims[l] < 1 || m->dims[l] > VOILA_MAX_WIDTH) return false;
+  for (int l = 0; l < m->n_layers; ++l)
+    if (!m->W[l] || !m->b[l]) return false;
+  return true;
+}
+
+int max_width(const voila_mlp* m) {
+  int w = 0;
+  for (int l = 0; l <= m->n_layers; ++l) w = m->dims[l] > w ? m->dims[l] : w;
+  return w;
+}
+
+int simt_ld(int maxw) { return (maxw % 2 == 0) ? maxw + 1 : maxw; }
+
+MlpDev to_dev(const voila_mlp* m) {
+  MlpDev d;
+  memset(&d, 0, sizeof(d));
+  if (!m) return d;
+  d.n_layers = m->n_layers;
+  d.act = m->act;
+  d.prec = m->prec;
+  for (int l = 0; l <= VOILA_MAX_LAYERS; ++l) d.dims[l] = m->dims[l];
+  for (int l = 0; l < VOILA_MAX_LAYERS; ++l) {
+    d.W[l] = m->W[l];
+    d.b[l] = m->b[l];
+  }
+  return d;
+}
+
+void philox_key(uint64_t seed, uint32_t& k0, uint32_t& k1) {
+  k0 = (uint32_t)(seed & 0xffffffffu);
+  k1 = (uint32_t)(seed >> 32);
+}
+
+voila_status cuda_status(cudaError_t e) { return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA; }
+
+// Rollout workspace: [header | G (if not caller-provided) | tensor-core scratch]
+struct RolloutLayout {
+  size_t g_off, tc_off, total;
+};
+
+RolloutLayout rollout_layout(const voila_mlp* g_T, const voila_reward* R, long long N, long long K,
+                             int H, bool need_g) {
+  RolloutLayout L;
+  size_t off = kHeaderBytes;
+  L.g_off = off;
+  if (need_g) off = align_up(off + (size_t)N * K * sizeof(double));
+  L.tc_off = off;
+  if (g_T->prec == VOILA_BF16) off = align_up(off + tc_rollout_scratch_bytes(g_T, R));
+  L.total = off;
+  return L;
+}
+
+voila_status check_rollout(const voila_mlp* g_T, const voila_reward* R, int32_t N, int32_t d_s,
+                           int32_t K, int32_t H, int32_t d_a, int32_t d_omega) {
+  if (!valid_mlp(g_T) || !R) return VOILA_ERR_ARG;
+  if (N < 0 || K < 0 || H < 0 || d_s < 1 || d_a < 0 || d_omega < 0) return VOILA_ERR_ARG;
+  if (d_s > 32 || d_a > 32 || d_omega > 64) return VOILA_ERR_SHAPE;
+  if (g_T->dims[0] != d_s + d_a + d_omega || g_T->dims[g_T->n_layers] != d_s)
+    return VOILA_ERR_SHAPE;
+  if (R->kind == VOILA_REWARD_GOAL) {
+    if (R->goal_dims < 1 || R->goal_dims > VOILA_MAX_GOAL || R->goal_dims > d_s)
+      return VOILA_ERR_SHAPE;
+  } else if (R->kind == VOILA_REWARD_MLP) {
+    if (!valid_mlp(R->mlp)) return VOILA_ERR_ARG;
+    if (R->mlp->dims[0] != d_s + d_a || R->mlp->dims[R->mlp->n_layers] != 1)
+      return VOILA_ERR_SHAPE;
+    if (R->mlp->prec != g_T->prec) return VOILA_ERR_UNSUPPORTED;
+  } else {
+    return VOILA_ERR_ARG;
+  }
+  if (g_T->prec == VOILA_FP8E4M3) return VOILA_ERR_UNSUPPORTED;
+  if ((long long)N * K > (1LL << 31)) return VOILA_ERR_SHAPE;
+  return VOILA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* voila_status_string(voila_status s) {
+  switch (s) {
+    case VOILA_OK: return "ok";
+    case VOILA_ERR_ARG: return "invalid argument";
+    case VOILA_ERR_SHAPE: return "inconsistent shapes";
+    case VOILA_ERR_CUDA: return "CUDA error";
+    case VOILA_ERR_NONFINITE: return "non-finite log-weight";
+    case VOILA_ERR_DEGENERATE: return "all log-weights are -inf";
+    case VOILA_ERR_TIMEOUT: return "bounded device wait timed out";
+    case VOILA_ERR_UNSUPPORTED: return "unsupported configuration";
+    case VOILA_ERR_WORKSPACE: return "workspace missing or too small";
+  }
+  return "unknown status";
+}
+
+voila_status voila_workspace_status(const void* workspace, voila_stream_t stream) {
+  if (!workspace) return VOILA_ERR_ARG;
+  WsHeader h;
+  cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost,
+                                  (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return VOILA_ERR_CUDA;
+  return (voila_status)h.status;
+}
+
+voila_status voila_rollout_workspace_size(const voila_mlp* g_T, const voila_reward* R, int32_t N,
+                                          int32_t K, int32_t H, size_t* bytes) {
+  if (!bytes || !valid_mlp(g_T) || !R || N < 0 || K < 0 || H < 0) return VOILA_ERR_ARG;
+  // G scratch is always reserved so callers may pass G == NULL.
+  *bytes = rollout_layout(g_T, R, N, K, H, true).total;
+  return VOILA_OK;
+}
+
+voila_status voila_rollout(const voila_mlp* g_T, const voila_reward* R, const float* particles,
+                           const double* w, int32_t N, int32_t d_s, const float* actions,
+                           int32_t K, int32_t H, int32_t d_a, int32_t d_omega, double gamma,
+                           uint64_t seed, uint32_t planner_id, double* J, double* G,
+                           int32_t* best_k, void* workspace, size_t ws_bytes,
+                           voila_stream_t stream) {
+  voila_status st = check_rollout(g_T, R, N, d_s, K, H, d_a, d_omega);
+  if (st != VOILA_OK) return st;
+  if (planner_id >= 65536u) return VOILA_ERR_ARG;
+  if (N == 0 || K == 0) return VOILA_OK;
+  if (!particles || !J || (H > 0 && d_a > 0 && !actions)) return VOILA_ERR_ARG;
+  if (!workspace || ((uintptr_t)workspace % kAlign)) return VOILA_ERR_WORKSPACE;
+  const RolloutLayout L = rollout_layout(g_T, R, N, K, H, G == nullptr);
+  if (ws_bytes < L.total) return VOILA_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  if (cudaMemsetAsync(ws, 0, sizeof(WsHeader), s) != cudaSuccess) return VOILA_ERR_CUDA;
+  double* Gbuf = G ? G : (double*)(ws + L.g_off);
+
+  RolloutArgs a;
+  memset(&a, 0, sizeof(a));
+  a.g = to_dev(g_T);
+  a.reward_kind = R->kind;
+  a.goal_dims = R->goal_dims;
+  for (int i = 0; i < VOILA_MAX_GOAL; ++i) a.goal[i] = R->goal[i];
+  if (R->kind == VOILA_REWARD_MLP) a.r = to_dev(R->mlp);
+  a.particles = particles;
+  a.actions = actions;
+  a.N = N;
+  a.K = K;
+  a.H = H;
+  a.d_s = d_s;
+  a.d_a = d_a;
+  a.d_omega = d_omega;
+  a.gamma = gamma;
+  philox_key(seed, a.key0, a.key1);
+  a.planner = planner_id;
+  a.G = Gbuf;
+
+  if (g_T->prec == VOILA_BF16) {
+    st = tc_rollout(g_T, R, a, (WsHeader*)ws, ws + L.tc_off, s);
+    if (st != VOILA_OK) return st;
+  } else {
+    int maxw = max_width(g_T);
+    if (R->kind == VOILA_REWARD_MLP && max_width(R->mlp) > maxw) maxw = max_width(R->mlp);
+    a.ld = simt_ld(maxw);
+    if (cudaError_t e = launch_rollout_simt(a, s)) return cuda_status(e);
+  }
+  return cuda_status(launch_reduce_returns(Gbuf, w, N, K, J, best_k, s));
+}
+
+voila_status voila_belief_update_workspace_size(const voila_mlp* g_T, const voila_likelihood* ell,
+                                                int32_t N, size_t* bytes) {
+  if (!bytes || !valid_mlp(g_T) || N < 0) return VOILA_ERR_ARG;
+  const int d_s = g_T->dims[g_T->n_layers];
+  size_t off = kHeaderBytes;
+  off = align_up(off + (size_t)N * d_s * sizeof(float));
+  off = align_up(off + (size_t)N * sizeof(double));
+  off = align_up(off + (size_t)N * sizeof(double));
+  *bytes = off;
+  return VOILA_OK;
+}
+
+voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* ell,
+                                 const float* particles_in, const double* logw_in, int32_t N,
+                                 int32_t d_s, const float* action, const float* obs, int32_t d_a,
+                                 int32_t d_o, int32_t d_omega, float lambda, uint64_t seed,
+                                 uint32_t step, uint32_t planner_id, float* particles_out,
+                                 int32_t* idx_out, double* w_out, double* logZ_out,
+                                 double* ess_out, void* workspace, size_t ws_bytes,
+                                 voila_stream_t stream) {
+  if (!valid_mlp(g_T) || !ell) return VOILA_ERR_ARG;
+  if (N < 0 || d_s < 1 || d_a < 0 || d_o < 0 || d_omega < 0) return VOILA_ERR_ARG;
+  if (d_s > 32 || d_a > 32 || d_o > 64 || d_omega > 64 || N > 262144) return VOILA_ERR_SHAPE;
+  if (!(lambda > 0.0f) || planner_id >= 65536u) return VOILA_ERR_ARG;
+  if (g_T->dims[0] != d_s + d_a + d_omega || g_T->dims[g_T->n_layers] != d_s)
+    return VOILA_ERR_SHAPE;
+  if (g_T->prec == VOILA_FP8E4M3) return VOILA_ERR_UNSUPPORTED;
+  int maxw = max_width(g_T);
+  if (ell->kind == VOILA_LIK_MLP) {
+    if (!valid_mlp(ell->mlp)) return VOILA_ERR_ARG;
+    if (ell->mlp->dims[0] != d_s + d_a + d_o || ell->mlp->dims[ell->mlp->n_layers] != 1)
+      return VOILA_ERR_SHAPE;
+    if (ell->mlp->prec == VOILA_FP8E4M3) return VOILA_ERR_UNSUPPORTED;
+    if (max_width(ell->mlp) > maxw) maxw = max_width(ell->mlp);
+  } else if (ell->kind == VOILA_LIK_GAUSSIAN) {
+    if (d_o > d_s || !(ell->sigma > 0.0f)) return VOILA_ERR_ARG;
+  } else {
+    return VOILA_ERR_ARG;
+  }
+  if (N == 0) return VOILA_OK;
+  if (!particles_in || !particles_out || (d_a > 0 && !action) || (d_o > 0 && !obs))
+    return VOILA_ERR_ARG;
+  if (particles_in == particles_out) return VOILA_ERR_ARG;
+  size_t need = 0;
+  voila_belief_update_workspace_size(g_T, ell, N, &need);
+  if (!workspace || ((uintptr_t)workspace % kAlign)) return VOILA_ERR_WORKSPACE;
+  if (ws_bytes < need) return VOILA_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  size_t off = kHeaderBytes;
+  float* s_prop = (float*)(ws + off);
+  off = align_up(off + (size_t)N * d_s * sizeof(float));
+  double* ellv = (double*)(ws + off);
+  off = align_up(off + (size_t)N * sizeof(double));
+  double* C = (double*)(ws + off);
+  if (cudaMemsetAsync(ws, 0, sizeof(WsHeader), s) != cudaSuccess) return VOILA_ERR_CUDA;
+
+  BeliefArgs b;
+  memset(&b, 0, sizeof(b));
+  b.g = to_dev(g_T);
+  b.lik_kind = ell->kind;
+  b.sigma = ell->sigma;
+  if (ell->kind == VOILA_LIK_MLP) b.l = to_dev(ell->mlp);
+  b.particles = particles_in;
+  b.action = action;
+  b.obs = obs;
+  b.N = N;
+  b.d_s = d_s;
+  b.d_a = d_a;
+  b.d_o = d_o;
+  b.d_omega = d_omega;
+  philox_key(seed, b.key0, b.key1);
+  b.planner = planner_id;
+  b.step = step;
+  b.s_prop = s_prop;
+  b.ell = ellv;
+  b.ld = simt_ld(maxw);
+  if (cudaError_t e = launch_belief_propose(b, s)) return cuda_status(e);
+
+  ResampleArgs r;
+  memset(&r, 0, sizeof(r));
+  r.ell = ellv;
+  r.logw = logw_in;
+  r.s_prop = s_prop;
+  r.N = N;
+  r.d_s = d_s;
+  r.lambda = (double)lambda;
+  r.key0 = b.key0;
+  r.key1 = b.key1;
+  r.planner = planner_id;
+  r.step = step;
+  r.C = C;
+  r.w_out = w_out;
+  r.idx_out = idx_out;
+  r.particles_out = particles_out;
+  r.logZ_out = logZ_out;
+  r.ess_out = ess_out;
+  r.hdr = (WsHeader*)ws;
+  return cuda_status(launch_belief_resample(r, s));
+}
+
+voila_status voila_generator_fwd(const voila_mlp* mlp, const float* X, int32_t B, float* Y,
+                                 voila_stream_t stream) {
+  if (!valid_mlp(mlp) || B < 0) return VOILA_ERR_ARG;
+  if (mlp->prec == VOILA_FP8E4M3) return VOILA_ERR_UNSUPPORTED;
+  if (B == 0) return VOILA_OK;
+  if (!X || !Y) return VOILA_ERR_ARG;
+  FwdArgs a;
+  memset(&a, 0, sizeof(a));
+  a.m = to_dev(mlp);
+  a.X = X;
+  a.B = B;
+  a.Y = Y;
+  a.ld = simt_ld(max_width(mlp));
+  return cuda_status(launch_mlp_fwd(a, (cudaStream_t)stream));
+}
+
+voila_status voila_generator_fwd_seeded(const voila_mlp* mlp, const float* S, const float* A,
+                                        int32_t a_stride, int32_t B, int32_t d_s, int32_t d_a,
+                                        int32_t d_omega, uint64_t seed, uint32_t stream_id,
+                                        uint32_t step, uint32_t planner_id, float* Y,
+                                        voila_stream_t stream) {
+  if (!valid_mlp(mlp) || B < 0 || d_s < 1 || d_a < 0 || d_omega < 0 || a_stride < 0)
+    return VOILA_ERR_ARG;
+  if (mlp->dims[0] != d_s + d_a + d_omega || d_omega > 64 || stream_id > 15 ||
+      planner_id >= 65536u)
+    return VOILA_ERR_SHAPE;
+  if (mlp->prec == VOILA_FP8E4M3) return VOILA_ERR_UNSUPPORTED;
+  if (B == 0) return VOILA_OK;
+  if (!S || !Y || (d_a > 0 && !A)) return VOILA_ERR_ARG;
+  FwdArgs a;
+  memset(&a, 0, sizeof(a));
+  a.m = to_dev(mlp);
+  a.S = S;
+  a.A = A;
+  a.a_stride = a_stride;
+  a.B = B;
+  a.d_s = d_s;
+  a.d_a = d_a;
+  a.d_omega = d_omega;
+  philox_key(seed, a.key0, a.key1);
+  a.planner = planner_id;
+  a.step = step;
+  a.stream_id = stream_id;
+  a.Y = Y;
+  a.ld = simt_ld(max_width(mlp));
+  return cuda_status(launch_mlp_fwd(a, (cudaStream_t)stream));
+}
+
+voila_status voila_philox_fill(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3,
+                               uint32_t* out, int64_t n, voila_stream_t stream) {
+  if (n < 0 || (n > 0 && !out) || n > (1LL << 32)) return VOILA_ERR_ARG;
+  if (n == 0) return VOILA_OK;
+  uint32_t k0, k1;
+  philox_key(seed, k0, k1);
+  return cuda_status(launch_philox_fill(k0, k1, c1, c2, c3, out, n, (cudaStream_t)stream));
+}
+
+voila_status voila_normal_fill(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t stream_id,
+                               uint32_t planner_id, int32_t dim, float* out, int64_t n,
+                               voila_stream_t stream) {
+  if (n < 0 || dim < 1 || dim > 64 || stream_id > 15 || planner_id >= 65536u ||
+      (n > 0 && !out) || n > (1LL << 32))
+    return VOILA_ERR_ARG;
+  if (n == 0) return VOILA_OK;
+  uint32_t k0, k1;
+  philox_key(seed, k0, k1);
+  return cuda_status(
+      launch_normal_fill(k0, k1, c1, c2, stream_id, planner_id, dim, out, n, (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+// Log-weight normalisation, exact FP64 prefix sum, systematic resampling and
+// gather (SIR step of Sec. 3; weights exp(l / lambda), Sec. 4.2.3), plus the
+// deterministic per-sequence return reduction J_k = sum_n w_n G_{n,k}.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace voila {
+
+constexpr int kResampleThreads = 1024;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Fixed-order block reductions (warp butterfly, then warp 0 over the partials).
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double r = (lane < nw) ? red[lane] : 0.0;
+  if (wid == 0) r = warp_sum(r);
+  if (threadIdx.x == 0) red[32] = r;
+  __syncthreads();
+  return red[32];
+}
+__device__ double block_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double r = (lane < nw) ? red[lane] : -INFINITY;
+  if (wid == 0) r = warp_max(r);
+  if (threadIdx.x == 0) red[32] = r;
+  __syncthreads();
+  return red[32];
+}
+
+// Exclusive scan of one double per thread. The inputs are multiples of 2^-52
+// whose partial sums stay below 2, so every addition is exact and the result
+// does not depend on the order.
+__device__ double block_exclusive_scan(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  __syncthreads();
+  if (lane == 31) red[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    double t = (lane < nw) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double u = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += u;
+    }
+    if (lane < nw) red[lane] = t;  // inclusive over warps
+  }
+  __syncthreads();
+  const double warp_off = (wid > 0) ? red[wid - 1] : 0.0;
+  return warp_off + inc - v;
+}
+
+__global__ void __launch_bounds__(kResampleThreads) belief_resample_kernel(ResampleArgs a) {
+  __shared__ double red[33];
+  __shared__ int bad_s;
+  const int N = a.N, nt = blockDim.x, tid = threadIdx.x;
+  const int chunk = (N + nt - 1) / nt;
+  const int i0 = min(N, tid * chunk), i1 = min(N, i0 + chunk);
+  if (tid == 0) bad_s = 0;
+  __syncthreads();
+  // lw_i = l_i / lambda + logw_i
+  double lmax = -INFINITY;
+  int bad = 0;
+  for (int i = i0; i < i1; ++i) {
+    double lw = __ddiv_rn(a.ell[i], a.lambda);
+    if (a.logw) lw = __dadd_rn(lw, a.logw[i]);
+    a.C[i] = lw;
+    if (isnan(lw) || lw == INFINITY) bad = 1;
+    lmax = fmax(lmax, lw);
+  }
+  if (bad) atomicOr(&bad_s, 1);
+  const double m = block_max(lmax, red);
+  if (bad_s) {
+    if (tid == 0) set_status(a.hdr, VOILA_ERR_NONFINITE, 1);
+    return;
+  }
+  if (m == -INFINITY) {
+    if (tid == 0) set_status(a.hdr, VOILA_ERR_DEGENERATE, 1);
+    return;
+  }
+  // e_i = exp(lw_i - m), Z = sum e_i
+  double zl = 0.0;
+  for (int i = i0; i < i1; ++i) {
+    const double e = exp(a.C[i] - m);
+    a.C[i] = e;
+    zl += e;
+  }
+  const double Z = block_sum(zl, red);
+  // q_i = rn(w_i 2^52) 2^-52 and the local inclusive prefix
+  double acc = 0.0, q2 = 0.0;
+  for (int i = i0; i < i1; ++i) {
+    const double w = __ddiv_rn(a.C[i], Z);
+    const double q = rint(w * 4503599627370496.0) * 2.220446049250313e-16;
+    if (a.w_out) a.w_out[i] = q;
+    acc += q;
+    q2 += q * q;
+    a.C[i] = acc;
+  }
+  const double off = block_exclusive_scan(acc, red);
+  for (int i = i0; i < i1; ++i) a.C[i] += off;
+  const double sq = block_sum(q2, red);  // ends with __syncthreads: C is complete
+  const double total = a.C[N - 1];
+  const uint4 wd = philox(make_uint4(0u, 0u, a.step, ctr_word3(VOILA_STREAM_RESAMPLE, a.planner, 0)),
+                          a.key0, a.key1);
+  const double u0 = uniform53(wd.x, wd.y);
+  const double dN = (double)N;
+  for (int j = i0; j < i1; ++j) {
+    const double p = __ddiv_rn(__dmul_rn(__dadd_rn(u0, (double)j), total), dN);
+    int lo = 0, hi = N;  // first i with C_i > p
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (a.C[mid] > p) hi = mid;
+      else lo = mid + 1;
+    }
+    const int idx = lo < N ? lo : N - 1;
+    if (a.idx_out) a.idx_out[j] = idx;
+    for (int d = 0; d < a.d_s; ++d)
+      a.particles_out[(size_t)j * a.d_s + d] = a.s_prop[(size_t)idx * a.d_s + d];
+  }
+  if (tid == 0) {
+    if (a.logZ_out) *a.logZ_out = m + log(Z);
+    if (a.ess_out) *a.ess_out = 1.0 / sq;
+  }
+}
+
+cudaError_t launch_belief_resample(const ResampleArgs& a, cudaStream_t s) {
+  belief_resample_kernel<<<1, kResampleThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// J_k = sum_n w_n G[k][n]: one CTA per sequence, fixed summation order.
+__global__ void __launch_bounds__(256) reduce_returns_kernel(const double* __restrict__ G,
+                                                             const double* __restrict__ w, int N,
+                                                             int K, double* __restrict__ J) {
+  __shared__ double red[33];
+  const int k = blockIdx.x;
+  const double invN = 1.0 / (double)N;
+  double acc = 0.0;
+  const double* g = G + (size_t)k * N;
+  for (int n = threadIdx.x; n < N; n += blockDim.x) acc += g[n] * (w ? w[n] : invN);
+  const double tot = block_sum(acc, red);
+  if (threadIdx.x == 0) J[k] = tot;
+}
+
+// argmax_k J_k, lowest index on ties (NaN never wins).
+__global__ void __launch_bounds__(1024) argmax_kernel(const double* __restrict__ J, int K,
+                                                      int32_t* best) {
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  double v = -INFINITY;
+  int i = K;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double x = J[k];
+    if (!isnan(x) && (i == K || x > v)) {  // k rises: ties keep the lower index
+      v = x;
+      i = k;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) {
+      v = ov;
+      i = oi;
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    bv[wid] = v;
+    bi[wid] = i;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    v = lane < nw ? bv[lane] : -INFINITY;
+    i = lane < nw ? bi[lane] : K;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+      if (ov > v || (ov == v && oi < i)) {
+        v = ov;
+        i = oi;
+      }
+    }
+    if (lane == 0) *best = (i < K) ? i : 0;
+  }
+}
+
+cudaError_t launch_reduce_returns(const double* G, const double* w, int N, int K, double* J,
+                                  int32_t* best_k, cudaStream_t s) {
+  reduce_returns_kernel<<<K, 256, 0, s>>>(G, w, N, K, J);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !best_k) return e;
+  argmax_kernel<<<1, 1024, 0, s>>>(J, K, best_k);
+  return cudaGetLastError();
+}
+
+}  // namespace voila

@@ -1,0 +1,86 @@
+// Kernel argument blocks and launcher declarations (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace voila {
+
+constexpr int kSimtRows = 32;
+constexpr int kSimtThreads = 256;
+
+struct RolloutArgs {
+  MlpDev g;
+  MlpDev r;
+  int reward_kind;
+  int goal_dims;
+  float goal[VOILA_MAX_GOAL];
+  const float* particles;
+  const float* actions;
+  int N, K, H, d_s, d_a, d_omega;
+  double gamma;
+  uint32_t key0, key1, planner;
+  double* G;  // [K][N]
+  int ld;     // shared-memory row stride (floats)
+};
+
+struct BeliefArgs {
+  MlpDev g;
+  MlpDev l;
+  int lik_kind;
+  float sigma;
+  const float* particles;
+  const float* action;
+  const float* obs;
+  int N, d_s, d_a, d_o, d_omega;
+  uint32_t key0, key1, planner, step;
+  float* s_prop;  // [N][d_s]
+  double* ell;    // [N]
+  int ld;
+};
+
+struct ResampleArgs {
+  const double* ell;
+  const double* logw;
+  const float* s_prop;
+  int N, d_s;
+  double lambda;
+  uint32_t key0, key1, planner, step;
+  double* C;          // [N] workspace
+  double* w_out;      // [N] or null
+  int32_t* idx_out;   // [N] or null
+  float* particles_out;
+  double* logZ_out;
+  double* ess_out;
+  WsHeader* hdr;
+};
+
+struct FwdArgs {
+  MlpDev m;
+  const float* X;   // plain form, or null for the seeded form
+  const float* S;
+  const float* A;
+  int a_stride;
+  int B, d_s, d_a, d_omega;
+  uint32_t key0, key1, planner, step, stream_id;
+  float* Y;
+  int ld;
+};
+
+size_t rollout_simt_smem(int ld);
+size_t belief_propose_smem(int ld);
+cudaError_t launch_rollout_simt(const RolloutArgs& a, cudaStream_t s);
+cudaError_t launch_belief_propose(const BeliefArgs& a, cudaStream_t s);
+cudaError_t launch_belief_resample(const ResampleArgs& a, cudaStream_t s);
+cudaError_t launch_mlp_fwd(const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_reduce_returns(const double* G, const double* w, int N, int K, double* J,
+                                  int32_t* best_k, cudaStream_t s);
+cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,
+                               uint32_t* out, long long n, cudaStream_t s);
+cudaError_t launch_normal_fill(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2,
+                               uint32_t stream, uint32_t planner, int dim, float* out,
+                               long long n, cudaStream_t s);
+
+}  // namespace voila

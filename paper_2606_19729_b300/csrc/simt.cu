@@ -1,0 +1,385 @@
+// CUDA-core (FP32 FMA) kernels: the plain FP32 form of the rollout, the
+// belief-update proposal/likelihood pass, the seeded and plain generator
+// forward, and the noise fill kernels.
+//
+// A CTA owns a tile of kSimtRows rows (one row = one (particle, sequence)
+// pair, or one batch row) and runs whole MLP chains on it in shared memory:
+// activations ping-pong between two [rows][ld] FP32 buffers and every layer
+// is y = act(x W^T + b) with the weights read through the read-only cache.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace voila {
+
+// One layer on a tile held in shared memory. Threads are split into
+// `ng` row groups x `cpp` columns; a thread owns column j (stride cpp) and
+// rows rg, rg+ng, ... so narrow layers still keep most threads busy.
+template <typename TW>
+__device__ void simt_layer(const float* __restrict__ in, float* __restrict__ out, int ld,
+                           int nrows, int K, int Nout, const TW* __restrict__ W,
+                           const float* __restrict__ b, int act, bool last) {
+  const int nt = blockDim.x, tid = threadIdx.x;
+  int ng = nt / Nout;
+  if (ng < 1) ng = 1;
+  if (ng > kSimtRows) ng = kSimtRows;
+  const int cpp = nt / ng;
+  const int j0 = tid % cpp, rg = tid / cpp;
+  if (rg >= ng) return;
+  const int nr = (nrows - rg + ng - 1) / ng;  // rows this thread owns
+  for (int j = j0; j < Nout; j += cpp) {
+    float acc[kSimtRows];
+    const float bj = __ldg(b + j);
+#pragma unroll
+    for (int i = 0; i < kSimtRows; ++i) acc[i] = bj;
+    const TW* wj = W + (size_t)j * K;
+    for (int k = 0; k < K; ++k) {
+      const float wv = ldw<TW>(wj + k);
+#pragma unroll
+      for (int i = 0; i < kSimtRows; ++i)
+        if (i < nr) acc[i] = fmaf(in[(rg + i * ng) * ld + k], wv, acc[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < kSimtRows; ++i)
+      if (i < nr) out[(rg + i * ng) * ld + j] = last ? acc[i] : act_fp32(acc[i], act);
+  }
+}
+
+// Runs all layers; returns the buffer holding the output.
+template <typename TW>
+__device__ float* simt_mlp(const MlpDev& m, float* bufA, float* bufB, int ld, int nrows) {
+  float* cur = bufA;
+  float* nxt = bufB;
+  for (int l = 0; l < m.n_layers; ++l) {
+    __syncthreads();
+    simt_layer<TW>(cur, nxt, ld, nrows, m.dims[l], m.dims[l + 1],
+                   reinterpret_cast<const TW*>(m.W[l]), m.b[l], m.act, l == m.n_layers - 1);
+    float* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  __syncthreads();
+  return cur;
+}
+
+// Writes omega(c0_of_row, c1_of_row, c2) for rows [0, nrows) into columns
+// [col0, col0 + dim) of buf. c0/c1 come from the row's (n, k) mapping.
+__device__ __forceinline__ void put_noise(float* buf, int ld, int col0, int dim, int nrows,
+                                          long long row0, int N, bool rollout_map, uint32_t c2,
+                                          uint32_t stream, uint32_t planner, uint32_t k0,
+                                          uint32_t k1) {
+  const int nblk = (dim + 3) >> 2;
+  for (int i = threadIdx.x; i < nrows * nblk; i += blockDim.x) {
+    const int r = i / nblk, blk = i % nblk;
+    const long long row = row0 + r;
+    uint32_t c0, c1;
+    if (rollout_map) {
+      c0 = (uint32_t)(row % N);
+      c1 = (uint32_t)(row / N);
+    } else {
+      c0 = (uint32_t)row;
+      c1 = 0;
+    }
+    const float4 z = normal4(k0, k1, c0, c1, c2, stream, planner, (uint32_t)blk);
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (blk * 4 + q < dim) buf[r * ld + col0 + blk * 4 + q] = zz[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 rollout: one CTA per tile of rows (row = k * N + n), all H steps.
+// ---------------------------------------------------------------------------
+template <typename TW, typename TR>
+__global__ void __launch_bounds__(kSimtThreads)
+rollout_simt_kernel(RolloutArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  const int ld = a.ld;
+  float* bufA = sm;
+  float* bufB = bufA + kSimtRows * ld;
+  float* st = bufB + kSimtRows * ld;                      // [rows][d_s]
+  double* Gs = reinterpret_cast<double*>(st + kSimtRows * 32);  // [rows]
+  const long long rows = (long long)a.N * a.K;
+  const long long ntiles = (rows + kSimtRows - 1) / kSimtRows;
+  const int d_s = a.d_s, d_a = a.d_a, d_w = a.d_omega;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long row0 = tile * kSimtRows;
+    const int nr = (int)min((long long)kSimtRows, rows - row0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSimtRows * d_s; i += blockDim.x) {
+      const int r = i / d_s, d = i % d_s;
+      st[r * 32 + d] = (r < nr) ? a.particles[(size_t)((row0 + r) % a.N) * d_s + d] : 0.0f;
+    }
+    for (int r = threadIdx.x; r < kSimtRows; r += blockDim.x) Gs[r] = 0.0;
+    double disc = 1.0;
+    for (int t = 0; t < a.H; ++t) {
+      __syncthreads();
+      // x = [s_t ; a_{k,t} ; omega_T(n, k, t)]
+      for (int i = threadIdx.x; i < kSimtRows * (d_s + d_a); i += blockDim.x) {
+        const int r = i / (d_s + d_a), c = i % (d_s + d_a);
+        float v = 0.0f;
+        if (r < nr) {
+          if (c < d_s) {
+            v = st[r * 32 + c];
+          } else {
+            const long long k = (row0 + r) / a.N;
+            v = a.actions[((size_t)k * a.H + t) * d_a + (c - d_s)];
+          }
+        }
+        bufA[r * ld + c] = v;
+      }
+      if (d_w > 0)
+        put_noise(bufA, ld, d_s + d_a, d_w, nr, row0, a.N, true, (uint32_t)t,
+                  VOILA_STREAM_ROLLOUT_OMEGA, a.planner, a.key0, a.key1);
+      const float* y = simt_mlp<TW>(a.g, bufA, bufB, ld, nr);
+      for (int i = threadIdx.x; i < nr * d_s; i += blockDim.x) {
+        const int r = i / d_s, d = i % d_s;
+        st[r * 32 + d] = y[r * ld + d];
+      }
+      __syncthreads();
+      if (a.reward_kind == VOILA_REWARD_GOAL) {
+        for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+          float acc = 0.0f;
+          for (int d = 0; d < a.goal_dims; ++d) {
+            const float e = st[r * 32 + d] - a.goal[d];
+            acc = fmaf(e, e, acc);
+          }
+          Gs[r] += disc * (double)(-acc);
+        }
+      } else {
+        for (int i = threadIdx.x; i < kSimtRows * (d_s + d_a); i += blockDim.x) {
+          const int r = i / (d_s + d_a), c = i % (d_s + d_a);
+          float v = 0.0f;
+          if (r < nr) {
+            if (c < d_s) {
+              v = st[r * 32 + c];
+            } else {
+              const long long k = (row0 + r) / a.N;
+              v = a.actions[((size_t)k * a.H + t) * d_a + (c - d_s)];
+            }
+          }
+          bufA[r * ld + c] = v;
+        }
+        const float* rv = simt_mlp<TR>(a.r, bufA, bufB, ld, nr);
+        for (int r = threadIdx.x; r < nr; r += blockDim.x) Gs[r] += disc * (double)rv[r * ld];
+      }
+      disc *= a.gamma;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) a.G[row0 + r] = Gs[r];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Belief-update proposal + likelihood: s'_i = g_T([s_i; a; omega_i]),
+// l_i = ell([s'_i; a; o]) or the Gaussian test kind. Writes s' and l.
+// ---------------------------------------------------------------------------
+template <typename TW, typename TL>
+__global__ void __launch_bounds__(kSimtThreads)
+belief_propose_kernel(BeliefArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  const int ld = a.ld;
+  float* bufA = sm;
+  float* bufB = bufA + kSimtRows * ld;
+  float* sp = bufB + kSimtRows * ld;  // [rows][32]
+  const int d_s = a.d_s, d_a = a.d_a, d_o = a.d_o;
+  const long long ntiles = ((long long)a.N + kSimtRows - 1) / kSimtRows;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long row0 = tile * kSimtRows;
+    const int nr = (int)min((long long)kSimtRows, (long long)a.N - row0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSimtRows * (d_s + d_a); i += blockDim.x) {
+      const int r = i / (d_s + d_a), c = i % (d_s + d_a);
+      float v = 0.0f;
+      if (r < nr) v = (c < d_s) ? a.particles[(size_t)(row0 + r) * d_s + c] : a.action[c - d_s];
+      bufA[r * ld + c] = v;
+    }
+    if (a.d_omega > 0)
+      put_noise(bufA, ld, d_s + d_a, a.d_omega, nr, row0, 1, false, a.step,
+                VOILA_STREAM_BELIEF_OMEGA, a.planner, a.key0, a.key1);
+    const float* y = simt_mlp<TW>(a.g, bufA, bufB, ld, nr);
+    for (int i = threadIdx.x; i < nr * d_s; i += blockDim.x) {
+      const int r = i / d_s, d = i % d_s;
+      const float v = y[r * ld + d];
+      sp[r * 32 + d] = v;
+      a.s_prop[(size_t)(row0 + r) * d_s + d] = v;
+    }
+    __syncthreads();
+    if (a.lik_kind == VOILA_LIK_GAUSSIAN) {
+      for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        double acc = 0.0;
+        for (int d = 0; d < d_o; ++d) {
+          const double e = (double)a.obs[d] - (double)sp[r * 32 + d];
+          acc += e * e;
+        }
+        a.ell[row0 + r] = -acc / (2.0 * (double)a.sigma * (double)a.sigma);
+      }
+    } else {
+      for (int i = threadIdx.x; i < kSimtRows * (d_s + d_a + d_o); i += blockDim.x) {
+        const int r = i / (d_s + d_a + d_o), c = i % (d_s + d_a + d_o);
+        float v = 0.0f;
+        if (r < nr) {
+          if (c < d_s) v = sp[r * 32 + c];
+          else if (c < d_s + d_a) v = a.action[c - d_s];
+          else v = a.obs[c - d_s - d_a];
+        }
+        bufA[r * ld + c] = v;
+      }
+      const float* lv = simt_mlp<TL>(a.l, bufA, bufB, ld, nr);
+      for (int r = threadIdx.x; r < nr; r += blockDim.x) a.ell[row0 + r] = (double)lv[r * ld];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Generator forward: plain (X given) or seeded (X = [S; A; omega]).
+// ---------------------------------------------------------------------------
+template <typename TW>
+__global__ void __launch_bounds__(kSimtThreads)
+mlp_fwd_kernel(FwdArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  const int ld = a.ld;
+  float* bufA = sm;
+  float* bufB = bufA + kSimtRows * ld;
+  const int d_in = a.m.dims[0], d_out = a.m.dims[a.m.n_layers];
+  const long long ntiles = ((long long)a.B + kSimtRows - 1) / kSimtRows;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long row0 = tile * kSimtRows;
+    const int nr = (int)min((long long)kSimtRows, (long long)a.B - row0);
+    __syncthreads();
+    if (a.X) {
+      for (int i = threadIdx.x; i < kSimtRows * d_in; i += blockDim.x) {
+        const int r = i / d_in, c = i % d_in;
+        bufA[r * ld + c] = (r < nr) ? a.X[(size_t)(row0 + r) * d_in + c] : 0.0f;
+      }
+    } else {
+      const int ds = a.d_s, da = a.d_a;
+      for (int i = threadIdx.x; i < kSimtRows * (ds + da); i += blockDim.x) {
+        const int r = i / (ds + da), c = i % (ds + da);
+        float v = 0.0f;
+        if (r < nr)
+          v = (c < ds) ? a.S[(size_t)(row0 + r) * ds + c]
+                       : a.A[(size_t)(row0 + r) * a.a_stride + (c - ds)];
+        bufA[r * ld + c] = v;
+      }
+      if (a.d_omega > 0)
+        put_noise(bufA, ld, ds + da, a.d_omega, nr, row0, 1, false, a.step, a.stream_id,
+                  a.planner, a.key0, a.key1);
+    }
+    const float* y = simt_mlp<TW>(a.m, bufA, bufB, ld, nr);
+    for (int i = threadIdx.x; i < nr * d_out; i += blockDim.x) {
+      const int r = i / d_out, c = i % d_out;
+      a.Y[(size_t)(row0 + r) * d_out + c] = y[r * ld + c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Noise checks.
+// ---------------------------------------------------------------------------
+__global__ void philox_fill_kernel(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2,
+                                   uint32_t c3, uint32_t* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint4 w = philox(make_uint4((uint32_t)i, c1, c2, c3), k0, k1);
+    reinterpret_cast<uint4*>(out)[i] = w;
+  }
+}
+
+__global__ void normal_fill_kernel(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2,
+                                   uint32_t stream, uint32_t planner, int dim, float* out,
+                                   long long n) {
+  const int nblk = (dim + 3) >> 2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nblk;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long row = i / nblk;
+    const int blk = (int)(i % nblk);
+    const float4 z = normal4(k0, k1, (uint32_t)row, c1, c2, stream, planner, (uint32_t)blk);
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+    for (int q = 0; q < 4; ++q)
+      if (blk * 4 + q < dim) out[row * dim + blk * 4 + q] = zz[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
+static int simt_grid(long long ntiles, size_t smem) {
+  int per_sm = (int)(200 * 1024 / (smem + 1024));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 8) per_sm = 8;
+  long long g = 148LL * per_sm;
+  if (g > ntiles) g = ntiles;
+  return (int)(g < 1 ? 1 : g);
+}
+
+size_t rollout_simt_smem(int ld) {
+  return (size_t)2 * kSimtRows * ld * sizeof(float) + kSimtRows * 32 * sizeof(float) +
+         kSimtRows * sizeof(double);
+}
+
+cudaError_t launch_rollout_simt(const RolloutArgs& a, cudaStream_t s) {
+  const size_t smem = rollout_simt_smem(a.ld);
+  const long long ntiles = ((long long)a.N * a.K + kSimtRows - 1) / kSimtRows;
+  const int grid = simt_grid(ntiles, smem);
+  const bool gb = a.g.prec == VOILA_BF16;
+  const bool rb = a.reward_kind == VOILA_REWARD_MLP && a.r.prec == VOILA_BF16;
+  void (*k)(RolloutArgs);
+  if (gb) k = rb ? rollout_simt_kernel<__nv_bfloat16, __nv_bfloat16> : rollout_simt_kernel<__nv_bfloat16, float>;
+  else k = rb ? rollout_simt_kernel<float, __nv_bfloat16> : rollout_simt_kernel<float, float>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kSimtThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+size_t belief_propose_smem(int ld) {
+  return (size_t)2 * kSimtRows * ld * sizeof(float) + kSimtRows * 32 * sizeof(float);
+}
+
+cudaError_t launch_belief_propose(const BeliefArgs& a, cudaStream_t s) {
+  const size_t smem = belief_propose_smem(a.ld);
+  const long long ntiles = ((long long)a.N + kSimtRows - 1) / kSimtRows;
+  const int grid = simt_grid(ntiles, smem);
+  const bool gb = a.g.prec == VOILA_BF16;
+  const bool lb = a.lik_kind == VOILA_LIK_MLP && a.l.prec == VOILA_BF16;
+  void (*k)(BeliefArgs);
+  if (gb) k = lb ? belief_propose_kernel<__nv_bfloat16, __nv_bfloat16> : belief_propose_kernel<__nv_bfloat16, float>;
+  else k = lb ? belief_propose_kernel<float, __nv_bfloat16> : belief_propose_kernel<float, float>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kSimtThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_fwd(const FwdArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)2 * kSimtRows * a.ld * sizeof(float);
+  const long long ntiles = ((long long)a.B + kSimtRows - 1) / kSimtRows;
+  const int grid = simt_grid(ntiles, smem);
+  void (*k)(FwdArgs) = a.m.prec == VOILA_BF16 ? mlp_fwd_kernel<__nv_bfloat16> : mlp_fwd_kernel<float>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kSimtThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,
+                               uint32_t* out, long long n, cudaStream_t s) {
+  long long g = (n + 255) / 256;
+  if (g > 148 * 16) g = 148 * 16;
+  if (g < 1) g = 1;
+  philox_fill_kernel<<<(int)g, 256, 0, s>>>(k0, k1, c1, c2, c3, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normal_fill(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2,
+                               uint32_t stream, uint32_t planner, int dim, float* out,
+                               long long n, cudaStream_t s) {
+  long long g = (n * ((dim + 3) / 4) + 255) / 256;
+  if (g > 148 * 16) g = 148 * 16;
+  if (g < 1) g = 1;
+  normal_fill_kernel<<<(int)g, 256, 0, s>>>(k0, k1, c1, c2, stream, planner, dim, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace voila

@@ -1,0 +1,253 @@
+"""Thin ctypes binding of the C-ABI in include/voila.h.
+
+Argument marshalling only: every step of the path runs in the library's
+kernels. Tensors must be CUDA tensors of the dtype the header names; the
+library is loaded from this package's lib/ folder and importing this module
+raises if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_float, c_int32, c_int64, c_size_t, c_uint32, c_uint64, c_void_p
+from typing import List, Optional, Sequence
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libvoila.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"VOiLA CUDA library not built: {LIB_PATH} is missing "
+                      "(run __graft_entry__.build())")
+_lib = ctypes.CDLL(LIB_PATH)
+
+MAX_LAYERS = 8
+MAX_GOAL = 4
+OK, ERR_ARG, ERR_SHAPE, ERR_CUDA, ERR_NONFINITE, ERR_DEGENERATE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_WORKSPACE = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+ACT_IDENTITY, ACT_TANH, ACT_SILU = 0, 1, 2
+FP32, BF16, FP8E4M3 = 0, 1, 2
+REWARD_GOAL, REWARD_MLP = 0, 1
+LIK_MLP, LIK_GAUSSIAN = 0, 1
+STREAM_ROLLOUT_OMEGA, STREAM_BELIEF_OMEGA, STREAM_RESAMPLE, STREAM_OBS_OMEGA = 0, 1, 2, 3
+
+
+class voila_mlp(ctypes.Structure):
+    _fields_ = [("n_layers", c_int32), ("dims", c_int32 * (MAX_LAYERS + 1)), ("act", c_int32),
+                ("prec", c_int32), ("W", c_void_p * MAX_LAYERS), ("b", c_void_p * MAX_LAYERS),
+                ("w_scale", c_void_p * MAX_LAYERS)]
+
+
+class voila_reward(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("goal_dims", c_int32), ("goal", c_float * MAX_GOAL),
+                ("mlp", POINTER(voila_mlp))]
+
+
+class voila_likelihood(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("sigma", c_float), ("mlp", POINTER(voila_mlp))]
+
+
+def _sig(name, res, *args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = list(args)
+    return f
+
+
+_P = c_void_p
+_lib_status_string = _sig("voila_status_string", ctypes.c_char_p, c_int32)
+_lib_workspace_status = _sig("voila_workspace_status", c_int32, _P, _P)
+_lib_rollout_ws = _sig("voila_rollout_workspace_size", c_int32, POINTER(voila_mlp), POINTER(voila_reward),
+                       c_int32, c_int32, c_int32, POINTER(c_size_t))
+_lib_rollout = _sig("voila_rollout", c_int32, POINTER(voila_mlp), POINTER(voila_reward), _P, _P, c_int32,
+                    c_int32, _P, c_int32, c_int32, c_int32, c_int32, c_double, c_uint64, c_uint32, _P, _P,
+                    _P, _P, c_size_t, _P)
+_lib_belief_ws = _sig("voila_belief_update_workspace_size", c_int32, POINTER(voila_mlp),
+                      POINTER(voila_likelihood), c_int32, POINTER(c_size_t))
+_lib_belief = _sig("voila_belief_update", c_int32, POINTER(voila_mlp), POINTER(voila_likelihood), _P, _P,
+                   c_int32, c_int32, _P, _P, c_int32, c_int32, c_int32, c_float, c_uint64, c_uint32,
+                   c_uint32, _P, _P, _P, _P, _P, _P, c_size_t, _P)
+_lib_fwd = _sig("voila_generator_fwd", c_int32, POINTER(voila_mlp), _P, c_int32, _P, _P)
+_lib_fwd_seeded = _sig("voila_generator_fwd_seeded", c_int32, POINTER(voila_mlp), _P, _P, c_int32, c_int32,
+                       c_int32, c_int32, c_int32, c_uint64, c_uint32, c_uint32, c_uint32, _P, _P)
+_lib_philox = _sig("voila_philox_fill", c_int32, c_uint64, c_uint32, c_uint32, c_uint32, _P, c_int64, _P)
+_lib_normal = _sig("voila_normal_fill", c_int32, c_uint64, c_uint32, c_uint32, c_uint32, c_uint32, c_int32,
+                   _P, c_int64, _P)
+
+
+class VoilaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+
+
+def status_string(code: int) -> str:
+    return _lib_status_string(code).decode()
+
+
+def _check(code: int, where: str):
+    if code != OK:
+        raise VoilaError(code, where)
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=None):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class DeviceMLP:
+    """An MLP's weights on the device plus its voila_mlp descriptor.
+
+    W[l] is [out, in] (float32 for FP32, bfloat16 for BF16), b[l] float32.
+    """
+
+    def __init__(self, W: Sequence[torch.Tensor], b: Sequence[torch.Tensor], act: int, prec: int):
+        if len(W) != len(b) or not 1 <= len(W) <= MAX_LAYERS:
+            raise ValueError("bad layer count")
+        wdt = {FP32: torch.float32, BF16: torch.bfloat16}[prec]
+        self.W = [w.to(device="cuda", dtype=wdt).contiguous() for w in W]
+        self.b = [v.to(device="cuda", dtype=torch.float32).contiguous() for v in b]
+        self.act, self.prec = act, prec
+        self.desc = voila_mlp()
+        self.desc.n_layers = len(W)
+        dims = [self.W[0].shape[1]] + [w.shape[0] for w in self.W]
+        for i, d in enumerate(dims):
+            self.desc.dims[i] = d
+        self.desc.act = act
+        self.desc.prec = prec
+        for l in range(len(W)):
+            self.desc.W[l] = self.W[l].data_ptr()
+            self.desc.b[l] = self.b[l].data_ptr()
+        self.dims = dims
+
+    @classmethod
+    def from_spec(cls, spec) -> "DeviceMLP":
+        """From an object with W, b (numpy FP64 arrays already rounded), act, prec."""
+        return cls([torch.from_numpy(w) for w in spec.W], [torch.from_numpy(v) for v in spec.b],
+                   spec.act, spec.prec)
+
+
+def goal_reward(goal: Sequence[float]) -> voila_reward:
+    r = voila_reward()
+    r.kind = REWARD_GOAL
+    r.goal_dims = len(goal)
+    for i, g in enumerate(goal):
+        r.goal[i] = float(g)
+    return r
+
+
+def mlp_reward(mlp: DeviceMLP) -> voila_reward:
+    r = voila_reward()
+    r.kind = REWARD_MLP
+    r.mlp = ctypes.pointer(mlp.desc)
+    r._keep = mlp
+    return r
+
+
+def mlp_likelihood(mlp: DeviceMLP) -> voila_likelihood:
+    l = voila_likelihood()
+    l.kind = LIK_MLP
+    l.mlp = ctypes.pointer(mlp.desc)
+    l._keep = mlp
+    return l
+
+
+def gaussian_likelihood(sigma: float) -> voila_likelihood:
+    l = voila_likelihood()
+    l.kind = LIK_GAUSSIAN
+    l.sigma = sigma
+    return l
+
+
+def workspace_status(ws: torch.Tensor, stream=None) -> int:
+    return _lib_workspace_status(_ptr(ws), _stream(stream))
+
+
+def alloc_workspace(nbytes: int) -> torch.Tensor:
+    """A 256-byte aligned device workspace (torch allocations are 512-byte aligned)."""
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device="cuda")
+
+
+# ---------------------------------------------------------------------------
+# Entry points (same names as the C-ABI).
+# ---------------------------------------------------------------------------
+def voila_rollout_workspace_size(g_T: DeviceMLP, R: voila_reward, N: int, K: int, H: int) -> int:
+    n = c_size_t(0)
+    _check(_lib_rollout_ws(ctypes.byref(g_T.desc), ctypes.byref(R), N, K, H, ctypes.byref(n)),
+           "voila_rollout_workspace_size")
+    return n.value
+
+
+def voila_rollout(g_T: DeviceMLP, R: voila_reward, particles: torch.Tensor, w: Optional[torch.Tensor],
+                  actions: torch.Tensor, d_omega: int, gamma: float, seed: int, planner_id: int,
+                  J: torch.Tensor, G: Optional[torch.Tensor], best_k: Optional[torch.Tensor],
+                  workspace: torch.Tensor, stream=None):
+    N, d_s = particles.shape
+    K, H, d_a = actions.shape
+    code = _lib_rollout(ctypes.byref(g_T.desc), ctypes.byref(R), _ptr(particles, torch.float32),
+                        _ptr(w, torch.float64), N, d_s, _ptr(actions, torch.float32), K, H, d_a,
+                        d_omega, gamma, seed, planner_id, _ptr(J, torch.float64),
+                        _ptr(G, torch.float64), _ptr(best_k, torch.int32), _ptr(workspace),
+                        workspace.numel(), _stream(stream))
+    _check(code, "voila_rollout")
+
+
+def voila_belief_update_workspace_size(g_T: DeviceMLP, ell: voila_likelihood, N: int) -> int:
+    n = c_size_t(0)
+    _check(_lib_belief_ws(ctypes.byref(g_T.desc), ctypes.byref(ell), N, ctypes.byref(n)),
+           "voila_belief_update_workspace_size")
+    return n.value
+
+
+def voila_belief_update(g_T: DeviceMLP, ell: voila_likelihood, particles_in: torch.Tensor,
+                        logw_in: Optional[torch.Tensor], action: torch.Tensor, obs: torch.Tensor,
+                        d_omega: int, lam: float, seed: int, step: int, planner_id: int,
+                        particles_out: torch.Tensor, idx_out: Optional[torch.Tensor],
+                        w_out: Optional[torch.Tensor], logZ_out: Optional[torch.Tensor],
+                        ess_out: Optional[torch.Tensor], workspace: torch.Tensor, stream=None):
+    N, d_s = particles_in.shape
+    code = _lib_belief(ctypes.byref(g_T.desc), ctypes.byref(ell), _ptr(particles_in, torch.float32),
+                       _ptr(logw_in, torch.float64), N, d_s, _ptr(action, torch.float32),
+                       _ptr(obs, torch.float32), action.numel(), obs.numel(), d_omega, lam, seed, step,
+                       planner_id, _ptr(particles_out, torch.float32), _ptr(idx_out, torch.int32),
+                       _ptr(w_out, torch.float64), _ptr(logZ_out, torch.float64),
+                       _ptr(ess_out, torch.float64), _ptr(workspace), workspace.numel(), _stream(stream))
+    _check(code, "voila_belief_update")
+
+
+def voila_generator_fwd(mlp: DeviceMLP, X: torch.Tensor, Y: torch.Tensor, stream=None):
+    _check(_lib_fwd(ctypes.byref(mlp.desc), _ptr(X, torch.float32), X.shape[0], _ptr(Y, torch.float32),
+                    _stream(stream)), "voila_generator_fwd")
+
+
+def voila_generator_fwd_seeded(mlp: DeviceMLP, S: torch.Tensor, A: torch.Tensor, a_stride: int,
+                               d_omega: int, seed: int, stream_id: int, step: int, planner_id: int,
+                               Y: torch.Tensor, stream=None):
+    B, d_s = S.shape
+    d_a = A.shape[-1]
+    _check(_lib_fwd_seeded(ctypes.byref(mlp.desc), _ptr(S, torch.float32), _ptr(A, torch.float32), a_stride,
+                           B, d_s, d_a, d_omega, seed, stream_id, step, planner_id, _ptr(Y, torch.float32),
+                           _stream(stream)), "voila_generator_fwd_seeded")
+
+
+def voila_philox_fill(seed: int, c1: int, c2: int, c3: int, out: torch.Tensor, stream=None):
+    _check(_lib_philox(seed, c1, c2, c3, _ptr(out, torch.int32), out.numel() // 4, _stream(stream)),
+           "voila_philox_fill")
+
+
+def voila_normal_fill(seed: int, c1: int, c2: int, stream_id: int, planner_id: int, out: torch.Tensor,
+                      stream=None):
+    n, dim = out.shape
+    _check(_lib_normal(seed, c1, c2, stream_id, planner_id, dim, _ptr(out, torch.float32), n, _stream(stream)),
+           "voila_normal_fill")
