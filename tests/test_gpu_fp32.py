@@ -115,7 +115,7 @@ def _belief(V, wl, lik_dev, lik_or, N=None, logw=None, lam=1.0, step=3):
     s_true = WL.true_state(wl.seed, wl.d_s, 0.5)
     s_next = O.generator_forward_seeded(oracle_mlp(wl.g_T), s_true[None], a[None], wl.d_omega, wl.seed,
                                         O.STREAM_TRUE_STATE, 0)
-    o = O.sample_observation(oracle_mlp(wl.g_Z), s_next, a[None], wl.d_omega, wl.seed)[0]
+    o = O.sample_observation(oracle_mlp(wl.g_Z), s_next[0], a, wl.d_omega, wl.seed)
     out = torch.empty((N, wl.d_s), dtype=torch.float32, device="cuda")
     idx = torch.empty(N, dtype=torch.int32, device="cuda")
     w = torch.empty(N, dtype=torch.float64, device="cuda")
