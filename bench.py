@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Planning-step benchmark of the VOiLA hot path on B300.
+
+One step = one SIR belief update (N particles: propose with g_T, weight with
+the likelihood MLP, normalise, resample) followed by the Monte-Carlo rollout
+of the updated belief over K action sequences x H steps with the generator
+and reward MLPs, the per-sequence return reduction and the argmax.
+
+Default workload ("mid_bf16"): state 8, action 2, observation 6, latent 8;
+3x256 SiLU MLPs with BF16 weights; N=4096, K=1024, H=20, gamma=0.98; all
+inputs seeded and synthetic (random-init weights shaped like the paper's
+models). Metric: rollout transition-steps/s = N*K*H per step.
+
+Prints one JSON line. Under torchrun each rank runs an independent replica
+on its own GPU (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "rollout transition-steps/s"
+UNIT = "transition-steps/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["mid_bf16", "mid_fp32", "small_fp32"], default="mid_bf16")
+    ap.add_argument("--cpu-seqs", type=int, default=8, help="action sequences in the oracle CPU sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    from paper_2606_19729_b300 import workloads as WL
+    if name == "mid_bf16":
+        return WL.mid_bf16()
+    if name == "mid_fp32":
+        return WL.mid_bf16(prec=WL.PREC_FP32)
+    return WL.small_fp32()
+
+
+def flops_per_transition(wl) -> int:
+    """Algorithmic FLOPs of one transition: 2 * sum(in * out) over the generator
+    and (if it is an MLP) the reward head."""
+    f = sum(2 * w.shape[0] * w.shape[1] for w in wl.g_T.W)
+    if wl.reward_mlp is not None and wl.goal is None:
+        f += sum(2 * w.shape[0] * w.shape[1] for w in wl.reward_mlp.W)
+    return f
+
+
+def workload_config(wl, args):
+    return {
+        "workload": f"{wl.name}: N={wl.N} particles x K={wl.K} sequences x H={wl.H}, "
+                    f"d_s={wl.d_s} d_a={wl.d_a} d_o={wl.d_o} d_omega={wl.d_omega}, "
+                    f"MLPs {'x'.join(str(d) for d in wl.g_T.dims)} "
+                    f"{'BF16' if wl.prec == 1 else 'FP32'}; belief update + rollout per step",
+        "N": wl.N, "K": wl.K, "H": wl.H,
+        "l2": "flushed (256 MB write) before every timed step",
+        "inputs": "synthetic, seeded; random-init weights",
+    }
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        if not getattr(self, "out", ""):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wl, seqs):
+    """The FP64 oracle, as it stands, on a bounded sample: one belief update of all
+    N particles plus the rollout of `seqs` sequences x all N particles x H."""
+    import threadpoolctl
+
+    from oracle import voila_oracle as O
+
+    def om(spec):
+        return O.MLP(spec.W, spec.b, spec.act)
+
+    obs = np.zeros(wl.d_o)
+    ks = list(range(seqs))
+    t0 = time.perf_counter()
+    res = O.belief_update(om(wl.g_T), O.Likelihood(O.LIK_MLP, mlp=om(wl.ell)), wl.particles, wl.actions[0, 0],
+                          obs, wl.d_omega, wl.lam, wl.seed, 1)
+    R = O.Reward(O.REWARD_MLP, mlp=om(wl.reward_mlp)) if wl.goal is None else O.Reward(O.REWARD_GOAL, wl.goal)
+    O.rollout(om(wl.g_T), R, res.particles_out, wl.actions, wl.d_omega, wl.gamma, wl.seed, k_index=ks)
+    dt = time.perf_counter() - t0
+    info = threadpoolctl.threadpool_info()
+    cores = max([i.get("num_threads", 1) for i in info] + [1])
+    trans = seqs * wl.N * wl.H
+    return {"value": trans / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 numpy oracle: 1 belief update of {wl.N} particles + rollout of {seqs} of {wl.K} "
+                      f"sequences x {wl.N} particles x H={wl.H} ({trans} transitions) in {dt:.2f} s"}
+
+
+def run_reference(args, rank):
+    """The oracle as the reference arm: bounded samples of the same workload, timed on the host."""
+    if rank != 0:
+        return
+    wl = make_workload(args.workload)
+    seqs = 2
+    for _ in range(args.warmup):
+        cpu_baseline(wl, seqs)
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(wl, seqs)
+    dt = time.perf_counter() - t0
+    value = args.steps * seqs * wl.N * wl.H / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(wl, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": f"each step: {last['sample']}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2606_19729_b300 import voila as V
+
+    wl = make_workload(args.workload)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    planner = rank  # independent noise per replica
+
+    g = V.DeviceMLP.from_spec(wl.g_T)
+    gz = V.DeviceMLP.from_spec(wl.g_Z)
+    ell = V.DeviceMLP.from_spec(wl.ell)
+    lik = V.mlp_likelihood(ell)
+    if wl.goal is None:
+        rm = V.DeviceMLP.from_spec(wl.reward_mlp)
+        R = V.mlp_reward(rm)
+    else:
+        R = V.goal_reward(list(wl.goal))
+    N, K, H = wl.N, wl.K, wl.H
+
+    particles = torch.from_numpy(wl.particles).float().to(dev)
+    actions = torch.from_numpy(wl.actions).float().to(dev)
+    action = actions[0, 0].contiguous()
+    # the observation is drawn from the samplers: s' = g_T(s_true, a, w), o = g_Z(s', a, w_Z)
+    from paper_2606_19729_b300 import workloads as WL
+    s_true = torch.from_numpy(WL.true_state(wl.seed, wl.d_s, 1.0)).float().to(dev).reshape(1, -1)
+    s_next = torch.empty((1, wl.d_s), device=dev)
+    V.voila_generator_fwd_seeded(g, s_true, action.reshape(1, -1), 0, wl.d_omega, wl.seed, 5, 0, planner, s_next)
+    obs2 = torch.empty((1, wl.d_o), device=dev)
+    V.voila_generator_fwd_seeded(gz, s_next, action.reshape(1, -1), 0, wl.d_omega, wl.seed, V.STREAM_OBS_OMEGA, 0,
+                                 planner, obs2)
+    obs = obs2.reshape(-1).contiguous()
+
+    p_new = torch.empty_like(particles)
+    J = torch.empty(K, dtype=torch.float64, device=dev)
+    best = torch.empty(1, dtype=torch.int32, device=dev)
+    ws_b = V.alloc_workspace(V.voila_belief_update_workspace_size(g, lik, N))
+    ws_r = V.alloc_workspace(V.voila_rollout_workspace_size(g, R, N, K, H))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(p_in, obs_t, act_seq, a0):
+        V.voila_belief_update(g, lik, p_in, None, a0, obs_t, wl.d_omega, wl.lam, wl.seed, 1, planner, p_new, None,
+                              None, None, None, ws_b)
+        V.voila_rollout(g, R, p_new, None, act_seq, wl.d_omega, wl.gamma, wl.seed, planner, J, None, best, ws_r)
+
+    for _ in range(args.warmup):
+        step(particles, obs, actions, action)
+    torch.cuda.synchronize()
+    assert V.workspace_status(ws_b) == V.OK and V.workspace_status(ws_r) == V.OK
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            V.voila_belief_update(g, lik, particles, None, action, obs, wl.d_omega, wl.lam, wl.seed, 1, planner,
+                                  p_new, None, None, None, None, ws_b)
+            ev[i][1].record(stream)
+            V.voila_rollout(g, R, p_new, None, actions, wl.d_omega, wl.gamma, wl.seed, planner, J, None, best,
+                            ws_r)
+            ev[i][2].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    roll_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    assert V.workspace_status(ws_b) == V.OK and V.workspace_status(ws_r) == V.OK
+    trans_per_step = N * K * H
+    value = trans_per_step * args.steps * world / total_s
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    h_particles = torch.from_numpy(wl.particles).float().pin_memory()
+    h_actions = torch.from_numpy(wl.actions).float().pin_memory()
+    h_obs = obs.cpu().pin_memory()
+    h_J = torch.empty(K, dtype=torch.float64).pin_memory()
+    h_best = torch.empty(1, dtype=torch.int32).pin_memory()
+    d_particles = torch.empty_like(particles)
+    d_actions = torch.empty_like(actions)
+    d_obs = torch.empty_like(obs)
+    h2d = h_particles.numel() * 4 + h_actions.numel() * 4 + h_obs.numel() * 4
+    d2h = K * 8 + 4
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for i in range(args.steps + 1):
+        flush.fill_(i & 0xFF)
+        if i > 0:
+            e2e_ev[i - 1][0].record(stream)
+        d_particles.copy_(h_particles, non_blocking=True)
+        d_actions.copy_(h_actions, non_blocking=True)
+        d_obs.copy_(h_obs, non_blocking=True)
+        step(d_particles, d_obs, d_actions, d_actions[0, 0])
+        h_J.copy_(J, non_blocking=True)
+        h_best.copy_(best, non_blocking=True)
+        if i > 0:
+            e2e_ev[i - 1][1].record(stream)
+        torch.cuda.synchronize()
+    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = trans_per_step * args.steps * world / e2e_s
+
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    fpt = flops_per_transition(wl)
+    roll_avg_s = sum(roll_ms) / len(roll_ms) / 1e3
+    if wl.prec == 1:
+        achieved = fpt * trans_per_step / roll_avg_s / 1e12
+        peak = peaks.get("bf16_tflops_sustained", 1400.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "rollout_tc_kernel (voila_rollout call: weight pack + rollout + return reduction)",
+                "peak_source": "measured bf16 sustained (MEASURED_PEAKS.json)" if peaks else "fallback"}
+    else:
+        achieved = fpt * trans_per_step / roll_avg_s / 1e12
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = nsm * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "rollout_simt_kernel",
+                "peak_source": "FP32 FMA: SMs x 128 lanes x 2 FLOP x max SM clock"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if wl.prec == 1 else "f32",
+            "data": "synthetic (seeded inputs, random-init weights)",
+            "config": dict(workload_config(wl, args), parallelism=f"replicas x{world}"),
+            "rollout_ms": statistics.median(roll_ms), "belief_update_ms": statistics.median(
+                [e[0].elapsed_time(e[1]) for e in ev]),
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 6 * args.steps,
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seqs)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
