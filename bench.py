@@ -128,11 +128,25 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def blas_threads() -> int:
+    """Threads numpy's BLAS runs with (the oracle's parallelism), else the host's cores."""
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        n = max([i.get("num_threads", 1) for i in info if i.get("user_api") == "blas"] + [0])
+        if n:
+            return n
+    except ImportError:
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            return int(os.environ[var])
+    return len(os.sched_getaffinity(0))
+
+
 def cpu_baseline(wl, seqs):
     """The FP64 oracle, as it stands, on a bounded sample: one belief update of all
     N particles plus the rollout of `seqs` sequences x all N particles x H."""
-    import threadpoolctl
-
     from oracle import voila_oracle as O
 
     def om(spec):
@@ -146,8 +160,7 @@ def cpu_baseline(wl, seqs):
     R = O.Reward(O.REWARD_MLP, mlp=om(wl.reward_mlp)) if wl.goal is None else O.Reward(O.REWARD_GOAL, wl.goal)
     O.rollout(om(wl.g_T), R, res.particles_out, wl.actions, wl.d_omega, wl.gamma, wl.seed, k_index=ks)
     dt = time.perf_counter() - t0
-    info = threadpoolctl.threadpool_info()
-    cores = max([i.get("num_threads", 1) for i in info] + [1])
+    cores = blas_threads()
     trans = seqs * wl.N * wl.H
     return {"value": trans / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 numpy oracle: 1 belief update of {wl.N} particles + rollout of {seqs} of {wl.K} "

@@ -202,7 +202,7 @@ def test_generator_fwd_plain_and_seeded(V):
     want = O.mlp_forward(oracle_mlp(wl.g_T), X.astype(np.float64))
     assert rel_err(Y.cpu().numpy(), want) < TOL_FP32
     S = wl.particles[:77]
-    A = np.asarray(wl.actions[:77, 0], np.float32)
+    A = rng.uniform(-1, 1, size=(77, wl.d_a)).astype(np.float32)
     Y2 = torch.empty((77, wl.d_s), dtype=torch.float32, device="cuda")
     V.voila_generator_fwd_seeded(g, cuda(S), cuda(A), wl.d_a, wl.d_omega, 5, O.STREAM_OBS_OMEGA, 9, 1, Y2)
     want2 = O.generator_forward_seeded(oracle_mlp(wl.g_T), S, A, wl.d_omega, 5, O.STREAM_OBS_OMEGA, 9, 1)
