@@ -193,6 +193,42 @@ voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* e
                                  double* logZ_out, double* ess_out,
                                  void* workspace, size_t ws_bytes, voila_stream_t stream);
 
+/* Size of the fixed device scratch behind voila_belief_update_noalloc (4 MiB). */
+#define VOILA_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+/*
+ * voila_belief_update for callers that cannot allocate device memory: a
+ * control loop that forbids allocation once it runs (an allocation can block
+ * or fail at an arbitrary moment), a plug-in inside a framework that owns all
+ * device memory, or a caller with no way to size and keep a workspace. The
+ * paper has no counterpart; this is a convenience of this library.
+ *
+ * Same arguments and results as voila_belief_update, without the workspace:
+ * the scratch is one array of VOILA_NOALLOC_SCRATCH_BYTES compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits. N is accepted while voila_belief_update_workspace_size(g_T, ell, N)
+ * fits in that array (N <= 87368 for d_s = 8); larger N returns
+ * VOILA_ERR_WORKSPACE before any device work.
+ *   status_out  device int32 or NULL: receives the device-side status
+ *               (VOILA_OK, VOILA_ERR_NONFINITE or VOILA_ERR_DEGENERATE),
+ *               asynchronously on `stream`.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture. The call
+ * runs on the current device, so `stream` must belong to it.
+ * All calls share the one array and it keeps the last call's contents: calls
+ * whose work overlaps on the GPU (different streams, or different host
+ * threads) race and must be serialised by the caller.
+ */
+voila_status voila_belief_update_noalloc(const voila_mlp* g_T, const voila_likelihood* ell,
+                                         const float* particles_in, const double* logw_in,
+                                         int32_t N, int32_t d_s, const float* action,
+                                         const float* obs, int32_t d_a, int32_t d_o,
+                                         int32_t d_omega, float lambda, uint64_t seed,
+                                         uint32_t step, uint32_t planner_id, float* particles_out,
+                                         int32_t* idx_out, double* w_out, double* logZ_out,
+                                         double* ess_out, int32_t* status_out,
+                                         voila_stream_t stream);
+
 /*
  * Batched MLP forward Y = mlp(X) (Eq. 2 / Eq. 5 generator form).
  *   X [B][dims[0]] float, Y [B][dims[n_layers]] float. No workspace.

@@ -67,6 +67,9 @@ _lib_belief_ws = _sig("voila_belief_update_workspace_size", c_int32, POINTER(voi
 _lib_belief = _sig("voila_belief_update", c_int32, POINTER(voila_mlp), POINTER(voila_likelihood), _P, _P,
                    c_int32, c_int32, _P, _P, c_int32, c_int32, c_int32, c_float, c_uint64, c_uint32,
                    c_uint32, _P, _P, _P, _P, _P, _P, c_size_t, _P)
+_lib_belief_noalloc = _sig("voila_belief_update_noalloc", c_int32, POINTER(voila_mlp), POINTER(voila_likelihood),
+                           _P, _P, c_int32, c_int32, _P, _P, c_int32, c_int32, c_int32, c_float, c_uint64,
+                           c_uint32, c_uint32, _P, _P, _P, _P, _P, _P, _P)
 _lib_fwd = _sig("voila_generator_fwd", c_int32, POINTER(voila_mlp), _P, c_int32, _P, _P)
 _lib_fwd_seeded = _sig("voila_generator_fwd_seeded", c_int32, POINTER(voila_mlp), _P, _P, c_int32, c_int32,
                        c_int32, c_int32, c_int32, c_uint64, c_uint32, c_uint32, c_uint32, _P, _P)
@@ -224,6 +227,24 @@ def voila_belief_update(g_T: DeviceMLP, ell: voila_likelihood, particles_in: tor
                        _ptr(w_out, torch.float64), _ptr(logZ_out, torch.float64),
                        _ptr(ess_out, torch.float64), _ptr(workspace), workspace.numel(), _stream(stream))
     _check(code, "voila_belief_update")
+
+
+def voila_belief_update_noalloc(g_T: DeviceMLP, ell: voila_likelihood, particles_in: torch.Tensor,
+                                logw_in: Optional[torch.Tensor], action: torch.Tensor, obs: torch.Tensor,
+                                d_omega: int, lam: float, seed: int, step: int, planner_id: int,
+                                particles_out: torch.Tensor, idx_out: Optional[torch.Tensor],
+                                w_out: Optional[torch.Tensor], logZ_out: Optional[torch.Tensor],
+                                ess_out: Optional[torch.Tensor], status_out: Optional[torch.Tensor],
+                                stream=None):
+    """voila_belief_update without a workspace: the library's fixed device scratch is used."""
+    N, d_s = particles_in.shape
+    code = _lib_belief_noalloc(ctypes.byref(g_T.desc), ctypes.byref(ell), _ptr(particles_in, torch.float32),
+                               _ptr(logw_in, torch.float64), N, d_s, _ptr(action, torch.float32),
+                               _ptr(obs, torch.float32), action.numel(), obs.numel(), d_omega, lam, seed,
+                               step, planner_id, _ptr(particles_out, torch.float32), _ptr(idx_out, torch.int32),
+                               _ptr(w_out, torch.float64), _ptr(logZ_out, torch.float64),
+                               _ptr(ess_out, torch.float64), _ptr(status_out, torch.int32), _stream(stream))
+    _check(code, "voila_belief_update_noalloc")
 
 
 def voila_generator_fwd(mlp: DeviceMLP, X: torch.Tensor, Y: torch.Tensor, stream=None):
