@@ -42,16 +42,24 @@ def parse_args():
     ap.add_argument("--workload", choices=["mid_bf16", "mid_fp32", "small_fp32"], default="mid_bf16")
     ap.add_argument("--cpu-seqs", type=int, default=8, help="action sequences in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--N", type=int, default=None, help="override particles (profiling runs)")
+    ap.add_argument("--K", type=int, default=None, help="override action sequences (profiling runs)")
+    ap.add_argument("--H", type=int, default=None, help="override horizon (profiling runs)")
     return ap.parse_args()
 
 
-def make_workload(name):
+def make_workload(name, args=None):
     from paper_2606_19729_b300 import workloads as WL
+    kw = {}
+    for key in ("N", "K", "H"):
+        v = getattr(args, key, None) if args is not None else None
+        if v is not None:
+            kw[key] = v
     if name == "mid_bf16":
-        return WL.mid_bf16()
+        return WL.mid_bf16(**kw)
     if name == "mid_fp32":
-        return WL.mid_bf16(prec=WL.PREC_FP32)
-    return WL.small_fp32()
+        return WL.mid_bf16(prec=WL.PREC_FP32, **kw)
+    return WL.small_fp32(**kw)
 
 
 def flops_per_transition(wl) -> int:
@@ -171,7 +179,7 @@ def run_reference(args, rank):
     """The oracle as the reference arm: bounded samples of the same workload, timed on the host."""
     if rank != 0:
         return
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args)
     seqs = 2
     for _ in range(args.warmup):
         cpu_baseline(wl, seqs)
@@ -209,7 +217,7 @@ def main():
 
     from paper_2606_19729_b300 import voila as V
 
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     planner = rank  # independent noise per replica
