@@ -10,11 +10,13 @@
 //               of every layer through a ring of shared-memory slots with
 //               cp.async.bulk (the whole weight set, 560 KB for the 3x256
 //               generator + reward, does not fit in 227 KB of shared memory);
-//   warp 1      MMA issuer: allocates the 512 TMEM columns and, per weight
-//               chunk, issues tcgen05.mma for both tiles (so every chunk read
-//               from L2 feeds 256 rows);
+//   warp 1      MMA issuer: allocates the 512 TMEM columns and issues the
+//               tcgen05.mma of the two tiles alternately, one layer at a time,
+//               so one tile's MMAs run while the other tile's epilogue runs
+//               (each tile streams its own pass over the weights; L2 has the
+//               bandwidth for it);
 //   warps 2-9   epilogue, four warps per tile, one thread per row: TMEM ->
-//               registers, bias + activation, BF16 pack into the next
+//               registers, bias + SiLU (1/2 folded into W, b; FP16x2 tanh), BF16 pack into the next
 //               layer's A operand (128B-swizzled K-major), plus the row's
 //               state s_t, Philox noise, reward and FP64 return.
 // Accumulators: tile 0 in TMEM columns [0, 256), tile 1 in [256, 512).
@@ -83,13 +85,21 @@ __device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, vola
   }
 }
 
-__device__ __forceinline__ float act_fast(float h, int act) {
+// Activation of two accumulator values, packed to BF16x2 for the next layer.
+// SiLU: the weights and bias of a SiLU layer are packed pre-scaled by 1/2
+// (exact in BF16/FP32), so the accumulator holds u = x/2 and
+// silu(x) = x sigmoid(x) = u (1 + tanh u); tanh runs on two values per MUFU
+// op in FP16 (relative error about 2^-11, below the BF16 rounding that follows).
+__device__ __forceinline__ uint32_t act_pair(float u0, float u1, int act) {
   if (act == VOILA_ACT_SILU) {
-    const float hh = 0.5f * h;  // silu(h) = h/2 (1 + tanh(h/2))
-    return fmaf(hh, ptx::tanh_approx(hh), hh);
+    const float2 t = ptx::tanh2_f16(u0, u1);
+    return ptx::pack_bf16x2(fmaf(u0, t.x, u0), fmaf(u1, t.y, u1));
   }
-  if (act == VOILA_ACT_TANH) return ptx::tanh_approx(h);
-  return h;
+  if (act == VOILA_ACT_TANH) {
+    const float2 t = ptx::tanh2_f16(u0, u1);
+    return ptx::pack_bf16x2(t.x, t.y);
+  }
+  return ptx::pack_bf16x2(u0, u1);
 }
 
 // Byte address of 16-byte chunk j (8 BF16 columns) of row r in a 128B-swizzled
@@ -199,21 +209,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
       for (int s = 0; s < kStages; ++s) last_round[s] = -1;
       for (long long pr = blockIdx.x; pr < p.pairs && ok; pr += gridDim.x)
         for (int t = 0; t < p.H && ok; ++t)
-          for (int l = 0; l < p.n_total && ok; ++l) {
-            const TcLayer& L = p.layers[l];
-            for (int c = 0; c < L.nchunks; ++c, ++it) {
-              const int slot = (int)(it % kStages);
-              const uint32_t round = (uint32_t)(it / kStages);
-              if (!bounded_wait(ptx::smem_u32(&empty[slot]), (round & 1) ^ 1, abort_flag, p.hdr, 10)) {
-                ok = false;
-                break;
+          for (int l = 0; l < p.n_total && ok; ++l)
+            for (int g = 0; g < 2 && ok; ++g) {
+              const TcLayer& L = p.layers[l];
+              for (int c = 0; c < L.nchunks; ++c, ++it) {
+                const int slot = (int)(it % kStages);
+                const uint32_t round = (uint32_t)(it / kStages);
+                if (!bounded_wait(ptx::smem_u32(&empty[slot]), (round & 1) ^ 1, abort_flag, p.hdr, 10)) {
+                  ok = false;
+                  break;
+                }
+                ptx::mbar_arrive_expect_tx(ptx::smem_u32(&full[slot]), (uint32_t)L.chunk_bytes);
+                ptx::bulk_g2s(ring_addr + slot * kSlotBytes, p.wstream + L.wofs + (long long)c * L.chunk_bytes,
+                              (uint32_t)L.chunk_bytes, ptx::smem_u32(&full[slot]));
+                last_round[slot] = (int)round;
               }
-              ptx::mbar_arrive_expect_tx(ptx::smem_u32(&full[slot]), (uint32_t)L.chunk_bytes);
-              ptx::bulk_g2s(ring_addr + slot * kSlotBytes, p.wstream + L.wofs + (long long)c * L.chunk_bytes,
-                            (uint32_t)L.chunk_bytes, ptx::smem_u32(&full[slot]));
-              last_round[slot] = (int)round;
             }
-          }
       if (!ok) {  // drain copies still in flight before the CTA's shared memory goes away
         for (int s = 0; s < kStages; ++s)
           if (last_round[s] >= 0) {
@@ -233,28 +244,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
       const uint32_t a_addr0 = ptx::smem_u32(Abuf[0]), a_addr1 = ptx::smem_u32(Abuf[1]);
       for (long long pr = blockIdx.x; pr < p.pairs && ok; pr += gridDim.x)
         for (int t = 0; t < p.H && ok; ++t)
-          for (int l = 0; l < p.n_total && ok; ++l) {
-            const TcLayer& L = p.layers[l];
-            for (int c = 0; c < L.nchunks; ++c, ++it) {
-              const int slot = (int)(it % kStages);
-              const uint32_t round = (uint32_t)(it / kStages);
-              if (!bounded_wait(ptx::smem_u32(&full[slot]), round & 1, abort_flag, p.hdr, 20)) {
+          for (int l = 0; l < p.n_total && ok; ++l)
+            for (int g = 0; g < 2 && ok; ++g) {
+              // tile g's A operand for layer l is ready and its accumulator is free
+              const uint32_t nr = g ? nready1 : nready0;
+              if (!bounded_wait(ptx::smem_u32(&ready[g]), nr & 1, abort_flag, p.hdr, 21 + g)) {
                 ok = false;
                 break;
               }
+              if (g) ++nready1;
+              else ++nready0;
               ptx::tc_fence_after();
-              for (int g = 0; g < 2; ++g) {
-                if (c == 0) {
-                  const uint32_t nr = g ? nready1 : nready0;
-                  if (!bounded_wait(ptx::smem_u32(&ready[g]), nr & 1, abort_flag, p.hdr, 21 + g)) {
-                    ok = false;
-                    break;
-                  }
-                  if (g) ++nready1;
-                  else ++nready0;
-                  ptx::tc_fence_after();
+              const TcLayer& L = p.layers[l];
+              const uint32_t a_addr = g ? a_addr1 : a_addr0;
+              for (int c = 0; c < L.nchunks; ++c, ++it) {
+                const int slot = (int)(it % kStages);
+                const uint32_t round = (uint32_t)(it / kStages);
+                if (!bounded_wait(ptx::smem_u32(&full[slot]), round & 1, abort_flag, p.hdr, 20)) {
+                  ok = false;
+                  break;
                 }
-                const uint32_t a_addr = g ? a_addr1 : a_addr0;
+                ptx::tc_fence_after();
 #pragma unroll
                 for (int kk = 0; kk < 2; ++kk) {
                   const int kidx = 32 * c + 16 * kk;
@@ -266,13 +276,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
                     ptx::mma_bf16(tmem_base + g * 256, ad, bd, L.idesc, (c > 0 || kk > 0) ? 1u : 0u);
                   }
                 }
-                if (g == 0 && c == L.nchunks - 1) ptx::mma_commit(ptx::smem_u32(&accf[0]));
+                ptx::mma_commit(ptx::smem_u32(&empty[slot]));
+                if (c == L.nchunks - 1) ptx::mma_commit(ptx::smem_u32(&accf[g]));
               }
-              if (!ok) break;
-              ptx::mma_commit(ptx::smem_u32(&empty[slot]));
-              if (c == L.nchunks - 1) ptx::mma_commit(ptx::smem_u32(&accf[1]));
             }
-          }
       // wait for every MMA this thread issued (normal exit and abort alike)
       ptx::mma_commit(ptx::smem_u32(drain));
       const long long t0 = clock64();
@@ -330,10 +337,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
                 const float4 b0 = *reinterpret_cast<const float4*>(bl + c0 + 8 * j);
                 const float4 b1 = *reinterpret_cast<const float4*>(bl + c0 + 8 * j + 4);
                 uint4 o;
-                o.x = ptx::pack_bf16x2(act_fast(v[8 * j + 0] + b0.x, L.act), act_fast(v[8 * j + 1] + b0.y, L.act));
-                o.y = ptx::pack_bf16x2(act_fast(v[8 * j + 2] + b0.z, L.act), act_fast(v[8 * j + 3] + b0.w, L.act));
-                o.z = ptx::pack_bf16x2(act_fast(v[8 * j + 4] + b1.x, L.act), act_fast(v[8 * j + 5] + b1.y, L.act));
-                o.w = ptx::pack_bf16x2(act_fast(v[8 * j + 6] + b1.z, L.act), act_fast(v[8 * j + 7] + b1.w, L.act));
+                o.x = act_pair(v[8 * j + 0] + b0.x, v[8 * j + 1] + b0.y, L.act);
+                o.y = act_pair(v[8 * j + 2] + b0.z, v[8 * j + 3] + b0.w, L.act);
+                o.z = act_pair(v[8 * j + 4] + b1.x, v[8 * j + 5] + b1.y, L.act);
+                o.w = act_pair(v[8 * j + 6] + b1.z, v[8 * j + 7] + b1.w, L.act);
                 *reinterpret_cast<uint4*>(a_chunk(slab, r, j)) = o;
               }
             }
@@ -406,6 +413,7 @@ struct PackTable {
   int N[kMaxTcLayers], K[kMaxTcLayers], Npad[kMaxTcLayers], nchunks[kMaxTcLayers];
   long long wofs[kMaxTcLayers], welems_end[kMaxTcLayers];
   int bias_off[kMaxTcLayers];
+  int half[kMaxTcLayers];  // 1: SiLU layer, pack W and b scaled by 1/2
   int n;
   uint8_t* wout;
   float* bout;
@@ -423,15 +431,17 @@ __global__ void pack_kernel(const __grid_constant__ PackTable t) {
     const int rem = (int)(e0 % (Npad * 32));
     const int nrow = rem / 32, kk = rem % 32;
     const int kg = 32 * c + kk;
-    const __nv_bfloat16 v =
+    __nv_bfloat16 v =
         (nrow < t.N[l] && kg < t.K[l]) ? t.W[l][(size_t)nrow * t.K[l] + kg] : __float2bfloat16(0.0f);
+    if (t.half[l]) v = __hmul(v, __float2bfloat16(0.5f));  // exact: power-of-two scaling
     const int j = kk >> 3;
     const size_t byte =
         (size_t)t.wofs[l] + (size_t)c * Npad * 64 + (size_t)nrow * 64 + (((j ^ ((nrow >> 1) & 3)) << 4)) + (kk & 7) * 2;
     *reinterpret_cast<__nv_bfloat16*>(t.wout + byte) = v;
     if (c == 0 && kk == 0) {
       const int np4 = (Npad + 3) / 4 * 4;
-      if (nrow < np4) t.bout[t.bias_off[l] + nrow] = nrow < t.N[l] ? t.b[l][nrow] : 0.0f;
+      if (nrow < np4)
+        t.bout[t.bias_off[l] + nrow] = nrow < t.N[l] ? (t.half[l] ? 0.5f : 1.0f) * t.b[l][nrow] : 0.0f;
       if (nrow == Npad - 1)
         for (int i = Npad; i < np4; ++i) t.bout[t.bias_off[l] + i] = 0.0f;
     }
@@ -484,6 +494,7 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
       T.nchunks[nl] = L.nchunks;
       T.wofs[nl] = wofs;
       T.bias_off[nl] = boff;
+      T.half[nl] = (!last && M->act == VOILA_ACT_SILU) ? 1 : 0;
       welems += (long long)L.nchunks * L.Npad * 32;
       T.welems_end[nl] = welems;
       wofs += (long long)L.nchunks * L.chunk_bytes;
