@@ -16,7 +16,7 @@
 //               (each tile streams its own pass over the weights; L2 has the
 //               bandwidth for it);
 //   warps 2-9   epilogue, four warps per tile, one thread per row: TMEM ->
-//               registers, bias + SiLU (1/2 folded into W, b; FP16x2 tanh), BF16 pack into the next
+//               registers, bias + SiLU (1/2 folded into W, b; packed BF16x2 tanh and FMA), BF16 into the next
 //               layer's A operand (128B-swizzled K-major), plus the row's
 //               state s_t, Philox noise, reward and FP64 return.
 // Accumulators: tile 0 in TMEM columns [0, 256), tile 1 in [256, 512).
@@ -88,18 +88,31 @@ __device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, vola
 // Activation of two accumulator values, packed to BF16x2 for the next layer.
 // SiLU: the weights and bias of a SiLU layer are packed pre-scaled by 1/2
 // (exact in BF16/FP32), so the accumulator holds u = x/2 and
-// silu(x) = x sigmoid(x) = u (1 + tanh u); tanh runs on two values per MUFU
-// op in FP16 (relative error about 2^-11, below the BF16 rounding that follows).
+// silu(x) = x sigmoid(x) = u (1 + tanh u) = fma(u, tanh u, u), evaluated on
+// the packed BF16 pair: one convert, one MUFU op and one FMA per two values.
 __device__ __forceinline__ uint32_t act_pair(float u0, float u1, int act) {
-  if (act == VOILA_ACT_SILU) {
-    const float2 t = ptx::tanh2_f16(u0, u1);
-    return ptx::pack_bf16x2(fmaf(u0, t.x, u0), fmaf(u1, t.y, u1));
+  const uint32_t h = ptx::pack_bf16x2(u0, u1);
+  if (act == VOILA_ACT_SILU) return ptx::fma_bf16x2(h, ptx::tanh_bf16x2(h), h);
+  if (act == VOILA_ACT_TANH) return ptx::tanh_bf16x2(h);
+  return h;
+}
+
+// 32 accumulator columns [32c, 32c + 32) of row r -> bias + activation ->
+// four 16-byte chunks of the next layer's A operand.
+__device__ __forceinline__ void epi_cols32(const float* v, const float* bl, int c, int act, uint8_t* A,
+                                           int r) {
+  uint8_t* slab = A + (c >> 1) * (128 * 128);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float4 b0 = *reinterpret_cast<const float4*>(bl + 32 * c + 8 * j);
+    const float4 b1 = *reinterpret_cast<const float4*>(bl + 32 * c + 8 * j + 4);
+    uint4 o;
+    o.x = act_pair(v[8 * j + 0] + b0.x, v[8 * j + 1] + b0.y, act);
+    o.y = act_pair(v[8 * j + 2] + b0.z, v[8 * j + 3] + b0.w, act);
+    o.z = act_pair(v[8 * j + 4] + b1.x, v[8 * j + 5] + b1.y, act);
+    o.w = act_pair(v[8 * j + 6] + b1.z, v[8 * j + 7] + b1.w, act);
+    *reinterpret_cast<uint4*>(slab + r * 128 + ((((c & 1) * 4 + j) ^ (r & 7)) << 4)) = o;
   }
-  if (act == VOILA_ACT_TANH) {
-    const float2 t = ptx::tanh2_f16(u0, u1);
-    return ptx::pack_bf16x2(t.x, t.y);
-  }
-  return ptx::pack_bf16x2(u0, u1);
 }
 
 // Byte address of 16-byte chunk j (8 BF16 columns) of row r in a 128B-swizzled
@@ -325,24 +338,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
           const float* bl = bias_s + L.bias_off;
           bool arrive = true;
           if (L.act >= 0) {
-            // hidden layer: bias + activation -> BF16 A operand of the next layer
-            for (int c0 = 0; c0 < L.Npad; c0 += 64) {
-              float v[64];
-              ptx::tmem_ld32(tm + c0, v);
-              ptx::tmem_ld32(tm + c0 + 32, v + 32);
-              ptx::tmem_wait_ld();
-              uint8_t* slab = A + (c0 >> 6) * (128 * 128);
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const float4 b0 = *reinterpret_cast<const float4*>(bl + c0 + 8 * j);
-                const float4 b1 = *reinterpret_cast<const float4*>(bl + c0 + 8 * j + 4);
-                uint4 o;
-                o.x = act_pair(v[8 * j + 0] + b0.x, v[8 * j + 1] + b0.y, L.act);
-                o.y = act_pair(v[8 * j + 2] + b0.z, v[8 * j + 3] + b0.w, L.act);
-                o.z = act_pair(v[8 * j + 4] + b1.x, v[8 * j + 5] + b1.y, L.act);
-                o.w = act_pair(v[8 * j + 6] + b1.z, v[8 * j + 7] + b1.w, L.act);
-                *reinterpret_cast<uint4*>(a_chunk(slab, r, j)) = o;
-              }
+            // hidden layer: bias + activation -> BF16 A operand of the next layer;
+            // the TMEM load of the next 32 columns overlaps the math on the current ones
+            float va[32], vb[32];
+            const int nc = L.Npad >> 5;  // even: hidden widths are multiples of 64
+            ptx::tmem_ld32(tm, va);
+            ptx::tmem_wait_ld32(va);
+            for (int c = 0; c < nc; c += 2) {
+              ptx::tmem_ld32(tm + 32 * (c + 1), vb);
+              epi_cols32(va, bl, c, L.act, A, r);
+              ptx::tmem_wait_ld32(vb);
+              if (c + 2 < nc) ptx::tmem_ld32(tm + 32 * (c + 2), va);
+              epi_cols32(vb, bl, c + 1, L.act, A, r);
+              if (c + 2 < nc) ptx::tmem_wait_ld32(va);
             }
           } else if (l == p.n_gen - 1) {
             // generator output: s_{t+1} (FP32, kept in registers)
