@@ -16,7 +16,7 @@
 //               (each tile streams its own pass over the weights; L2 has the
 //               bandwidth for it);
 //   warps 2-9   epilogue, four warps per tile, one thread per row: TMEM ->
-//               registers, bias + SiLU (1/2 folded into W, b; packed BF16x2 tanh and FMA), BF16 into the next
+//               registers, bias + SiLU (1/2 folded into W, b; one tanh.approx per value), BF16 into the next
 //               layer's A operand (128B-swizzled K-major), plus the row's
 //               state s_t, Philox noise, reward and FP64 return.
 // Accumulators: tile 0 in TMEM columns [0, 256), tile 1 in [256, 512).
@@ -88,13 +88,14 @@ __device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, vola
 // Activation of two accumulator values, packed to BF16x2 for the next layer.
 // SiLU: the weights and bias of a SiLU layer are packed pre-scaled by 1/2
 // (exact in BF16/FP32), so the accumulator holds u = x/2 and
-// silu(x) = x sigmoid(x) = u (1 + tanh u) = fma(u, tanh u, u), evaluated on
-// the packed BF16 pair: one convert, one MUFU op and one FMA per two values.
+// silu(x) = x sigmoid(x) = u (1 + tanh u) = fma(u, tanh u, u): one MUFU op
+// (tanh.approx.f32; the packed BF16x2/FP16x2 forms measured slower on this
+// part) and one FMA per value.
 __device__ __forceinline__ uint32_t act_pair(float u0, float u1, int act) {
-  const uint32_t h = ptx::pack_bf16x2(u0, u1);
-  if (act == VOILA_ACT_SILU) return ptx::fma_bf16x2(h, ptx::tanh_bf16x2(h), h);
-  if (act == VOILA_ACT_TANH) return ptx::tanh_bf16x2(h);
-  return h;
+  if (act == VOILA_ACT_SILU)
+    return ptx::pack_bf16x2(fmaf(u0, ptx::tanh_approx(u0), u0), fmaf(u1, ptx::tanh_approx(u1), u1));
+  if (act == VOILA_ACT_TANH) return ptx::pack_bf16x2(ptx::tanh_approx(u0), ptx::tanh_approx(u1));
+  return ptx::pack_bf16x2(u0, u1);
 }
 
 // 32 accumulator columns [32c, 32c + 32) of row r -> bias + activation ->
@@ -338,19 +339,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
           const float* bl = bias_s + L.bias_off;
           bool arrive = true;
           if (L.act >= 0) {
-            // hidden layer: bias + activation -> BF16 A operand of the next layer;
-            // the TMEM load of the next 32 columns overlaps the math on the current ones
-            float va[32], vb[32];
-            const int nc = L.Npad >> 5;  // even: hidden widths are multiples of 64
-            ptx::tmem_ld32(tm, va);
-            ptx::tmem_wait_ld32(va);
-            for (int c = 0; c < nc; c += 2) {
-              ptx::tmem_ld32(tm + 32 * (c + 1), vb);
-              epi_cols32(va, bl, c, L.act, A, r);
-              ptx::tmem_wait_ld32(vb);
-              if (c + 2 < nc) ptx::tmem_ld32(tm + 32 * (c + 2), va);
-              epi_cols32(vb, bl, c + 1, L.act, A, r);
-              if (c + 2 < nc) ptx::tmem_wait_ld32(va);
+            // hidden layer: bias + activation -> BF16 A operand of the next layer,
+            // 32 columns per TMEM load (measured faster than larger batches)
+            for (int c = 0; c < (L.Npad >> 5); ++c) {
+              float v[32];
+              ptx::tmem_ld32(tm + 32 * c, v);
+              ptx::tmem_wait_ld32(v);
+              epi_cols32(v, bl, c, L.act, A, r);
             }
           } else if (l == p.n_gen - 1) {
             // generator output: s_{t+1} (FP32, kept in registers)

@@ -167,31 +167,6 @@ __device__ __forceinline__ void tmem_wait_ld32(float* v) {
       : "memory");
 }
 
-// Packed BF16x2 tanh (one MUFU op for two values) and fused multiply-add.
-__device__ __forceinline__ uint32_t tanh_bf16x2(uint32_t x) {
-  uint32_t y;
-  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(x));
-  return y;
-}
-__device__ __forceinline__ uint32_t fma_bf16x2(uint32_t a, uint32_t b, uint32_t c) {
-  uint32_t d;
-  asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-  return d;
-}
-
-// tanh of two FP32 values through one packed FP16 MUFU op (tanh.approx.f16x2).
-__device__ __forceinline__ float2 tanh2_f16(float a, float b) {
-  uint32_t h, t;
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(b), "f"(a));
-  asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h));
-  unsigned short lo, hi;
-  asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(t));
-  float2 r;
-  asm("cvt.f32.f16 %0, %1;" : "=f"(r.x) : "h"(lo));
-  asm("cvt.f32.f16 %0, %1;" : "=f"(r.y) : "h"(hi));
-  return r;
-}
-
 // Two FP32 values -> one BF16x2 word (round to nearest even), lo in bits 0-15.
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   uint32_t r;
