@@ -5,7 +5,7 @@
 // generator s' = g_T([s; a; omega]) (Eq. 2) and the reward head, and
 // accumulates G = sum_t gamma^t r_t in FP64 (value definition, Sec. 2.1).
 //
-// Warp roles (320 threads):
+// Warp roles (576 threads):
 //   warp 0      producer: streams the packed, pre-swizzled BF16 weight chunks
 //               of every layer through a ring of shared-memory slots with
 //               cp.async.bulk (the whole weight set, 560 KB for the 3x256
@@ -15,7 +15,8 @@
 //               so one tile's MMAs run while the other tile's epilogue runs
 //               (each tile streams its own pass over the weights; L2 has the
 //               bandwidth for it);
-//   warps 2-9   epilogue, four warps per tile, one thread per row: TMEM ->
+//   warps 2-17  epilogue, eight warps per tile (two per TMEM lane quadrant,
+//               splitting the columns), one thread per row: TMEM ->
 //               registers, bias + SiLU (1/2 folded into W, b; one tanh.approx per value), BF16 into the next
 //               layer's A operand (128B-swizzled K-major), plus the row's
 //               state s_t, Philox noise, reward and FP64 return.
@@ -33,7 +34,8 @@ namespace voila {
 
 namespace {
 
-constexpr int kTcThreads = 320;
+constexpr int kTcThreads = 576;   // producer warp, MMA warp, 16 epilogue warps
+constexpr int kEpiWarpsPerTile = 8;
 constexpr int kTileRows = 128;
 constexpr int kStages = 5;
 constexpr int kSlotBytes = 256 * 64;      // N <= 256 rows x 32 BF16 of K
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
     }
     for (int g = 0; g < 2; ++g) {
       ptx::mbar_init(ptx::smem_u32(&accf[g]), 1);
-      ptx::mbar_init(ptx::smem_u32(&ready[g]), kTileRows);
+      ptx::mbar_init(ptx::smem_u32(&ready[g]), kEpiWarpsPerTile);  // one arrival per epilogue warp
     }
     ptx::mbar_init(ptx::smem_u32(drain), 1);
     *abort_flag = 0;
@@ -302,7 +304,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int g = (warp - 2) >> 2;          // tile of this warp
+    // Eight warps per tile: warp w may read TMEM lanes 32*(w % 4) .. +31 (its
+    // rows); the two warps of a lane quadrant split the hidden columns. The
+    // "sub 0" warps also own the row state (s_t, omega, reward, G).
+    const int e = warp - 2;
+    const int g = e >> 3;                   // tile of this warp
+    const int sub = (e >> 2) & 1;           // column half of the hidden layers
     const int q = warp & 3;                 // TMEM lane quadrant this warp may access
     const int r = 32 * q + lane;            // row within the tile
     uint8_t* A = Abuf[g];
@@ -316,16 +323,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
       const bool valid = row < p.rows;
       const uint32_t n = valid ? (uint32_t)(row % p.N) : 0u;
       const uint32_t k = valid ? (uint32_t)(row / p.N) : 0u;
-      float s[DS];
-#pragma unroll
-      for (int i = 0; i < DS; ++i) s[i] = valid ? __ldg(p.particles + (size_t)n * DS + i) : 0.0f;
       const float* act_row = p.actions + (size_t)k * p.H * DA;
-      float a[DA];
+      float s[DS], a[DA];
+      if (sub == 0) {
 #pragma unroll
-      for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + i);
-      write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, 0, p.planner);
+        for (int i = 0; i < DS; ++i) s[i] = valid ? __ldg(p.particles + (size_t)n * DS + i) : 0.0f;
+#pragma unroll
+        for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + i);
+        write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, 0, p.planner);
+      }
       ptx::fence_proxy_async_smem();
-      ptx::mbar_arrive(ready_bar);
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(ready_bar);
       double Gacc = 0.0, disc = 1.0;
       for (int t = 0; t < p.H && ok; ++t) {
         for (int l = 0; l < p.n_total; ++l) {
@@ -337,17 +346,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
           ++nacc;
           ptx::tc_fence_after();
           const float* bl = bias_s + L.bias_off;
-          bool arrive = true;
+          // no A operand follows the final layer of the final step
+          const bool arrive = !(t == p.H - 1 && l == p.n_total - 1);
           if (L.act >= 0) {
             // hidden layer: bias + activation -> BF16 A operand of the next layer,
             // 32 columns per TMEM load (measured faster than larger batches)
-            for (int c = 0; c < (L.Npad >> 5); ++c) {
+            const int nc = L.Npad >> 6;  // 32-column batches per warp (half the columns)
+            for (int c = sub * nc; c < (sub + 1) * nc; ++c) {
               float v[32];
               ptx::tmem_ld32(tm + 32 * c, v);
               ptx::tmem_wait_ld32(v);
               epi_cols32(v, bl, c, L.act, A, r);
             }
-          } else if (l == p.n_gen - 1) {
+          } else if (sub == 0 && l == p.n_gen - 1) {
             // generator output: s_{t+1} (FP32, kept in registers)
             float v[32];
             ptx::tmem_ld16(tm, v);
@@ -360,8 +371,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
 #pragma unroll
               for (int i = 0; i < VOILA_MAX_GOAL; ++i)
                 if (i < p.goal_dims && i < DS) {
-                  const float e = s[i] - p.goal[i];
-                  acc = fmaf(e, e, acc);
+                  const float d = s[i] - p.goal[i];
+                  acc = fmaf(d, d, acc);
                 }
               Gacc += disc * (double)(-acc);
               disc *= p.gamma;
@@ -369,13 +380,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
 #pragma unroll
                 for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + (t + 1) * DA + i);
                 write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), p.planner);
-              } else {
-                arrive = false;
               }
             } else {
               write_rew_input<DS, DA>(A, r, s, a);
             }
-          } else {
+          } else if (sub == 0) {
             // reward output r_t: G += gamma^t r_t in FP64
             float v[16];
             ptx::tmem_ld16(tm, v);
@@ -386,18 +395,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
 #pragma unroll
               for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + (t + 1) * DA + i);
               write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), p.planner);
-            } else {
-              arrive = false;
             }
           }
           ptx::tc_fence_before();
           if (arrive) {
             ptx::fence_proxy_async_smem();
-            ptx::mbar_arrive(ready_bar);
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(ready_bar);
           }
         }
       }
-      if (valid && ok) p.G[row] = Gacc;
+      if (sub == 0 && valid && ok) p.G[row] = Gacc;
     }
   }
 
