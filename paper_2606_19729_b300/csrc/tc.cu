@@ -1,29 +1,37 @@
-// BF16 tensor-core rollout on sm_103a (tcgen05 + TMEM).
+// BF16 tensor-core rollout on sm_103a (tcgen05 + TMEM, CTA-pair MMA).
 //
-// One persistent CTA per SM runs pairs of 128-row tiles (row = k * N + n, one
-// (particle, action-sequence) pair per row) through all H steps of the
-// generator s' = g_T([s; a; omega]) (Eq. 2) and the reward head, and
-// accumulates G = sum_t gamma^t r_t in FP64 (value definition, Sec. 2.1).
+// Clusters of two CTAs on two SMs run "super-pairs" of 512 rows (row =
+// k * N + n, one (particle, action-sequence) pair per row): each CTA owns two
+// 128-row tiles, and the pair's matching tiles form one M = 256 tcgen05.mma
+// (cta_group::2). Every row goes through all H steps of the generator
+// s' = g_T([s; a; omega]) (Eq. 2) and the reward head, accumulating
+// G = sum_t gamma^t r_t in FP64 (value definition, Sec. 2.1).
 //
-// Warp roles (576 threads):
-//   warp 0      producer: streams the packed, pre-swizzled BF16 weight chunks
-//               of every layer through a ring of shared-memory slots with
-//               cp.async.bulk (the whole weight set, 560 KB for the 3x256
-//               generator + reward, does not fit in 227 KB of shared memory);
-//   warp 1      MMA issuer: allocates the 512 TMEM columns and issues the
-//               tcgen05.mma of the two tiles alternately, one layer at a time,
-//               so one tile's MMAs run while the other tile's epilogue runs
-//               (each tile streams its own pass over the weights; L2 has the
-//               bandwidth for it);
+// The pair MMA is what makes the contraction fit this part: an M = 128 MMA
+// reads A (4 KB) and B (8 KB) from one SM's shared memory per K = 16 step,
+// and with the weight stream on top that exceeds the shared-memory bandwidth
+// the tensor core gets; in the pair each SM reads its A and only half of B,
+// and loads only half of every weight chunk.
+//
+// Warp roles (576 threads per CTA):
+//   warp 0      producer: TMA-loads this CTA's half (N/2 rows) of every
+//               [N][64] weight chunk into a ring of shared-memory slots; the
+//               loads of both CTAs complete on the even CTA's barrier;
+//   warp 1      allocates the 512 TMEM columns (both CTAs); in the even CTA
+//               it issues the pair MMAs of the two tiles alternately, one
+//               layer at a time, so one tile's MMAs run while the other
+//               tile's epilogue runs, and commits to both CTAs' barriers;
 //   warps 2-17  epilogue, eight warps per tile (two per TMEM lane quadrant,
 //               splitting the columns), one thread per row: TMEM ->
-//               registers, bias + SiLU (1/2 folded into W, b; one tanh.approx per value), BF16 into the next
-//               layer's A operand (128B-swizzled K-major), plus the row's
-//               state s_t, Philox noise, reward and FP64 return.
+//               registers, bias + SiLU (1/2 folded into W and b; one
+//               tanh.approx per value), BF16 into the next layer's A operand
+//               (128B-swizzled K-major), plus the row's state s_t, Philox
+//               noise, reward and FP64 return.
 // Accumulators: tile 0 in TMEM columns [0, 256), tile 1 in [256, 512).
 // Every wait on an mbarrier is bounded; on expiry the kernel records
-// VOILA_ERR_TIMEOUT in the workspace status word, drains its own copies and
-// MMAs, frees TMEM and returns.
+// VOILA_ERR_TIMEOUT in the workspace status word, drains its copies and MMAs,
+// frees TMEM and returns.
+#include <cuda.h>
 #include <string.h>
 
 #include "common.cuh"
@@ -38,32 +46,32 @@ constexpr int kTcThreads = 576;   // producer warp, MMA warp, 16 epilogue warps
 constexpr int kEpiWarpsPerTile = 8;
 constexpr int kTileRows = 128;
 constexpr int kStages = 5;
-constexpr int kSlotBytes = 256 * 64;      // N <= 256 rows x 32 BF16 of K
+constexpr int kSlotBytes = 128 * 128;     // half of a [256][64] BF16 weight chunk
 constexpr int kABytes = 4 * 128 * 128;    // 128 rows x 256 BF16, four 64-wide K slabs
 constexpr int kMaxTcLayers = 16;
 constexpr long long kSpinLimit = 4000000000LL;  // ~2 s of SM clock per wait
 
 struct TcLayer {
   int Kp;           // input width rounded up to 16 (MMA K steps of 16)
-  int Npad;         // output width (hidden: multiple of 64; output layer: rounded up to 16)
-  int nchunks;      // ceil(Kp / 32) weight chunks of [Npad][32]
-  int chunk_bytes;  // Npad * 64
+  int Npad;         // output width (hidden: multiple of 64; output layer: rounded up to 32)
+  int nchunks;      // ceil(Kp / 64) weight chunks of [Npad][64]
+  int half_bytes;   // one CTA's half of a chunk: Npad / 2 rows x 128 B
   int bias_off;     // offset into the concatenated bias vector
   int act;          // activation after this layer (-1: linear output layer)
   uint32_t idesc;
-  long long wofs;   // byte offset of chunk 0 in the packed weight stream
+  int row0;         // first row of chunk 0 in the [rows][64] weight tensor
 };
 
 struct TcParams {
+  CUtensorMap tmap[kMaxTcLayers];  // per layer: box of [Npad / 2][64], 128B swizzle
   TcLayer layers[kMaxTcLayers];
   int n_gen, n_total;
-  const uint8_t* wstream;
   const float* bias_all;
   int bias_total;  // floats, multiple of 4
   const float* particles;
   const float* actions;
   int N, K, H;
-  long long rows, pairs;
+  long long rows, super_pairs;
   double gamma;
   uint32_t key0, key1, planner;
   int reward_kind, goal_dims;
@@ -176,7 +184,8 @@ __device__ __forceinline__ void write_rew_input(uint8_t* A, int r, const float* 
 }
 
 template <int DS, int DA, int DW>
-__global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_constant__ TcParams p) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
+    rollout_tc_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* Abuf[2] = {smem, smem + kABytes};
@@ -192,14 +201,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = ptx::cluster_ctarank();  // 0: issues the pair MMAs
+  const long long cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      ptx::mbar_init(ptx::smem_u32(&full[s]), 1);
-      ptx::mbar_init(ptx::smem_u32(&empty[s]), 1);
+      ptx::mbar_init(ptx::smem_u32(&full[s]), 1);   // even CTA's expect_tx; both CTAs' bytes
+      ptx::mbar_init(ptx::smem_u32(&empty[s]), 1);  // one multicast commit
     }
     for (int g = 0; g < 2; ++g) {
       ptx::mbar_init(ptx::smem_u32(&accf[g]), 1);
-      ptx::mbar_init(ptx::smem_u32(&ready[g]), kEpiWarpsPerTile);  // one arrival per epilogue warp
+      ptx::mbar_init(ptx::smem_u32(&ready[g]), 2 * kEpiWarpsPerTile);  // every epilogue warp of both CTAs
     }
     ptx::mbar_init(ptx::smem_u32(drain), 1);
     *abort_flag = 0;
@@ -207,11 +218,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
   }
   for (int i = threadIdx.x; i < p.bias_total; i += blockDim.x) bias_s[i] = p.bias_all[i];
   if (warp == 1) {
-    ptx::tmem_alloc(ptx::smem_u32(tmem_holder), 512);
-    ptx::tmem_relinquish();
+    ptx::tmem_alloc_pair(ptx::smem_u32(tmem_holder), 512);
+    ptx::tmem_relinquish_pair();
   }
   ptx::tc_fence_before();
   __syncthreads();
+  ptx::cluster_sync();  // barriers of both CTAs initialised before any remote arrive
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
   const uint32_t ring_addr = ptx::smem_u32(ring);
@@ -219,11 +231,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
+      for (int l = 0; l < p.n_total; ++l) ptx::prefetch_tmap(&p.tmap[l]);
       long long it = 0;
       bool ok = true;
       int last_round[kStages];
       for (int s = 0; s < kStages; ++s) last_round[s] = -1;
-      for (long long pr = blockIdx.x; pr < p.pairs && ok; pr += gridDim.x)
+      for (long long sp = cl; sp < p.super_pairs && ok; sp += ncl)
         for (int t = 0; t < p.H && ok; ++t)
           for (int l = 0; l < p.n_total && ok; ++l)
             for (int g = 0; g < 2 && ok; ++g) {
@@ -235,69 +248,103 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
                   ok = false;
                   break;
                 }
-                ptx::mbar_arrive_expect_tx(ptx::smem_u32(&full[slot]), (uint32_t)L.chunk_bytes);
-                ptx::bulk_g2s(ring_addr + slot * kSlotBytes, p.wstream + L.wofs + (long long)c * L.chunk_bytes,
-                              (uint32_t)L.chunk_bytes, ptx::smem_u32(&full[slot]));
+                const uint32_t full_local = ptx::smem_u32(&full[slot]);
+                if (rank == 0) ptx::mbar_arrive_expect_tx(full_local, (uint32_t)(2 * L.half_bytes));
+                ptx::tma_load_2d_pair(ring_addr + slot * kSlotBytes, &p.tmap[l], 0,
+                                      L.row0 + c * L.Npad + (int)rank * (L.Npad >> 1),
+                                      ptx::mapa_shared(full_local, 0));
                 last_round[slot] = (int)round;
               }
             }
-      if (!ok) {  // drain copies still in flight before the CTA's shared memory goes away
+      if (!ok && rank == 0) {  // drain loads still in flight before shared memory goes away
         for (int s = 0; s < kStages; ++s)
           if (last_round[s] >= 0) {
             const long long t0 = clock64();
-            while (!ptx::mbar_try_wait(ptx::smem_u32(&full[s]), (uint32_t)last_round[s] & 1) &&
+            while (!ptx::mbar_try_wait_cluster(ptx::smem_u32(&full[s]), (uint32_t)last_round[s] & 1) &&
                    clock64() - t0 < kSpinLimit) {
             }
           }
       }
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
+    // ------------------------------------------------------------ MMA issuer (even CTA)
     if (lane == 0) {
-      long long it = 0;
-      uint32_t nready0 = 0, nready1 = 0;
-      bool ok = true;
-      const uint32_t a_addr0 = ptx::smem_u32(Abuf[0]), a_addr1 = ptx::smem_u32(Abuf[1]);
-      for (long long pr = blockIdx.x; pr < p.pairs && ok; pr += gridDim.x)
-        for (int t = 0; t < p.H && ok; ++t)
-          for (int l = 0; l < p.n_total && ok; ++l)
-            for (int g = 0; g < 2 && ok; ++g) {
-              // tile g's A operand for layer l is ready and its accumulator is free
-              const uint32_t nr = g ? nready1 : nready0;
-              if (!bounded_wait(ptx::smem_u32(&ready[g]), nr & 1, abort_flag, p.hdr, 21 + g)) {
-                ok = false;
-                break;
-              }
-              if (g) ++nready1;
-              else ++nready0;
-              ptx::tc_fence_after();
-              const TcLayer& L = p.layers[l];
-              const uint32_t a_addr = g ? a_addr1 : a_addr0;
-              for (int c = 0; c < L.nchunks; ++c, ++it) {
-                const int slot = (int)(it % kStages);
-                const uint32_t round = (uint32_t)(it / kStages);
-                if (!bounded_wait(ptx::smem_u32(&full[slot]), round & 1, abort_flag, p.hdr, 20)) {
+      if (rank == 0) {
+        long long it = 0;
+        uint32_t nready0 = 0, nready1 = 0;
+        bool ok = true;
+        // Descriptors are built once; per chunk and K step only the start
+        // address field (bits 0-13, address >> 4) moves. The issuing thread
+        // shares its scheduler with epilogue warps, so its loop is kept short.
+        const uint64_t adesc0 = ptx::smem_desc(ptx::smem_u32(Abuf[0]), 1024, ptx::kSwizzle128B);
+        const uint64_t adesc1 = ptx::smem_desc(ptx::smem_u32(Abuf[1]), 1024, ptx::kSwizzle128B);
+        const uint64_t bdesc0 = ptx::smem_desc(ring_addr, 1024, ptx::kSwizzle128B);
+        for (long long sp = cl; sp < p.super_pairs && ok; sp += ncl)
+          for (int t = 0; t < p.H && ok; ++t)
+            for (int l = 0; l < p.n_total && ok; ++l) {
+              const int nch = p.layers[l].nchunks, ksteps = p.layers[l].Kp >> 4;
+              const uint32_t idesc = p.layers[l].idesc;
+              for (int g = 0; g < 2 && ok; ++g) {
+                // both CTAs' A operands of tile g are written and their accumulators read
+                const uint32_t nr = g ? nready1 : nready0;
+                const uint32_t rb = ptx::smem_u32(&ready[g]);
+                bool got = ptx::mbar_try_wait_cluster(rb, nr & 1);
+                if (!got) {
+                  const long long t0 = clock64();
+                  while (!(got = ptx::mbar_try_wait_cluster(rb, nr & 1))) {
+                    if (*abort_flag) break;
+                    if (clock64() - t0 > kSpinLimit) {
+                      *abort_flag = 1;
+                      set_status(p.hdr, VOILA_ERR_TIMEOUT, 21 + g);
+                      break;
+                    }
+                  }
+                }
+                if (!got) {
                   ok = false;
                   break;
                 }
+                if (g) ++nready1;
+                else ++nready0;
                 ptx::tc_fence_after();
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                  const int kidx = 32 * c + 16 * kk;
-                  if (kidx < L.Kp) {
-                    const uint64_t ad = ptx::smem_desc(a_addr + (kidx >> 6) * (128 * 128) + (kidx & 63) * 2,
-                                                       1024, ptx::kSwizzle128B);
-                    const uint64_t bd = ptx::smem_desc(ring_addr + slot * kSlotBytes + kk * 32, 512,
-                                                       ptx::kSwizzle64B);
-                    ptx::mma_bf16(tmem_base + g * 256, ad, bd, L.idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                const uint64_t ad_tile = g ? adesc1 : adesc0;
+                const uint32_t d_tmem = tmem_base + g * 256;
+                for (int c = 0; c < nch; ++c, ++it) {
+                  const int slot = (int)(it % kStages);
+                  const uint32_t round = (uint32_t)(it / kStages);
+                  const uint32_t fb = ptx::smem_u32(&full[slot]);
+                  bool landed = ptx::mbar_try_wait_cluster(fb, round & 1);
+                  if (!landed) {
+                    const long long t0 = clock64();
+                    while (!(landed = ptx::mbar_try_wait_cluster(fb, round & 1))) {
+                      if (*abort_flag) break;
+                      if (clock64() - t0 > kSpinLimit) {
+                        *abort_flag = 1;
+                        set_status(p.hdr, VOILA_ERR_TIMEOUT, 20);
+                        break;
+                      }
+                    }
                   }
+                  if (!landed) {
+                    ok = false;
+                    break;
+                  }
+                  ptx::tc_fence_after();
+                  // chunk c = K columns [64c, 64c + 64): A slab c, B slot; K step kk is +32 bytes
+                  const uint64_t ad = ad_tile + (uint64_t)(c * ((128 * 128) >> 4));
+                  const uint64_t bd = bdesc0 + (uint64_t)(slot * (kSlotBytes >> 4));
+                  const int ks = ksteps - 4 * c < 4 ? ksteps - 4 * c : 4;
+#pragma unroll
+                  for (int kk = 0; kk < 4; ++kk)
+                    if (kk < ks) ptx::mma_bf16_pair(d_tmem, ad + 2 * kk, bd + 2 * kk, idesc, (c | kk) ? 1u : 0u);
+                  ptx::mma_commit_pair(ptx::smem_u32(&empty[slot]), 0x3);
+                  if (c == nch - 1) ptx::mma_commit_pair(ptx::smem_u32(&accf[g]), 0x3);
                 }
-                ptx::mma_commit(ptx::smem_u32(&empty[slot]));
-                if (c == L.nchunks - 1) ptx::mma_commit(ptx::smem_u32(&accf[g]));
               }
             }
-      // wait for every MMA this thread issued (normal exit and abort alike)
-      ptx::mma_commit(ptx::smem_u32(drain));
+        // every MMA issued so far has completed once both CTAs' drain barriers arrive
+        ptx::mma_commit_pair(ptx::smem_u32(drain), 0x3);
+      }
       const long long t0 = clock64();
       while (!ptx::mbar_try_wait(ptx::smem_u32(drain), 0) && clock64() - t0 < kSpinLimit) {
       }
@@ -314,12 +361,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
     const int r = 32 * q + lane;            // row within the tile
     uint8_t* A = Abuf[g];
     const uint32_t tm = tmem_base + (uint32_t)(g * 256) + ((uint32_t)(32 * q) << 16);
-    const uint32_t ready_bar = ptx::smem_u32(&ready[g]);
+    const uint32_t ready_remote = ptx::mapa_shared(ptx::smem_u32(&ready[g]), 0);  // the even CTA's barrier
     const uint32_t acc_bar = ptx::smem_u32(&accf[g]);
     uint32_t nacc = 0;
     bool ok = true;
-    for (long long pr = blockIdx.x; pr < p.pairs && ok; pr += gridDim.x) {
-      const long long row = pr * (2 * kTileRows) + g * kTileRows + r;
+    for (long long sp = cl; sp < p.super_pairs && ok; sp += ncl) {
+      const long long row = sp * (4 * kTileRows) + g * (2 * kTileRows) + (long long)rank * kTileRows + r;
       const bool valid = row < p.rows;
       const uint32_t n = valid ? (uint32_t)(row % p.N) : 0u;
       const uint32_t k = valid ? (uint32_t)(row / p.N) : 0u;
@@ -334,7 +381,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
       }
       ptx::fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(ready_bar);
+      if (lane == 0) ptx::mbar_arrive_cluster(ready_remote);
       double Gacc = 0.0, disc = 1.0;
       for (int t = 0; t < p.H && ok; ++t) {
         for (int l = 0; l < p.n_total; ++l) {
@@ -401,7 +448,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
           if (arrive) {
             ptx::fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(ready_bar);
+            if (lane == 0) ptx::mbar_arrive_cluster(ready_remote);
           }
         }
       }
@@ -411,57 +458,52 @@ __global__ void __launch_bounds__(kTcThreads, 1) rollout_tc_kernel(const __grid_
 
   ptx::tc_fence_before();
   __syncthreads();
+  ptx::cluster_sync();  // neither CTA leaves while the pair may still touch its memory
   ptx::tc_fence_after();
-  if (warp == 1) ptx::tmem_dealloc(tmem_base, 512);
+  if (warp == 1) ptx::tmem_dealloc_pair(tmem_base, 512);
 }
 
-// One launch packs every layer: W[l] ([N][K] BF16 row-major) becomes chunks
-// of [Npad][32] with the 64B swizzle (16-byte chunk j of row n lands at
-// j ^ ((n >> 1) & 3)), zero padded; biases are copied zero padded.
+// One launch packs every layer into the [rows][64] BF16 weight tensor that
+// the TMA reads: chunk c of layer l is rows row0 + c * Npad + n holding
+// W[n][64c .. 64c + 63], zero padded; SiLU layers are scaled by 1/2 (exact).
+// Biases are copied (scaled alike) and zero padded.
 struct PackTable {
   const __nv_bfloat16* W[kMaxTcLayers];
   const float* b[kMaxTcLayers];
   int N[kMaxTcLayers], K[kMaxTcLayers], Npad[kMaxTcLayers], nchunks[kMaxTcLayers];
-  long long wofs[kMaxTcLayers], welems_end[kMaxTcLayers];
-  int bias_off[kMaxTcLayers];
+  int row0[kMaxTcLayers], bias_off[kMaxTcLayers];
+  long long elems_end[kMaxTcLayers];
   int half[kMaxTcLayers];  // 1: SiLU layer, pack W and b scaled by 1/2
   int n;
-  uint8_t* wout;
+  __nv_bfloat16* wout;
   float* bout;
 };
 
 __global__ void pack_kernel(const __grid_constant__ PackTable t) {
-  const long long total = t.welems_end[t.n - 1];
+  const long long total = t.elems_end[t.n - 1];
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     int l = 0;
-    while (e >= t.welems_end[l]) ++l;
-    const long long e0 = e - (l ? t.welems_end[l - 1] : 0);
+    while (e >= t.elems_end[l]) ++l;
+    const long long e0 = e - (l ? t.elems_end[l - 1] : 0);
     const int Npad = t.Npad[l];
-    const int c = (int)(e0 / (Npad * 32));
-    const int rem = (int)(e0 % (Npad * 32));
-    const int nrow = rem / 32, kk = rem % 32;
-    const int kg = 32 * c + kk;
+    const int c = (int)(e0 / (Npad * 64));
+    const int rem = (int)(e0 % (Npad * 64));
+    const int nrow = rem / 64, kk = rem % 64;
+    const int kg = 64 * c + kk;
     __nv_bfloat16 v =
         (nrow < t.N[l] && kg < t.K[l]) ? t.W[l][(size_t)nrow * t.K[l] + kg] : __float2bfloat16(0.0f);
-    if (t.half[l]) v = __hmul(v, __float2bfloat16(0.5f));  // exact: power-of-two scaling
-    const int j = kk >> 3;
-    const size_t byte =
-        (size_t)t.wofs[l] + (size_t)c * Npad * 64 + (size_t)nrow * 64 + (((j ^ ((nrow >> 1) & 3)) << 4)) + (kk & 7) * 2;
-    *reinterpret_cast<__nv_bfloat16*>(t.wout + byte) = v;
-    if (c == 0 && kk == 0) {
-      const int np4 = (Npad + 3) / 4 * 4;
-      if (nrow < np4)
-        t.bout[t.bias_off[l] + nrow] = nrow < t.N[l] ? (t.half[l] ? 0.5f : 1.0f) * t.b[l][nrow] : 0.0f;
-      if (nrow == Npad - 1)
-        for (int i = Npad; i < np4; ++i) t.bout[t.bias_off[l] + i] = 0.0f;
-    }
+    if (t.half[l]) v = __hmul(v, __float2bfloat16(0.5f));
+    t.wout[((size_t)t.row0[l] + (size_t)c * Npad + nrow) * 64 + kk] = v;
+    if (c == 0 && kk == 0)
+      t.bout[t.bias_off[l] + nrow] = nrow < t.N[l] ? (t.half[l] ? 0.5f : 1.0f) * t.b[l][nrow] : 0.0f;
   }
 }
 
 struct Plan {
   TcParams p;
   PackTable pack;
+  int total_rows;
   size_t wbytes, bias_bytes, total;
   bool ok;
 };
@@ -473,8 +515,8 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
   memset(&pl, 0, sizeof(pl));
   pl.ok = false;
   const voila_mlp* mlps[2] = {g, R && R->kind == VOILA_REWARD_MLP ? R->mlp : nullptr};
-  int nl = 0, boff = 0;
-  long long wofs = 0, welems = 0;
+  int nl = 0, boff = 0, rows = 0;
+  long long elems = 0;
   for (int m = 0; m < 2; ++m) {
     const voila_mlp* M = mlps[m];
     if (!M) continue;
@@ -489,13 +531,13 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
       if (last && N > 32) return pl;
       TcLayer& L = pl.p.layers[nl];
       L.Kp = round_up(K, 16);
-      L.Npad = last ? round_up(N, 16) : N;
-      L.nchunks = (L.Kp + 31) / 32;
-      L.chunk_bytes = L.Npad * 64;
+      L.Npad = last ? 32 : N;
+      L.nchunks = (L.Kp + 63) / 64;
+      L.half_bytes = (L.Npad / 2) * 128;
       L.bias_off = boff;
       L.act = last ? -1 : M->act;
-      L.idesc = ptx::idesc_bf16(128, L.Npad);
-      L.wofs = wofs;
+      L.idesc = ptx::idesc_bf16(256, L.Npad);
+      L.row0 = rows;
       PackTable& T = pl.pack;
       T.W[nl] = (const __nv_bfloat16*)M->W[l];
       T.b[nl] = M->b[l];
@@ -503,13 +545,13 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
       T.K[nl] = K;
       T.Npad[nl] = L.Npad;
       T.nchunks[nl] = L.nchunks;
-      T.wofs[nl] = wofs;
+      T.row0[nl] = rows;
       T.bias_off[nl] = boff;
       T.half[nl] = (!last && M->act == VOILA_ACT_SILU) ? 1 : 0;
-      welems += (long long)L.nchunks * L.Npad * 32;
-      T.welems_end[nl] = welems;
-      wofs += (long long)L.nchunks * L.chunk_bytes;
-      boff += round_up(L.Npad, 4);
+      elems += (long long)L.nchunks * L.Npad * 64;
+      T.elems_end[nl] = elems;
+      rows += L.nchunks * L.Npad;
+      boff += L.Npad;  // multiple of 32
       ++nl;
     }
     if (m == 0) pl.p.n_gen = nl;
@@ -517,9 +559,10 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
   pl.p.n_total = nl;
   pl.pack.n = nl;
   pl.p.bias_total = boff;
-  pl.wbytes = (size_t)wofs;
+  pl.total_rows = rows;
+  pl.wbytes = (size_t)rows * 128;
   pl.bias_bytes = (size_t)boff * sizeof(float);
-  pl.total = (pl.wbytes + 255) / 256 * 256 + (pl.bias_bytes + 255) / 256 * 256;
+  pl.total = (pl.wbytes + 1023) / 1024 * 1024 + (pl.bias_bytes + 255) / 256 * 256;
   pl.ok = true;
   return pl;
 }
@@ -528,12 +571,31 @@ size_t tc_smem_bytes(int bias_total) {
   return 1024 + 2 * kABytes + kStages * kSlotBytes + (size_t)bias_total * 4 + (2 * kStages + 5) * 8 + 16;
 }
 
+// Launches one persistent CTA pair per co-resident cluster slot (at most
+// `max_clusters`, never more than there are super-pairs).
 template <int DS, int DA, int DW>
-cudaError_t launch_tc(const TcParams& p, size_t smem, int grid, cudaStream_t s) {
+cudaError_t launch_tc(const TcParams& p, size_t smem, long long max_clusters, cudaStream_t s) {
   auto k = rollout_tc_kernel<DS, DA, DW>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<grid, kTcThreads, smem, s>>>(p);
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)(2 * max_clusters));
+  cfg.blockDim = dim3(kTcThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = 2;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int active = 0;
+  e = cudaOccupancyMaxActiveClusters(&active, k, &cfg);
+  if (e != cudaSuccess) return e;
+  if (active < 1) return cudaErrorInvalidConfiguration;
+  long long ncl = max_clusters < active ? max_clusters : active;
+  k<<<(unsigned)(2 * ncl), kTcThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -555,19 +617,31 @@ voila_status tc_rollout(const voila_mlp* g_T, const voila_reward* R, const Rollo
     return cudaMemsetAsync(a.G, 0, (size_t)a.N * a.K * sizeof(double), s) == cudaSuccess ? VOILA_OK
                                                                                        : VOILA_ERR_CUDA;
   }
-  uint8_t* wst = (uint8_t*)scratch;
-  float* bias_all = (float*)(wst + (pl.wbytes + 255) / 256 * 256);
+  if ((uintptr_t)scratch % 16) return VOILA_ERR_WORKSPACE;  // TMA global base alignment
+  __nv_bfloat16* wst = (__nv_bfloat16*)scratch;
+  float* bias_all = (float*)((uint8_t*)scratch + (pl.wbytes + 1023) / 1024 * 1024);
   pl.pack.wout = wst;
   pl.pack.bout = bias_all;
   {
-    const long long total = pl.pack.welems_end[pl.pack.n - 1];
+    const long long total = pl.pack.elems_end[pl.pack.n - 1];
     long long blocks = (total + 255) / 256;
     if (blocks > 148 * 8) blocks = 148 * 8;
     pack_kernel<<<(int)blocks, 256, 0, s>>>(pl.pack);
     if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   }
   TcParams& p = pl.p;
-  p.wstream = wst;
+  // one tensor map per layer over the [rows][64] BF16 weight tensor
+  for (int l = 0; l < p.n_total; ++l) {
+    const cuuint64_t gdim[2] = {64, (cuuint64_t)pl.total_rows};
+    const cuuint64_t gstride[1] = {128};
+    const cuuint32_t box[2] = {64, (cuuint32_t)(p.layers[l].Npad / 2)};
+    const cuuint32_t estride[2] = {1, 1};
+    if (cuTensorMapEncodeTiled(&p.tmap[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)wst, gdim, gstride, box,
+                               estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return VOILA_ERR_CUDA;
+  }
   p.bias_all = bias_all;
   p.particles = a.particles;
   p.actions = a.actions;
@@ -575,7 +649,7 @@ voila_status tc_rollout(const voila_mlp* g_T, const voila_reward* R, const Rollo
   p.K = a.K;
   p.H = a.H;
   p.rows = (long long)a.N * a.K;
-  p.pairs = (p.rows + 2 * kTileRows - 1) / (2 * kTileRows);
+  p.super_pairs = (p.rows + 4 * kTileRows - 1) / (4 * kTileRows);
   p.gamma = a.gamma;
   p.key0 = a.key0;
   p.key1 = a.key1;
@@ -588,9 +662,9 @@ voila_status tc_rollout(const voila_mlp* g_T, const voila_reward* R, const Rollo
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = (int)(p.pairs < nsm ? p.pairs : nsm);
+  const long long nclusters = p.super_pairs < nsm / 2 ? p.super_pairs : nsm / 2;
   const size_t smem = tc_smem_bytes(p.bias_total);
-  cudaError_t e = dims_a ? launch_tc<8, 2, 8>(p, smem, grid, s) : launch_tc<12, 3, 16>(p, smem, grid, s);
+  cudaError_t e = dims_a ? launch_tc<8, 2, 8>(p, smem, nclusters, s) : launch_tc<12, 3, 16>(p, smem, nclusters, s);
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
 
