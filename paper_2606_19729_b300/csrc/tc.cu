@@ -590,10 +590,18 @@ cudaError_t launch_tc(const TcParams& p, size_t smem, long long max_clusters, cu
   attr.val.clusterDim.z = 1;
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
-  int active = 0;
-  e = cudaOccupancyMaxActiveClusters(&active, k, &cfg);
+  // co-resident cluster slots: queried once per device and instantiation
+  static int cached[64] = {};
+  int dev = 0;
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (active < 1) return cudaErrorInvalidConfiguration;
+  int active = (dev >= 0 && dev < 64) ? cached[dev] : 0;
+  if (active == 0) {
+    e = cudaOccupancyMaxActiveClusters(&active, k, &cfg);
+    if (e != cudaSuccess) return e;
+    if (active < 1) return cudaErrorInvalidConfiguration;
+    if (dev >= 0 && dev < 64) cached[dev] = active;
+  }
   long long ncl = max_clusters < active ? max_clusters : active;
   k<<<(unsigned)(2 * ncl), kTcThreads, smem, s>>>(p);
   return cudaGetLastError();
