@@ -54,8 +54,10 @@ constexpr long long kSpinLimit = 4000000000LL;  // ~2 s of SM clock per wait
 struct TcLayer {
   int Kp;           // input width rounded up to 16 (MMA K steps of 16)
   int Npad;         // output width (hidden: multiple of 64; output layer: rounded up to 32)
-  int nchunks;      // ceil(Kp / 64) weight chunks of [Npad][64]
-  int half_bytes;   // one CTA's half of a chunk: Npad / 2 rows x 128 B
+  int nslabs;       // ceil(Kp / 64) K-slabs of [Npad][64]
+  int slab_bytes;   // one CTA's half of a slab: Npad / 2 rows x 128 B
+  int spc;          // slabs per ring chunk (several for narrow layers)
+  int nchunks;      // ceil(nslabs / spc)
   int bias_off;     // offset into the concatenated bias vector
   int act;          // activation after this layer (-1: linear output layer)
   uint32_t idesc;
@@ -232,7 +234,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       for (int l = 0; l < p.n_total; ++l) ptx::prefetch_tmap(&p.tmap[l]);
-      long long it = 0;
+      int slot = 0;
+      uint32_t phase = 0;  // parity of the ring round of `slot`
       bool ok = true;
       int last_round[kStages];
       for (int s = 0; s < kStages; ++s) last_round[s] = -1;
@@ -241,19 +244,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           for (int l = 0; l < p.n_total && ok; ++l)
             for (int g = 0; g < 2 && ok; ++g) {
               const TcLayer& L = p.layers[l];
-              for (int c = 0; c < L.nchunks; ++c, ++it) {
-                const int slot = (int)(it % kStages);
-                const uint32_t round = (uint32_t)(it / kStages);
-                if (!bounded_wait(ptx::smem_u32(&empty[slot]), (round & 1) ^ 1, abort_flag, p.hdr, 10)) {
+              for (int c = 0; c < L.nchunks; ++c) {
+                if (!bounded_wait(ptx::smem_u32(&empty[slot]), phase ^ 1, abort_flag, p.hdr, 10)) {
                   ok = false;
                   break;
                 }
                 const uint32_t full_local = ptx::smem_u32(&full[slot]);
-                if (rank == 0) ptx::mbar_arrive_expect_tx(full_local, (uint32_t)(2 * L.half_bytes));
-                ptx::tma_load_2d_pair(ring_addr + slot * kSlotBytes, &p.tmap[l], 0,
-                                      L.row0 + c * L.Npad + (int)rank * (L.Npad >> 1),
-                                      ptx::mapa_shared(full_local, 0));
-                last_round[slot] = (int)round;
+                const int s0 = c * L.spc;
+                const int ns = L.nslabs - s0 < L.spc ? L.nslabs - s0 : L.spc;
+                if (rank == 0) ptx::mbar_arrive_expect_tx(full_local, (uint32_t)(2 * ns * L.slab_bytes));
+                const uint32_t full_leader = ptx::mapa_shared(full_local, 0);
+                for (int j = 0; j < ns; ++j)
+                  ptx::tma_load_2d_pair(ring_addr + slot * kSlotBytes + j * L.slab_bytes, &p.tmap[l], 0,
+                                        L.row0 + (s0 + j) * L.Npad + (int)rank * (L.Npad >> 1), full_leader);
+                last_round[slot] = (int)phase;
+                if (++slot == kStages) {
+                  slot = 0;
+                  phase ^= 1;
+                }
               }
             }
       if (!ok && rank == 0) {  // drain loads still in flight before shared memory goes away
@@ -270,7 +278,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     // ------------------------------------------------------------ MMA issuer (even CTA)
     if (lane == 0) {
       if (rank == 0) {
-        long long it = 0;
+        int slot = 0;
+        uint32_t phase = 0;  // parity of the ring round of `slot`
         uint32_t nready0 = 0, nready1 = 0;
         bool ok = true;
         // Descriptors are built once; per chunk and K step only the start
@@ -283,6 +292,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           for (int t = 0; t < p.H && ok; ++t)
             for (int l = 0; l < p.n_total && ok; ++l) {
               const int nch = p.layers[l].nchunks, ksteps = p.layers[l].Kp >> 4;
+              const int kpc = 4 * p.layers[l].spc;  // K steps per chunk
+              const uint32_t slab16 = (uint32_t)p.layers[l].slab_bytes >> 4;
               const uint32_t idesc = p.layers[l].idesc;
               for (int g = 0; g < 2 && ok; ++g) {
                 // both CTAs' A operands of tile g are written and their accumulators read
@@ -308,15 +319,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 else ++nready0;
                 ptx::tc_fence_after();
                 const uint64_t ad_tile = g ? adesc1 : adesc0;
+                const uint32_t ad_lo = (uint32_t)ad_tile, ad_hi = (uint32_t)(ad_tile >> 32);
+                const uint32_t bd_lo = (uint32_t)bdesc0, bd_hi = (uint32_t)(bdesc0 >> 32);
                 const uint32_t d_tmem = tmem_base + g * 256;
-                for (int c = 0; c < nch; ++c, ++it) {
-                  const int slot = (int)(it % kStages);
-                  const uint32_t round = (uint32_t)(it / kStages);
+                for (int c = 0; c < nch; ++c) {
+                  // the TMA transaction count on this CTA's barrier covers both halves
                   const uint32_t fb = ptx::smem_u32(&full[slot]);
-                  bool landed = ptx::mbar_try_wait_cluster(fb, round & 1);
+                  bool landed = ptx::mbar_try_wait(fb, phase);
                   if (!landed) {
                     const long long t0 = clock64();
-                    while (!(landed = ptx::mbar_try_wait_cluster(fb, round & 1))) {
+                    while (!(landed = ptx::mbar_try_wait(fb, phase))) {
                       if (*abort_flag) break;
                       if (clock64() - t0 > kSpinLimit) {
                         *abort_flag = 1;
@@ -329,16 +341,31 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                     ok = false;
                     break;
                   }
-                  ptx::tc_fence_after();
-                  // chunk c = K columns [64c, 64c + 64): A slab c, B slot; K step kk is +32 bytes
-                  const uint64_t ad = ad_tile + (uint64_t)(c * ((128 * 128) >> 4));
-                  const uint64_t bd = bdesc0 + (uint64_t)(slot * (kSlotBytes >> 4));
-                  const int ks = ksteps - 4 * c < 4 ? ksteps - 4 * c : 4;
+                  // chunk c = K steps [kpc c, kpc c + kpc): K step j sits in A slab j / 4 and in B
+                  // slab (j mod kpc) / 4 of the slot; each K step is +32 bytes (+2 in the
+                  // descriptor's address field) inside a slab
+                  const int kb = kpc * c;
+                  const uint32_t a_lo = ad_lo + (uint32_t)(kb >> 2) * 1024u;
+                  const uint32_t b_lo = bd_lo + (uint32_t)slot * (uint32_t)(kSlotBytes >> 4);
+                  const int ks = ksteps - kb < kpc ? ksteps - kb : kpc;
+                  if (kpc == 4) {
 #pragma unroll
-                  for (int kk = 0; kk < 4; ++kk)
-                    if (kk < ks) ptx::mma_bf16_pair(d_tmem, ad + 2 * kk, bd + 2 * kk, idesc, (c | kk) ? 1u : 0u);
+                    for (int kk = 0; kk < 4; ++kk)
+                      if (kk < ks)
+                        ptx::mma_bf16_pair(d_tmem, ptx::desc_with_lo(ad_hi, a_lo + 2 * kk),
+                                           ptx::desc_with_lo(bd_hi, b_lo + 2 * kk), idesc, (c | kk) ? 1u : 0u);
+                  } else {
+                    for (int kk = 0; kk < ks; ++kk)
+                      ptx::mma_bf16_pair(d_tmem, ptx::desc_with_lo(ad_hi, a_lo + (kk >> 2) * 1024u + 2 * (kk & 3)),
+                                         ptx::desc_with_lo(bd_hi, b_lo + (kk >> 2) * slab16 + 2 * (kk & 3)), idesc,
+                                         (c | kk) ? 1u : 0u);
+                  }
                   ptx::mma_commit_pair(ptx::smem_u32(&empty[slot]), 0x3);
                   if (c == nch - 1) ptx::mma_commit_pair(ptx::smem_u32(&accf[g]), 0x3);
+                  if (++slot == kStages) {
+                    slot = 0;
+                    phase ^= 1;
+                  }
                 }
               }
             }
@@ -392,7 +419,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           }
           ++nacc;
           ptx::tc_fence_after();
-          const float* bl = bias_s + L.bias_off;
+          const float* bl = bias_s + L.bias_off;  // shared memory (L1 loads measured slower)
           // no A operand follows the final layer of the final step
           const bool arrive = !(t == p.H - 1 && l == p.n_total - 1);
           if (L.act >= 0) {
@@ -532,8 +559,12 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
       TcLayer& L = pl.p.layers[nl];
       L.Kp = round_up(K, 16);
       L.Npad = last ? 32 : N;
-      L.nchunks = (L.Kp + 63) / 64;
-      L.half_bytes = (L.Npad / 2) * 128;
+      L.nslabs = (L.Kp + 63) / 64;
+      L.slab_bytes = (L.Npad / 2) * 128;
+      L.spc = kSlotBytes / L.slab_bytes;
+      if (L.spc > 4) L.spc = 4;  // at most 16 K steps per chunk
+      if (L.spc > L.nslabs) L.spc = L.nslabs;
+      L.nchunks = (L.nslabs + L.spc - 1) / L.spc;
       L.bias_off = boff;
       L.act = last ? -1 : M->act;
       L.idesc = ptx::idesc_bf16(256, L.Npad);
@@ -544,13 +575,13 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
       T.N[nl] = N;
       T.K[nl] = K;
       T.Npad[nl] = L.Npad;
-      T.nchunks[nl] = L.nchunks;
+      T.nchunks[nl] = L.nslabs;
       T.row0[nl] = rows;
       T.bias_off[nl] = boff;
       T.half[nl] = (!last && M->act == VOILA_ACT_SILU) ? 1 : 0;
-      elems += (long long)L.nchunks * L.Npad * 64;
+      elems += (long long)L.nslabs * L.Npad * 64;
       T.elems_end[nl] = elems;
-      rows += L.nchunks * L.Npad;
+      rows += L.nslabs * L.Npad;
       boff += L.Npad;  // multiple of 32
       ++nl;
     }
