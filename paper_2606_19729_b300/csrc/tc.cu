@@ -299,10 +299,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 // both CTAs' A operands of tile g are written and their accumulators read
                 const uint32_t nr = g ? nready1 : nready0;
                 const uint32_t rb = ptx::smem_u32(&ready[g]);
-                bool got = ptx::mbar_try_wait_cluster(rb, nr & 1);
+                bool got = ptx::mbar_try_wait(rb, nr & 1);
                 if (!got) {
                   const long long t0 = clock64();
-                  while (!(got = ptx::mbar_try_wait_cluster(rb, nr & 1))) {
+                  while (!(got = ptx::mbar_try_wait(rb, nr & 1))) {
                     if (*abort_flag) break;
                     if (clock64() - t0 > kSpinLimit) {
                       *abort_flag = 1;
