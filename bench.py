@@ -333,11 +333,23 @@ def main():
         pass
     fpt = flops_per_transition(wl)
     roll_avg_s = sum(roll_ms) / len(roll_ms) / 1e3
+    traffic = None
+    try:  # ncu DRAM bytes per launch, valid only for the kernel source they were taken on
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", "rollout_tc_mid_bf16_traffic.json")) as f:
+            prof = json.load(f)
+        src = b"".join(open(os.path.join(ROOT, "paper_2606_19729_b300", "csrc", n), "rb").read()
+                       for n in ("tc.cu", "tc_ptx.cuh"))
+        if (hashlib.sha256(src).hexdigest()[:16] == prof["source_sha16"] and wl.name == "mid_bf16"
+                and (wl.N, wl.K, wl.H) == (4096, 1024, 20)):
+            traffic = prof["dram_read_bytes"] + prof["dram_write_bytes"]
+    except (OSError, KeyError, ValueError):
+        traffic = None
     if wl.prec == 1:
         achieved = fpt * trans_per_step / roll_avg_s / 1e12
         peak = peaks.get("bf16_tflops_sustained", 1400.0)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": "rollout_tc_kernel (voila_rollout call: weight pack + rollout + return reduction)",
                 "peak_source": "measured bf16 sustained (MEASURED_PEAKS.json)" if peaks else "fallback"}
     else:
