@@ -42,6 +42,7 @@ def parse_args():
     ap.add_argument("--workload", choices=["mid_bf16", "mid_fp32", "small_fp32"], default="mid_bf16")
     ap.add_argument("--cpu-seqs", type=int, default=8, help="action sequences in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp32-seqs", type=int, default=16, help="sequences for the FP32-form comparison (0: skip)")
     ap.add_argument("--N", type=int, default=None, help="override particles (profiling runs)")
     ap.add_argument("--K", type=int, default=None, help="override action sequences (profiling runs)")
     ap.add_argument("--H", type=int, default=None, help="override horizon (profiling runs)")
@@ -152,9 +153,11 @@ def blas_threads() -> int:
     return len(os.sched_getaffinity(0))
 
 
-def cpu_baseline(wl, seqs):
+def cpu_baseline(wl, seqs, particles=None):
     """The FP64 oracle, as it stands, on a bounded sample: one belief update of all
-    N particles plus the rollout of `seqs` sequences x all N particles x H."""
+    N particles plus the rollout of `seqs` sequences x all N particles x H.
+    With `particles` (the device's resampled belief) the rollout starts from
+    them, so its returns are the FP64 reference for the device's J[:seqs]."""
     from oracle import voila_oracle as O
 
     def om(spec):
@@ -165,14 +168,41 @@ def cpu_baseline(wl, seqs):
     t0 = time.perf_counter()
     res = O.belief_update(om(wl.g_T), O.Likelihood(O.LIK_MLP, mlp=om(wl.ell)), wl.particles, wl.actions[0, 0],
                           obs, wl.d_omega, wl.lam, wl.seed, 1)
+    start = res.particles_out if particles is None else particles
     R = O.Reward(O.REWARD_MLP, mlp=om(wl.reward_mlp)) if wl.goal is None else O.Reward(O.REWARD_GOAL, wl.goal)
-    O.rollout(om(wl.g_T), R, res.particles_out, wl.actions, wl.d_omega, wl.gamma, wl.seed, k_index=ks)
+    J, _ = O.rollout(om(wl.g_T), R, start, wl.actions, wl.d_omega, wl.gamma, wl.seed, k_index=ks)
     dt = time.perf_counter() - t0
     cores = blas_threads()
     trans = seqs * wl.N * wl.H
     return {"value": trans / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 numpy oracle: 1 belief update of {wl.N} particles + rollout of {seqs} of {wl.K} "
-                      f"sequences x {wl.N} particles x H={wl.H} ({trans} transitions) in {dt:.2f} s"}
+                      f"sequences x {wl.N} particles x H={wl.H} ({trans} transitions) in {dt:.2f} s"}, J
+
+
+def fp32_form(V, wl, seqs, planner, particles, stream):
+    """The plain FP32 CUDA-core form on the same workload, timed on a slice of
+    `seqs` action sequences (throughput per transition does not depend on K)."""
+    import torch
+    from paper_2606_19729_b300 import workloads as WL
+    g32 = V.DeviceMLP([torch.from_numpy(w) for w in wl.g_T.W], [torch.from_numpy(b) for b in wl.g_T.b],
+                      wl.g_T.act, V.FP32)
+    r32 = V.DeviceMLP([torch.from_numpy(w) for w in wl.reward_mlp.W], [torch.from_numpy(b) for b in wl.reward_mlp.b],
+                      wl.reward_mlp.act, V.FP32)
+    R32 = V.mlp_reward(r32)
+    acts = torch.from_numpy(np.ascontiguousarray(wl.actions[:seqs])).float().cuda()
+    J = torch.empty(seqs, dtype=torch.float64, device="cuda")
+    ws = V.alloc_workspace(V.voila_rollout_workspace_size(g32, R32, wl.N, seqs, wl.H))
+    V.voila_rollout(g32, R32, particles, None, acts, wl.d_omega, wl.gamma, wl.seed, planner, J, None, None, ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = 2
+    for _ in range(reps):
+        V.voila_rollout(g32, R32, particles, None, acts, wl.d_omega, wl.gamma, wl.seed, planner, J, None, None, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / reps
+    return {"value": seqs * wl.N * wl.H / sec, "unit": UNIT, "dtype": "f32",
+            "sample": f"{seqs} of {wl.K} sequences x {wl.N} particles x H={wl.H}, same weights in FP32"}
 
 
 def run_reference(args, rank):
@@ -186,7 +216,7 @@ def run_reference(args, rank):
     t0 = time.perf_counter()
     last = None
     for _ in range(args.steps):
-        last = cpu_baseline(wl, seqs)
+        last, _ = cpu_baseline(wl, seqs)
     dt = time.perf_counter() - t0
     value = args.steps * seqs * wl.N * wl.H / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -371,8 +401,21 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 6 * args.steps,
             "clocks": clk.summary()}
+    if args.fp32_seqs > 0 and wl.prec == 1 and rank == 0:
+        line["forms"] = {"fp32_cuda_cores": fp32_form(V, wl, args.fp32_seqs, planner, p_new, stream)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seqs)
+        # the device's resampled particles and J of this exact step, against FP64
+        V.voila_belief_update(g, lik, particles, None, action, obs, wl.d_omega, wl.lam, wl.seed, 1, planner, p_new,
+                              None, None, None, None, ws_b)
+        V.voila_rollout(g, R, p_new, None, actions, wl.d_omega, wl.gamma, wl.seed, planner, J, None, best, ws_r)
+        torch.cuda.synchronize()
+        cb, Jo = cpu_baseline(wl, args.cpu_seqs, p_new.cpu().double().numpy())
+        line["cpu_baseline"] = cb
+        Jd = J[: args.cpu_seqs].cpu().numpy()
+        line["err_vs_fp64"] = {"J_normwise": float(np.max(np.abs(Jd - Jo)) / np.max(np.abs(Jo))),
+                               "sample": f"J of {args.cpu_seqs} of {wl.K} sequences (all particles) vs the FP64 oracle "
+                                         "from the same resampled particles",
+                               "tolerance": 2e-2 if wl.prec == 1 else 1e-5}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -78,6 +78,7 @@ enum {
 #define VOILA_MAX_LAYERS 8
 #define VOILA_MAX_WIDTH 512
 #define VOILA_MAX_GOAL 4
+#define VOILA_MAX_PLANNERS 64
 
 /*
  * A feed-forward MLP y = L_n(act(... act(L_1(x)))), L_l(h) = h W_l^T + b_l,
@@ -161,6 +162,65 @@ voila_status voila_rollout(const voila_mlp* g_T, const voila_reward* R,
                            int32_t d_omega, double gamma, uint64_t seed, uint32_t planner_id,
                            double* J, double* G, int32_t* best_k,
                            void* workspace, size_t ws_bytes, voila_stream_t stream);
+
+/*
+ * One independent planning problem of a batched rollout: its own belief
+ * (particles, optional weights), action sequences, horizon and noise stream,
+ * sharing the generator and reward of the call. All pointers are device
+ * memory; the array of voila_planner itself is host memory.
+ */
+typedef struct {
+  const float* particles;  /* [N][d_s] */
+  const double* w;         /* [N] or NULL (uniform 1/N) */
+  const float* actions;    /* [K][H][d_a] */
+  int32_t N, K, H;
+  uint32_t planner_id;     /* < 65536, selects the noise stream */
+  double* J;               /* [K], required */
+  double* G;               /* [K][N] or NULL */
+  int32_t* best_k;         /* [1] or NULL */
+} voila_planner;
+
+/* Schedules of voila_rollout_batched: bit 0 = order work by descending
+ * horizon (longest first); bits 8-15 = cap on CTA pairs (0 = all resident). */
+#define VOILA_SCHED_LONGEST_FIRST 1
+#define VOILA_SCHED_CLUSTERS(n) ((n) << 8)
+
+/* Workspace bytes for voila_rollout_batched (host call, no device work). */
+voila_status voila_rollout_batched_workspace_size(const voila_mlp* g_T, const voila_reward* R,
+                                                  const voila_planner* planners, int32_t P,
+                                                  size_t* bytes);
+
+/*
+ * Many independent planners (uneven N, K, H) in one launch: the rollout of
+ * voila_rollout for every planner, with the same generator, reward, gamma and
+ * seed (the planner id separates the noise streams), as one persistent
+ * tensor-core launch over all planners' work plus one reduction launch. The
+ * call issues no host synchronisation and can be captured in a CUDA graph
+ * once voila_rollout_batched (or voila_rollout) has run outside capture on
+ * the device. P <= VOILA_MAX_PLANNERS. BF16 runs batched; FP32 runs the
+ * planners one after another on CUDA cores.
+ * Batched execution of VOPP's many simulations (Sec. 2.2, Sec. 4.3), with the
+ * per-planner semantics of voila_rollout.
+ */
+voila_status voila_rollout_batched(const voila_mlp* g_T, const voila_reward* R,
+                                   const voila_planner* planners, int32_t P, int32_t d_s,
+                                   int32_t d_a, int32_t d_omega, double gamma, uint64_t seed,
+                                   int32_t schedule, void* workspace, size_t ws_bytes,
+                                   voila_stream_t stream);
+
+/*
+ * Autotuner for voila_rollout_batched: runs each candidate schedule (work
+ * order x number of CTA pairs) on these inputs, times it with CUDA events and
+ * writes the fastest to *best_schedule (host int32). Synchronises `stream`;
+ * do not call it during stream capture. Outputs are left as the last
+ * candidate's (all candidates compute the same values).
+ */
+voila_status voila_rollout_batched_autotune(const voila_mlp* g_T, const voila_reward* R,
+                                            const voila_planner* planners, int32_t P,
+                                            int32_t d_s, int32_t d_a, int32_t d_omega,
+                                            double gamma, uint64_t seed, void* workspace,
+                                            size_t ws_bytes, int32_t* best_schedule,
+                                            float* best_ms, voila_stream_t stream);
 
 /* Workspace bytes for voila_belief_update. */
 voila_status voila_belief_update_workspace_size(const voila_mlp* g_T, const voila_likelihood* ell,

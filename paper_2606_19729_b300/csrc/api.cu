@@ -187,6 +187,169 @@ voila_status voila_rollout(const voila_mlp* g_T, const voila_reward* R, const fl
   return cuda_status(launch_reduce_returns(Gbuf, w, N, K, J, best_k, s));
 }
 
+// Batched rollout workspace: [header | tensor-core scratch | G of every planner
+// that has no caller-provided G].
+static size_t batched_layout(const voila_mlp* g_T, const voila_reward* R, const voila_planner* pl, int32_t P,
+                             size_t* g_off /* [P] or NULL */) {
+  size_t off = kHeaderBytes;
+  off = align_up(off, 1024);
+  if (g_T->prec == VOILA_BF16) off = align_up(off + tc_rollout_scratch_bytes(g_T, R));
+  for (int i = 0; i < P; ++i) {
+    if (g_off) g_off[i] = off;
+    if (!pl[i].G) off = align_up(off + (size_t)pl[i].N * pl[i].K * sizeof(double));
+  }
+  return off;
+}
+
+static voila_status check_batched(const voila_mlp* g_T, const voila_reward* R, const voila_planner* pl, int32_t P,
+                                  int32_t d_s, int32_t d_a, int32_t d_omega) {
+  if (!pl || P < 1 || P > VOILA_MAX_PLANNERS) return VOILA_ERR_ARG;
+  for (int i = 0; i < P; ++i) {
+    voila_status st = check_rollout(g_T, R, pl[i].N, d_s, pl[i].K, pl[i].H, d_a, d_omega);
+    if (st != VOILA_OK) return st;
+    if (pl[i].planner_id >= 65536u) return VOILA_ERR_ARG;
+    if ((long long)pl[i].N * pl[i].K > 0 &&
+        (!pl[i].particles || !pl[i].J || (pl[i].H > 0 && d_a > 0 && !pl[i].actions)))
+      return VOILA_ERR_ARG;
+  }
+  return VOILA_OK;
+}
+
+voila_status voila_rollout_batched_workspace_size(const voila_mlp* g_T, const voila_reward* R,
+                                                  const voila_planner* planners, int32_t P, size_t* bytes) {
+  if (!bytes || !valid_mlp(g_T) || !R || !planners || P < 1 || P > VOILA_MAX_PLANNERS) return VOILA_ERR_ARG;
+  for (int i = 0; i < P; ++i)
+    if (planners[i].N < 0 || planners[i].K < 0 || planners[i].H < 0) return VOILA_ERR_ARG;
+  *bytes = batched_layout(g_T, R, planners, P, nullptr);
+  return VOILA_OK;
+}
+
+voila_status voila_rollout_batched(const voila_mlp* g_T, const voila_reward* R, const voila_planner* planners,
+                                   int32_t P, int32_t d_s, int32_t d_a, int32_t d_omega, double gamma,
+                                   uint64_t seed, int32_t schedule, void* workspace, size_t ws_bytes,
+                                   voila_stream_t stream) {
+  voila_status st = check_batched(g_T, R, planners, P, d_s, d_a, d_omega);
+  if (st != VOILA_OK) return st;
+  if (!workspace || ((uintptr_t)workspace % kAlign)) return VOILA_ERR_WORKSPACE;
+  size_t g_off[VOILA_MAX_PLANNERS];
+  if (ws_bytes < batched_layout(g_T, R, planners, P, g_off)) return VOILA_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  if (cudaMemsetAsync(ws, 0, sizeof(WsHeader), s) != cudaSuccess) return VOILA_ERR_CUDA;
+  uint32_t k0, k1;
+  philox_key(seed, k0, k1);
+  double* Gp[VOILA_MAX_PLANNERS];
+  for (int i = 0; i < P; ++i) Gp[i] = planners[i].G ? planners[i].G : (double*)(ws + g_off[i]);
+  if (g_T->prec == VOILA_BF16) {
+    TcProblem probs[VOILA_MAX_PLANNERS];
+    for (int i = 0; i < P; ++i) {
+      probs[i].particles = planners[i].particles;
+      probs[i].actions = planners[i].actions;
+      probs[i].G = Gp[i];
+      probs[i].N = planners[i].N;
+      probs[i].K = planners[i].K;
+      probs[i].H = planners[i].H;
+      probs[i].planner = planners[i].planner_id;
+    }
+    st = tc_rollout_batched(g_T, R, probs, P, d_s, d_a, d_omega, gamma, k0, k1, schedule & 1,
+                            (schedule >> 8) & 0xff, (WsHeader*)ws, ws + align_up(kHeaderBytes, 1024), s);
+    if (st != VOILA_OK) return st;
+  } else {
+    for (int i = 0; i < P; ++i) {
+      const voila_planner& q = planners[i];
+      if ((long long)q.N * q.K == 0) continue;
+      RolloutArgs a;
+      memset(&a, 0, sizeof(a));
+      a.g = to_dev(g_T);
+      a.reward_kind = R->kind;
+      a.goal_dims = R->goal_dims;
+      for (int j = 0; j < VOILA_MAX_GOAL; ++j) a.goal[j] = R->goal[j];
+      if (R->kind == VOILA_REWARD_MLP) a.r = to_dev(R->mlp);
+      a.particles = q.particles;
+      a.actions = q.actions;
+      a.N = q.N;
+      a.K = q.K;
+      a.H = q.H;
+      a.d_s = d_s;
+      a.d_a = d_a;
+      a.d_omega = d_omega;
+      a.gamma = gamma;
+      a.key0 = k0;
+      a.key1 = k1;
+      a.planner = q.planner_id;
+      a.G = Gp[i];
+      int maxw = max_width(g_T);
+      if (R->kind == VOILA_REWARD_MLP && max_width(R->mlp) > maxw) maxw = max_width(R->mlp);
+      a.ld = simt_ld(maxw);
+      if (cudaError_t e = launch_rollout_simt(a, s)) return cuda_status(e);
+    }
+  }
+  BatchedReduceArgs r;
+  memset(&r, 0, sizeof(r));
+  long long kacc = 0;
+  for (int i = 0; i < P; ++i) {
+    const voila_planner& q = planners[i];
+    if ((long long)q.N * q.K == 0) continue;
+    const int j = r.P++;
+    r.G[j] = Gp[i];
+    r.w[j] = q.w;
+    r.J[j] = q.J;
+    r.best[j] = q.best_k;
+    r.N[j] = q.N;
+    r.K[j] = q.K;
+    kacc += q.K;
+    r.k_end[j] = kacc;
+  }
+  if (r.P == 0) return VOILA_OK;
+  return cuda_status(launch_reduce_returns_batched(r, s));
+}
+
+voila_status voila_rollout_batched_autotune(const voila_mlp* g_T, const voila_reward* R,
+                                            const voila_planner* planners, int32_t P, int32_t d_s, int32_t d_a,
+                                            int32_t d_omega, double gamma, uint64_t seed, void* workspace,
+                                            size_t ws_bytes, int32_t* best_schedule, float* best_ms,
+                                            voila_stream_t stream) {
+  if (!best_schedule) return VOILA_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int nsm = 148, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int full = nsm / 2;
+  const int32_t cands[6] = {VOILA_SCHED_LONGEST_FIRST,
+                            0,
+                            VOILA_SCHED_LONGEST_FIRST | VOILA_SCHED_CLUSTERS(full - 2),
+                            VOILA_SCHED_LONGEST_FIRST | VOILA_SCHED_CLUSTERS(full * 7 / 8),
+                            VOILA_SCHED_LONGEST_FIRST | VOILA_SCHED_CLUSTERS(full * 3 / 4),
+                            VOILA_SCHED_CLUSTERS(full * 3 / 4)};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return VOILA_ERR_CUDA;
+  float best = 1e30f;
+  int32_t arg = cands[0];
+  voila_status st = VOILA_OK;
+  for (int c = 0; c < 6 && st == VOILA_OK; ++c) {
+    st = voila_rollout_batched(g_T, R, planners, P, d_s, d_a, d_omega, gamma, seed, cands[c], workspace, ws_bytes,
+                               stream);  // warm-up
+    if (st != VOILA_OK) break;
+    cudaEventRecord(e0, s);
+    st = voila_rollout_batched(g_T, R, planners, P, d_s, d_a, d_omega, gamma, seed, cands[c], workspace, ws_bytes,
+                               stream);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) st = VOILA_ERR_CUDA;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (st == VOILA_OK && ms < best) {
+      best = ms;
+      arg = cands[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != VOILA_OK) return st;
+  *best_schedule = arg;
+  if (best_ms) *best_ms = best;
+  return VOILA_OK;
+}
+
 voila_status voila_belief_update_workspace_size(const voila_mlp* g_T, const voila_likelihood* ell,
                                                 int32_t N, size_t* bytes) {
   if (!bytes || !valid_mlp(g_T) || N < 0) return VOILA_ERR_ARG;

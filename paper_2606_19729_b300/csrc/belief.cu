@@ -213,6 +213,82 @@ __global__ void __launch_bounds__(1024) argmax_kernel(const double* __restrict__
   }
 }
 
+// All planners of a batched rollout in one launch: block b is sequence
+// b - k_start(q) of planner q (fixed summation order, as above).
+__global__ void __launch_bounds__(256) reduce_returns_batched_kernel(const __grid_constant__ BatchedReduceArgs a) {
+  __shared__ double red[33];
+  const long long b = blockIdx.x;
+  int q = 0;
+  while (q < a.P - 1 && b >= a.k_end[q]) ++q;
+  const int k = (int)(b - (q ? a.k_end[q - 1] : 0));
+  const int N = a.N[q];
+  const double invN = 1.0 / (double)N;
+  const double* g = a.G[q] + (size_t)k * N;
+  const double* w = a.w[q];
+  double acc = 0.0;
+  for (int n = threadIdx.x; n < N; n += blockDim.x) acc += g[n] * (w ? w[n] : invN);
+  const double tot = block_sum(acc, red);
+  if (threadIdx.x == 0) a.J[q][k] = tot;
+}
+
+__global__ void __launch_bounds__(1024) argmax_batched_kernel(const __grid_constant__ BatchedReduceArgs a) {
+  const int q = blockIdx.x;
+  if (a.best[q] == nullptr) return;
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  const int K = a.K[q];
+  const double* J = a.J[q];
+  double v = -INFINITY;
+  int i = K;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double x = J[k];
+    if (!isnan(x) && (i == K || x > v)) {
+      v = x;
+      i = k;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) {
+      v = ov;
+      i = oi;
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    bv[wid] = v;
+    bi[wid] = i;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    v = lane < nw ? bv[lane] : -INFINITY;
+    i = lane < nw ? bi[lane] : K;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+      if (ov > v || (ov == v && oi < i)) {
+        v = ov;
+        i = oi;
+      }
+    }
+    if (lane == 0) *a.best[q] = (i < K) ? i : 0;
+  }
+}
+
+cudaError_t launch_reduce_returns_batched(const BatchedReduceArgs& a, cudaStream_t s) {
+  const long long blocks = a.k_end[a.P - 1];
+  if (blocks <= 0) return cudaSuccess;
+  reduce_returns_batched_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  argmax_batched_kernel<<<a.P, 1024, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_returns(const double* G, const double* w, int N, int K, double* J,
                                   int32_t* best_k, cudaStream_t s) {
   reduce_returns_kernel<<<K, 256, 0, s>>>(G, w, N, K, J);

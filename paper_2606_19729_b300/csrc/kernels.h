@@ -9,6 +9,7 @@
 namespace voila {
 
 constexpr int kSimtRows = 32;
+constexpr int kMaxPlanners = VOILA_MAX_PLANNERS;
 constexpr int kSimtThreads = 256;
 
 struct RolloutArgs {
@@ -77,6 +78,18 @@ cudaError_t launch_belief_resample(const ResampleArgs& a, cudaStream_t s);
 cudaError_t launch_mlp_fwd(const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_reduce_returns(const double* G, const double* w, int N, int K, double* J,
                                   int32_t* best_k, cudaStream_t s);
+// Returns of P planners in one launch: J_q[k] = sum_n w_q[n] G_q[k][n], then argmax per planner.
+struct BatchedReduceArgs {
+  const double* G[kMaxPlanners];
+  const double* w[kMaxPlanners];
+  double* J[kMaxPlanners];
+  int32_t* best[kMaxPlanners];
+  int N[kMaxPlanners], K[kMaxPlanners];
+  long long k_end[kMaxPlanners];  // inclusive prefix sum of K
+  int P;
+};
+cudaError_t launch_reduce_returns_batched(const BatchedReduceArgs& a, cudaStream_t s);
+
 cudaError_t launch_philox_fill(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3,
                                uint32_t* out, long long n, cudaStream_t s);
 cudaError_t launch_normal_fill(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2,

@@ -49,6 +49,7 @@ constexpr int kStages = 5;
 constexpr int kSlotBytes = 128 * 128;     // half of a [256][64] BF16 weight chunk
 constexpr int kABytes = 4 * 128 * 128;    // 128 rows x 256 BF16, four 64-wide K slabs
 constexpr int kMaxTcLayers = 16;
+constexpr int kSuperRows = 4 * kTileRows;  // rows of one work item (two tiles on each CTA of the pair)
 constexpr long long kSpinLimit = 4000000000LL;  // ~2 s of SM clock per wait
 
 struct TcLayer {
@@ -64,23 +65,42 @@ struct TcLayer {
   int row0;         // first row of chunk 0 in the [rows][64] weight tensor
 };
 
+// One independent planning problem of a (batched) launch.
+struct TcPlanner {
+  const float* particles;  // [N][d_s]
+  const float* actions;    // [K][H][d_a]
+  double* G;               // [K][N]
+  long long rows;          // N * K
+  int N, H;
+  uint32_t planner;        // noise stream id
+  int pad;
+};
+
 struct TcParams {
   CUtensorMap tmap[kMaxTcLayers];  // per layer: box of [Npad / 2][64], 128B swizzle
   TcLayer layers[kMaxTcLayers];
   int n_gen, n_total;
   const float* bias_all;
   int bias_total;  // floats, multiple of 4
-  const float* particles;
-  const float* actions;
-  int N, K, H;
-  long long rows, super_pairs;
   double gamma;
-  uint32_t key0, key1, planner;
+  uint32_t key0, key1;
   int reward_kind, goal_dims;
   float goal[VOILA_MAX_GOAL];
-  double* G;
   WsHeader* hdr;
+  // Work items are 512-row super-pairs, numbered planner by planner in table
+  // order; cluster c takes items c, c + clusters, ... (with the table sorted
+  // by descending horizon this approximates longest-processing-time first).
+  int P;
+  long long total_items;
+  long long item_end[kMaxPlanners];  // inclusive prefix sum of items per planner
+  TcPlanner pl[kMaxPlanners];
 };
+
+__device__ __forceinline__ int item_planner(const TcParams& p, long long it) {
+  int q = 0;
+  while (q < p.P - 1 && it >= p.item_end[q]) ++q;
+  return q;
+}
 
 __device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                              WsHeader* hdr, int where) {
@@ -239,8 +259,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       bool ok = true;
       int last_round[kStages];
       for (int s = 0; s < kStages; ++s) last_round[s] = -1;
-      for (long long sp = cl; sp < p.super_pairs && ok; sp += ncl)
-        for (int t = 0; t < p.H && ok; ++t)
+      for (long long it = cl; it < p.total_items && ok; it += ncl) {
+        const int H = p.pl[item_planner(p, it)].H;
+        for (int t = 0; t < H && ok; ++t)
           for (int l = 0; l < p.n_total && ok; ++l)
             for (int g = 0; g < 2 && ok; ++g) {
               const TcLayer& L = p.layers[l];
@@ -264,6 +285,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 }
               }
             }
+      }
       if (!ok && rank == 0) {  // drain loads still in flight before shared memory goes away
         for (int s = 0; s < kStages; ++s)
           if (last_round[s] >= 0) {
@@ -288,8 +310,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         const uint64_t adesc0 = ptx::smem_desc(ptx::smem_u32(Abuf[0]), 1024, ptx::kSwizzle128B);
         const uint64_t adesc1 = ptx::smem_desc(ptx::smem_u32(Abuf[1]), 1024, ptx::kSwizzle128B);
         const uint64_t bdesc0 = ptx::smem_desc(ring_addr, 1024, ptx::kSwizzle128B);
-        for (long long sp = cl; sp < p.super_pairs && ok; sp += ncl)
-          for (int t = 0; t < p.H && ok; ++t)
+        for (long long it = cl; it < p.total_items && ok; it += ncl) {
+          const int H = p.pl[item_planner(p, it)].H;
+          for (int t = 0; t < H && ok; ++t)
             for (int l = 0; l < p.n_total && ok; ++l) {
               const int nch = p.layers[l].nchunks, ksteps = p.layers[l].Kp >> 4;
               const int kpc = 4 * p.layers[l].spc;  // K steps per chunk
@@ -369,6 +392,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 }
               }
             }
+        }
         // every MMA issued so far has completed once both CTAs' drain barriers arrive
         ptx::mma_commit_pair(ptx::smem_u32(drain), 0x3);
       }
@@ -392,25 +416,29 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     const uint32_t acc_bar = ptx::smem_u32(&accf[g]);
     uint32_t nacc = 0;
     bool ok = true;
-    for (long long sp = cl; sp < p.super_pairs && ok; sp += ncl) {
-      const long long row = sp * (4 * kTileRows) + g * (2 * kTileRows) + (long long)rank * kTileRows + r;
-      const bool valid = row < p.rows;
-      const uint32_t n = valid ? (uint32_t)(row % p.N) : 0u;
-      const uint32_t k = valid ? (uint32_t)(row / p.N) : 0u;
-      const float* act_row = p.actions + (size_t)k * p.H * DA;
+    for (long long it = cl; it < p.total_items && ok; it += ncl) {
+      const int q = item_planner(p, it);
+      const long long sp = it - (q ? p.item_end[q - 1] : 0);
+      const TcPlanner& PL = p.pl[q];
+      const int H = PL.H;
+      const long long row = sp * kSuperRows + g * (2 * kTileRows) + (long long)rank * kTileRows + r;
+      const bool valid = row < PL.rows;
+      const uint32_t n = valid ? (uint32_t)(row % PL.N) : 0u;
+      const uint32_t k = valid ? (uint32_t)(row / PL.N) : 0u;
+      const float* act_row = PL.actions + (size_t)k * H * DA;
       float s[DS], a[DA];
       if (sub == 0) {
 #pragma unroll
-        for (int i = 0; i < DS; ++i) s[i] = valid ? __ldg(p.particles + (size_t)n * DS + i) : 0.0f;
+        for (int i = 0; i < DS; ++i) s[i] = valid ? __ldg(PL.particles + (size_t)n * DS + i) : 0.0f;
 #pragma unroll
         for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + i);
-        write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, 0, p.planner);
+        write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, 0, PL.planner);
       }
       ptx::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive_cluster(ready_remote);
       double Gacc = 0.0, disc = 1.0;
-      for (int t = 0; t < p.H && ok; ++t) {
+      for (int t = 0; t < H && ok; ++t) {
         for (int l = 0; l < p.n_total; ++l) {
           const TcLayer& L = p.layers[l];
           if (!bounded_wait(acc_bar, nacc & 1, abort_flag, p.hdr, 30 + g)) {
@@ -421,7 +449,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           ptx::tc_fence_after();
           const float* bl = bias_s + L.bias_off;  // shared memory (L1 loads measured slower)
           // no A operand follows the final layer of the final step
-          const bool arrive = !(t == p.H - 1 && l == p.n_total - 1);
+          const bool arrive = !(t == H - 1 && l == p.n_total - 1);
           if (L.act >= 0) {
             // hidden layer: bias + activation -> BF16 A operand of the next layer,
             // 32 columns per TMEM load (measured faster than larger batches)
@@ -450,10 +478,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 }
               Gacc += disc * (double)(-acc);
               disc *= p.gamma;
-              if (t + 1 < p.H) {
+              if (t + 1 < H) {
 #pragma unroll
                 for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + (t + 1) * DA + i);
-                write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), p.planner);
+                write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
               }
             } else {
               write_rew_input<DS, DA>(A, r, s, a);
@@ -465,10 +493,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
             ptx::tmem_wait_ld();
             Gacc += disc * (double)(v[0] + bl[0]);
             disc *= p.gamma;
-            if (t + 1 < p.H) {
+            if (t + 1 < H) {
 #pragma unroll
               for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + (t + 1) * DA + i);
-              write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), p.planner);
+              write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
             }
           }
           ptx::tc_fence_before();
@@ -479,7 +507,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           }
         }
       }
-      if (sub == 0 && valid && ok) p.G[row] = Gacc;
+      if (sub == 0 && valid && ok) PL.G[row] = Gacc;
     }
   }
 
@@ -645,18 +673,54 @@ size_t tc_rollout_scratch_bytes(const voila_mlp* g_T, const voila_reward* R) {
   return pl.ok ? pl.total : 0;
 }
 
-voila_status tc_rollout(const voila_mlp* g_T, const voila_reward* R, const RolloutArgs& a,
-                        WsHeader* hdr, void* scratch, cudaStream_t s) {
+voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, const TcProblem* probs, int P,
+                                int d_s, int d_a, int d_omega, double gamma, uint32_t key0, uint32_t key1,
+                                int order, int max_clusters, WsHeader* hdr, void* scratch, cudaStream_t s) {
   Plan pl = make_plan(g_T, R);
   if (!pl.ok) return VOILA_ERR_UNSUPPORTED;
-  const bool dims_a = a.d_s == 8 && a.d_a == 2 && a.d_omega == 8;
-  const bool dims_b = a.d_s == 12 && a.d_a == 3 && a.d_omega == 16;
+  if (P < 1 || P > kMaxPlanners) return VOILA_ERR_ARG;
+  const bool dims_a = d_s == 8 && d_a == 2 && d_omega == 8;
+  const bool dims_b = d_s == 12 && d_a == 3 && d_omega == 16;
   if (!dims_a && !dims_b) return VOILA_ERR_UNSUPPORTED;
-  if (a.H == 0) {
-    return cudaMemsetAsync(a.G, 0, (size_t)a.N * a.K * sizeof(double), s) == cudaSuccess ? VOILA_OK
-                                                                                       : VOILA_ERR_CUDA;
-  }
   if ((uintptr_t)scratch % 16) return VOILA_ERR_WORKSPACE;  // TMA global base alignment
+  TcParams& p = pl.p;
+  // work table: planners with rows and steps, optionally longest horizon first
+  int idx[kMaxPlanners];
+  int nq = 0;
+  for (int i = 0; i < P; ++i) {
+    const TcProblem& q = probs[i];
+    if ((long long)q.N * q.K == 0) continue;
+    if (q.H == 0) {  // no steps: zero returns
+      if (cudaMemsetAsync(q.G, 0, (size_t)q.N * q.K * sizeof(double), s) != cudaSuccess) return VOILA_ERR_CUDA;
+      continue;
+    }
+    idx[nq++] = i;
+  }
+  if (nq == 0) return VOILA_OK;
+  if (order == 1)
+    for (int i = 1; i < nq; ++i)  // stable insertion sort by descending H
+      for (int j = i; j > 0 && probs[idx[j]].H > probs[idx[j - 1]].H; --j) {
+        const int t = idx[j];
+        idx[j] = idx[j - 1];
+        idx[j - 1] = t;
+      }
+  long long items = 0;
+  for (int j = 0; j < nq; ++j) {
+    const TcProblem& q = probs[idx[j]];
+    TcPlanner& t = p.pl[j];
+    t.particles = q.particles;
+    t.actions = q.actions;
+    t.G = q.G;
+    t.rows = (long long)q.N * q.K;
+    t.N = q.N;
+    t.H = q.H;
+    t.planner = q.planner;
+    items += (t.rows + kSuperRows - 1) / kSuperRows;
+    p.item_end[j] = items;
+  }
+  p.P = nq;
+  p.total_items = items;
+
   __nv_bfloat16* wst = (__nv_bfloat16*)scratch;
   float* bias_all = (float*)((uint8_t*)scratch + (pl.wbytes + 1023) / 1024 * 1024);
   pl.pack.wout = wst;
@@ -668,7 +732,6 @@ voila_status tc_rollout(const voila_mlp* g_T, const voila_reward* R, const Rollo
     pack_kernel<<<(int)blocks, 256, 0, s>>>(pl.pack);
     if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   }
-  TcParams& p = pl.p;
   // one tensor map per layer over the [rows][64] BF16 weight tensor
   for (int l = 0; l < p.n_total; ++l) {
     const cuuint64_t gdim[2] = {64, (cuuint64_t)pl.total_rows};
@@ -682,29 +745,34 @@ voila_status tc_rollout(const voila_mlp* g_T, const voila_reward* R, const Rollo
       return VOILA_ERR_CUDA;
   }
   p.bias_all = bias_all;
-  p.particles = a.particles;
-  p.actions = a.actions;
-  p.N = a.N;
-  p.K = a.K;
-  p.H = a.H;
-  p.rows = (long long)a.N * a.K;
-  p.super_pairs = (p.rows + 4 * kTileRows - 1) / (4 * kTileRows);
-  p.gamma = a.gamma;
-  p.key0 = a.key0;
-  p.key1 = a.key1;
-  p.planner = a.planner;
-  p.reward_kind = a.reward_kind;
-  p.goal_dims = a.goal_dims;
-  for (int i = 0; i < VOILA_MAX_GOAL; ++i) p.goal[i] = a.goal[i];
-  p.G = a.G;
+  p.gamma = gamma;
+  p.key0 = key0;
+  p.key1 = key1;
+  p.reward_kind = R->kind;
+  p.goal_dims = R->goal_dims;
+  for (int i = 0; i < VOILA_MAX_GOAL; ++i) p.goal[i] = R->goal[i];
   p.hdr = hdr;
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const long long nclusters = p.super_pairs < nsm / 2 ? p.super_pairs : nsm / 2;
+  long long nclusters = items < nsm / 2 ? items : nsm / 2;
+  if (max_clusters > 0 && nclusters > max_clusters) nclusters = max_clusters;
   const size_t smem = tc_smem_bytes(p.bias_total);
   cudaError_t e = dims_a ? launch_tc<8, 2, 8>(p, smem, nclusters, s) : launch_tc<12, 3, 16>(p, smem, nclusters, s);
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
+}
+
+voila_status tc_rollout(const voila_mlp* g_T, const voila_reward* R, const RolloutArgs& a,
+                        WsHeader* hdr, void* scratch, cudaStream_t s) {
+  TcProblem q;
+  q.particles = a.particles;
+  q.actions = a.actions;
+  q.G = a.G;
+  q.N = a.N;
+  q.K = a.K;
+  q.H = a.H;
+  q.planner = a.planner;
+  return tc_rollout_batched(g_T, R, &q, 1, a.d_s, a.d_a, a.d_omega, a.gamma, a.key0, a.key1, 0, 0, hdr, scratch, s);
 }
 
 }  // namespace voila

@@ -13,6 +13,22 @@ namespace voila {
 // rollout needs inside the caller's workspace.
 size_t tc_rollout_scratch_bytes(const voila_mlp* g_T, const voila_reward* R);
 
+// One planning problem of a batched tensor-core rollout.
+struct TcProblem {
+  const float* particles;  // [N][d_s]
+  const float* actions;    // [K][H][d_a]
+  double* G;               // [K][N]
+  int N, K, H;
+  uint32_t planner;
+};
+
+// Launches one persistent BF16 tcgen05 rollout over P problems sharing the
+// MLPs. order = 1 sorts the work by descending horizon (longest first);
+// max_clusters > 0 caps the number of CTA pairs.
+voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, const TcProblem* probs, int P,
+                                int d_s, int d_a, int d_omega, double gamma, uint32_t key0, uint32_t key1,
+                                int order, int max_clusters, WsHeader* hdr, void* scratch, cudaStream_t s);
+
 // Launches the BF16 tcgen05 rollout; writes G [K][N]. Returns
 // VOILA_ERR_UNSUPPORTED for shapes the kernel does not cover.
 voila_status tc_rollout(const voila_mlp* g_T, const voila_reward* R, const RolloutArgs& a,

@@ -43,6 +43,11 @@ class voila_reward(ctypes.Structure):
                 ("mlp", POINTER(voila_mlp))]
 
 
+class voila_planner(ctypes.Structure):
+    _fields_ = [("particles", c_void_p), ("w", c_void_p), ("actions", c_void_p), ("N", c_int32), ("K", c_int32),
+                ("H", c_int32), ("planner_id", c_uint32), ("J", c_void_p), ("G", c_void_p), ("best_k", c_void_p)]
+
+
 class voila_likelihood(ctypes.Structure):
     _fields_ = [("kind", c_int32), ("sigma", c_float), ("mlp", POINTER(voila_mlp))]
 
@@ -62,6 +67,13 @@ _lib_rollout_ws = _sig("voila_rollout_workspace_size", c_int32, POINTER(voila_ml
 _lib_rollout = _sig("voila_rollout", c_int32, POINTER(voila_mlp), POINTER(voila_reward), _P, _P, c_int32,
                     c_int32, _P, c_int32, c_int32, c_int32, c_int32, c_double, c_uint64, c_uint32, _P, _P,
                     _P, _P, c_size_t, _P)
+_lib_batched_ws = _sig("voila_rollout_batched_workspace_size", c_int32, POINTER(voila_mlp), POINTER(voila_reward),
+                       POINTER(voila_planner), c_int32, POINTER(c_size_t))
+_lib_batched = _sig("voila_rollout_batched", c_int32, POINTER(voila_mlp), POINTER(voila_reward), POINTER(voila_planner),
+                    c_int32, c_int32, c_int32, c_int32, c_double, c_uint64, c_int32, _P, c_size_t, _P)
+_lib_batched_tune = _sig("voila_rollout_batched_autotune", c_int32, POINTER(voila_mlp), POINTER(voila_reward),
+                         POINTER(voila_planner), c_int32, c_int32, c_int32, c_int32, c_double, c_uint64, _P, c_size_t,
+                         POINTER(c_int32), POINTER(c_float), _P)
 _lib_belief_ws = _sig("voila_belief_update_workspace_size", c_int32, POINTER(voila_mlp),
                       POINTER(voila_likelihood), c_int32, POINTER(c_size_t))
 _lib_belief = _sig("voila_belief_update", c_int32, POINTER(voila_mlp), POINTER(voila_likelihood), _P, _P,
@@ -204,6 +216,49 @@ def voila_rollout(g_T: DeviceMLP, R: voila_reward, particles: torch.Tensor, w: O
                         _ptr(G, torch.float64), _ptr(best_k, torch.int32), _ptr(workspace),
                         workspace.numel(), _stream(stream))
     _check(code, "voila_rollout")
+
+
+SCHED_LONGEST_FIRST = 1
+
+
+def make_planners(items) -> "ctypes.Array":
+    """items: sequence of dicts with particles, actions, J (tensors) and optional w, G, best_k, planner_id."""
+    arr = (voila_planner * len(items))()
+    for i, it in enumerate(items):
+        N = it["particles"].shape[0]
+        K, H = it["actions"].shape[0], it["actions"].shape[1]
+        arr[i].particles = _ptr(it["particles"], torch.float32)
+        arr[i].w = _ptr(it.get("w"), torch.float64)
+        arr[i].actions = _ptr(it["actions"], torch.float32)
+        arr[i].N, arr[i].K, arr[i].H = N, K, H
+        arr[i].planner_id = it.get("planner_id", i)
+        arr[i].J = _ptr(it["J"], torch.float64)
+        arr[i].G = _ptr(it.get("G"), torch.float64)
+        arr[i].best_k = _ptr(it.get("best_k"), torch.int32)
+    return arr
+
+
+def voila_rollout_batched_workspace_size(g_T: DeviceMLP, R: voila_reward, planners) -> int:
+    n = c_size_t(0)
+    _check(_lib_batched_ws(ctypes.byref(g_T.desc), ctypes.byref(R), planners, len(planners), ctypes.byref(n)),
+           "voila_rollout_batched_workspace_size")
+    return n.value
+
+
+def voila_rollout_batched(g_T: DeviceMLP, R: voila_reward, planners, d_s: int, d_a: int, d_omega: int,
+                          gamma: float, seed: int, schedule: int, workspace: torch.Tensor, stream=None):
+    _check(_lib_batched(ctypes.byref(g_T.desc), ctypes.byref(R), planners, len(planners), d_s, d_a, d_omega, gamma,
+                        seed, schedule, _ptr(workspace), workspace.numel(), _stream(stream)), "voila_rollout_batched")
+
+
+def voila_rollout_batched_autotune(g_T: DeviceMLP, R: voila_reward, planners, d_s: int, d_a: int, d_omega: int,
+                                   gamma: float, seed: int, workspace: torch.Tensor, stream=None):
+    best = c_int32(0)
+    ms = c_float(0.0)
+    _check(_lib_batched_tune(ctypes.byref(g_T.desc), ctypes.byref(R), planners, len(planners), d_s, d_a, d_omega,
+                             gamma, seed, _ptr(workspace), workspace.numel(), ctypes.byref(best), ctypes.byref(ms),
+                             _stream(stream)), "voila_rollout_batched_autotune")
+    return best.value, ms.value
 
 
 def voila_belief_update_workspace_size(g_T: DeviceMLP, ell: voila_likelihood, N: int) -> int:

@@ -153,3 +153,11 @@ def batched_planners(seed: int = 4, P: int = 64):
     K = rng.integers(128, 1025, size=P)
     H = rng.integers(5, 31, size=P)
     return N, K, H
+
+
+def planner_inputs(seed: int, N: int, K: int, H: int, d_s: int = 8, d_a: int = 2):
+    """Particles ~N(0, I) and actions U[-1,1]^d_a of one planner of the batched workload."""
+    rng = np.random.default_rng(seed)
+    particles = round_to(rng.normal(0.0, 1.0, size=(N, d_s)), PREC_FP32)
+    actions = round_to(rng.uniform(-1.0, 1.0, size=(K, H, d_a)), PREC_FP32)
+    return particles, actions

@@ -1,0 +1,111 @@
+"""Batched multi-planner rollout: one launch over planners with uneven N, K, H.
+
+Every planner's returns must equal what voila_rollout computes for it alone
+(the same rows, noise counters and reduction order, so bit-identical), for
+every schedule, inside a captured CUDA graph, and match the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import voila_oracle as O
+from paper_2606_19729_b300 import workloads as WL
+from tests.helpers import cuda, oracle_mlp, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL_BF16 = 2e-2
+SIZES = [(300, 3, 4), (64, 5, 2), (1000, 2, 7), (129, 1, 1), (7, 4, 0), (513, 2, 3)]
+
+
+@pytest.fixture(scope="module")
+def V():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_19729_b300 import voila
+    return voila
+
+
+def _setup(V, prec=WL.PREC_BF16, sizes=SIZES):
+    wl = WL.mid_bf16(N=8, K=1, H=1, prec=prec)
+    g = V.DeviceMLP.from_spec(wl.g_T)
+    rm = V.DeviceMLP.from_spec(wl.reward_mlp)
+    R = V.mlp_reward(rm)
+    items, host = [], []
+    for i, (N, K, H) in enumerate(sizes):
+        parts, acts = WL.planner_inputs(100 + i, N, K, H)
+        host.append((parts, acts))
+        items.append({"particles": cuda(parts), "actions": cuda(acts), "planner_id": 10 + i,
+                      "J": torch.empty(K, dtype=torch.float64, device="cuda"),
+                      "G": torch.empty((K, N), dtype=torch.float64, device="cuda"),
+                      "best_k": torch.empty(1, dtype=torch.int32, device="cuda")})
+    return wl, g, rm, R, items, host
+
+
+def _single(V, wl, g, R, it):
+    N, K, H = it["particles"].shape[0], it["actions"].shape[0], it["actions"].shape[1]
+    J = torch.empty(K, dtype=torch.float64, device="cuda")
+    G = torch.empty((K, N), dtype=torch.float64, device="cuda")
+    ws = V.alloc_workspace(V.voila_rollout_workspace_size(g, R, N, K, H))
+    V.voila_rollout(g, R, it["particles"], None, it["actions"], wl.d_omega, wl.gamma, wl.seed, it["planner_id"], J, G,
+                    None, ws)
+    return J, G
+
+
+@pytest.mark.parametrize("schedule", [0, 1, 1 | (40 << 8), 3 << 8])
+def test_batched_equals_single_calls(V, schedule):
+    wl, g, rm, R, items, _ = _setup(V)
+    pl = V.make_planners(items)
+    ws = V.alloc_workspace(V.voila_rollout_batched_workspace_size(g, R, pl))
+    V.voila_rollout_batched(g, R, pl, wl.d_s, wl.d_a, wl.d_omega, wl.gamma, wl.seed, schedule, ws)
+    assert V.workspace_status(ws) == V.OK
+    for it in items:
+        J, G = _single(V, wl, g, R, it)
+        assert torch.equal(it["G"], G)
+        assert torch.equal(it["J"], J)
+        assert int(it["best_k"].item()) == int(torch.argmax(J).item())
+
+
+def test_batched_matches_oracle(V):
+    wl, g, rm, R, items, host = _setup(V)
+    pl = V.make_planners(items)
+    ws = V.alloc_workspace(V.voila_rollout_batched_workspace_size(g, R, pl))
+    V.voila_rollout_batched(g, R, pl, wl.d_s, wl.d_a, wl.d_omega, wl.gamma, wl.seed, 1, ws)
+    torch.cuda.synchronize()
+    Ro = O.Reward(O.REWARD_MLP, mlp=oracle_mlp(wl.reward_mlp))
+    for i in [0, 2, 5]:
+        parts, acts = host[i]
+        Jo, Go = O.rollout(oracle_mlp(wl.g_T), Ro, parts, acts, wl.d_omega, wl.gamma, wl.seed, planner=10 + i)
+        assert rel_err(items[i]["G"].cpu().numpy(), Go) < TOL_BF16
+        assert rel_err(items[i]["J"].cpu().numpy(), Jo) < TOL_BF16
+    assert torch.all(items[4]["G"] == 0)  # H = 0
+
+
+def test_batched_in_cuda_graph_and_autotune(V):
+    wl, g, rm, R, items, _ = _setup(V)
+    pl = V.make_planners(items)
+    ws = V.alloc_workspace(V.voila_rollout_batched_workspace_size(g, R, pl))
+    best, ms = V.voila_rollout_batched_autotune(g, R, pl, wl.d_s, wl.d_a, wl.d_omega, wl.gamma, wl.seed, ws)
+    assert ms > 0
+    V.voila_rollout_batched(g, R, pl, wl.d_s, wl.d_a, wl.d_omega, wl.gamma, wl.seed, best, ws)
+    torch.cuda.synchronize()
+    ref = [it["J"].clone() for it in items]
+    for it in items:
+        it["J"].zero_()
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            V.voila_rollout_batched(g, R, pl, wl.d_s, wl.d_a, wl.d_omega, wl.gamma, wl.seed, best, ws, stream=s)
+    graph.replay()
+    torch.cuda.synchronize()
+    for it, r in zip(items, ref):
+        assert torch.equal(it["J"], r)
+
+
+def test_batched_fp32_form_equals_single_calls(V):
+    wl, g, rm, R, items, _ = _setup(V, prec=WL.PREC_FP32, sizes=SIZES[:3])
+    pl = V.make_planners(items)
+    ws = V.alloc_workspace(V.voila_rollout_batched_workspace_size(g, R, pl))
+    V.voila_rollout_batched(g, R, pl, wl.d_s, wl.d_a, wl.d_omega, wl.gamma, wl.seed, 0, ws)
+    for it in items:
+        J, G = _single(V, wl, g, R, it)
+        assert torch.equal(it["G"], G) and torch.equal(it["J"], J)
