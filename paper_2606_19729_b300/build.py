@@ -31,7 +31,7 @@ def build(verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed on {src}")
         objs.append(obj)
     cmd = [NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs,
-           "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-lcuda"]
+           "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)

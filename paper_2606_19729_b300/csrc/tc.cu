@@ -32,6 +32,7 @@
 // VOILA_ERR_TIMEOUT in the workspace status word, drains its copies and MMAs,
 // frees TMEM and returns.
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <string.h>
 
 #include "common.cuh"
@@ -666,6 +667,21 @@ cudaError_t launch_tc(const TcParams& p, size_t smem, long long max_clusters, cu
   return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point, so the
+// library does not link libcuda directly (it loads on hosts without a driver).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
 }  // namespace
 
 size_t tc_rollout_scratch_bytes(const voila_mlp* g_T, const voila_reward* R) {
@@ -733,12 +749,14 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
     if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   }
   // one tensor map per layer over the [rows][64] BF16 weight tensor
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return VOILA_ERR_CUDA;
   for (int l = 0; l < p.n_total; ++l) {
     const cuuint64_t gdim[2] = {64, (cuuint64_t)pl.total_rows};
     const cuuint64_t gstride[1] = {128};
     const cuuint32_t box[2] = {64, (cuuint32_t)(p.layers[l].Npad / 2)};
     const cuuint32_t estride[2] = {1, 1};
-    if (cuTensorMapEncodeTiled(&p.tmap[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)wst, gdim, gstride, box,
+    if (encode(&p.tmap[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)wst, gdim, gstride, box,
                                estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
