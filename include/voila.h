@@ -85,9 +85,12 @@ enum {
  * with a linear last layer: the distilled generator form of Eq. 2 and the
  * model shapes of Sec. 5.2 (widths up to VOILA_MAX_WIDTH).
  *   W[l]  device, row-major [dims[l+1]][dims[l]] ("[out][in]"), element type
- *         float for VOILA_FP32, __nv_bfloat16 for VOILA_BF16.
+ *         float for VOILA_FP32, __nv_bfloat16 for VOILA_BF16 and VOILA_FP8E4M3.
+ *         The FP8 form (rollout only) quantises every hidden-to-hidden layer to
+ *         E4M3 with per-output-channel FP32 scales max_k|W[n][k]| / 448 and runs it
+ *         on E4M3 activations (FP32 accumulation); first and last layers stay BF16.
  *   b[l]  device, float [dims[l+1]].
- *   w_scale[l]  FP8 form only (per-output-channel scales); NULL otherwise.
+ *   w_scale[l]  reserved, NULL (the FP8 form computes its channel scales).
  * The struct itself is read on the host during the call and may be freed
  * after the call returns.
  */
@@ -152,7 +155,9 @@ voila_status voila_rollout_workspace_size(const voila_mlp* g_T, const voila_rewa
  *   J [K] double (required); G [K][N] double or NULL; best_k [1] int32 or NULL.
  *   planner_id < 65536 selects an independent noise stream per planner.
  * Precision forms: VOILA_FP32 runs on CUDA cores in FP32; VOILA_BF16 runs on
- * the tcgen05 tensor cores (BF16 operands, FP32 accumulation in TMEM).
+ * the tcgen05 tensor cores (BF16 operands, FP32 accumulation in TMEM);
+ * VOILA_FP8E4M3 runs its hidden layers as E4M3 tensor-core MMAs with
+ * per-channel scales (see voila_mlp).
  * Returns are accumulated in FP64 in both forms.
  * N == 0 or K == 0 is a no-op; H == 0 gives zero returns.
  */

@@ -71,7 +71,7 @@ RolloutLayout rollout_layout(const voila_mlp* g_T, const voila_reward* R, long l
   L.g_off = off;
   if (need_g) off = align_up(off + (size_t)N * K * sizeof(double));
   L.tc_off = off;
-  if (g_T->prec == VOILA_BF16) off = align_up(off + tc_rollout_scratch_bytes(g_T, R));
+  if (g_T->prec != VOILA_FP32) off = align_up(off + tc_rollout_scratch_bytes(g_T, R));
   L.total = off;
   return L;
 }
@@ -94,7 +94,6 @@ voila_status check_rollout(const voila_mlp* g_T, const voila_reward* R, int32_t 
   } else {
     return VOILA_ERR_ARG;
   }
-  if (g_T->prec == VOILA_FP8E4M3) return VOILA_ERR_UNSUPPORTED;
   if ((long long)N * K > (1LL << 31)) return VOILA_ERR_SHAPE;
   return VOILA_OK;
 }
@@ -175,7 +174,7 @@ voila_status voila_rollout(const voila_mlp* g_T, const voila_reward* R, const fl
   a.planner = planner_id;
   a.G = Gbuf;
 
-  if (g_T->prec == VOILA_BF16) {
+  if (g_T->prec != VOILA_FP32) {  // BF16 and FP8 forms: tensor cores
     st = tc_rollout(g_T, R, a, (WsHeader*)ws, ws + L.tc_off, s);
     if (st != VOILA_OK) return st;
   } else {
@@ -193,7 +192,7 @@ static size_t batched_layout(const voila_mlp* g_T, const voila_reward* R, const 
                              size_t* g_off /* [P] or NULL */) {
   size_t off = kHeaderBytes;
   off = align_up(off, 1024);
-  if (g_T->prec == VOILA_BF16) off = align_up(off + tc_rollout_scratch_bytes(g_T, R));
+  if (g_T->prec != VOILA_FP32) off = align_up(off + tc_rollout_scratch_bytes(g_T, R));
   for (int i = 0; i < P; ++i) {
     if (g_off) g_off[i] = off;
     if (!pl[i].G) off = align_up(off + (size_t)pl[i].N * pl[i].K * sizeof(double));
@@ -240,7 +239,7 @@ voila_status voila_rollout_batched(const voila_mlp* g_T, const voila_reward* R, 
   philox_key(seed, k0, k1);
   double* Gp[VOILA_MAX_PLANNERS];
   for (int i = 0; i < P; ++i) Gp[i] = planners[i].G ? planners[i].G : (double*)(ws + g_off[i]);
-  if (g_T->prec == VOILA_BF16) {
+  if (g_T->prec != VOILA_FP32) {
     TcProblem probs[VOILA_MAX_PLANNERS];
     for (int i = 0; i < P; ++i) {
       probs[i].particles = planners[i].particles;

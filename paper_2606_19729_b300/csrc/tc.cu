@@ -35,6 +35,8 @@
 #include <cudaTypedefs.h>
 #include <string.h>
 
+#include <cuda_fp8.h>
+
 #include "common.cuh"
 #include "tc.h"
 #include "tc_ptx.cuh"
@@ -62,6 +64,10 @@ struct TcLayer {
   int nchunks;      // ceil(nslabs / spc)
   int bias_off;     // offset into the concatenated bias vector
   int act;          // activation after this layer (-1: linear output layer)
+  int fp8;          // 1: E4M3 operands (kind::f8f6f4, 128 K per slab), else BF16 (64 K per slab)
+  int out_fp8;      // 1: this layer's epilogue writes the next layer's A operand as E4M3
+  int ksteps;       // MMA K steps (32 K each for FP8, 16 for BF16)
+  int scale_off;    // per-output-channel weight scales (FP8 layers), offset into the scale vector
   uint32_t idesc;
   int row0;         // first row of chunk 0 in the [rows][64] weight tensor
 };
@@ -82,7 +88,8 @@ struct TcParams {
   TcLayer layers[kMaxTcLayers];
   int n_gen, n_total;
   const float* bias_all;
-  int bias_total;  // floats, multiple of 4
+  int bias_total;   // floats, multiple of 4
+  int scale_total;  // floats after the biases in the same vector (FP8 channel scales)
   double gamma;
   uint32_t key0, key1;
   int reward_kind, goal_dims;
@@ -124,6 +131,12 @@ __device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, vola
 // silu(x) = x sigmoid(x) = u (1 + tanh u) = fma(u, tanh u, u): one MUFU op
 // (tanh.approx.f32; the packed BF16x2/FP16x2 forms measured slower on this
 // part) and one FMA per value.
+__device__ __forceinline__ float act_value(float u, int act) {
+  if (act == VOILA_ACT_SILU) return fmaf(u, ptx::tanh_approx(u), u);
+  if (act == VOILA_ACT_TANH) return ptx::tanh_approx(u);
+  return u;
+}
+
 __device__ __forceinline__ uint32_t act_pair(float u0, float u1, int act) {
   if (act == VOILA_ACT_SILU)
     return ptx::pack_bf16x2(fmaf(u0, ptx::tanh_approx(u0), u0), fmaf(u1, ptx::tanh_approx(u1), u1));
@@ -131,21 +144,54 @@ __device__ __forceinline__ uint32_t act_pair(float u0, float u1, int act) {
   return ptx::pack_bf16x2(u0, u1);
 }
 
-// 32 accumulator columns [32c, 32c + 32) of row r -> bias + activation ->
-// four 16-byte chunks of the next layer's A operand.
-__device__ __forceinline__ void epi_cols32(const float* v, const float* bl, int c, int act, uint8_t* A,
-                                           int r) {
-  uint8_t* slab = A + (c >> 1) * (128 * 128);
+// 32 accumulator columns [32c, 32c + 32) of row r -> (channel scale) + bias +
+// activation -> the next layer's A operand: BF16 (four 16-byte chunks, 64 K
+// per 128-byte swizzled row) or E4M3 (two chunks, 128 K per row).
+template <bool SCALE, bool OUT_FP8>
+__device__ __forceinline__ void epi_cols32(float* u, const float* bl, const float* sl, int c, int act,
+                                           uint8_t* A, int r) {
+  const float* v = u;  // transformed in place (register pressure)
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float4 b0 = *reinterpret_cast<const float4*>(bl + 32 * c + 8 * j);
-    const float4 b1 = *reinterpret_cast<const float4*>(bl + 32 * c + 8 * j + 4);
-    uint4 o;
-    o.x = act_pair(v[8 * j + 0] + b0.x, v[8 * j + 1] + b0.y, act);
-    o.y = act_pair(v[8 * j + 2] + b0.z, v[8 * j + 3] + b0.w, act);
-    o.z = act_pair(v[8 * j + 4] + b1.x, v[8 * j + 5] + b1.y, act);
-    o.w = act_pair(v[8 * j + 6] + b1.z, v[8 * j + 7] + b1.w, act);
-    *reinterpret_cast<uint4*>(slab + r * 128 + ((((c & 1) * 4 + j) ^ (r & 7)) << 4)) = o;
+  for (int j = 0; j < 8; ++j) {
+    const float4 b = *reinterpret_cast<const float4*>(bl + 32 * c + 4 * j);
+    if (SCALE) {
+      const float4 sc = *reinterpret_cast<const float4*>(sl + 32 * c + 4 * j);
+      u[4 * j + 0] = fmaf(v[4 * j + 0], sc.x, b.x);
+      u[4 * j + 1] = fmaf(v[4 * j + 1], sc.y, b.y);
+      u[4 * j + 2] = fmaf(v[4 * j + 2], sc.z, b.z);
+      u[4 * j + 3] = fmaf(v[4 * j + 3], sc.w, b.w);
+    } else {
+      u[4 * j + 0] = v[4 * j + 0] + b.x;
+      u[4 * j + 1] = v[4 * j + 1] + b.y;
+      u[4 * j + 2] = v[4 * j + 2] + b.z;
+      u[4 * j + 3] = v[4 * j + 3] + b.w;
+    }
+  }
+  if (!OUT_FP8) {
+    uint8_t* slab = A + (c >> 1) * (128 * 128);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint4 o;
+      o.x = act_pair(u[8 * j + 0], u[8 * j + 1], act);
+      o.y = act_pair(u[8 * j + 2], u[8 * j + 3], act);
+      o.z = act_pair(u[8 * j + 4], u[8 * j + 5], act);
+      o.w = act_pair(u[8 * j + 6], u[8 * j + 7], act);
+      *reinterpret_cast<uint4*>(slab + r * 128 + ((((c & 1) * 4 + j) ^ (r & 7)) << 4)) = o;
+    }
+  } else {
+    uint8_t* slab = A + (c >> 2) * (128 * 128);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      float y[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) y[i] = act_value(u[16 * j + i], act);
+      uint4 o;
+      o.x = ptx::pack_e4m3x4(y[0], y[1], y[2], y[3]);
+      o.y = ptx::pack_e4m3x4(y[4], y[5], y[6], y[7]);
+      o.z = ptx::pack_e4m3x4(y[8], y[9], y[10], y[11]);
+      o.w = ptx::pack_e4m3x4(y[12], y[13], y[14], y[15]);
+      *reinterpret_cast<uint4*>(slab + r * 128 + ((((c & 3) * 2 + j) ^ (r & 7)) << 4)) = o;
+    }
   }
 }
 
@@ -207,14 +253,15 @@ __device__ __forceinline__ void write_rew_input(uint8_t* A, int r, const float* 
 }
 
 template <int DS, int DA, int DW>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
+__global__ void __cluster_dims__(2, 1, 1) __maxnreg__(112)
     rollout_tc_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* Abuf[2] = {smem, smem + kABytes};
   uint8_t* ring = smem + 2 * kABytes;
   float* bias_s = reinterpret_cast<float*>(ring + kStages * kSlotBytes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(bias_s + p.bias_total);
+  float* scale_s = bias_s + p.bias_total;  // FP8 channel scales follow the biases
+  uint64_t* bars = reinterpret_cast<uint64_t*>(scale_s + p.scale_total);
   uint64_t* full = bars;
   uint64_t* empty = bars + kStages;
   uint64_t* accf = bars + 2 * kStages;      // [2]
@@ -239,7 +286,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
-  for (int i = threadIdx.x; i < p.bias_total; i += blockDim.x) bias_s[i] = p.bias_all[i];
+  for (int i = threadIdx.x; i < p.bias_total + p.scale_total; i += blockDim.x) bias_s[i] = p.bias_all[i];
   if (warp == 1) {
     ptx::tmem_alloc_pair(ptx::smem_u32(tmem_holder), 512);
     ptx::tmem_relinquish_pair();
@@ -315,7 +362,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           const int H = p.pl[item_planner(p, it)].H;
           for (int t = 0; t < H && ok; ++t)
             for (int l = 0; l < p.n_total && ok; ++l) {
-              const int nch = p.layers[l].nchunks, ksteps = p.layers[l].Kp >> 4;
+              const int nch = p.layers[l].nchunks, ksteps = p.layers[l].ksteps;
+              const bool f8 = p.layers[l].fp8 != 0;
               const int kpc = 4 * p.layers[l].spc;  // K steps per chunk
               const uint32_t slab16 = (uint32_t)p.layers[l].slab_bytes >> 4;
               const uint32_t idesc = p.layers[l].idesc;
@@ -372,7 +420,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                   const uint32_t a_lo = ad_lo + (uint32_t)(kb >> 2) * 1024u;
                   const uint32_t b_lo = bd_lo + (uint32_t)slot * (uint32_t)(kSlotBytes >> 4);
                   const int ks = ksteps - kb < kpc ? ksteps - kb : kpc;
-                  if (kpc == 4) {
+                  if (kpc == 4 && f8) {
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                      if (kk < ks)
+                        ptx::mma_f8_pair(d_tmem, ptx::desc_with_lo(ad_hi, a_lo + 2 * kk),
+                                         ptx::desc_with_lo(bd_hi, b_lo + 2 * kk), idesc, (c | kk) ? 1u : 0u);
+                  } else if (kpc == 4) {
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
                       if (kk < ks)
@@ -459,7 +513,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
               float v[32];
               ptx::tmem_ld32(tm + 32 * c, v);
               ptx::tmem_wait_ld32(v);
-              epi_cols32(v, bl, c, L.act, A, r);
+              if (L.out_fp8) {
+                if (L.fp8) epi_cols32<true, true>(v, bl, scale_s + L.scale_off, c, L.act, A, r);
+                else epi_cols32<false, true>(v, bl, nullptr, c, L.act, A, r);
+              } else {
+                if (L.fp8) epi_cols32<true, false>(v, bl, scale_s + L.scale_off, c, L.act, A, r);
+                else epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
+              }
             }
           } else if (sub == 0 && l == p.n_gen - 1) {
             // generator output: s_{t+1} (FP32, kept in registers)
@@ -519,21 +579,44 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
   if (warp == 1) ptx::tmem_dealloc_pair(tmem_base, 512);
 }
 
-// One launch packs every layer into the [rows][64] BF16 weight tensor that
+// One launch packs every layer into the [rows][128-byte] weight tensor that
 // the TMA reads: chunk c of layer l is rows row0 + c * Npad + n holding
-// W[n][64c .. 64c + 63], zero padded; SiLU layers are scaled by 1/2 (exact).
+// W[n][E c .. E c + E - 1], E = 64 BF16 or 128 E4M3 values, zero padded;
+// SiLU layers are scaled by 1/2 (exact); an E4M3 row n is W[n][.] / scale_n.
 // Biases are copied (scaled alike) and zero padded.
 struct PackTable {
   const __nv_bfloat16* W[kMaxTcLayers];
   const float* b[kMaxTcLayers];
-  int N[kMaxTcLayers], K[kMaxTcLayers], Npad[kMaxTcLayers], nchunks[kMaxTcLayers];
-  int row0[kMaxTcLayers], bias_off[kMaxTcLayers];
+  int N[kMaxTcLayers], K[kMaxTcLayers], Npad[kMaxTcLayers];
+  int row0[kMaxTcLayers], bias_off[kMaxTcLayers], scale_off[kMaxTcLayers];
   long long elems_end[kMaxTcLayers];
   int half[kMaxTcLayers];  // 1: SiLU layer, pack W and b scaled by 1/2
+  int fp8[kMaxTcLayers];
   int n;
-  __nv_bfloat16* wout;
-  float* bout;
+  uint8_t* wout;
+  float* bout;   // biases, then channel scales
 };
+
+// Per-output-channel scale of every E4M3 layer: max_k |W'[n][k]| / 448 (W'
+// includes the SiLU 1/2), 1 for all-zero or padded rows. One warp per row.
+__global__ void scale_kernel(const __grid_constant__ PackTable t) {
+  const int lane = threadIdx.x & 31;
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int base = 0;
+  for (int l = 0; l < t.n; ++l) {
+    if (!t.fp8[l]) continue;
+    const int rowl = wg - base;
+    base += t.Npad[l];
+    if (rowl < 0 || rowl >= t.Npad[l]) continue;
+    float m = 0.0f;
+    if (rowl < t.N[l])
+      for (int k = lane; k < t.K[l]; k += 32) m = fmaxf(m, fabsf(__bfloat162float(t.W[l][(size_t)rowl * t.K[l] + k])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (t.half[l]) m *= 0.5f;
+    if (lane == 0) t.bout[t.scale_off[l] + rowl] = m > 0.0f ? m / 448.0f : 1.0f;
+  }
+}
 
 __global__ void pack_kernel(const __grid_constant__ PackTable t) {
   const long long total = t.elems_end[t.n - 1];
@@ -543,14 +626,20 @@ __global__ void pack_kernel(const __grid_constant__ PackTable t) {
     while (e >= t.elems_end[l]) ++l;
     const long long e0 = e - (l ? t.elems_end[l - 1] : 0);
     const int Npad = t.Npad[l];
-    const int c = (int)(e0 / (Npad * 64));
-    const int rem = (int)(e0 % (Npad * 64));
-    const int nrow = rem / 64, kk = rem % 64;
-    const int kg = 64 * c + kk;
-    __nv_bfloat16 v =
-        (nrow < t.N[l] && kg < t.K[l]) ? t.W[l][(size_t)nrow * t.K[l] + kg] : __float2bfloat16(0.0f);
-    if (t.half[l]) v = __hmul(v, __float2bfloat16(0.5f));
-    t.wout[((size_t)t.row0[l] + (size_t)c * Npad + nrow) * 64 + kk] = v;
+    const int epr = t.fp8[l] ? 128 : 64;  // values per 128-byte row
+    const int c = (int)(e0 / (Npad * epr));
+    const int rem = (int)(e0 % (Npad * epr));
+    const int nrow = rem / epr, kk = rem % epr;
+    const int kg = epr * c + kk;
+    float w = (nrow < t.N[l] && kg < t.K[l]) ? __bfloat162float(t.W[l][(size_t)nrow * t.K[l] + kg]) : 0.0f;
+    if (t.half[l]) w *= 0.5f;  // exact
+    uint8_t* row = t.wout + ((size_t)t.row0[l] + (size_t)c * Npad + nrow) * 128;
+    if (t.fp8[l]) {
+      const __nv_fp8_e4m3 q(w / t.bout[t.scale_off[l] + nrow]);
+      row[kk] = *reinterpret_cast<const uint8_t*>(&q);
+    } else {
+      *reinterpret_cast<__nv_bfloat16*>(row + 2 * kk) = __float2bfloat16(w);
+    }
     if (c == 0 && kk == 0)
       t.bout[t.bias_off[l] + nrow] = nrow < t.N[l] ? (t.half[l] ? 0.5f : 1.0f) * t.b[l][nrow] : 0.0f;
   }
@@ -576,7 +665,7 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
   for (int m = 0; m < 2; ++m) {
     const voila_mlp* M = mlps[m];
     if (!M) continue;
-    if (M->prec != VOILA_BF16 || M->n_layers < 2) return pl;
+    if ((M->prec != VOILA_BF16 && M->prec != VOILA_FP8E4M3) || M->n_layers < 2) return pl;
     for (int l = 0; l < M->n_layers; ++l) {
       if (nl >= kMaxTcLayers) return pl;
       const int K = M->dims[l], N = M->dims[l + 1];
@@ -586,9 +675,13 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
       if (!last && (N % 64 != 0 || N > 256)) return pl;
       if (last && N > 32) return pl;
       TcLayer& L = pl.p.layers[nl];
-      L.Kp = round_up(K, 16);
+      // FP8 form: hidden x hidden layers in E4M3, first and last layers in BF16
+      L.fp8 = (M->prec == VOILA_FP8E4M3 && l > 0 && !last) ? 1 : 0;
+      L.out_fp8 = (M->prec == VOILA_FP8E4M3 && l + 1 < M->n_layers - 1) ? 1 : 0;
+      L.Kp = round_up(K, L.fp8 ? 32 : 16);
+      L.ksteps = L.fp8 ? L.Kp / 32 : L.Kp / 16;
       L.Npad = last ? 32 : N;
-      L.nslabs = (L.Kp + 63) / 64;
+      L.nslabs = (L.Kp + (L.fp8 ? 127 : 63)) / (L.fp8 ? 128 : 64);
       L.slab_bytes = (L.Npad / 2) * 128;
       L.spc = kSlotBytes / L.slab_bytes;
       if (L.spc > 4) L.spc = 4;  // at most 16 K steps per chunk
@@ -596,7 +689,7 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
       L.nchunks = (L.nslabs + L.spc - 1) / L.spc;
       L.bias_off = boff;
       L.act = last ? -1 : M->act;
-      L.idesc = ptx::idesc_bf16(256, L.Npad);
+      L.idesc = L.fp8 ? ptx::idesc_e4m3(256, L.Npad) : ptx::idesc_bf16(256, L.Npad);
       L.row0 = rows;
       PackTable& T = pl.pack;
       T.W[nl] = (const __nv_bfloat16*)M->W[l];
@@ -604,11 +697,11 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
       T.N[nl] = N;
       T.K[nl] = K;
       T.Npad[nl] = L.Npad;
-      T.nchunks[nl] = L.nslabs;
       T.row0[nl] = rows;
       T.bias_off[nl] = boff;
       T.half[nl] = (!last && M->act == VOILA_ACT_SILU) ? 1 : 0;
-      elems += (long long)L.nslabs * L.Npad * 64;
+      T.fp8[nl] = L.fp8;
+      elems += (long long)L.nslabs * L.Npad * (L.fp8 ? 128 : 64);
       T.elems_end[nl] = elems;
       rows += L.nslabs * L.Npad;
       boff += L.Npad;  // multiple of 32
@@ -619,16 +712,23 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
   pl.p.n_total = nl;
   pl.pack.n = nl;
   pl.p.bias_total = boff;
+  int soff = 0;  // channel scales follow the biases in the same vector
+  for (int l = 0; l < nl; ++l) {
+    pl.p.layers[l].scale_off = soff;
+    pl.pack.scale_off[l] = boff + soff;
+    if (pl.p.layers[l].fp8) soff += pl.p.layers[l].Npad;
+  }
+  pl.p.scale_total = soff;
   pl.total_rows = rows;
   pl.wbytes = (size_t)rows * 128;
-  pl.bias_bytes = (size_t)boff * sizeof(float);
+  pl.bias_bytes = (size_t)(boff + soff) * sizeof(float);
   pl.total = (pl.wbytes + 1023) / 1024 * 1024 + (pl.bias_bytes + 255) / 256 * 256;
   pl.ok = true;
   return pl;
 }
 
-size_t tc_smem_bytes(int bias_total) {
-  return 1024 + 2 * kABytes + kStages * kSlotBytes + (size_t)bias_total * 4 + (2 * kStages + 5) * 8 + 16;
+size_t tc_smem_bytes(int vec_floats) {
+  return 1024 + 2 * kABytes + kStages * kSlotBytes + (size_t)vec_floats * 4 + (2 * kStages + 5) * 8 + 16;
 }
 
 // Launches one persistent CTA pair per co-resident cluster slot (at most
@@ -737,7 +837,7 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
   p.P = nq;
   p.total_items = items;
 
-  __nv_bfloat16* wst = (__nv_bfloat16*)scratch;
+  uint8_t* wst = (uint8_t*)scratch;
   float* bias_all = (float*)((uint8_t*)scratch + (pl.wbytes + 1023) / 1024 * 1024);
   pl.pack.wout = wst;
   pl.pack.bout = bias_all;
@@ -745,6 +845,12 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
     const long long total = pl.pack.elems_end[pl.pack.n - 1];
     long long blocks = (total + 255) / 256;
     if (blocks > 148 * 8) blocks = 148 * 8;
+    if (p.scale_total > 0) {
+      int srows = 0;
+      for (int l = 0; l < pl.pack.n; ++l)
+        if (pl.pack.fp8[l]) srows += pl.pack.Npad[l];
+      scale_kernel<<<(srows * 32 + 255) / 256, 256, 0, s>>>(pl.pack);
+    }
     pack_kernel<<<(int)blocks, 256, 0, s>>>(pl.pack);
     if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   }
@@ -752,11 +858,11 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
   PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
   if (!encode) return VOILA_ERR_CUDA;
   for (int l = 0; l < p.n_total; ++l) {
-    const cuuint64_t gdim[2] = {64, (cuuint64_t)pl.total_rows};
+    const cuuint64_t gdim[2] = {128, (cuuint64_t)pl.total_rows};  // bytes
     const cuuint64_t gstride[1] = {128};
-    const cuuint32_t box[2] = {64, (cuuint32_t)(p.layers[l].Npad / 2)};
+    const cuuint32_t box[2] = {128, (cuuint32_t)(p.layers[l].Npad / 2)};
     const cuuint32_t estride[2] = {1, 1};
-    if (encode(&p.tmap[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)wst, gdim, gstride, box,
+    if (encode(&p.tmap[l], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)wst, gdim, gstride, box,
                                estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -775,7 +881,7 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   long long nclusters = items < nsm / 2 ? items : nsm / 2;
   if (max_clusters > 0 && nclusters > max_clusters) nclusters = max_clusters;
-  const size_t smem = tc_smem_bytes(p.bias_total);
+  const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total);
   cudaError_t e = dims_a ? launch_tc<8, 2, 8>(p, smem, nclusters, s) : launch_tc<12, 3, 16>(p, smem, nclusters, s);
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }

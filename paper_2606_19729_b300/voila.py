@@ -130,7 +130,8 @@ class DeviceMLP:
     def __init__(self, W: Sequence[torch.Tensor], b: Sequence[torch.Tensor], act: int, prec: int):
         if len(W) != len(b) or not 1 <= len(W) <= MAX_LAYERS:
             raise ValueError("bad layer count")
-        wdt = {FP32: torch.float32, BF16: torch.bfloat16}[prec]
+        # the FP8 form takes BF16 weights; the library quantises its hidden layers
+        wdt = {FP32: torch.float32, BF16: torch.bfloat16, FP8E4M3: torch.bfloat16}[prec]
         self.W = [w.to(device="cuda", dtype=wdt).contiguous() for w in W]
         self.b = [v.to(device="cuda", dtype=torch.float32).contiguous() for v in b]
         self.act, self.prec = act, prec

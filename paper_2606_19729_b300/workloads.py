@@ -39,8 +39,9 @@ def round_bf16(x: np.ndarray) -> np.ndarray:
 
 
 def round_to(x: np.ndarray, prec: int) -> np.ndarray:
-    """Storage rounding of a weight tensor for precision form `prec`."""
-    if prec == PREC_BF16:
+    """Storage rounding of a weight tensor for precision form `prec` (the FP8 form
+    is handed BF16 weights and quantises them itself)."""
+    if prec in (PREC_BF16, PREC_FP8):
         return round_bf16(x)
     return np.asarray(x, np.float32).astype(np.float64)
 
