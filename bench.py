@@ -43,6 +43,7 @@ def parse_args():
     ap.add_argument("--cpu-seqs", type=int, default=8, help="action sequences in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-seqs", type=int, default=16, help="sequences for the FP32-form comparison (0: skip)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP32/FP8 form comparison")
     ap.add_argument("--N", type=int, default=None, help="override particles (profiling runs)")
     ap.add_argument("--K", type=int, default=None, help="override action sequences (profiling runs)")
     ap.add_argument("--H", type=int, default=None, help="override horizon (profiling runs)")
@@ -203,6 +204,32 @@ def fp32_form(V, wl, seqs, planner, particles, stream):
     sec = e0.elapsed_time(e1) / 1e3 / reps
     return {"value": seqs * wl.N * wl.H / sec, "unit": UNIT, "dtype": "f32",
             "sample": f"{seqs} of {wl.K} sequences x {wl.N} particles x H={wl.H}, same weights in FP32"}
+
+
+def fp8_form(V, wl, planner, particles, stream):
+    """The FP8 e4m3 form (hidden layers E4M3 with per-channel scales) on the full
+    workload, same particles and weights; returns its throughput and J."""
+    import torch
+    g8 = V.DeviceMLP([torch.from_numpy(w) for w in wl.g_T.W], [torch.from_numpy(b) for b in wl.g_T.b],
+                     wl.g_T.act, V.FP8E4M3)
+    r8 = V.DeviceMLP([torch.from_numpy(w) for w in wl.reward_mlp.W], [torch.from_numpy(b) for b in wl.reward_mlp.b],
+                     wl.reward_mlp.act, V.FP8E4M3)
+    R8 = V.mlp_reward(r8)
+    acts = torch.from_numpy(wl.actions).float().cuda()
+    J = torch.empty(wl.K, dtype=torch.float64, device="cuda")
+    ws = V.alloc_workspace(V.voila_rollout_workspace_size(g8, R8, wl.N, wl.K, wl.H))
+    V.voila_rollout(g8, R8, particles, None, acts, wl.d_omega, wl.gamma, wl.seed, planner, J, None, None, ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        V.voila_rollout(g8, R8, particles, None, acts, wl.d_omega, wl.gamma, wl.seed, planner, J, None, None, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    assert V.workspace_status(ws) == V.OK
+    sec = e0.elapsed_time(e1) / 1e3 / reps
+    return {"value": wl.N * wl.K * wl.H / sec, "unit": UNIT, "dtype": "e4m3 hidden layers, bf16 first/last",
+            "rollout_ms": 1e3 * sec, "sample": "full workload, same particles and weights"}, J.cpu().numpy()
 
 
 def run_reference(args, rank):
@@ -498,8 +525,12 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 6 * args.steps,
             "clocks": clk.summary()}
-    if args.fp32_seqs > 0 and wl.prec == 1 and rank == 0:
-        line["forms"] = {"fp32_cuda_cores": fp32_form(V, wl, args.fp32_seqs, planner, p_new, stream)}
+    J8 = None
+    if wl.prec == 1 and rank == 0 and not args.no_forms:
+        line["forms"] = {}
+        if args.fp32_seqs > 0:
+            line["forms"]["fp32_cuda_cores"] = fp32_form(V, wl, args.fp32_seqs, planner, p_new, stream)
+        line["forms"]["fp8_e4m3"], J8 = fp8_form(V, wl, planner, p_new, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the device's resampled particles and J of this exact step, against FP64
         V.voila_belief_update(g, lik, particles, None, action, obs, wl.d_omega, wl.lam, wl.seed, 1, planner, p_new,
@@ -509,6 +540,9 @@ def main():
         cb, Jo = cpu_baseline(wl, args.cpu_seqs, p_new.cpu().double().numpy())
         line["cpu_baseline"] = cb
         Jd = J[: args.cpu_seqs].cpu().numpy()
+        if J8 is not None:
+            line["forms"]["fp8_e4m3"]["err_vs_fp64"] = float(
+                np.max(np.abs(J8[: args.cpu_seqs] - Jo)) / np.max(np.abs(Jo)))
         line["err_vs_fp64"] = {"J_normwise": float(np.max(np.abs(Jd - Jo)) / np.max(np.abs(Jo))),
                                "sample": f"J of {args.cpu_seqs} of {wl.K} sequences (all particles) vs the FP64 oracle "
                                          "from the same resampled particles",

@@ -150,21 +150,35 @@ __device__ __forceinline__ uint32_t act_pair(float u0, float u1, int act) {
 template <bool SCALE, bool OUT_FP8>
 __device__ __forceinline__ void epi_cols32(float* u, const float* bl, const float* sl, int c, int act,
                                            uint8_t* A, int r) {
-  const float* v = u;  // transformed in place (register pressure)
+  if (!SCALE && !OUT_FP8) {  // BF16 -> BF16: bias, activation and store, eight columns at a time
+    uint8_t* slab = A + (c >> 1) * (128 * 128);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < 4; ++j) {
+      const float4 b0 = *reinterpret_cast<const float4*>(bl + 32 * c + 8 * j);
+      const float4 b1 = *reinterpret_cast<const float4*>(bl + 32 * c + 8 * j + 4);
+      uint4 o;
+      o.x = act_pair(u[8 * j + 0] + b0.x, u[8 * j + 1] + b0.y, act);
+      o.y = act_pair(u[8 * j + 2] + b0.z, u[8 * j + 3] + b0.w, act);
+      o.z = act_pair(u[8 * j + 4] + b1.x, u[8 * j + 5] + b1.y, act);
+      o.w = act_pair(u[8 * j + 6] + b1.z, u[8 * j + 7] + b1.w, act);
+      *reinterpret_cast<uint4*>(slab + r * 128 + ((((c & 1) * 4 + j) ^ (r & 7)) << 4)) = o;
+    }
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {  // transformed in place (register pressure)
     const float4 b = *reinterpret_cast<const float4*>(bl + 32 * c + 4 * j);
     if (SCALE) {
       const float4 sc = *reinterpret_cast<const float4*>(sl + 32 * c + 4 * j);
-      u[4 * j + 0] = fmaf(v[4 * j + 0], sc.x, b.x);
-      u[4 * j + 1] = fmaf(v[4 * j + 1], sc.y, b.y);
-      u[4 * j + 2] = fmaf(v[4 * j + 2], sc.z, b.z);
-      u[4 * j + 3] = fmaf(v[4 * j + 3], sc.w, b.w);
+      u[4 * j + 0] = fmaf(u[4 * j + 0], sc.x, b.x);
+      u[4 * j + 1] = fmaf(u[4 * j + 1], sc.y, b.y);
+      u[4 * j + 2] = fmaf(u[4 * j + 2], sc.z, b.z);
+      u[4 * j + 3] = fmaf(u[4 * j + 3], sc.w, b.w);
     } else {
-      u[4 * j + 0] = v[4 * j + 0] + b.x;
-      u[4 * j + 1] = v[4 * j + 1] + b.y;
-      u[4 * j + 2] = v[4 * j + 2] + b.z;
-      u[4 * j + 3] = v[4 * j + 3] + b.w;
+      u[4 * j + 0] += b.x;
+      u[4 * j + 1] += b.y;
+      u[4 * j + 2] += b.z;
+      u[4 * j + 3] += b.w;
     }
   }
   if (!OUT_FP8) {
@@ -182,14 +196,12 @@ __device__ __forceinline__ void epi_cols32(float* u, const float* bl, const floa
     uint8_t* slab = A + (c >> 2) * (128 * 128);
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      float y[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) y[i] = act_value(u[16 * j + i], act);
+      const float* y = u + 16 * j;
       uint4 o;
-      o.x = ptx::pack_e4m3x4(y[0], y[1], y[2], y[3]);
-      o.y = ptx::pack_e4m3x4(y[4], y[5], y[6], y[7]);
-      o.z = ptx::pack_e4m3x4(y[8], y[9], y[10], y[11]);
-      o.w = ptx::pack_e4m3x4(y[12], y[13], y[14], y[15]);
+      o.x = ptx::pack_e4m3x4(act_value(y[0], act), act_value(y[1], act), act_value(y[2], act), act_value(y[3], act));
+      o.y = ptx::pack_e4m3x4(act_value(y[4], act), act_value(y[5], act), act_value(y[6], act), act_value(y[7], act));
+      o.z = ptx::pack_e4m3x4(act_value(y[8], act), act_value(y[9], act), act_value(y[10], act), act_value(y[11], act));
+      o.w = ptx::pack_e4m3x4(act_value(y[12], act), act_value(y[13], act), act_value(y[14], act), act_value(y[15], act));
       *reinterpret_cast<uint4*>(slab + r * 128 + ((((c & 3) * 2 + j) ^ (r & 7)) << 4)) = o;
     }
   }
@@ -252,8 +264,10 @@ __device__ __forceinline__ void write_rew_input(uint8_t* A, int r, const float* 
   store_row<KP>(A, r, x);
 }
 
-template <int DS, int DA, int DW>
-__global__ void __cluster_dims__(2, 1, 1) __maxnreg__(112)
+// F8: the MLPs contain E4M3 layers (a separate instantiation keeps the BF16
+// form free of the FP8 code paths).
+template <int DS, int DA, int DW, bool F8>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     rollout_tc_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -363,7 +377,7 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(112)
           for (int t = 0; t < H && ok; ++t)
             for (int l = 0; l < p.n_total && ok; ++l) {
               const int nch = p.layers[l].nchunks, ksteps = p.layers[l].ksteps;
-              const bool f8 = p.layers[l].fp8 != 0;
+              const bool f8 = F8 && p.layers[l].fp8 != 0;
               const int kpc = 4 * p.layers[l].spc;  // K steps per chunk
               const uint32_t slab16 = (uint32_t)p.layers[l].slab_bytes >> 4;
               const uint32_t idesc = p.layers[l].idesc;
@@ -420,7 +434,7 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(112)
                   const uint32_t a_lo = ad_lo + (uint32_t)(kb >> 2) * 1024u;
                   const uint32_t b_lo = bd_lo + (uint32_t)slot * (uint32_t)(kSlotBytes >> 4);
                   const int ks = ksteps - kb < kpc ? ksteps - kb : kpc;
-                  if (kpc == 4 && f8) {
+                  if (F8 && kpc == 4 && f8) {
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
                       if (kk < ks)
@@ -513,7 +527,9 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(112)
               float v[32];
               ptx::tmem_ld32(tm + 32 * c, v);
               ptx::tmem_wait_ld32(v);
-              if (L.out_fp8) {
+              if (!F8) {
+                epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
+              } else if (L.out_fp8) {
                 if (L.fp8) epi_cols32<true, true>(v, bl, scale_s + L.scale_off, c, L.act, A, r);
                 else epi_cols32<false, true>(v, bl, nullptr, c, L.act, A, r);
               } else {
@@ -733,9 +749,9 @@ size_t tc_smem_bytes(int vec_floats) {
 
 // Launches one persistent CTA pair per co-resident cluster slot (at most
 // `max_clusters`, never more than there are super-pairs).
-template <int DS, int DA, int DW>
+template <int DS, int DA, int DW, bool F8>
 cudaError_t launch_tc(const TcParams& p, size_t smem, long long max_clusters, cudaStream_t s) {
-  auto k = rollout_tc_kernel<DS, DA, DW>;
+  auto k = rollout_tc_kernel<DS, DA, DW, F8>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
@@ -882,7 +898,10 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
   long long nclusters = items < nsm / 2 ? items : nsm / 2;
   if (max_clusters > 0 && nclusters > max_clusters) nclusters = max_clusters;
   const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total);
-  cudaError_t e = dims_a ? launch_tc<8, 2, 8>(p, smem, nclusters, s) : launch_tc<12, 3, 16>(p, smem, nclusters, s);
+  const bool f8 = p.scale_total > 0;
+  cudaError_t e;
+  if (dims_a) e = f8 ? launch_tc<8, 2, 8, true>(p, smem, nclusters, s) : launch_tc<8, 2, 8, false>(p, smem, nclusters, s);
+  else e = f8 ? launch_tc<12, 3, 16, true>(p, smem, nclusters, s) : launch_tc<12, 3, 16, false>(p, smem, nclusters, s);
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
 
