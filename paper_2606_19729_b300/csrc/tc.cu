@@ -68,6 +68,8 @@ struct TcLayer {
   int out_fp8;      // 1: this layer's epilogue writes the next layer's A operand as E4M3
   int ksteps;       // MMA K steps (32 K each for FP8, 16 for BF16)
   int scale_off;    // per-output-channel weight scales (FP8 layers), offset into the scale vector
+  int ngroups;      // 256-column groups of the output (2 for a 512-wide layer in the wide kernel)
+  int box_rows;     // rows of one CTA's TMA box: min(Npad, 256) / 2
   uint32_t idesc;
   int row0;         // first row of chunk 0 in the [rows][64] weight tensor
 };
@@ -266,7 +268,11 @@ __device__ __forceinline__ void write_rew_input(uint8_t* A, int r, const float* 
 
 // F8: the MLPs contain E4M3 layers (a separate instantiation keeps the BF16
 // form free of the FP8 code paths).
-template <int DS, int DA, int DW, bool F8>
+// WIDE: layers up to 512 wide. Each CTA owns one 128-row tile per work item
+// (256 rows per pair); the two 256-column TMEM halves and the two 64 KB A
+// buffers hold the two column halves of a layer (K up to 512); the epilogue
+// starts when both halves' MMAs are done (the next input overwrites A).
+template <int DS, int DA, int DW, bool F8, bool WIDE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     rollout_tc_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -294,7 +300,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     }
     for (int g = 0; g < 2; ++g) {
       ptx::mbar_init(ptx::smem_u32(&accf[g]), 1);
-      ptx::mbar_init(ptx::smem_u32(&ready[g]), 2 * kEpiWarpsPerTile);  // every epilogue warp of both CTAs
+      // every epilogue warp of both CTAs (of one tile, or of both groups in the wide kernel)
+      ptx::mbar_init(ptx::smem_u32(&ready[g]), (WIDE ? 4 : 2) * kEpiWarpsPerTile);
     }
     ptx::mbar_init(ptx::smem_u32(drain), 1);
     *abort_flag = 0;
@@ -325,8 +332,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         const int H = p.pl[item_planner(p, it)].H;
         for (int t = 0; t < H && ok; ++t)
           for (int l = 0; l < p.n_total && ok; ++l)
-            for (int g = 0; g < 2 && ok; ++g) {
+            for (int g = 0; g < (WIDE ? p.layers[l].ngroups : 2) && ok; ++g) {
               const TcLayer& L = p.layers[l];
+              // rows of this CTA's half of the chunk (wide: of column group g)
+              const int rowoff = (WIDE ? g * 256 : 0) + (int)rank * L.box_rows;
               for (int c = 0; c < L.nchunks; ++c) {
                 if (!bounded_wait(ptx::smem_u32(&empty[slot]), phase ^ 1, abort_flag, p.hdr, 10)) {
                   ok = false;
@@ -339,7 +348,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 const uint32_t full_leader = ptx::mapa_shared(full_local, 0);
                 for (int j = 0; j < ns; ++j)
                   ptx::tma_load_2d_pair(ring_addr + slot * kSlotBytes + j * L.slab_bytes, &p.tmap[l], 0,
-                                        L.row0 + (s0 + j) * L.Npad + (int)rank * (L.Npad >> 1), full_leader);
+                                        L.row0 + (s0 + j) * L.Npad + rowoff, full_leader);
                 last_round[slot] = (int)phase;
                 if (++slot == kStages) {
                   slot = 0;
@@ -381,11 +390,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
               const int kpc = 4 * p.layers[l].spc;  // K steps per chunk
               const uint32_t slab16 = (uint32_t)p.layers[l].slab_bytes >> 4;
               const uint32_t idesc = p.layers[l].idesc;
-              for (int g = 0; g < 2 && ok; ++g) {
+              for (int g = 0; g < (WIDE ? p.layers[l].ngroups : 2) && ok; ++g) {
                 // both CTAs' A operands of tile g are written and their accumulators read
+                // (wide: the whole layer input, once per layer)
                 const uint32_t nr = g ? nready1 : nready0;
                 const uint32_t rb = ptx::smem_u32(&ready[g]);
-                bool got = ptx::mbar_try_wait(rb, nr & 1);
+                bool got = (WIDE && g == 1) ? true : ptx::mbar_try_wait(rb, nr & 1);
                 if (!got) {
                   const long long t0 = clock64();
                   while (!(got = ptx::mbar_try_wait(rb, nr & 1))) {
@@ -401,10 +411,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                   ok = false;
                   break;
                 }
-                if (g) ++nready1;
-                else ++nready0;
-                ptx::tc_fence_after();
-                const uint64_t ad_tile = g ? adesc1 : adesc0;
+                if (!WIDE || g == 0) {
+                  if (g) ++nready1;
+                  else ++nready0;
+                  ptx::tc_fence_after();
+                }
+                const uint64_t ad_tile = (!WIDE && g) ? adesc1 : adesc0;
                 const uint32_t ad_lo = (uint32_t)ad_tile, ad_hi = (uint32_t)(ad_tile >> 32);
                 const uint32_t bd_lo = (uint32_t)bdesc0, bd_hi = (uint32_t)(bdesc0 >> 32);
                 const uint32_t d_tmem = tmem_base + g * 256;
@@ -475,28 +487,31 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     // rows); the two warps of a lane quadrant split the hidden columns. The
     // "sub 0" warps also own the row state (s_t, omega, reward, G).
     const int e = warp - 2;
-    const int g = e >> 3;                   // tile of this warp
+    const int g = e >> 3;                   // tile of this warp (wide kernel: column group)
     const int sub = (e >> 2) & 1;           // column half of the hidden layers
     const int q = warp & 3;                 // TMEM lane quadrant this warp may access
     const int r = 32 * q + lane;            // row within the tile
-    uint8_t* A = Abuf[g];
+    const bool owner = sub == 0 && (!WIDE || g == 0);  // holds the row state
+    uint8_t* A = WIDE ? Abuf[0] : Abuf[g];
     const uint32_t tm = tmem_base + (uint32_t)(g * 256) + ((uint32_t)(32 * q) << 16);
-    const uint32_t ready_remote = ptx::mapa_shared(ptx::smem_u32(&ready[g]), 0);  // the even CTA's barrier
-    const uint32_t acc_bar = ptx::smem_u32(&accf[g]);
-    uint32_t nacc = 0;
+    const uint32_t ready_remote = ptx::mapa_shared(ptx::smem_u32(&ready[WIDE ? 0 : g]), 0);  // even CTA's
+    const uint32_t acc_bar = ptx::smem_u32(&accf[WIDE ? 0 : g]);
+    const uint32_t acc_bar1 = ptx::smem_u32(&accf[1]);
+    uint32_t nacc = 0, nacc1 = 0;
     bool ok = true;
     for (long long it = cl; it < p.total_items && ok; it += ncl) {
       const int q = item_planner(p, it);
       const long long sp = it - (q ? p.item_end[q - 1] : 0);
       const TcPlanner& PL = p.pl[q];
       const int H = PL.H;
-      const long long row = sp * kSuperRows + g * (2 * kTileRows) + (long long)rank * kTileRows + r;
+      const long long row = WIDE ? sp * (2 * kTileRows) + (long long)rank * kTileRows + r
+                                 : sp * kSuperRows + g * (2 * kTileRows) + (long long)rank * kTileRows + r;
       const bool valid = row < PL.rows;
       const uint32_t n = valid ? (uint32_t)(row % PL.N) : 0u;
       const uint32_t k = valid ? (uint32_t)(row / PL.N) : 0u;
       const float* act_row = PL.actions + (size_t)k * H * DA;
       float s[DS], a[DA];
-      if (sub == 0) {
+      if (owner) {
 #pragma unroll
         for (int i = 0; i < DS; ++i) s[i] = valid ? __ldg(PL.particles + (size_t)n * DS + i) : 0.0f;
 #pragma unroll
@@ -515,6 +530,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
             break;
           }
           ++nacc;
+          const bool mine = !WIDE || g < L.ngroups;  // wide kernel: does this layer have column group g
+          // Wide layers: both column groups wait for both halves' MMAs, because
+          // the next layer's input overwrites the A slabs the second half reads.
+          if (WIDE && L.ngroups == 2) {
+            if (!bounded_wait(acc_bar1, nacc1 & 1, abort_flag, p.hdr, 32)) {
+              ok = false;
+              break;
+            }
+            ++nacc1;
+          }
           ptx::tc_fence_after();
           const float* bl = bias_s + L.bias_off;  // shared memory (L1 loads measured slower)
           // no A operand follows the final layer of the final step
@@ -522,10 +547,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           if (L.act >= 0) {
             // hidden layer: bias + activation -> BF16 A operand of the next layer,
             // 32 columns per TMEM load (measured faster than larger batches)
-            const int nc = L.Npad >> 6;  // 32-column batches per warp (half the columns)
-            for (int c = sub * nc; c < (sub + 1) * nc; ++c) {
+            const int gcols = (L.Npad > 256 ? 256 : L.Npad);  // columns of this warp's group
+            const int nc = gcols >> 6;                          // 32-column batches per warp
+            const int cbase = WIDE ? g * 8 : 0;                 // first batch of the group in the layer
+            for (int c = cbase + sub * nc; mine && c < cbase + (sub + 1) * nc; ++c) {
               float v[32];
-              ptx::tmem_ld32(tm + 32 * c, v);
+              ptx::tmem_ld32(tm + 32 * (c - cbase), v);
               ptx::tmem_wait_ld32(v);
               if (!F8) {
                 epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
@@ -537,7 +564,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 else epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
               }
             }
-          } else if (sub == 0 && l == p.n_gen - 1) {
+          } else if (owner && l == p.n_gen - 1) {
             // generator output: s_{t+1} (FP32, kept in registers)
             float v[32];
             ptx::tmem_ld16(tm, v);
@@ -563,7 +590,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
             } else {
               write_rew_input<DS, DA>(A, r, s, a);
             }
-          } else if (sub == 0) {
+          } else if (owner) {
             // reward output r_t: G += gamma^t r_t in FP64
             float v[16];
             ptx::tmem_ld16(tm, v);
@@ -584,7 +611,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           }
         }
       }
-      if (sub == 0 && valid && ok) PL.G[row] = Gacc;
+      if (owner && valid && ok) PL.G[row] = Gacc;
     }
   }
 
@@ -667,6 +694,7 @@ struct Plan {
   int total_rows;
   size_t wbytes, bias_bytes, total;
   bool ok;
+  bool wide;  // some layer is wider than 256: the wide kernel
 };
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -687,9 +715,10 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
       const int K = M->dims[l], N = M->dims[l + 1];
       const bool last = l == M->n_layers - 1;
       if (l == 0 && K > 64) return pl;
-      if (l > 0 && (K % 64 != 0 || K > 256)) return pl;
-      if (!last && (N % 64 != 0 || N > 256)) return pl;
+      if (l > 0 && (K % 64 != 0 || K > 512)) return pl;
+      if (!last && (N % 64 != 0 || N > 512 || (N > 256 && N != 512))) return pl;
       if (last && N > 32) return pl;
+      if (K > 256 || N > 256) pl.wide = true;
       TcLayer& L = pl.p.layers[nl];
       // FP8 form: hidden x hidden layers in E4M3, first and last layers in BF16
       L.fp8 = (M->prec == VOILA_FP8E4M3 && l > 0 && !last) ? 1 : 0;
@@ -698,14 +727,17 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
       L.ksteps = L.fp8 ? L.Kp / 32 : L.Kp / 16;
       L.Npad = last ? 32 : N;
       L.nslabs = (L.Kp + (L.fp8 ? 127 : 63)) / (L.fp8 ? 128 : 64);
-      L.slab_bytes = (L.Npad / 2) * 128;
+      L.slab_bytes = ((L.Npad > 256 ? 256 : L.Npad) / 2) * 128;
       L.spc = kSlotBytes / L.slab_bytes;
       if (L.spc > 4) L.spc = 4;  // at most 16 K steps per chunk
       if (L.spc > L.nslabs) L.spc = L.nslabs;
       L.nchunks = (L.nslabs + L.spc - 1) / L.spc;
       L.bias_off = boff;
       L.act = last ? -1 : M->act;
-      L.idesc = L.fp8 ? ptx::idesc_e4m3(256, L.Npad) : ptx::idesc_bf16(256, L.Npad);
+      const int ncols = L.Npad > 256 ? 256 : L.Npad;  // N of one MMA
+      L.ngroups = L.Npad > 256 ? 2 : 1;
+      L.box_rows = ncols / 2;
+      L.idesc = L.fp8 ? ptx::idesc_e4m3(256, ncols) : ptx::idesc_bf16(256, ncols);
       L.row0 = rows;
       PackTable& T = pl.pack;
       T.W[nl] = (const __nv_bfloat16*)M->W[l];
@@ -749,9 +781,9 @@ size_t tc_smem_bytes(int vec_floats) {
 
 // Launches one persistent CTA pair per co-resident cluster slot (at most
 // `max_clusters`, never more than there are super-pairs).
-template <int DS, int DA, int DW, bool F8>
+template <int DS, int DA, int DW, bool F8, bool WIDE>
 cudaError_t launch_tc(const TcParams& p, size_t smem, long long max_clusters, cudaStream_t s) {
-  auto k = rollout_tc_kernel<DS, DA, DW, F8>;
+  auto k = rollout_tc_kernel<DS, DA, DW, F8, WIDE>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
@@ -814,6 +846,7 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
   const bool dims_a = d_s == 8 && d_a == 2 && d_omega == 8;
   const bool dims_b = d_s == 12 && d_a == 3 && d_omega == 16;
   if (!dims_a && !dims_b) return VOILA_ERR_UNSUPPORTED;
+  if (pl.wide && !dims_b) return VOILA_ERR_UNSUPPORTED;  // the wide kernel is built for the sweep dimensions
   if ((uintptr_t)scratch % 16) return VOILA_ERR_WORKSPACE;  // TMA global base alignment
   TcParams& p = pl.p;
   // work table: planners with rows and steps, optionally longest horizon first
@@ -847,7 +880,8 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
     t.N = q.N;
     t.H = q.H;
     t.planner = q.planner;
-    items += (t.rows + kSuperRows - 1) / kSuperRows;
+    const long long item_rows = pl.wide ? 2 * kTileRows : kSuperRows;
+    items += (t.rows + item_rows - 1) / item_rows;
     p.item_end[j] = items;
   }
   p.P = nq;
@@ -876,7 +910,7 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
   for (int l = 0; l < p.n_total; ++l) {
     const cuuint64_t gdim[2] = {128, (cuuint64_t)pl.total_rows};  // bytes
     const cuuint64_t gstride[1] = {128};
-    const cuuint32_t box[2] = {128, (cuuint32_t)(p.layers[l].Npad / 2)};
+    const cuuint32_t box[2] = {128, (cuuint32_t)p.layers[l].box_rows};
     const cuuint32_t estride[2] = {1, 1};
     if (encode(&p.tmap[l], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)wst, gdim, gstride, box,
                                estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -900,8 +934,14 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
   const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total);
   const bool f8 = p.scale_total > 0;
   cudaError_t e;
-  if (dims_a) e = f8 ? launch_tc<8, 2, 8, true>(p, smem, nclusters, s) : launch_tc<8, 2, 8, false>(p, smem, nclusters, s);
-  else e = f8 ? launch_tc<12, 3, 16, true>(p, smem, nclusters, s) : launch_tc<12, 3, 16, false>(p, smem, nclusters, s);
+  if (dims_a)
+    e = f8 ? launch_tc<8, 2, 8, true, false>(p, smem, nclusters, s) : launch_tc<8, 2, 8, false, false>(p, smem, nclusters, s);
+  else if (!pl.wide)
+    e = f8 ? launch_tc<12, 3, 16, true, false>(p, smem, nclusters, s)
+           : launch_tc<12, 3, 16, false, false>(p, smem, nclusters, s);
+  else
+    e = f8 ? launch_tc<12, 3, 16, true, true>(p, smem, nclusters, s)
+           : launch_tc<12, 3, 16, false, true>(p, smem, nclusters, s);
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
 
