@@ -39,11 +39,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mid_bf16", "mid_fp32", "small_fp32", "batched"], default="mid_bf16")
+    ap.add_argument("--workload", choices=["mid_bf16", "mid_fp32", "small_fp32", "batched", "sweep"], default="mid_bf16")
     ap.add_argument("--cpu-seqs", type=int, default=8, help="action sequences in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-seqs", type=int, default=16, help="sequences for the FP32-form comparison (0: skip)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32/FP8 form comparison")
+    ap.add_argument("--sweep-err-seqs", type=int, default=2, help="sequences of the sweep's FP64 error sample")
     ap.add_argument("--N", type=int, default=None, help="override particles (profiling runs)")
     ap.add_argument("--K", type=int, default=None, help="override action sequences (profiling runs)")
     ap.add_argument("--H", type=int, default=None, help="override horizon (profiling runs)")
@@ -350,6 +351,83 @@ def run_batched(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_sweep(args, rank, world, local):
+    """Precision sweep (state 12, action 3, latent 16, 4x512 SiLU generator, GOAL
+    reward, 16384 x 2048 x 25): FP32 (CUDA cores, on a slice of sequences), BF16 and
+    FP8 (tensor cores, full workload), each form's return error against the FP64
+    oracle on the first `--sweep-err-seqs` sequences."""
+    import torch
+    from paper_2606_19729_b300 import voila as V
+    from paper_2606_19729_b300 import workloads as WL
+
+    torch.cuda.set_device(local)
+    wl = WL.sweep()
+    stream = torch.cuda.current_stream()
+    parts = torch.from_numpy(wl.particles).float().cuda()
+    acts = torch.from_numpy(wl.actions).float().cuda()
+    R = V.goal_reward(list(wl.goal))
+    forms = {}
+    Js = {}
+    for name, prec in (("bf16", V.BF16), ("fp8_e4m3", V.FP8E4M3), ("fp32_cuda_cores", V.FP32)):
+        g = V.DeviceMLP([torch.from_numpy(w) for w in wl.g_T.W], [torch.from_numpy(b) for b in wl.g_T.b],
+                        wl.g_T.act, prec)
+        K = wl.K if prec != V.FP32 else args.fp32_seqs
+        a = acts if prec != V.FP32 else acts[:K].contiguous()
+        J = torch.empty(K, dtype=torch.float64, device="cuda")
+        ws = V.alloc_workspace(V.voila_rollout_workspace_size(g, R, wl.N, K, wl.H))
+        V.voila_rollout(g, R, parts, None, a, wl.d_omega, wl.gamma, wl.seed, 0, J, None, None, ws)
+        torch.cuda.synchronize()
+        reps = max(1, args.steps) if prec != V.FP32 else 1
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        with Clocks(local) as clk:
+            for e0, e1 in ev:
+                e0.record(stream)
+                V.voila_rollout(g, R, parts, None, a, wl.d_omega, wl.gamma, wl.seed, 0, J, None, None, ws)
+                e1.record(stream)
+            torch.cuda.synchronize()
+        assert V.workspace_status(ws) == V.OK
+        sec = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3 / reps
+        fpt = sum(2 * w.shape[0] * w.shape[1] for w in wl.g_T.W)
+        forms[name] = {"value": wl.N * K * wl.H / sec, "unit": UNIT, "rollout_ms": 1e3 * sec,
+                       "achieved_tflops": fpt * wl.N * K * wl.H / sec / 1e12,
+                       "sample": f"{K} of {wl.K} sequences x {wl.N} particles x H={wl.H}", "clocks": clk.summary()}
+        Js[name] = J[: args.sweep_err_seqs].cpu().numpy()
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import voila_oracle as O
+        ks = list(range(args.sweep_err_seqs))
+        t0 = time.perf_counter()
+        Jo, _ = O.rollout(O.MLP(wl.g_T.W, wl.g_T.b, wl.g_T.act), O.Reward(O.REWARD_GOAL, wl.goal), wl.particles,
+                          wl.actions, wl.d_omega, wl.gamma, wl.seed, k_index=ks)
+        dt = time.perf_counter() - t0
+        for name in forms:
+            forms[name]["err_vs_fp64"] = float(np.max(np.abs(Js[name] - Jo)) / np.max(np.abs(Jo)))
+        cpu = {"value": len(ks) * wl.N * wl.H / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": f"FP64 oracle rollout of {len(ks)} sequences x {wl.N} particles x H={wl.H} in {dt:.1f} s"}
+    else:
+        cpu = None
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = peaks.get("bf16_tflops_sustained", 1400.0)
+    b = forms["bf16"]
+    line = {"metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": 1, "ms_per_step": b["rollout_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded inputs, random-init weights)",
+            "config": {"workload": "sweep: N=16384 x K=2048 x H=25, d_s=12 d_a=3 d_omega=16, generator 31x512x512x512x512x12 "
+                                   "SiLU, GOAL reward; forms FP32 / BF16 / FP8 e4m3 (per-channel scales)"},
+            "forms": forms,
+            "roofline": {"bound": "tensor", "achieved": b["achieved_tflops"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": b["achieved_tflops"] / peak, "traffic": None, "kernel": "rollout_tc_kernel (wide)"},
+            "gpu_launches": 3 * args.steps}
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -360,6 +438,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args, rank, world, local)
+        return
+    if args.workload == "sweep":
+        run_sweep(args, rank, world, local)
         return
 
     import torch
