@@ -51,6 +51,22 @@ def parse_args():
     return ap.parse_args()
 
 
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The slowest rank's time (the whole-job clock) across `world` replicas."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: int, world: int, slowest_s: float) -> float:
+    """Whole-job throughput of `world` independent replicas (weak scaling)."""
+    return units_per_rank * world / slowest_s
+
+
 def make_workload(name, args=None):
     from paper_2606_19729_b300 import workloads as WL
     kw = {}
@@ -518,14 +534,10 @@ def main():
     torch.cuda.synchronize()
     step_ms = [e[0].elapsed_time(e[2]) for e in ev]
     roll_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
     assert V.workspace_status(ws_b) == V.OK and V.workspace_status(ws_r) == V.OK
     trans_per_step = N * K * H
-    value = trans_per_step * args.steps * world / total_s
+    value = aggregate_rate(trans_per_step * args.steps, world, total_s)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     h_particles = torch.from_numpy(wl.particles).float().pin_memory()
@@ -553,12 +565,8 @@ def main():
         if i > 0:
             e2e_ev[i - 1][1].record(stream)
         torch.cuda.synchronize()
-    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = trans_per_step * args.steps * world / e2e_s
+    e2e_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3, world, dev)
+    e2e_value = aggregate_rate(trans_per_step * args.steps, world, e2e_s)
 
     peaks = {}
     try:
