@@ -429,3 +429,63 @@ def generator_forward_seeded(g_T: MLP, s: np.ndarray, a: np.ndarray, d_omega: in
     if d_omega > 0:
         parts.append(normals(seed, np.arange(B), 0, step, stream, planner, d_omega))
     return mlp_forward(g_T, np.concatenate(parts, axis=-1))
+
+
+# ---------------------------------------------------------------------------
+# Distillation (Sec. 4.2.1, Eq. 3): the teacher's deterministic ODE sampler
+# (DDIM, eta = 0) on a v-prediction denoiser, and the student's MSE loss.
+# Readings (the paper names a cosine schedule and v-prediction without the
+# step count; the workload fixes 32 steps and a linear beta from 1e-4 to 0.02):
+#   abar_t = prod_{s <= t} (1 - beta_s), t = 0 .. T-1, abar_{-1} = 1;
+#   x_{T-1} = omega (the student's latent noise, so s_hat is a function of
+#   (s, a, omega) as Eq. 3 needs); for t = T-1 .. 0, with v = v_T(s, a, x_t, t):
+#     x0 = sqrt(abar_t) x_t - sqrt(1 - abar_t) v,
+#     eps = sqrt(1 - abar_t) x_t + sqrt(abar_t) v,
+#     x_{t-1} = sqrt(abar_{t-1}) x0 + sqrt(1 - abar_{t-1}) eps;
+#   s_hat = x_{-1}. The step embedding is [sin(t f_i), cos(t f_i)],
+#   f_i = 10000^(-i/(dim/2)), i < dim/2, appended to [s; a; x_t].
+# ---------------------------------------------------------------------------
+def step_embedding(t: float, dim: int = 64) -> np.ndarray:
+    half = dim // 2
+    f = 10000.0 ** (-np.arange(half, dtype=np.float64) / half)
+    return np.concatenate([np.sin(t * f), np.cos(t * f)])
+
+
+def ddim_schedule(T: int = 32, beta0: float = 1e-4, beta1: float = 0.02) -> np.ndarray:
+    """abar_t for t = 0 .. T-1 (linear beta)."""
+    beta = np.linspace(beta0, beta1, T)
+    return np.cumprod(1.0 - beta)
+
+
+def ddim_sample(v_pred, s: np.ndarray, a: np.ndarray, omega: np.ndarray, abar: np.ndarray) -> np.ndarray:
+    """Deterministic DDIM from x = omega; v_pred(s, a, x, t) -> v (batched)."""
+    x = np.asarray(omega, np.float64).copy()
+    T = abar.shape[0]
+    for t in range(T - 1, -1, -1):
+        v = v_pred(s, a, x, t)
+        ab = abar[t]
+        ab_prev = abar[t - 1] if t > 0 else 1.0
+        x0 = math.sqrt(ab) * x - math.sqrt(1.0 - ab) * v
+        eps = math.sqrt(1.0 - ab) * x + math.sqrt(ab) * v
+        x = math.sqrt(ab_prev) * x0 + math.sqrt(1.0 - ab_prev) * eps
+    return x
+
+
+def teacher_v(teacher: MLP, emb_dim: int = 64):
+    """The denoising MLP v_T([s; a; x_t; emb(t)]) as a v-predictor."""
+    def f(s, a, x, t):
+        B = x.shape[0]
+        e = np.broadcast_to(step_embedding(t, emb_dim), (B, emb_dim))
+        return mlp_forward(teacher, np.concatenate([s, a, x, e], axis=-1))
+    return f
+
+
+def distill_loss_and_grad(student: MLP, s, a, omega, s_hat):
+    """L = mean_i ||s_hat_i - f_T(s_i, a_i, omega_i)||^2 (Eq. 3) and its gradient."""
+    x = np.concatenate([s, a, omega], axis=-1)
+    y = mlp_forward(student, x)
+    B = x.shape[0]
+    r = y - s_hat
+    L = float(np.sum(r * r) / B)
+    dX, dW, db = mlp_backward(student, x, 2.0 * r / B)
+    return L, dW, db

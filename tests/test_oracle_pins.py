@@ -363,3 +363,60 @@ def test_belief_update_identity_proposal_gaussian():
     # temperature lambda flattens: lambda -> large gives ESS -> N
     res2 = O.belief_update(g, O.Likelihood(O.LIK_GAUSSIAN, sigma=0.5), s, a, o, 0, 1e6, 5, 2)
     assert res2.ess > N * 0.999
+
+
+# --------------------------------------------------------------------------
+# Distillation pieces: schedule, embedding, DDIM sampler, loss gradient.
+# --------------------------------------------------------------------------
+def test_ddim_schedule_and_embedding():
+    ab = O.ddim_schedule(32)
+    assert ab.shape == (32,) and np.all(np.diff(ab) < 0) and 0 < ab[-1] < ab[0] < 1
+    assert abs(ab[0] - (1 - 1e-4)) < 1e-15 and abs(ab[1] - (1 - 1e-4) * (1 - (1e-4 + (0.02 - 1e-4) / 31))) < 1e-15
+    e = O.step_embedding(7.0, 64)
+    np.testing.assert_allclose(e[:32] ** 2 + e[32:] ** 2, 1.0, rtol=1e-14)
+    assert e[0] == math.sin(7.0) and e[32] == math.cos(7.0)
+    z = O.step_embedding(0.0, 64)
+    assert np.all(z[:32] == 0) and np.all(z[32:] == 1)
+
+
+def test_ddim_exact_predictor_recovers_target():
+    # A predictor that returns the exact v of a fixed clean sample x0*
+    # (v = sqrt(ab) eps - sqrt(1-ab) x0*, eps implied by x_t) must land on x0*.
+    rng = np.random.default_rng(11)
+    ab = O.ddim_schedule(32)
+    x_star = rng.normal(size=(5, 8))
+
+    def v_exact(s, a, x, t):
+        eps = (x - math.sqrt(ab[t]) * x_star) / math.sqrt(1 - ab[t])
+        return math.sqrt(ab[t]) * eps - math.sqrt(1 - ab[t]) * x_star
+
+    out = O.ddim_sample(v_exact, None, None, rng.normal(size=(5, 8)), ab)
+    np.testing.assert_allclose(out, x_star, rtol=1e-9, atol=1e-9)
+
+
+def test_ddim_zero_predictor_closed_form():
+    ab = O.ddim_schedule(32)
+    w = np.random.default_rng(12).normal(size=(4, 8))
+    out = O.ddim_sample(lambda s, a, x, t: np.zeros_like(x), None, None, w, ab)
+    f = 1.0
+    for t in range(31, -1, -1):
+        abp = ab[t - 1] if t > 0 else 1.0
+        f *= math.sqrt(abp * ab[t]) + math.sqrt((1 - abp) * (1 - ab[t]))
+    np.testing.assert_allclose(out, f * w, rtol=1e-12)
+
+
+def test_distill_gradient_matches_finite_differences():
+    rng = np.random.default_rng(13)
+    spec = WL.xavier_mlp(rng, [18, 16, 16, 8], O.ACT_SILU, WL.PREC_FP32)
+    m = O.MLP(spec.W, spec.b, O.ACT_SILU)
+    s, a, w = rng.normal(size=(16, 8)), rng.uniform(-1, 1, size=(16, 2)), rng.normal(size=(16, 8))
+    target = rng.normal(size=(16, 8))
+    L, dW, db = O.distill_loss_and_grad(m, s, a, w, target)
+    for l, (i, j) in [(0, (2, 5)), (2, (7, 3))]:
+        Wp = [x.copy() for x in spec.W]
+        Wm = [x.copy() for x in spec.W]
+        Wp[l][i, j] += 1e-6
+        Wm[l][i, j] -= 1e-6
+        Lp, _, _ = O.distill_loss_and_grad(O.MLP(Wp, spec.b, O.ACT_SILU), s, a, w, target)
+        Lm, _, _ = O.distill_loss_and_grad(O.MLP(Wm, spec.b, O.ACT_SILU), s, a, w, target)
+        assert abs((Lp - Lm) / 2e-6 - dW[l][i, j]) < 1e-6 * max(1.0, abs(dW[l][i, j]))
