@@ -489,3 +489,45 @@ def distill_loss_and_grad(student: MLP, s, a, omega, s_hat):
     L = float(np.sum(r * r) / B)
     dX, dW, db = mlp_backward(student, x, 2.0 * r / B)
     return L, dW, db
+
+
+# ---------------------------------------------------------------------------
+# Optimiser of the distillation step. The paper does not name one (reading:
+# Adam, Kingma and Ba, ICLR 2015, Algorithm 1, on FP32-kept master weights).
+# ---------------------------------------------------------------------------
+@dataclass
+class AdamState:
+    m: List[np.ndarray]
+    v: List[np.ndarray]
+    t: int = 0
+
+
+def adam_init(params: Sequence[np.ndarray]) -> AdamState:
+    return AdamState([np.zeros_like(p, dtype=np.float64) for p in params],
+                     [np.zeros_like(p, dtype=np.float64) for p in params], 0)
+
+
+def adam_step(params: Sequence[np.ndarray], grads: Sequence[np.ndarray], state: AdamState,
+              lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> List[np.ndarray]:
+    """Biased moment estimates, their bias corrections, and the update."""
+    state.t += 1
+    out = []
+    for i, (p, g) in enumerate(zip(params, grads)):
+        g = np.asarray(g, np.float64)
+        state.m[i] = beta1 * state.m[i] + (1.0 - beta1) * g
+        state.v[i] = beta2 * state.v[i] + (1.0 - beta2) * g * g
+        m_hat = state.m[i] / (1.0 - beta1 ** state.t)
+        v_hat = state.v[i] / (1.0 - beta2 ** state.t)
+        out.append(np.asarray(p, np.float64) - lr * m_hat / (np.sqrt(v_hat) + eps))
+    return out
+
+
+def flat_params(m: MLP) -> np.ndarray:
+    """[W_0, b_0, W_1, b_1, ...] flattened row-major."""
+    return np.concatenate([x for l in range(len(m.W)) for x in (m.W[l].ravel(), m.b[l].ravel())])
+
+
+def distill_targets(teacher: MLP, s, a, omega, T: int = 32, beta0: float = 1e-4, beta1: float = 0.02,
+                    emb_dim: int = 64) -> np.ndarray:
+    """s_hat' of Eq. 3: the teacher's DDIM sample from omega."""
+    return ddim_sample(teacher_v(teacher, emb_dim), s, a, omega, ddim_schedule(T, beta0, beta1))

@@ -420,3 +420,46 @@ def test_distill_gradient_matches_finite_differences():
         Lp, _, _ = O.distill_loss_and_grad(O.MLP(Wp, spec.b, O.ACT_SILU), s, a, w, target)
         Lm, _, _ = O.distill_loss_and_grad(O.MLP(Wm, spec.b, O.ACT_SILU), s, a, w, target)
         assert abs((Lp - Lm) / 2e-6 - dW[l][i, j]) < 1e-6 * max(1.0, abs(dW[l][i, j]))
+
+
+# --------------------------------------------------------------------------
+# Adam (Kingma and Ba, Algorithm 1): a closed form and an independent
+# implementation (torch.optim.Adam in FP64).
+# --------------------------------------------------------------------------
+def test_adam_constant_gradient_closed_form():
+    # with a constant gradient the bias-corrected moments are exactly g and g^2,
+    # so every step moves p by -lr g / (|g| + eps)
+    rng = np.random.default_rng(7)
+    p0 = [rng.standard_normal((5, 3)), rng.standard_normal(5)]
+    g = [rng.standard_normal((5, 3)), rng.standard_normal(5) * 1e-3]
+    st = O.adam_init(p0)
+    p = p0
+    lr, eps = 1e-2, 1e-6
+    for _ in range(7):
+        p = O.adam_step(p, g, st, lr=lr, beta1=0.8, beta2=0.95, eps=eps)
+    for pi, p0i, gi in zip(p, p0, g):
+        np.testing.assert_allclose(pi, p0i - 7 * lr * gi / (np.abs(gi) + eps), rtol=0, atol=1e-12)
+
+
+def test_adam_matches_torch_optim():
+    rng = np.random.default_rng(8)
+    shapes = [(4, 6), (4,), (2, 4), (2,)]
+    p0 = [rng.standard_normal(s) for s in shapes]
+    tp = [torch.tensor(x, dtype=torch.float64, requires_grad=True) for x in p0]
+    opt = torch.optim.Adam(tp, lr=3e-3, betas=(0.9, 0.99), eps=1e-7)
+    st = O.adam_init(p0)
+    p = p0
+    for _ in range(5):
+        g = [rng.standard_normal(s) for s in shapes]
+        for t, gi in zip(tp, g):
+            t.grad = torch.tensor(gi)
+        opt.step()
+        p = O.adam_step(p, g, st, lr=3e-3, beta1=0.9, beta2=0.99, eps=1e-7)
+    for pi, t in zip(p, tp):
+        np.testing.assert_allclose(pi, t.detach().numpy(), rtol=1e-13, atol=1e-15)
+
+
+def test_flat_params_layout():
+    m = O.MLP([np.arange(6.0).reshape(3, 2), np.arange(3.0).reshape(1, 3)],
+              [np.array([10.0, 11.0, 12.0]), np.array([20.0])], act=O.ACT_SILU)
+    np.testing.assert_array_equal(O.flat_params(m), [0, 1, 2, 3, 4, 5, 10, 11, 12, 0, 1, 2, 20])
