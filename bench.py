@@ -39,12 +39,14 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mid_bf16", "mid_fp32", "small_fp32", "batched", "sweep"], default="mid_bf16")
+    ap.add_argument("--workload", choices=["mid_bf16", "mid_fp32", "small_fp32", "batched", "sweep", "distill"], default="mid_bf16")
     ap.add_argument("--cpu-seqs", type=int, default=8, help="action sequences in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-seqs", type=int, default=16, help="sequences for the FP32-form comparison (0: skip)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32/FP8 form comparison")
     ap.add_argument("--sweep-err-seqs", type=int, default=2, help="sequences of the sweep's FP64 error sample")
+    ap.add_argument("--distill-cpu-rows", type=int, default=48, help="rows of the distillation oracle sample")
+    ap.add_argument("--B", type=int, default=None, help="override the distillation batch (profiling runs)")
     ap.add_argument("--N", type=int, default=None, help="override particles (profiling runs)")
     ap.add_argument("--K", type=int, default=None, help="override action sequences (profiling runs)")
     ap.add_argument("--H", type=int, default=None, help="override horizon (profiling runs)")
@@ -444,6 +446,120 @@ def run_sweep(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+# FP32 FMA peak of the CUDA cores: 148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz.
+FP32_ALU_TFLOPS = 148 * 128 * 2 * 2032e6 / 1e12
+
+
+def distill_flops(wl):
+    """Algorithmic FLOPs per sample: T teacher calls, student forward, backward (2x forward)."""
+    teacher = sum(2 * w.shape[0] * w.shape[1] for w in wl.teacher.W) * wl.T
+    student = sum(2 * w.shape[0] * w.shape[1] for w in wl.student.W)
+    return teacher, student * 3
+
+
+def run_distill(args, rank, world, local):
+    """Distillation training step (Eq. 3), B=65536: teacher DDIM targets (32 steps of
+    the 82-512-512-512-8 SiLU denoiser), student 18-256-256-256-8 forward with BF16
+    weights, MSE, hand-written backward, Adam on FP32 master weights."""
+    import torch
+    from paper_2606_19729_b300 import voila as V
+    from paper_2606_19729_b300 import workloads as WL
+    from paper_2606_19729_b300.distill import Distiller
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = WL.distill(B=args.B or 65536)
+    B = wl.B
+    stream = torch.cuda.current_stream()
+    teacher = V.DeviceMLP.from_spec(wl.teacher)
+    d = Distiller(teacher, [torch.from_numpy(w) for w in wl.student.W], [torch.from_numpy(b) for b in wl.student.b],
+                  wl.student.act, V.BF16, B, wl.T, wl.beta0, wl.beta1, wl.emb_dim, lr=wl.lr)
+    S, A, om = (torch.from_numpy(x).float().cuda() for x in (wl.S, wl.A, wl.omega))
+    losses = torch.empty(args.warmup + args.steps, dtype=torch.float64, device="cuda")
+    for i in range(args.warmup):
+        d.step(S, A, om, loss_out=losses[i:i + 1])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        t_all0 = torch.cuda.Event(enable_timing=True)
+        t_all1 = torch.cuda.Event(enable_timing=True)
+        t_all0.record(stream)
+        for i, (e0, e1) in enumerate(ev):
+            e0.record(stream)
+            d.step(S, A, om, loss_out=losses[args.warmup + i:args.warmup + i + 1])
+            e1.record(stream)
+        t_all1.record(stream)
+        torch.cuda.synchronize()
+    sec = max_over_ranks(t_all0.elapsed_time(t_all1) / 1e3, world, torch.device("cuda", local))
+    value = aggregate_rate(B * args.steps, world, sec)
+    lo = losses.cpu().numpy()
+    # the dominant kernel alone: the teacher sampler, same inputs, CUDA events on its stream
+    Y = torch.empty(B, wl.d_x, device="cuda")
+    reps = max(3, args.steps)
+    tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for e0, e1 in tev:
+        e0.record(stream)
+        V.voila_ddim_sample(teacher, S, A, om, wl.T, wl.beta0, wl.beta1, wl.emb_dim, Y, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ddim_s = sum(e0.elapsed_time(e1) for e0, e1 in tev) / 1e3 / reps
+    f_teacher, f_student = distill_flops(wl)
+    achieved = f_teacher * B / ddim_s / 1e12
+    # end to end: inputs copied from pinned host memory each step, the loss read back
+    hS, hA, hO = (x.cpu().pin_memory() for x in (S, A, om))
+    hl = torch.empty(1, dtype=torch.float64).pin_memory()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, args.steps)
+    for _ in range(e2e_steps):
+        dS, dA, dO = (x.to("cuda", non_blocking=True) for x in (hS, hA, hO))
+        l = d.step(dS, dA, dO)
+        hl.copy_(l, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_sec = max_over_ranks((time.perf_counter() - t0), world, torch.device("cuda", local))
+    line = {"metric": "distillation samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded inputs, random-init teacher and student)",
+            "config": {"workload": f"distill: B={B}, teacher 82x512x512x512x8 SiLU + 64-d step embedding, "
+                                   f"{wl.T} DDIM steps, linear beta 1e-4..0.02; student 18x256x256x256x8 SiLU, "
+                                   "BF16 forward copy, FP32 master, Adam",
+                       "l2": "inputs resident; the step's working set (teacher activations, saved "
+                             "pre-activations, gradients) exceeds L2"},
+            "loss": {"first": float(lo[0]), "last": float(lo[-1])},
+            "teacher_ms": 1e3 * ddim_s,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_ALU_TFLOPS, "traffic": None, "kernel": "ddim_kernel",
+                         "peak_kind": "FP32 FMA lanes x max SM clock (derived)"},
+            "e2e": {"value": B * e2e_steps * world / e2e_sec, "unit": "samples/s",
+                    "h2d_bytes_per_step": int(sum(x.numel() * 4 for x in (hS, hA, hO))), "d2h_bytes_per_step": 8},
+            "gpu_launches": None, "clocks": clk.summary()}
+    n_layers = len(wl.student.W)
+    # per step: ddim 1, concat 1, fwd L, mse 2, bwd (L x 3 + (L-1) delta), adam 1, publish 1
+    line["gpu_launches"] = args.steps * (1 + 1 + n_layers + 2 + 3 * n_layers + (n_layers - 1) + 2)
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import voila_oracle as O
+        rows = args.distill_cpu_rows
+        t0 = time.perf_counter()
+        tm = O.MLP(wl.teacher.W, wl.teacher.b, wl.teacher.act)
+        fwd = O.MLP([WL.round_bf16(w) for w in wl.student.W], wl.student.b, wl.student.act)
+        s_hat = O.distill_targets(tm, wl.S[:rows], wl.A[:rows], wl.omega[:rows], wl.T, wl.beta0, wl.beta1,
+                                  wl.emb_dim)
+        L, gW, gb = O.distill_loss_and_grad(fwd, wl.S[:rows], wl.A[:rows], wl.omega[:rows], s_hat)
+        p0 = O.flat_params(O.MLP(wl.student.W, wl.student.b, wl.student.act))
+        g = np.concatenate([x for l in range(len(gW)) for x in (gW[l].ravel(), gb[l].ravel())])
+        O.adam_step([p0], [g], O.adam_init([p0]), lr=wl.lr)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": rows / dt, "unit": "samples/s", "cores": blas_threads(), "kind": "oracle",
+                                "sample": f"FP64 oracle distillation step on {rows} of {B} rows "
+                                          f"(DDIM targets, loss, gradient, Adam) in {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -457,6 +573,9 @@ def main():
         return
     if args.workload == "sweep":
         run_sweep(args, rank, world, local)
+        return
+    if args.workload == "distill":
+        run_distill(args, rank, world, local)
         return
 
     import torch

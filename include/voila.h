@@ -16,6 +16,8 @@
  *                        weight with l, normalise, resample systematically
  *                        (Sec. 3, belief operator of Sec. 2.1).
  *   voila_generator_fwd  batched forward of a generator MLP (Eq. 2 / Eq. 5).
+ *   voila_generator_bwd  its hand-written backward, and voila_ddim_sample the
+ *                        teacher sampler, for the distillation step (Eq. 3).
  *   voila_philox_fill    raw Philox4x32-10 words, for checking the noise stream.
  *
  * Conventions shared by every call:
@@ -311,6 +313,115 @@ voila_status voila_generator_fwd_seeded(const voila_mlp* mlp, const float* S, co
                                         int32_t d_omega, uint64_t seed, uint32_t stream_id,
                                         uint32_t step, uint32_t planner_id, float* Y,
                                         voila_stream_t stream);
+
+/*
+ * Training forward of a generator MLP, the first half of the distillation step
+ * (Eq. 3): Y = mlp(X) as voila_generator_fwd, and the pre-activations of every
+ * hidden layer kept for voila_generator_bwd.
+ *   X [B][dims[0]], Y [B][dims[L]] float (device), L = n_layers.
+ *   saved  [B][dims[1] + ... + dims[L-1]] float (device) or NULL: row b holds
+ *          z_1(b), ..., z_{L-1}(b) side by side, z_l = h_{l-1} W_l^T + b_l.
+ *   workspace  device, >= 2 * B * max_l dims[l] * 4 bytes (caller-owned).
+ * mlp->prec FP32 or BF16 (BF16 weights, FP32 arithmetic); FP8 returns
+ * VOILA_ERR_UNSUPPORTED. B = 0 returns VOILA_OK with no launch.
+ */
+voila_status voila_generator_fwd_train(const voila_mlp* mlp, const float* X, int32_t B, float* Y,
+                                       float* saved, void* workspace, size_t ws_bytes,
+                                       voila_stream_t stream);
+
+/* Workspace of voila_generator_bwd for a batch of B rows, in bytes. */
+voila_status voila_generator_bwd_workspace_size(const voila_mlp* mlp, int32_t B, size_t* bytes);
+
+/*
+ * Hand-written backward of the generator MLP for the distillation loss of
+ * Eq. 3. With delta_L = dY and h_l = act(z_l) (h_0 = X):
+ *   dW_l = delta_l^T h_{l-1},  db_l = sum over rows of delta_l,
+ *   delta_{l-1} = (delta_l W_l) * act'(z_{l-1}),  dX = delta_1 W_1.
+ *   X, saved   the inputs and `saved` of voila_generator_fwd_train (device).
+ *   dY [B][dims[L]] float (device): gradient of the loss with respect to Y.
+ *   dX [B][dims[0]] float (device) or NULL (not computed).
+ *   dW, db     HOST arrays of L device pointers: dW[l] [dims[l+1]][dims[l]],
+ *              db[l] [dims[l+1]] float, overwritten (not accumulated).
+ * Batch sums run over fixed chunks of 1024 rows added in chunk order: the
+ * result is the same on every run. The weights read are the ones given
+ * (BF16 weights when prec is BF16); the gradients are FP32.
+ */
+voila_status voila_generator_bwd(const voila_mlp* mlp, const float* X, const float* saved,
+                                 const float* dY, int32_t B, float* dX, float* const* dW,
+                                 float* const* db, void* workspace, size_t ws_bytes,
+                                 voila_stream_t stream);
+
+/*
+ * Deterministic (eta = 0) DDIM sampler of the conditional diffusion teacher
+ * (Sec. 4.2.1): the targets s'_hat of Eq. 3. For each row i, x_T-1 = omega[i]
+ * and for t = T-1 ... 0, with v = teacher([S[i]; A[i]; x_t; e(t)]),
+ *   x0 = sqrt(abar_t) x_t - sqrt(1 - abar_t) v,
+ *   eps = sqrt(1 - abar_t) x_t + sqrt(abar_t) v,
+ *   x_{t-1} = sqrt(abar_{t-1}) x0 + sqrt(1 - abar_{t-1}) eps   (abar_{-1} = 1),
+ * abar_t = prod_{u<=t} (1 - beta_u), beta linear from beta0 to beta1 over T
+ * steps, e(t) = [sin(t f_i); cos(t f_i)], f_i = 10000^(-i / (emb_dim/2)).
+ * Y[i] = x_{-1} = x0 of the last step.
+ *   S [B][d_s], A [B][d_a], omega [B][d_x], Y [B][d_x] float (device).
+ *   teacher dims[0] = d_s + d_a + d_x + emb_dim, dims[L] = d_x.
+ * Limits: 1 <= T <= 64, 1 <= d_x <= 16, emb_dim even and <= 64, widths <= 512.
+ * The paper names a cosine schedule; the linear one is the workload's.
+ */
+voila_status voila_ddim_sample(const voila_mlp* teacher, const float* S, const float* A,
+                               const float* omega, int32_t B, int32_t d_s, int32_t d_a,
+                               int32_t d_x, int32_t T, double beta0, double beta1,
+                               int32_t emb_dim, float* Y, voila_stream_t stream);
+
+/*
+ * One Adam step (Kingma & Ba, 2015) on a flat FP32 vector of n parameters,
+ * in place: m = beta1 m + (1 - beta1) g,  v = beta2 v + (1 - beta2) g^2,
+ * p -= lr (m / (1 - beta1^step)) / (sqrt(v / (1 - beta2^step)) + eps).
+ * params, grads, m, v: device float [n]; m and v start at zero; step >= 1.
+ * The paper does not name its optimiser; Adam is this library's choice.
+ */
+voila_status voila_adam_step(float* params, const float* grads, float* m, float* v, int64_t n,
+                             float lr, float beta1, float beta2, float eps, int32_t step,
+                             voila_stream_t stream);
+
+typedef struct {
+  int32_t T;        /* sampler steps, 1 .. 64 */
+  double beta0;     /* linear beta schedule from beta0 ... */
+  double beta1;     /* ... to beta1 */
+  int32_t emb_dim;  /* step-embedding width, even, <= 64 */
+} voila_ddim;
+
+typedef struct {
+  float lr, beta1, beta2, eps;
+  int32_t step;     /* 1-based step count (bias correction) */
+} voila_adam;
+
+/* Workspace of voila_distill_step for B rows and output width d_x, in bytes. */
+voila_status voila_distill_step_workspace_size(const voila_mlp* student, int32_t B, int32_t d_x,
+                                               size_t* bytes);
+
+/*
+ * One distillation training step of the transition generator (Eq. 3):
+ *   1. s_hat = voila_ddim_sample(teacher, S, A, omega)        (teacher targets)
+ *   2. Y = student([S; A; omega])                              (Eq. 2)
+ *   3. loss = (1/B) sum_b ||Y_b - s_hat_b||^2, dY = 2 (Y - s_hat) / B
+ *   4. gradients by voila_generator_bwd
+ *   5. voila_adam_step on `master`, then the student's W (in its precision)
+ *      and b are overwritten from the updated master.
+ *   master, adam_m, adam_v  device float [n_params], the flat layout
+ *            [W_0, b_0, W_1, b_1, ...] with W_l [dims[l+1]][dims[l]].
+ *   student  the forward copy: its W and b arrays are WRITTEN by step 5
+ *            (the const in voila_mlp is not honoured here). FP32 or BF16.
+ *   S [B][d_s], A [B][d_a], omega [B][d_x] float (device).
+ *   loss_out  device double, the loss of step 3 (before the update).
+ *   grad_out  device float [n_params] or NULL: receives the gradient.
+ *   workspace device, 256-byte aligned, voila_distill_step_workspace_size bytes.
+ * Deterministic: every reduction runs in a fixed order.
+ */
+voila_status voila_distill_step(const voila_mlp* teacher, const voila_mlp* student,
+                                const voila_ddim* ddim, float* master, float* adam_m,
+                                float* adam_v, const voila_adam* opt, const float* S,
+                                const float* A, const float* omega, int32_t B, int32_t d_s,
+                                int32_t d_a, int32_t d_x, double* loss_out, float* grad_out,
+                                void* workspace, size_t ws_bytes, voila_stream_t stream);
 
 /*
  * Raw Philox4x32-10 words: out[4 i + j] = word j of counter (i, c1, c2, c3),

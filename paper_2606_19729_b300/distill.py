@@ -1,0 +1,116 @@
+"""Distillation of the transition generator (Eq. 3) on the library's kernels.
+
+``GeneratorFn`` wraps ``voila_generator_fwd_train`` / ``voila_generator_bwd``
+as a ``torch.autograd.Function`` for callers that build their own loss.
+``Distiller`` keeps the FP32 master weights, the Adam moments and the
+forward copy of a student generator and runs whole training steps through
+``voila_distill_step`` (teacher DDIM targets, forward, MSE, backward, Adam).
+"""
+from __future__ import annotations
+
+from typing import List, Optional, Sequence, Tuple
+
+import torch
+
+from . import voila as V
+
+
+def flat_views(flat: torch.Tensor, dims: Sequence[int]) -> List[Tuple[torch.Tensor, torch.Tensor]]:
+    """(W_l, b_l) views of a flat vector laid out [W_0, b_0, W_1, b_1, ...]."""
+    out, o = [], 0
+    for din, dout in zip(dims[:-1], dims[1:]):
+        W = flat[o:o + din * dout].view(dout, din)
+        o += din * dout
+        b = flat[o:o + dout]
+        o += dout
+        out.append((W, b))
+    if o != flat.numel():
+        raise ValueError("flat vector does not match the layer widths")
+    return out
+
+
+def n_params(dims: Sequence[int]) -> int:
+    return sum(din * dout + dout for din, dout in zip(dims[:-1], dims[1:]))
+
+
+class GeneratorFn(torch.autograd.Function):
+    """Y = mlp(X) with the hand-written backward.
+
+    ``params`` are tensors shaped like W_0, b_0, W_1, b_1, ... (for example FP32
+    master weights); they receive the gradients. The forward reads the weights
+    held by ``mlp`` (its FP32 or BF16 copy), which the caller keeps in step
+    with ``params``.
+    """
+
+    @staticmethod
+    def forward(ctx, X: torch.Tensor, mlp: V.DeviceMLP, *params: torch.Tensor) -> torch.Tensor:
+        X = X.contiguous()
+        B = X.shape[0]
+        dims = mlp.dims
+        Y = torch.empty(B, dims[-1], device=X.device, dtype=torch.float32)
+        saved = torch.empty(B, max(sum(dims[1:-1]), 1), device=X.device, dtype=torch.float32)
+        ws = V.alloc_workspace(2 * B * max(dims) * 4)
+        V.voila_generator_fwd_train(mlp, X, Y, saved, ws)
+        ctx.save_for_backward(X, saved)
+        ctx.mlp = mlp
+        return Y
+
+    @staticmethod
+    def backward(ctx, dY: torch.Tensor):
+        X, saved = ctx.saved_tensors
+        mlp = ctx.mlp
+        dims = mlp.dims
+        dev = X.device
+        dW = [torch.empty(dout, din, device=dev) for din, dout in zip(dims[:-1], dims[1:])]
+        db = [torch.empty(dout, device=dev) for dout in dims[1:]]
+        dX = torch.empty_like(X) if ctx.needs_input_grad[0] else None
+        ws = V.alloc_workspace(V.voila_generator_bwd_workspace_size(mlp, X.shape[0]))
+        V.voila_generator_bwd(mlp, X, saved, dY.contiguous().float(), dX, dW, db, ws)
+        grads = [g for pair in zip(dW, db) for g in pair]
+        return (dX, None, *grads)
+
+
+def generator(X: torch.Tensor, mlp: V.DeviceMLP, *params: torch.Tensor) -> torch.Tensor:
+    return GeneratorFn.apply(X, mlp, *params)
+
+
+class Distiller:
+    """Distillation training state of one student generator (Eq. 3).
+
+    teacher      DeviceMLP of the denoiser v_T([s; a; x_t; e(t)]).
+    W, b         the student's initial FP32 weights (host or device tensors).
+    prec         precision of the student's forward copy (FP32 or BF16).
+    """
+
+    def __init__(self, teacher: V.DeviceMLP, W: Sequence[torch.Tensor], b: Sequence[torch.Tensor], act: int,
+                 prec: int, B: int, T: int = 32, beta0: float = 1e-4, beta1: float = 0.02, emb_dim: int = 64,
+                 lr: float = 1e-3, betas=(0.9, 0.999), eps: float = 1e-8):
+        self.teacher = teacher
+        dims = [W[0].shape[1]] + [w.shape[0] for w in W]
+        self.dims = dims
+        self.master = torch.cat([t for l in range(len(W)) for t in
+                                 (torch.as_tensor(W[l]).reshape(-1), torch.as_tensor(b[l]).reshape(-1))]
+                                ).to(device="cuda", dtype=torch.float32).contiguous()
+        self.m = torch.zeros_like(self.master)
+        self.v = torch.zeros_like(self.master)
+        views = flat_views(self.master, dims)
+        self.student = V.DeviceMLP([w for w, _ in views], [bb for _, bb in views], act, prec)
+        self.ddim = V.voila_ddim(T, beta0, beta1, emb_dim)
+        self.lr, self.betas, self.eps = lr, betas, eps
+        self.t = 0
+        self.B = B
+        self.d_x = dims[-1]
+        self.ws = V.alloc_workspace(V.voila_distill_step_workspace_size(self.student, B, self.d_x))
+        self.loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def step(self, S: torch.Tensor, A: torch.Tensor, omega: torch.Tensor, grad_out: Optional[torch.Tensor] = None,
+             loss_out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """One step; returns the (device) loss before the update."""
+        if omega.shape[0] > self.B:
+            raise ValueError("batch larger than the workspace was sized for")
+        self.t += 1
+        opt = V.voila_adam(self.lr, self.betas[0], self.betas[1], self.eps, self.t)
+        out = self.loss if loss_out is None else loss_out
+        V.voila_distill_step(self.teacher, self.student, self.ddim, self.master, self.m, self.v, opt, S, A, omega,
+                             out, grad_out, self.ws, stream)
+        return out

@@ -52,6 +52,14 @@ class voila_likelihood(ctypes.Structure):
     _fields_ = [("kind", c_int32), ("sigma", c_float), ("mlp", POINTER(voila_mlp))]
 
 
+class voila_ddim(ctypes.Structure):
+    _fields_ = [("T", c_int32), ("beta0", c_double), ("beta1", c_double), ("emb_dim", c_int32)]
+
+
+class voila_adam(ctypes.Structure):
+    _fields_ = [("lr", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float), ("step", c_int32)]
+
+
 def _sig(name, res, *args):
     f = getattr(_lib, name)
     f.restype = res
@@ -85,6 +93,18 @@ _lib_belief_noalloc = _sig("voila_belief_update_noalloc", c_int32, POINTER(voila
 _lib_fwd = _sig("voila_generator_fwd", c_int32, POINTER(voila_mlp), _P, c_int32, _P, _P)
 _lib_fwd_seeded = _sig("voila_generator_fwd_seeded", c_int32, POINTER(voila_mlp), _P, _P, c_int32, c_int32,
                        c_int32, c_int32, c_int32, c_uint64, c_uint32, c_uint32, c_uint32, _P, _P)
+_lib_fwd_train = _sig("voila_generator_fwd_train", c_int32, POINTER(voila_mlp), _P, c_int32, _P, _P, _P, c_size_t,
+                      _P)
+_lib_bwd_ws = _sig("voila_generator_bwd_workspace_size", c_int32, POINTER(voila_mlp), c_int32, POINTER(c_size_t))
+_lib_bwd = _sig("voila_generator_bwd", c_int32, POINTER(voila_mlp), _P, _P, _P, c_int32, _P, POINTER(c_void_p),
+                POINTER(c_void_p), _P, c_size_t, _P)
+_lib_ddim = _sig("voila_ddim_sample", c_int32, POINTER(voila_mlp), _P, _P, _P, c_int32, c_int32, c_int32, c_int32,
+                 c_int32, c_double, c_double, c_int32, _P, _P)
+_lib_adam = _sig("voila_adam_step", c_int32, _P, _P, _P, _P, c_int64, c_float, c_float, c_float, c_float, c_int32, _P)
+_lib_distill_ws = _sig("voila_distill_step_workspace_size", c_int32, POINTER(voila_mlp), c_int32, c_int32,
+                       POINTER(c_size_t))
+_lib_distill = _sig("voila_distill_step", c_int32, POINTER(voila_mlp), POINTER(voila_mlp), POINTER(voila_ddim), _P, _P,
+                    _P, POINTER(voila_adam), _P, _P, _P, c_int32, c_int32, c_int32, c_int32, _P, _P, _P, c_size_t, _P)
 _lib_philox = _sig("voila_philox_fill", c_int32, c_uint64, c_uint32, c_uint32, c_uint32, _P, c_int64, _P)
 _lib_normal = _sig("voila_normal_fill", c_int32, c_uint64, c_uint32, c_uint32, c_uint32, c_uint32, c_int32,
                    _P, c_int64, _P)
@@ -328,3 +348,63 @@ def voila_normal_fill(seed: int, c1: int, c2: int, stream_id: int, planner_id: i
     n, dim = out.shape
     _check(_lib_normal(seed, c1, c2, stream_id, planner_id, dim, _ptr(out, torch.float32), n, _stream(stream)),
            "voila_normal_fill")
+
+
+def voila_generator_fwd_train(mlp: DeviceMLP, X: torch.Tensor, Y: torch.Tensor, saved: Optional[torch.Tensor],
+                              workspace: torch.Tensor, stream=None):
+    _check(_lib_fwd_train(ctypes.byref(mlp.desc), _ptr(X, torch.float32), X.shape[0], _ptr(Y, torch.float32),
+                          _ptr(saved, torch.float32), _ptr(workspace), workspace.numel(), _stream(stream)),
+           "voila_generator_fwd_train")
+
+
+def voila_generator_bwd_workspace_size(mlp: DeviceMLP, B: int) -> int:
+    n = c_size_t(0)
+    _check(_lib_bwd_ws(ctypes.byref(mlp.desc), B, ctypes.byref(n)), "voila_generator_bwd_workspace_size")
+    return n.value
+
+
+def voila_generator_bwd(mlp: DeviceMLP, X: torch.Tensor, saved: Optional[torch.Tensor], dY: torch.Tensor,
+                        dX: Optional[torch.Tensor], dW: Sequence[torch.Tensor], db: Sequence[torch.Tensor],
+                        workspace: torch.Tensor, stream=None):
+    L = len(mlp.W)
+    if len(dW) != L or len(db) != L:
+        raise ValueError("one dW and one db per layer")
+    pw = (c_void_p * L)(*[_ptr(x, torch.float32).value for x in dW])
+    pb = (c_void_p * L)(*[_ptr(x, torch.float32).value for x in db])
+    _check(_lib_bwd(ctypes.byref(mlp.desc), _ptr(X, torch.float32), _ptr(saved, torch.float32),
+                    _ptr(dY, torch.float32), X.shape[0], _ptr(dX, torch.float32), pw, pb, _ptr(workspace),
+                    workspace.numel(), _stream(stream)), "voila_generator_bwd")
+
+
+def voila_ddim_sample(teacher: DeviceMLP, S: torch.Tensor, A: torch.Tensor, omega: torch.Tensor, T: int,
+                      beta0: float, beta1: float, emb_dim: int, Y: torch.Tensor, stream=None):
+    B, d_x = omega.shape
+    _check(_lib_ddim(ctypes.byref(teacher.desc), _ptr(S, torch.float32), _ptr(A, torch.float32),
+                     _ptr(omega, torch.float32), B, S.shape[1], A.shape[1], d_x, T, beta0, beta1, emb_dim,
+                     _ptr(Y, torch.float32), _stream(stream)), "voila_ddim_sample")
+
+
+def voila_adam_step(params: torch.Tensor, grads: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float,
+                    beta1: float, beta2: float, eps: float, step: int, stream=None):
+    _check(_lib_adam(_ptr(params, torch.float32), _ptr(grads, torch.float32), _ptr(m, torch.float32),
+                     _ptr(v, torch.float32), params.numel(), lr, beta1, beta2, eps, step, _stream(stream)),
+           "voila_adam_step")
+
+
+def voila_distill_step_workspace_size(student: DeviceMLP, B: int, d_x: int) -> int:
+    n = c_size_t(0)
+    _check(_lib_distill_ws(ctypes.byref(student.desc), B, d_x, ctypes.byref(n)), "voila_distill_step_workspace_size")
+    return n.value
+
+
+def voila_distill_step(teacher: DeviceMLP, student: DeviceMLP, ddim: voila_ddim, master: torch.Tensor,
+                       adam_m: torch.Tensor, adam_v: torch.Tensor, opt: voila_adam, S: torch.Tensor,
+                       A: torch.Tensor, omega: torch.Tensor, loss_out: torch.Tensor,
+                       grad_out: Optional[torch.Tensor], workspace: torch.Tensor, stream=None):
+    B, d_x = omega.shape
+    _check(_lib_distill(ctypes.byref(teacher.desc), ctypes.byref(student.desc), ctypes.byref(ddim),
+                        _ptr(master, torch.float32), _ptr(adam_m, torch.float32), _ptr(adam_v, torch.float32),
+                        ctypes.byref(opt), _ptr(S, torch.float32), _ptr(A, torch.float32),
+                        _ptr(omega, torch.float32), B, S.shape[1], A.shape[1], d_x, _ptr(loss_out, torch.float64),
+                        _ptr(grad_out, torch.float32), _ptr(workspace), workspace.numel(), _stream(stream)),
+           "voila_distill_step")

@@ -146,6 +146,44 @@ def true_state(rng_seed: int, d_s: int, scale: float) -> np.ndarray:
     return round_to(rng.normal(0.0, scale, size=(d_s,)), PREC_FP32)
 
 
+
+@dataclass
+class DistillWorkload:
+    """Distillation step (Eq. 3): teacher denoiser, student generator, one batch."""
+    name: str
+    d_s: int
+    d_a: int
+    d_x: int
+    B: int
+    T: int
+    beta0: float
+    beta1: float
+    emb_dim: int
+    seed: int
+    teacher: MLPSpec
+    student: MLPSpec               # FP32 master values (the forward copy rounds them)
+    S: np.ndarray                  # [B, d_s] ~ N(0, I)
+    A: np.ndarray                  # [B, d_a] ~ U[-1, 1]
+    omega: np.ndarray              # [B, d_x] ~ N(0, I)
+    lr: float = 1e-3
+    adam_betas: tuple = (0.9, 0.999)
+    adam_eps: float = 1e-8
+
+
+def distill(seed: int = 3, B: int = 65536, teacher_prec: int = PREC_FP32) -> DistillWorkload:
+    """Teacher 82->512x3->8 SiLU (input [s; a; x_t; 64-d step embedding]), 32 DDIM
+    steps with linear beta 1e-4..0.02; student 18->256x3->8 SiLU with FP32
+    master weights; s ~ N(0, I_8), a ~ U[-1, 1]^2, omega ~ N(0, I_8)."""
+    rng = np.random.default_rng(seed)
+    d_s, d_a, d_x, emb = 8, 2, 8, 64
+    teacher = xavier_mlp(rng, [d_s + d_a + d_x + emb, 512, 512, 512, d_x], ACT_SILU, teacher_prec)
+    student = xavier_mlp(rng, [d_s + d_a + d_x, 256, 256, 256, d_x], ACT_SILU, PREC_FP32)
+    S = round_to(rng.normal(0.0, 1.0, size=(B, d_s)), PREC_FP32)
+    A = round_to(rng.uniform(-1.0, 1.0, size=(B, d_a)), PREC_FP32)
+    omega = round_to(rng.normal(0.0, 1.0, size=(B, d_x)), PREC_FP32)
+    return DistillWorkload("distill", d_s, d_a, d_x, B, 32, 1e-4, 0.02, emb, seed, teacher, student, S, A, omega)
+
+
 def batched_planners(seed: int = 4, P: int = 64):
     """Per-planner (N_p, K_p, H_p): N log-uniform in [512, 16384], K uniform in
     {128..1024}, H uniform in {5..30}."""
