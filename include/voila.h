@@ -365,11 +365,21 @@ voila_status voila_generator_bwd(const voila_mlp* mlp, const float* X, const flo
  *   teacher dims[0] = d_s + d_a + d_x + emb_dim, dims[L] = d_x.
  * Limits: 1 <= T <= 64, 1 <= d_x <= 16, emb_dim even and <= 64, widths <= 512.
  * The paper names a cosine schedule; the linear one is the workload's.
+ * Kernels: a BF16 teacher with d_s = 8, d_a = 2, d_x = 8, emb_dim = 64 and
+ * hidden layers of width 512 runs on the tensor cores (BF16 operands and
+ * activations, FP32 accumulation, x kept in FP32); every other teacher runs
+ * on the CUDA cores in FP32.
+ *   workspace  device, 1024-byte aligned, voila_ddim_sample_workspace_size
+ *              bytes; it starts with the status word voila_workspace_status
+ *              reads (VOILA_ERR_TIMEOUT if a tensor-core wait expired).
  */
+voila_status voila_ddim_sample_workspace_size(const voila_mlp* teacher, int32_t T, size_t* bytes);
+
 voila_status voila_ddim_sample(const voila_mlp* teacher, const float* S, const float* A,
                                const float* omega, int32_t B, int32_t d_s, int32_t d_a,
                                int32_t d_x, int32_t T, double beta0, double beta1,
-                               int32_t emb_dim, float* Y, voila_stream_t stream);
+                               int32_t emb_dim, float* Y, void* workspace, size_t ws_bytes,
+                               voila_stream_t stream);
 
 /*
  * One Adam step (Kingma & Ba, 2015) on a flat FP32 vector of n parameters,
@@ -394,9 +404,10 @@ typedef struct {
   int32_t step;     /* 1-based step count (bias correction) */
 } voila_adam;
 
-/* Workspace of voila_distill_step for B rows and output width d_x, in bytes. */
-voila_status voila_distill_step_workspace_size(const voila_mlp* student, int32_t B, int32_t d_x,
-                                               size_t* bytes);
+/* Workspace of voila_distill_step for B rows, output width d_x and T sampler
+ * steps, in bytes. */
+voila_status voila_distill_step_workspace_size(const voila_mlp* teacher, const voila_mlp* student,
+                                               int32_t B, int32_t d_x, int32_t T, size_t* bytes);
 
 /*
  * One distillation training step of the transition generator (Eq. 3):
@@ -413,7 +424,9 @@ voila_status voila_distill_step_workspace_size(const voila_mlp* student, int32_t
  *   S [B][d_s], A [B][d_a], omega [B][d_x] float (device).
  *   loss_out  device double, the loss of step 3 (before the update).
  *   grad_out  device float [n_params] or NULL: receives the gradient.
- *   workspace device, 256-byte aligned, voila_distill_step_workspace_size bytes.
+ *   workspace device, 1024-byte aligned, voila_distill_step_workspace_size
+ *            bytes; its first bytes are the teacher sampler's workspace, so
+ *            voila_workspace_status(workspace) reports the sampler's status.
  * Deterministic: every reduction runs in a fixed order.
  */
 voila_status voila_distill_step(const voila_mlp* teacher, const voila_mlp* student,

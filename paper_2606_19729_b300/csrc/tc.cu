@@ -104,6 +104,15 @@ struct TcParams {
   long long total_items;
   long long item_end[kMaxPlanners];  // inclusive prefix sum of items per planner
   TcPlanner pl[kMaxPlanners];
+  // DDIM teacher sampling (the sampler's step t of the launch is diffusion step
+  // T-1-t): x_{next} = cx[t] x + cv[t] v, conditioning rows s [B][8], a [B][2],
+  // step embeddings as BF16 rows of 64 ([T][8] uint4), samples out [B][8].
+  const float* ddim_s;
+  const float* ddim_a;
+  const uint4* ddim_emb;
+  float* ddim_y;
+  float ddim_cx[64];
+  float ddim_cv[64];
 };
 
 __device__ __forceinline__ int item_planner(const TcParams& p, long long it) {
@@ -266,15 +275,41 @@ __device__ __forceinline__ void write_rew_input(uint8_t* A, int r, const float* 
   store_row<KP>(A, r, x);
 }
 
+// Teacher input row of the DDIM sampler, in the column order the packed first
+// layer expects: [x (8) | s (8) | a (2), 0 (6) | 0 (8) | e(t) (64)], 96 BF16
+// columns = chunks 0-7 of slab 0 and chunks 0-3 of slab 1.
+__device__ __forceinline__ void write_ddim_input(uint8_t* A, int r, const float* x, const float* c,
+                                                 const uint4* emb_row) {
+  store_row<8>(A, r, x);
+  uint4 v;
+  v.x = ptx::pack_bf16x2(c[0], c[1]);
+  v.y = ptx::pack_bf16x2(c[2], c[3]);
+  v.z = ptx::pack_bf16x2(c[4], c[5]);
+  v.w = ptx::pack_bf16x2(c[6], c[7]);
+  *reinterpret_cast<uint4*>(a_chunk(A, r, 1)) = v;
+  v.x = ptx::pack_bf16x2(c[8], c[9]);
+  v.y = v.z = v.w = 0u;
+  *reinterpret_cast<uint4*>(a_chunk(A, r, 2)) = v;
+  v.x = 0u;
+  *reinterpret_cast<uint4*>(a_chunk(A, r, 3)) = v;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4*>(a_chunk(A, r, 4 + j)) = __ldg(emb_row + j);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4*>(a_chunk(A + 128 * 128, r, j)) = __ldg(emb_row + 4 + j);
+}
+
 // F8: the MLPs contain E4M3 layers (a separate instantiation keeps the BF16
 // form free of the FP8 code paths).
 // WIDE: layers up to 512 wide. Each CTA owns one 128-row tile per work item
 // (256 rows per pair); the two 256-column TMEM halves and the two 64 KB A
 // buffers hold the two column halves of a layer (K up to 512); the epilogue
 // starts when both halves' MMAs are done (the next input overwrites A).
-template <int DS, int DA, int DW, bool F8, bool WIDE>
+// DDIM (with WIDE, DS = 8, DA = 10, DW = 0): the rows are teacher samples and
+// the H steps are the sampler's steps; no reward, the output is x per row.
+template <int DS, int DA, int DW, bool F8, bool WIDE, bool DDIM = false>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     rollout_tc_kernel(const __grid_constant__ TcParams p) {
+  static_assert(!DDIM || (WIDE && !F8 && DS == 8 && DA == 10 && DW == 0), "DDIM sampler layout");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* Abuf[2] = {smem, smem + kABytes};
@@ -511,7 +546,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       const uint32_t k = valid ? (uint32_t)(row / PL.N) : 0u;
       const float* act_row = PL.actions + (size_t)k * H * DA;
       float s[DS], a[DA];
-      if (owner) {
+      if constexpr (DDIM) {
+        if (owner) {  // s holds x_t, a the conditioning [s; a] of the row
+#pragma unroll
+          for (int i = 0; i < DS; ++i) s[i] = valid ? __ldg(PL.particles + (size_t)row * DS + i) : 0.0f;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) a[i] = valid ? __ldg(p.ddim_s + (size_t)row * 8 + i) : 0.0f;
+          a[8] = valid ? __ldg(p.ddim_a + (size_t)row * 2) : 0.0f;
+          a[9] = valid ? __ldg(p.ddim_a + (size_t)row * 2 + 1) : 0.0f;
+          write_ddim_input(A, r, s, a, p.ddim_emb);
+        }
+      } else if (owner) {
 #pragma unroll
         for (int i = 0; i < DS; ++i) s[i] = valid ? __ldg(PL.particles + (size_t)n * DS + i) : 0.0f;
 #pragma unroll
@@ -564,6 +609,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 else epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
               }
             }
+          } else if (DDIM && owner) {
+            // teacher output v: x <- cx[t] x + cv[t] (v + b), then the next step's input
+            float v[16];
+            ptx::tmem_ld16(tm, v);
+            ptx::tmem_wait_ld();
+            const float cx = p.ddim_cx[t], cv = p.ddim_cv[t];
+#pragma unroll
+            for (int i = 0; i < DS; ++i) s[i] = fmaf(cx, s[i], cv * (v[i] + bl[i]));
+            if (t + 1 < H) write_ddim_input(A, r, s, a, p.ddim_emb + (size_t)(t + 1) * 8);
           } else if (owner && l == p.n_gen - 1) {
             // generator output: s_{t+1} (FP32, kept in registers)
             float v[32];
@@ -611,7 +665,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           }
         }
       }
-      if (owner && valid && ok) PL.G[row] = Gacc;
+      if constexpr (DDIM) {
+        if (owner && valid && ok) {
+#pragma unroll
+          for (int i = 0; i < DS; i += 4)
+            *reinterpret_cast<float4*>(p.ddim_y + (size_t)row * DS + i) = make_float4(s[i], s[i + 1], s[i + 2], s[i + 3]);
+        }
+      } else if (owner && valid && ok) {
+        PL.G[row] = Gacc;
+      }
     }
   }
 
@@ -635,6 +697,9 @@ struct PackTable {
   long long elems_end[kMaxTcLayers];
   int half[kMaxTcLayers];  // 1: SiLU layer, pack W and b scaled by 1/2
   int fp8[kMaxTcLayers];
+  int ldk[kMaxTcLayers];   // row stride of W[l] (its input width)
+  int colmap_layer;        // layer whose packed column kg reads W column colmap[kg] (-1: none)
+  short colmap[128];       // -1: zero column
   int n;
   uint8_t* wout;
   float* bout;   // biases, then channel scales
@@ -674,7 +739,9 @@ __global__ void pack_kernel(const __grid_constant__ PackTable t) {
     const int rem = (int)(e0 % (Npad * epr));
     const int nrow = rem / epr, kk = rem % epr;
     const int kg = epr * c + kk;
-    float w = (nrow < t.N[l] && kg < t.K[l]) ? __bfloat162float(t.W[l][(size_t)nrow * t.K[l] + kg]) : 0.0f;
+    int src = kg < t.K[l] ? kg : -1;
+    if (l == t.colmap_layer) src = kg < 128 ? t.colmap[kg] : -1;
+    float w = (nrow < t.N[l] && src >= 0) ? __bfloat162float(t.W[l][(size_t)nrow * t.ldk[l] + src]) : 0.0f;
     if (t.half[l]) w *= 0.5f;  // exact
     uint8_t* row = t.wout + ((size_t)t.row0[l] + (size_t)c * Npad + nrow) * 128;
     if (t.fp8[l]) {
@@ -699,10 +766,14 @@ struct Plan {
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-Plan make_plan(const voila_mlp* g, const voila_reward* R) {
+// ddim: g is the DDIM teacher [s (8); a (2); x (8); e (64)] -> ... -> 8; its
+// first layer is packed with 96 input columns in the order write_ddim_input
+// writes them.
+Plan make_plan(const voila_mlp* g, const voila_reward* R, bool ddim = false) {
   Plan pl;
   memset(&pl, 0, sizeof(pl));
   pl.ok = false;
+  pl.pack.colmap_layer = -1;
   const voila_mlp* mlps[2] = {g, R && R->kind == VOILA_REWARD_MLP ? R->mlp : nullptr};
   int nl = 0, boff = 0, rows = 0;
   long long elems = 0;
@@ -712,9 +783,9 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
     if ((M->prec != VOILA_BF16 && M->prec != VOILA_FP8E4M3) || M->n_layers < 2) return pl;
     for (int l = 0; l < M->n_layers; ++l) {
       if (nl >= kMaxTcLayers) return pl;
-      const int K = M->dims[l], N = M->dims[l + 1];
+      const int K = (ddim && l == 0) ? 96 : M->dims[l], N = M->dims[l + 1];
       const bool last = l == M->n_layers - 1;
-      if (l == 0 && K > 64) return pl;
+      if (l == 0 && K > (ddim ? 96 : 64)) return pl;
       if (l > 0 && (K % 64 != 0 || K > 512)) return pl;
       if (!last && (N % 64 != 0 || N > 512 || (N > 256 && N != 512))) return pl;
       if (last && N > 32) return pl;
@@ -744,6 +815,7 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
       T.b[nl] = M->b[l];
       T.N[nl] = N;
       T.K[nl] = K;
+      T.ldk[nl] = M->dims[l];
       T.Npad[nl] = L.Npad;
       T.row0[nl] = rows;
       T.bias_off[nl] = boff;
@@ -756,6 +828,12 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R) {
       ++nl;
     }
     if (m == 0) pl.p.n_gen = nl;
+  }
+  if (ddim) {  // packed column -> teacher column: x 10..17, s 0..7, a 8..9, zeros, e 18..81
+    pl.pack.colmap_layer = 0;
+    for (int c = 0; c < 128; ++c)
+      pl.pack.colmap[c] = c < 8 ? (short)(10 + c) : c < 18 ? (short)(c - 8)
+                        : (c >= 32 && c < 96) ? (short)(c - 14) : (short)-1;
   }
   pl.p.n_total = nl;
   pl.pack.n = nl;
@@ -781,9 +859,9 @@ size_t tc_smem_bytes(int vec_floats) {
 
 // Launches one persistent CTA pair per co-resident cluster slot (at most
 // `max_clusters`, never more than there are super-pairs).
-template <int DS, int DA, int DW, bool F8, bool WIDE>
+template <int DS, int DA, int DW, bool F8, bool WIDE, bool DDIM = false>
 cudaError_t launch_tc(const TcParams& p, size_t smem, long long max_clusters, cudaStream_t s) {
-  auto k = rollout_tc_kernel<DS, DA, DW, F8, WIDE>;
+  auto k = rollout_tc_kernel<DS, DA, DW, F8, WIDE, DDIM>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
@@ -799,7 +877,7 @@ cudaError_t launch_tc(const TcParams& p, size_t smem, long long max_clusters, cu
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
   // co-resident cluster slots: queried once per device and instantiation
-  static int cached[64] = {};
+  static int cached[64] = {};  // one table per instantiation
   int dev = 0;
   e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -942,6 +1020,104 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
   else
     e = f8 ? launch_tc<12, 3, 16, true, true>(p, smem, nclusters, s)
            : launch_tc<12, 3, 16, false, true>(p, smem, nclusters, s);
+  return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
+}
+
+namespace {
+
+// Step embeddings of the sampler in launch order (row t is diffusion step
+// T-1-t): [sin(tau f_i), cos(tau f_i)], i < 32, as BF16.
+struct EmbFreq {
+  float f[32];
+};
+
+__global__ void ddim_emb_kernel(EmbFreq fr, int T, __nv_bfloat16* out) {
+  const int t = blockIdx.x, i = threadIdx.x;
+  const float tau = (float)(T - 1 - t);
+  const float a = tau * fr.f[i & 31];
+  out[t * 64 + i] = __float2bfloat16(i < 32 ? sinf(a) : cosf(a));
+}
+
+}  // namespace
+
+bool tc_ddim_supported(const voila_mlp* teacher, int d_s, int d_a, int d_x, int emb_dim) {
+  if (!teacher || teacher->prec != VOILA_BF16 || d_s != 8 || d_a != 2 || d_x != 8 || emb_dim != 64) return false;
+  if (teacher->dims[0] != 82) return false;
+  for (int l = 1; l < teacher->n_layers; ++l)
+    if (teacher->dims[l] != 512) return false;
+  return make_plan(teacher, nullptr, true).ok;
+}
+
+size_t tc_ddim_scratch_bytes(const voila_mlp* teacher, int T) {
+  Plan pl = make_plan(teacher, nullptr, true);
+  if (!pl.ok) return 0;
+  return pl.total + ((size_t)T * 128 + 1023) / 1024 * 1024;
+}
+
+voila_status tc_ddim_sample(const voila_mlp* teacher, const float* S, const float* A, const float* omega, int B,
+                            int T, const double* cx, const double* cv, const double* freq, float* Y, WsHeader* hdr,
+                            void* scratch, cudaStream_t s) {
+  Plan pl = make_plan(teacher, nullptr, true);
+  if (!pl.ok || !pl.wide) return VOILA_ERR_UNSUPPORTED;
+  if (T < 1 || T > 64) return VOILA_ERR_ARG;
+  if ((uintptr_t)scratch % 1024) return VOILA_ERR_WORKSPACE;
+  TcParams& p = pl.p;
+  TcPlanner& q = p.pl[0];
+  q.particles = omega;
+  q.actions = omega;  // unused by the sampler
+  q.G = nullptr;
+  q.rows = B;
+  q.N = B;
+  q.H = T;
+  q.planner = 0;
+  p.P = 1;
+  p.total_items = (B + 2 * kTileRows - 1) / (2 * kTileRows);
+  p.item_end[0] = p.total_items;
+  uint8_t* wst = (uint8_t*)scratch;
+  float* bias_all = (float*)(wst + (pl.wbytes + 1023) / 1024 * 1024);
+  __nv_bfloat16* emb = (__nv_bfloat16*)(wst + pl.total);
+  pl.pack.wout = wst;
+  pl.pack.bout = bias_all;
+  {
+    const long long total = pl.pack.elems_end[pl.pack.n - 1];
+    long long blocks = (total + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    pack_kernel<<<(int)blocks, 256, 0, s>>>(pl.pack);
+    EmbFreq fr;
+    for (int i = 0; i < 32; ++i) fr.f[i] = (float)freq[i];
+    ddim_emb_kernel<<<T, 64, 0, s>>>(fr, T, emb);
+    if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return VOILA_ERR_CUDA;
+  for (int l = 0; l < p.n_total; ++l) {
+    const cuuint64_t gdim[2] = {128, (cuuint64_t)pl.total_rows};  // bytes
+    const cuuint64_t gstride[1] = {128};
+    const cuuint32_t box[2] = {128, (cuuint32_t)p.layers[l].box_rows};
+    const cuuint32_t estride[2] = {1, 1};
+    if (encode(&p.tmap[l], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)wst, gdim, gstride, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return VOILA_ERR_CUDA;
+  }
+  p.bias_all = bias_all;
+  p.reward_kind = VOILA_REWARD_GOAL;
+  p.goal_dims = 0;
+  p.hdr = hdr;
+  p.ddim_s = S;
+  p.ddim_a = A;
+  p.ddim_emb = reinterpret_cast<const uint4*>(emb);
+  p.ddim_y = Y;
+  for (int t = 0; t < T; ++t) {
+    p.ddim_cx[t] = (float)cx[t];
+    p.ddim_cv[t] = (float)cv[t];
+  }
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long nclusters = p.total_items < nsm / 2 ? p.total_items : nsm / 2;
+  const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total);
+  const cudaError_t e = launch_tc<8, 10, 0, false, true, true>(p, smem, nclusters, s);
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
 

@@ -34,4 +34,15 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
 voila_status tc_rollout(const voila_mlp* g_T, const voila_reward* R, const RolloutArgs& a,
                         WsHeader* hdr, void* scratch, cudaStream_t s);
 
+// DDIM teacher sampling on the tensor cores (BF16 teacher 82 -> 512 x L -> 8,
+// s 8, a 2, x 8, embedding 64): whether the shape is covered, the scratch it
+// needs (packed weights, biases, step embeddings; 1024-byte aligned), and the
+// launch. cx[t], cv[t]: x <- cx x + cv v at launch step t (diffusion step
+// T-1-t); freq[i], i < 32: embedding frequencies.
+bool tc_ddim_supported(const voila_mlp* teacher, int d_s, int d_a, int d_x, int emb_dim);
+size_t tc_ddim_scratch_bytes(const voila_mlp* teacher, int T);
+voila_status tc_ddim_sample(const voila_mlp* teacher, const float* S, const float* A, const float* omega, int B,
+                            int T, const double* cx, const double* cv, const double* freq, float* Y, WsHeader* hdr,
+                            void* scratch, cudaStream_t s);
+
 }  // namespace voila

@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "simt_mlp.cuh"
+#include "tc.h"
 
 namespace voila {
 
@@ -470,18 +471,29 @@ size_t bwd_ws_bytes(const voila_mlp* m, int B) {
   return ((size_t)2 * B * widest(m) + (size_t)chunks * (pmax + nmax)) * sizeof(float);
 }
 
+// Workspace of the teacher sampler: the status header (1024 bytes), then the
+// tensor-core scratch (packed teacher, step embeddings) when that path runs.
+constexpr size_t kDdimHeader = 1024;
+
+size_t ddim_ws_bytes(const voila_mlp* teacher, int T) {
+  const size_t tc = tc_ddim_scratch_bytes(teacher, T);
+  return kDdimHeader + (tc + 1023) / 1024 * 1024;
+}
+
 // Workspace of the distillation step, in this order (each 256-byte aligned):
-// s_hat [B][d_x], X [B][din], Y [B][d_x], dY [B][d_x], saved [B][hidden],
-// grads [n_params], loss partials [kLossBlocks] (FP64), scratch (bwd).
+// teacher-sampler workspace, s_hat [B][d_x], X [B][din], Y [B][d_x],
+// dY [B][d_x], saved [B][hidden], grads [n_params], loss partials
+// [kLossBlocks] (FP64), scratch (bwd).
 struct DistillLayout {
-  size_t s_hat, x, y, dy, saved, grads, part, scratch, total;
+  size_t ddim, s_hat, x, y, dy, saved, grads, part, scratch, total;
 };
 
-DistillLayout distill_layout(const voila_mlp* st, int B, int d_x) {
+DistillLayout distill_layout(const voila_mlp* teacher, const voila_mlp* st, int B, int d_x, int T) {
   DistillLayout L;
   long long off[2 * VOILA_MAX_LAYERS + 1];
   const long long np = param_layout(st, off);
   size_t o = 0;
+  L.ddim = o;  o += align256(ddim_ws_bytes(teacher, T));
   L.s_hat = o; o += align256((size_t)B * d_x * 4);
   L.x = o;     o += align256((size_t)B * st->dims[0] * 4);
   L.y = o;     o += align256((size_t)B * d_x * 4);
@@ -539,9 +551,17 @@ voila_status voila_generator_bwd(const voila_mlp* mlp, const float* X, const flo
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
 
+voila_status voila_ddim_sample_workspace_size(const voila_mlp* teacher, int32_t T, size_t* bytes) {
+  if (!teacher || !bytes || teacher->n_layers < 1 || teacher->n_layers > VOILA_MAX_LAYERS || T < 1 || T > 64)
+    return VOILA_ERR_ARG;
+  *bytes = ddim_ws_bytes(teacher, T);
+  return VOILA_OK;
+}
+
 voila_status voila_ddim_sample(const voila_mlp* teacher, const float* S, const float* A, const float* omega,
                                int32_t B, int32_t d_s, int32_t d_a, int32_t d_x, int32_t T, double beta0,
-                               double beta1, int32_t emb_dim, float* Y, voila_stream_t stream) {
+                               double beta1, int32_t emb_dim, float* Y, void* workspace, size_t ws_bytes,
+                               voila_stream_t stream) {
   if (!teacher || teacher->n_layers < 1 || teacher->n_layers > VOILA_MAX_LAYERS || B < 0) return VOILA_ERR_ARG;
   if (teacher->prec != VOILA_FP32 && teacher->prec != VOILA_BF16) return VOILA_ERR_UNSUPPORTED;
   if (T < 1 || T > 64 || d_x < 1 || d_x > 16 || emb_dim < 0 || emb_dim > 64 || (emb_dim & 1) || d_s < 0 ||
@@ -550,8 +570,32 @@ voila_status voila_ddim_sample(const voila_mlp* teacher, const float* S, const f
   if (teacher->dims[0] != d_s + d_a + d_x + emb_dim || teacher->dims[teacher->n_layers] != d_x ||
       widest(teacher) > VOILA_MAX_WIDTH)
     return VOILA_ERR_SHAPE;
+  if (!workspace || ws_bytes < ddim_ws_bytes(teacher, T) || ((uintptr_t)workspace & 1023))
+    return VOILA_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), s) != cudaSuccess) return VOILA_ERR_CUDA;
   if (B == 0) return VOILA_OK;
   if (!omega || !Y || (d_s && !S) || (d_a && !A)) return VOILA_ERR_ARG;
+  if (tc_ddim_supported(teacher, d_s, d_a, d_x, emb_dim)) {
+    // x_{tau-1} = cx x_tau + cv v with cx = sqrt(abar_{tau-1} abar_tau) + sqrt((1-abar_{tau-1})(1-abar_tau)),
+    // cv = sqrt((1-abar_{tau-1}) abar_tau) - sqrt(abar_{tau-1} (1-abar_tau)), abar_{-1} = 1
+    double abar[64], cx[64], cv[64], freq[32];
+    double ab = 1.0;
+    for (int u = 0; u < T; ++u) {
+      ab *= 1.0 - (T > 1 ? beta0 + (beta1 - beta0) * u / (T - 1) : beta0);
+      abar[u] = ab;
+    }
+    for (int t = 0; t < T; ++t) {
+      const int tau = T - 1 - t;
+      const double sab = sqrt(abar[tau]), s1 = sqrt(1.0 - abar[tau]);
+      const double sabp = tau > 0 ? sqrt(abar[tau - 1]) : 1.0, s1p = tau > 0 ? sqrt(1.0 - abar[tau - 1]) : 0.0;
+      cx[t] = sabp * sab + s1p * s1;
+      cv[t] = s1p * sab - sabp * s1;
+    }
+    for (int i = 0; i < 32; ++i) freq[i] = pow(10000.0, -(double)i / 32.0);
+    return tc_ddim_sample(teacher, S, A, omega, B, T, cx, cv, freq, Y, (WsHeader*)workspace,
+                          (char*)workspace + kDdimHeader, s);
+  }
   DdimArgs a;
   memset(&a, 0, sizeof(a));
   a.m.n_layers = teacher->n_layers;
@@ -583,7 +627,6 @@ voila_status voila_ddim_sample(const voila_mlp* teacher, const float* S, const f
   const int wmax = widest(teacher);
   a.ld = (wmax % 2 == 0) ? wmax + 1 : wmax;
   const size_t smem = (size_t)2 * kSimtRows * a.ld * sizeof(float) + kSimtRows * 16 * sizeof(float);
-  cudaStream_t s = (cudaStream_t)stream;
   auto k = teacher->prec == VOILA_BF16 ? ddim_kernel<__nv_bfloat16> : ddim_kernel<float>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return VOILA_ERR_CUDA;
@@ -611,10 +654,12 @@ voila_status voila_adam_step(float* params, const float* grads, float* m, float*
   return cudaGetLastError() == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
 
-voila_status voila_distill_step_workspace_size(const voila_mlp* student, int32_t B, int32_t d_x, size_t* bytes) {
-  if (!student || !bytes || student->n_layers < 1 || student->n_layers > VOILA_MAX_LAYERS || B < 0 || d_x < 1)
+voila_status voila_distill_step_workspace_size(const voila_mlp* teacher, const voila_mlp* student, int32_t B,
+                                               int32_t d_x, int32_t T, size_t* bytes) {
+  if (!teacher || !student || !bytes || student->n_layers < 1 || student->n_layers > VOILA_MAX_LAYERS || B < 0 ||
+      d_x < 1 || teacher->n_layers < 1 || teacher->n_layers > VOILA_MAX_LAYERS || T < 1 || T > 64)
     return VOILA_ERR_ARG;
-  *bytes = distill_layout(student, B, d_x).total;
+  *bytes = distill_layout(teacher, student, B, d_x, T).total;
   return VOILA_OK;
 }
 
@@ -630,9 +675,10 @@ voila_status voila_distill_step(const voila_mlp* teacher, const voila_mlp* stude
   if (student->dims[0] != d_s + d_a + d_x || student->dims[student->n_layers] != d_x) return VOILA_ERR_SHAPE;
   for (int l = 0; l < student->n_layers; ++l)
     if (!student->W[l] || !student->b[l]) return VOILA_ERR_ARG;
+  if (ddim->T < 1 || ddim->T > 64) return VOILA_ERR_ARG;
   if (B == 0) return VOILA_OK;
-  const DistillLayout L = distill_layout(student, B, d_x);
-  if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 255)) return VOILA_ERR_WORKSPACE;
+  const DistillLayout L = distill_layout(teacher, student, B, d_x, ddim->T);
+  if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 1023)) return VOILA_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   float* s_hat = (float*)(ws + L.s_hat);
@@ -647,7 +693,7 @@ voila_status voila_distill_step(const voila_mlp* teacher, const voila_mlp* stude
 
   // 1. teacher targets s_hat' (the ODE sampler of Eq. 3)
   voila_status st = voila_ddim_sample(teacher, S, A, omega, B, d_s, d_a, d_x, ddim->T, ddim->beta0, ddim->beta1,
-                                      ddim->emb_dim, s_hat, stream);
+                                      ddim->emb_dim, s_hat, ws + L.ddim, L.s_hat - L.ddim, stream);
   if (st != VOILA_OK) return st;
   // 2. student forward f_T(s, a, omega), pre-activations saved
   concat_input_kernel<<<grid_for((long long)B * student->dims[0], 256), 256, 0, s>>>(S, A, omega, B, d_s, d_a,

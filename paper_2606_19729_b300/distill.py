@@ -100,7 +100,7 @@ class Distiller:
         self.t = 0
         self.B = B
         self.d_x = dims[-1]
-        self.ws = V.alloc_workspace(V.voila_distill_step_workspace_size(self.student, B, self.d_x))
+        self.ws = V.alloc_workspace(V.voila_distill_step_workspace_size(teacher, self.student, B, self.d_x, T))
         self.loss = torch.zeros(1, dtype=torch.float64, device="cuda")
 
     def step(self, S: torch.Tensor, A: torch.Tensor, omega: torch.Tensor, grad_out: Optional[torch.Tensor] = None,

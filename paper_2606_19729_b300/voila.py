@@ -98,11 +98,12 @@ _lib_fwd_train = _sig("voila_generator_fwd_train", c_int32, POINTER(voila_mlp), 
 _lib_bwd_ws = _sig("voila_generator_bwd_workspace_size", c_int32, POINTER(voila_mlp), c_int32, POINTER(c_size_t))
 _lib_bwd = _sig("voila_generator_bwd", c_int32, POINTER(voila_mlp), _P, _P, _P, c_int32, _P, POINTER(c_void_p),
                 POINTER(c_void_p), _P, c_size_t, _P)
+_lib_ddim_ws = _sig("voila_ddim_sample_workspace_size", c_int32, POINTER(voila_mlp), c_int32, POINTER(c_size_t))
 _lib_ddim = _sig("voila_ddim_sample", c_int32, POINTER(voila_mlp), _P, _P, _P, c_int32, c_int32, c_int32, c_int32,
-                 c_int32, c_double, c_double, c_int32, _P, _P)
+                 c_int32, c_double, c_double, c_int32, _P, _P, c_size_t, _P)
 _lib_adam = _sig("voila_adam_step", c_int32, _P, _P, _P, _P, c_int64, c_float, c_float, c_float, c_float, c_int32, _P)
-_lib_distill_ws = _sig("voila_distill_step_workspace_size", c_int32, POINTER(voila_mlp), c_int32, c_int32,
-                       POINTER(c_size_t))
+_lib_distill_ws = _sig("voila_distill_step_workspace_size", c_int32, POINTER(voila_mlp), POINTER(voila_mlp), c_int32,
+                       c_int32, c_int32, POINTER(c_size_t))
 _lib_distill = _sig("voila_distill_step", c_int32, POINTER(voila_mlp), POINTER(voila_mlp), POINTER(voila_ddim), _P, _P,
                     _P, POINTER(voila_adam), _P, _P, _P, c_int32, c_int32, c_int32, c_int32, _P, _P, _P, c_size_t, _P)
 _lib_philox = _sig("voila_philox_fill", c_int32, c_uint64, c_uint32, c_uint32, c_uint32, _P, c_int64, _P)
@@ -211,8 +212,11 @@ def workspace_status(ws: torch.Tensor, stream=None) -> int:
 
 
 def alloc_workspace(nbytes: int) -> torch.Tensor:
-    """A 256-byte aligned device workspace (torch allocations are 512-byte aligned)."""
-    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device="cuda")
+    """A 1024-byte aligned device workspace (a view into a slightly larger allocation)."""
+    n = max(int(nbytes), 256)
+    buf = torch.empty(n + 1024, dtype=torch.uint8, device="cuda")
+    off = (-buf.data_ptr()) % 1024
+    return buf[off:off + n]
 
 
 # ---------------------------------------------------------------------------
@@ -376,12 +380,23 @@ def voila_generator_bwd(mlp: DeviceMLP, X: torch.Tensor, saved: Optional[torch.T
                     workspace.numel(), _stream(stream)), "voila_generator_bwd")
 
 
+def voila_ddim_sample_workspace_size(teacher: DeviceMLP, T: int) -> int:
+    n = c_size_t(0)
+    _check(_lib_ddim_ws(ctypes.byref(teacher.desc), T, ctypes.byref(n)), "voila_ddim_sample_workspace_size")
+    return n.value
+
+
 def voila_ddim_sample(teacher: DeviceMLP, S: torch.Tensor, A: torch.Tensor, omega: torch.Tensor, T: int,
-                      beta0: float, beta1: float, emb_dim: int, Y: torch.Tensor, stream=None):
+                      beta0: float, beta1: float, emb_dim: int, Y: torch.Tensor,
+                      workspace: Optional[torch.Tensor] = None, stream=None):
+    """Teacher DDIM targets; allocates the workspace when none is given."""
     B, d_x = omega.shape
+    if workspace is None:
+        workspace = alloc_workspace(voila_ddim_sample_workspace_size(teacher, T))
     _check(_lib_ddim(ctypes.byref(teacher.desc), _ptr(S, torch.float32), _ptr(A, torch.float32),
                      _ptr(omega, torch.float32), B, S.shape[1], A.shape[1], d_x, T, beta0, beta1, emb_dim,
-                     _ptr(Y, torch.float32), _stream(stream)), "voila_ddim_sample")
+                     _ptr(Y, torch.float32), _ptr(workspace), workspace.numel(), _stream(stream)),
+           "voila_ddim_sample")
 
 
 def voila_adam_step(params: torch.Tensor, grads: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float,
@@ -391,9 +406,10 @@ def voila_adam_step(params: torch.Tensor, grads: torch.Tensor, m: torch.Tensor, 
            "voila_adam_step")
 
 
-def voila_distill_step_workspace_size(student: DeviceMLP, B: int, d_x: int) -> int:
+def voila_distill_step_workspace_size(teacher: DeviceMLP, student: DeviceMLP, B: int, d_x: int, T: int) -> int:
     n = c_size_t(0)
-    _check(_lib_distill_ws(ctypes.byref(student.desc), B, d_x, ctypes.byref(n)), "voila_distill_step_workspace_size")
+    _check(_lib_distill_ws(ctypes.byref(teacher.desc), ctypes.byref(student.desc), B, d_x, T, ctypes.byref(n)),
+           "voila_distill_step_workspace_size")
     return n.value
 
 
