@@ -531,3 +531,63 @@ def distill_targets(teacher: MLP, s, a, omega, T: int = 32, beta0: float = 1e-4,
                     emb_dim: int = 64) -> np.ndarray:
     """s_hat' of Eq. 3: the teacher's DDIM sample from omega."""
     return ddim_sample(teacher_v(teacher, emb_dim), s, a, omega, ddim_schedule(T, beta0, beta1))
+
+
+# ---------------------------------------------------------------------------
+# PORPP preference backup over the root's action sequences (Sec. 2.2): with
+# one level of preferences Psi_k = (1/eta) log pi_0(a_k | b) + J_k, the value is
+# the log-sum-exp operator V = (1/eta) log sum_k exp(eta Psi_k) and the
+# induced policy is pi(a_k | b) = exp(eta Psi_k) / sum_j exp(eta Psi_j).
+# Reading: the reference policy pi_0 is uniform (1/K) unless given.
+# ---------------------------------------------------------------------------
+def preference_backup(J: np.ndarray, eta: float, log_pi0: Optional[np.ndarray] = None):
+    """Returns (V, pi) in FP64; the sum runs after subtracting the maximum."""
+    J = np.asarray(J, np.float64)
+    K = J.shape[0]
+    lp = np.full(K, -math.log(K)) if log_pi0 is None else np.asarray(log_pi0, np.float64)
+    x = eta * J + lp                       # eta * Psi_k
+    m = float(np.max(x))
+    e = np.exp(x - m)
+    Z = float(np.sum(e))
+    return (m + math.log(Z)) / eta, e / Z
+
+
+# ---------------------------------------------------------------------------
+# InfoNCE likelihood objective (Eq. 6, Sec. 4.2.3): the likelihood model on
+# all B x B combinations (s'_i, a_i, o_j), row log-sum-exp, the loss and its
+# gradient with respect to the B x B logits and to the model's weights.
+# ---------------------------------------------------------------------------
+def infonce_pairs(s_next: np.ndarray, a: np.ndarray, o: np.ndarray) -> np.ndarray:
+    """Rows [s'_i; a_i; o_j] in the order i * B + j."""
+    B = s_next.shape[0]
+    return np.concatenate([np.repeat(np.asarray(s_next, np.float64), B, axis=0),
+                           np.repeat(np.asarray(a, np.float64), B, axis=0),
+                           np.tile(np.asarray(o, np.float64), (B, 1))], axis=-1)
+
+
+def infonce_logits(ell: MLP, s_next, a, o) -> np.ndarray:
+    """L[i, j] = ell(s'_i, a_i, o_j)."""
+    B = s_next.shape[0]
+    return mlp_forward(ell, infonce_pairs(s_next, a, o))[:, 0].reshape(B, B)
+
+
+def infonce_loss(L: np.ndarray):
+    """Eq. 6 on a logit matrix: loss = -(1/B) sum_i (L_ii - lse_i), lse_i =
+    log sum_j exp(L_ij); dloss/dL = (softmax_j(L_i.) - [i == j]) / B."""
+    L = np.asarray(L, np.float64)
+    B = L.shape[0]
+    m = L.max(axis=1, keepdims=True)
+    lse = m[:, 0] + np.log(np.sum(np.exp(L - m), axis=1))
+    loss = -float(np.mean(np.diag(L) - lse))
+    G = (np.exp(L - lse[:, None]) - np.eye(B)) / B
+    return loss, lse, G
+
+
+def infonce_loss_and_grad(ell: MLP, s_next, a, o):
+    """Loss of Eq. 6 and its gradient with respect to the likelihood model's weights."""
+    X = infonce_pairs(s_next, a, o)
+    B = s_next.shape[0]
+    L = mlp_forward(ell, X)[:, 0].reshape(B, B)
+    loss, lse, G = infonce_loss(L)
+    _, dW, db = mlp_backward(ell, X, G.reshape(-1, 1))
+    return loss, lse, dW, db

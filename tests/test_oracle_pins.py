@@ -463,3 +463,84 @@ def test_flat_params_layout():
     m = O.MLP([np.arange(6.0).reshape(3, 2), np.arange(3.0).reshape(1, 3)],
               [np.array([10.0, 11.0, 12.0]), np.array([20.0])], act=O.ACT_SILU)
     np.testing.assert_array_equal(O.flat_params(m), [0, 1, 2, 3, 4, 5, 10, 11, 12, 0, 1, 2, 20])
+
+
+# --------------------------------------------------------------------------
+# PORPP log-sum-exp backup: scipy's logsumexp, the eta -> infinity limit and a
+# constant-preference closed form.
+# --------------------------------------------------------------------------
+def test_preference_backup_against_scipy_and_limits():
+    rng = np.random.default_rng(13)
+    J = rng.standard_normal(37) * 5.0
+    lp = np.log(rng.dirichlet(np.ones(37)))
+    for eta in (0.1, 1.0, 7.5):
+        V, pi = O.preference_backup(J, eta, lp)
+        assert math.isclose(V, scipy.special.logsumexp(eta * J + lp) / eta, rel_tol=1e-14)
+        np.testing.assert_allclose(pi, scipy.special.softmax(eta * J + lp), rtol=1e-12)
+        assert abs(pi.sum() - 1.0) < 1e-14
+    # eta -> infinity: V -> max_k J_k and pi -> one-hot on the argmax
+    V, pi = O.preference_backup(J, 1e6)
+    assert abs(V - J.max()) < 1e-4 and pi[np.argmax(J)] > 0.999
+    # equal preferences under the uniform reference policy: V = J, pi uniform
+    V, pi = O.preference_backup(np.full(16, -3.25), 2.0)
+    assert math.isclose(V, -3.25, rel_tol=1e-15) and np.allclose(pi, 1 / 16)
+    # huge returns do not overflow (the maximum is subtracted first)
+    V, _ = O.preference_backup(np.array([1e4, 1e4 - 1.0]), 1.0)
+    assert math.isclose(V, 1e4 + math.log1p(math.exp(-1.0)) - math.log(2.0), rel_tol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# InfoNCE (Eq. 6): brute-force pairs, scipy's logsumexp, the constant-logit
+# closed form log B, and finite differences of the loss.
+# --------------------------------------------------------------------------
+def _tiny_ell(rng, d_in=7, h=5):
+    return O.MLP([rng.standard_normal((h, d_in)) * 0.7, rng.standard_normal((1, h)) * 0.7],
+                 [rng.standard_normal(h) * 0.1, rng.standard_normal(1) * 0.1], O.ACT_TANH)
+
+
+def test_infonce_logits_brute_force():
+    rng = np.random.default_rng(21)
+    B, ds, da, do = 5, 3, 2, 2
+    s, a, o = rng.standard_normal((B, ds)), rng.standard_normal((B, da)), rng.standard_normal((B, do))
+    ell = _tiny_ell(rng)
+    L = O.infonce_logits(ell, s, a, o)
+    for i in range(B):
+        for j in range(B):
+            h = np.tanh(ell.W[0] @ np.concatenate([s[i], a[i], o[j]]) + ell.b[0])
+            assert math.isclose(L[i, j], float((ell.W[1] @ h + ell.b[1])[0]), rel_tol=1e-13, abs_tol=1e-14)
+
+
+def test_infonce_loss_scipy_and_constant_logits():
+    rng = np.random.default_rng(22)
+    L = rng.standard_normal((9, 9)) * 3
+    loss, lse, G = O.infonce_loss(L)
+    assert math.isclose(loss, -np.mean(np.diag(L) - scipy.special.logsumexp(L, axis=1)), rel_tol=1e-14)
+    np.testing.assert_allclose(G, (scipy.special.softmax(L, axis=1) - np.eye(9)) / 9, atol=1e-15)
+    np.testing.assert_allclose(G.sum(axis=1), 0.0, atol=1e-15)
+    loss, _, _ = O.infonce_loss(np.full((12, 12), 4.5))
+    assert math.isclose(loss, math.log(12.0), rel_tol=1e-15)
+
+
+def test_infonce_weight_gradient_finite_differences():
+    rng = np.random.default_rng(23)
+    B, ds, da, do = 4, 3, 2, 2
+    s, a, o = rng.standard_normal((B, ds)), rng.standard_normal((B, da)), rng.standard_normal((B, do))
+    ell = _tiny_ell(rng)
+    _, _, dW, db = O.infonce_loss_and_grad(ell, s, a, o)
+    h = 1e-6
+    for l in range(2):
+        for idx in [(0, 0), (ell.W[l].shape[0] - 1, ell.W[l].shape[1] - 1)]:
+            Wp = [w.copy() for w in ell.W]
+            Wm = [w.copy() for w in ell.W]
+            Wp[l][idx] += h
+            Wm[l][idx] -= h
+            fp = O.infonce_loss(O.infonce_logits(O.MLP(Wp, ell.b, ell.act), s, a, o))[0]
+            fm = O.infonce_loss(O.infonce_logits(O.MLP(Wm, ell.b, ell.act), s, a, o))[0]
+            assert math.isclose(dW[l][idx], (fp - fm) / (2 * h), rel_tol=1e-5, abs_tol=1e-9)
+        bp = [v.copy() for v in ell.b]
+        bm = [v.copy() for v in ell.b]
+        bp[l][0] += h
+        bm[l][0] -= h
+        fp = O.infonce_loss(O.infonce_logits(O.MLP(ell.W, bp, ell.act), s, a, o))[0]
+        fm = O.infonce_loss(O.infonce_logits(O.MLP(ell.W, bm, ell.act), s, a, o))[0]
+        assert math.isclose(db[l][0], (fp - fm) / (2 * h), rel_tol=1e-5, abs_tol=1e-9)
