@@ -437,6 +437,74 @@ voila_status voila_distill_step(const voila_mlp* teacher, const voila_mlp* stude
                                 void* workspace, size_t ws_bytes, voila_stream_t stream);
 
 /*
+ * Writes an MLP's weights from a flat FP32 vector [W_0, b_0, W_1, b_1, ...]
+ * (W_l [dims[l+1]][dims[l]] row-major): W in the MLP's precision (BF16 by
+ * round-to-nearest-even), b as FP32. The arrays the descriptor points to are
+ * WRITTEN (the const in voila_mlp is not honoured here). FP32 or BF16 MLPs.
+ */
+voila_status voila_mlp_load_flat(const voila_mlp* mlp, const float* flat, voila_stream_t stream);
+
+/*
+ * PORPP preference backup at the root (Sec. 2.2): with the preferences
+ * Psi_k = (1/eta) log pi_0(a_k | b) + J_k of the K action sequences,
+ *   V = (1/eta) log sum_k exp(eta Psi_k)   (the log-sum-exp operator L_eta),
+ *   pi_k = exp(eta Psi_k - eta V)          (the induced policy).
+ *   J [K] double (device): the Monte-Carlo returns of voila_rollout.
+ *   log_pi0 [K] double (device) or NULL: uniform reference policy (-log K).
+ *   V_out  device double; pi_out [K] device double or NULL.
+ * FP64, the maximum subtracted before the exponentials, one CTA in a fixed
+ * summation order. eta > 0.
+ */
+voila_status voila_preference_backup(const double* J, const double* log_pi0, int32_t K, double eta,
+                                     double* V_out, double* pi_out, voila_stream_t stream);
+
+/* Workspace of voila_infonce_forward for a batch of B tuples, in bytes. */
+voila_status voila_infonce_workspace_size(const voila_mlp* ell, int32_t B, size_t* bytes);
+
+/*
+ * InfoNCE objective of the likelihood model (Eq. 6) on B tuples
+ * (s'_i, a_i, o_i): the logits of all B x B combinations
+ *   L[i][j] = l([s'_i; a_i; o_j]),
+ * the row log-sum-exp lse_i = log sum_j exp(L[i][j]), the loss
+ * -(1/B) sum_i (L[i][i] - lse_i) and dloss/dL[i][j] = (exp(L[i][j] - lse_i)
+ * - [i == j]) / B.
+ *   S [B][d_s], A [B][d_a], Ob [B][d_o] float (device); ell dims[0] =
+ *   d_s + d_a + d_o, scalar output. B <= 46340.
+ *   L_out [B][B] float or NULL (kept in the workspace), lse_out [B] double or
+ *   NULL, loss_out device double, G_out [B][B] float or NULL.
+ *   workspace  device, 1024-byte aligned; starts with the status word.
+ * A BF16 likelihood with d_s = 8, d_a = 2, d_o = 6 and hidden widths that are
+ * multiples of 64 up to 256 runs on the tensor cores (BF16 operands and
+ * activations, FP32 accumulation); any other on the CUDA cores in FP32.
+ */
+voila_status voila_infonce_forward(const voila_mlp* ell, const float* S, const float* A,
+                                   const float* Ob, int32_t B, int32_t d_s, int32_t d_a,
+                                   int32_t d_o, float* L_out, double* lse_out, double* loss_out,
+                                   float* G_out, void* workspace, size_t ws_bytes,
+                                   voila_stream_t stream);
+
+/* Workspace of voila_infonce_step for a batch of B tuples, in bytes. */
+voila_status voila_infonce_step_workspace_size(const voila_mlp* ell, int32_t B, size_t* bytes);
+
+/*
+ * One training step of the likelihood model on Eq. 6: the training forward
+ * over the B^2 pair rows (CUDA cores, FP32 arithmetic on the MLP's FP32 or
+ * BF16 weights), the loss and dloss/dL as voila_infonce_forward, the
+ * hand-written backward, voila_adam_step on `master` (flat FP32 layout of
+ * voila_mlp_load_flat) and voila_mlp_load_flat(ell, master).
+ *   loss_out  device double (the loss before the update); grad_out [n_params]
+ *             float or NULL.
+ *   workspace device, 1024-byte aligned. The batch of B^2 rows saves its
+ *             hidden pre-activations: about 4 B^2 (d_in + 3 + 3 sum of hidden
+ *             widths) bytes.
+ */
+voila_status voila_infonce_step(const voila_mlp* ell, float* master, float* adam_m, float* adam_v,
+                                const voila_adam* opt, const float* S, const float* A,
+                                const float* Ob, int32_t B, int32_t d_s, int32_t d_a, int32_t d_o,
+                                double* loss_out, float* grad_out, void* workspace,
+                                size_t ws_bytes, voila_stream_t stream);
+
+/*
  * Raw Philox4x32-10 words: out[4 i + j] = word j of counter (i, c1, c2, c3),
  * i < n. out holds 4 n uint32 (device).
  */

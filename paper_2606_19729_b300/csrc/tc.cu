@@ -54,6 +54,10 @@ constexpr int kABytes = 4 * 128 * 128;    // 128 rows x 256 BF16, four 64-wide K
 constexpr int kMaxTcLayers = 16;
 constexpr int kSuperRows = 4 * kTileRows;  // rows of one work item (two tiles on each CTA of the pair)
 constexpr long long kSpinLimit = 4000000000LL;  // ~2 s of SM clock per wait
+// What the rows of a launch are: rollout rows (n, k) over H planning steps;
+// DDIM teacher samples over the sampler's steps; likelihood pairs (i, j) of
+// the InfoNCE objective (one evaluation, H = 1).
+constexpr int kModeRollout = 0, kModeDdim = 1, kModePairs = 2;
 
 struct TcLayer {
   int Kp;           // input width rounded up to 16 (MMA K steps of 16)
@@ -113,6 +117,12 @@ struct TcParams {
   float* ddim_y;
   float ddim_cx[64];
   float ddim_cv[64];
+  // likelihood pairs: row i * B + j evaluates l([s'_i (8); a_i (2); o_j (6)]) -> out[row]
+  const float* pair_s;
+  const float* pair_a;
+  const float* pair_o;
+  long long pair_B;
+  float* pair_out;
 };
 
 __device__ __forceinline__ int item_planner(const TcParams& p, long long it) {
@@ -304,12 +314,17 @@ __device__ __forceinline__ void write_ddim_input(uint8_t* A, int r, const float*
 // (256 rows per pair); the two 256-column TMEM halves and the two 64 KB A
 // buffers hold the two column halves of a layer (K up to 512); the epilogue
 // starts when both halves' MMAs are done (the next input overwrites A).
-// DDIM (with WIDE, DS = 8, DA = 10, DW = 0): the rows are teacher samples and
-// the H steps are the sampler's steps; no reward, the output is x per row.
-template <int DS, int DA, int DW, bool F8, bool WIDE, bool DDIM = false>
+// MODE kModeDdim (with WIDE, DS = 8, DA = 10, DW = 0): the rows are teacher
+// samples and the H steps are the sampler's steps; no reward, the output is x
+// per row. MODE kModePairs (DS = 8, DA = 2, DW = 6, not WIDE): the rows are
+// likelihood pairs; the MLP's scalar output is stored per row.
+template <int DS, int DA, int DW, bool F8, bool WIDE, int MODE = kModeRollout>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     rollout_tc_kernel(const __grid_constant__ TcParams p) {
+  constexpr bool DDIM = MODE == kModeDdim;
+  constexpr bool PAIRS = MODE == kModePairs;
   static_assert(!DDIM || (WIDE && !F8 && DS == 8 && DA == 10 && DW == 0), "DDIM sampler layout");
+  static_assert(!PAIRS || (!WIDE && !F8 && DS == 8 && DA == 2 && DW == 6), "likelihood pair layout");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* Abuf[2] = {smem, smem + kABytes};
@@ -556,6 +571,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           a[9] = valid ? __ldg(p.ddim_a + (size_t)row * 2 + 1) : 0.0f;
           write_ddim_input(A, r, s, a, p.ddim_emb);
         }
+      } else if constexpr (PAIRS) {
+        if (owner) {
+          const long long pi = valid ? row / p.pair_B : 0, pj = valid ? row % p.pair_B : 0;
+          float x[16];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) x[i] = valid ? __ldg(p.pair_s + pi * 8 + i) : 0.0f;
+          x[8] = valid ? __ldg(p.pair_a + pi * 2) : 0.0f;
+          x[9] = valid ? __ldg(p.pair_a + pi * 2 + 1) : 0.0f;
+#pragma unroll
+          for (int i = 0; i < 6; ++i) x[10 + i] = valid ? __ldg(p.pair_o + pj * 6 + i) : 0.0f;
+          store_row<16>(A, r, x);
+        }
       } else if (owner) {
 #pragma unroll
         for (int i = 0; i < DS; ++i) s[i] = valid ? __ldg(PL.particles + (size_t)n * DS + i) : 0.0f;
@@ -609,6 +636,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 else epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
               }
             }
+          } else if (PAIRS && owner) {
+            float v[16];
+            ptx::tmem_ld16(tm, v);
+            ptx::tmem_wait_ld();
+            if (valid) p.pair_out[row] = v[0] + bl[0];
           } else if (DDIM && owner) {
             // teacher output v: x <- cx[t] x + cv[t] (v + b), then the next step's input
             float v[16];
@@ -665,7 +697,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           }
         }
       }
-      if constexpr (DDIM) {
+      if constexpr (PAIRS) {
+      } else if constexpr (DDIM) {
         if (owner && valid && ok) {
 #pragma unroll
           for (int i = 0; i < DS; i += 4)
@@ -859,9 +892,9 @@ size_t tc_smem_bytes(int vec_floats) {
 
 // Launches one persistent CTA pair per co-resident cluster slot (at most
 // `max_clusters`, never more than there are super-pairs).
-template <int DS, int DA, int DW, bool F8, bool WIDE, bool DDIM = false>
+template <int DS, int DA, int DW, bool F8, bool WIDE, int MODE = kModeRollout>
 cudaError_t launch_tc(const TcParams& p, size_t smem, long long max_clusters, cudaStream_t s) {
-  auto k = rollout_tc_kernel<DS, DA, DW, F8, WIDE, DDIM>;
+  auto k = rollout_tc_kernel<DS, DA, DW, F8, WIDE, MODE>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
@@ -1117,7 +1150,77 @@ voila_status tc_ddim_sample(const voila_mlp* teacher, const float* S, const floa
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const long long nclusters = p.total_items < nsm / 2 ? p.total_items : nsm / 2;
   const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total);
-  const cudaError_t e = launch_tc<8, 10, 0, false, true, true>(p, smem, nclusters, s);
+  const cudaError_t e = launch_tc<8, 10, 0, false, true, kModeDdim>(p, smem, nclusters, s);
+  return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
+}
+
+bool tc_pairs_supported(const voila_mlp* ell, int d_s, int d_a, int d_o) {
+  if (!ell || ell->prec != VOILA_BF16 || d_s != 8 || d_a != 2 || d_o != 6) return false;
+  if (ell->dims[0] != 16 || ell->dims[ell->n_layers] != 1) return false;
+  Plan pl = make_plan(ell, nullptr);
+  return pl.ok && !pl.wide;
+}
+
+size_t tc_pairs_scratch_bytes(const voila_mlp* ell) {
+  Plan pl = make_plan(ell, nullptr);
+  return pl.ok ? pl.total : 0;
+}
+
+voila_status tc_likelihood_pairs(const voila_mlp* ell, const float* S, const float* A, const float* Ob, long long B,
+                                 float* out, WsHeader* hdr, void* scratch, cudaStream_t s) {
+  Plan pl = make_plan(ell, nullptr);
+  if (!pl.ok || pl.wide) return VOILA_ERR_UNSUPPORTED;
+  if ((uintptr_t)scratch % 1024) return VOILA_ERR_WORKSPACE;
+  TcParams& p = pl.p;
+  TcPlanner& q = p.pl[0];
+  q.particles = S;  // unused by the pair rows
+  q.actions = A;
+  q.G = nullptr;
+  q.rows = B * B;
+  q.N = 1;
+  q.H = 1;
+  q.planner = 0;
+  p.P = 1;
+  p.total_items = (q.rows + kSuperRows - 1) / kSuperRows;
+  p.item_end[0] = p.total_items;
+  uint8_t* wst = (uint8_t*)scratch;
+  float* bias_all = (float*)(wst + (pl.wbytes + 1023) / 1024 * 1024);
+  pl.pack.wout = wst;
+  pl.pack.bout = bias_all;
+  {
+    const long long total = pl.pack.elems_end[pl.pack.n - 1];
+    long long blocks = (total + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    pack_kernel<<<(int)blocks, 256, 0, s>>>(pl.pack);
+    if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return VOILA_ERR_CUDA;
+  for (int l = 0; l < p.n_total; ++l) {
+    const cuuint64_t gdim[2] = {128, (cuuint64_t)pl.total_rows};  // bytes
+    const cuuint64_t gstride[1] = {128};
+    const cuuint32_t box[2] = {128, (cuuint32_t)p.layers[l].box_rows};
+    const cuuint32_t estride[2] = {1, 1};
+    if (encode(&p.tmap[l], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)wst, gdim, gstride, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return VOILA_ERR_CUDA;
+  }
+  p.bias_all = bias_all;
+  p.reward_kind = VOILA_REWARD_GOAL;
+  p.goal_dims = 0;
+  p.hdr = hdr;
+  p.pair_s = S;
+  p.pair_a = A;
+  p.pair_o = Ob;
+  p.pair_B = B;
+  p.pair_out = out;
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long nclusters = p.total_items < nsm / 2 ? p.total_items : nsm / 2;
+  const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total);
+  const cudaError_t e = launch_tc<8, 2, 6, false, false, kModePairs>(p, smem, nclusters, s);
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
 

@@ -45,4 +45,11 @@ voila_status tc_ddim_sample(const voila_mlp* teacher, const float* S, const floa
                             int T, const double* cx, const double* cv, const double* freq, float* Y, WsHeader* hdr,
                             void* scratch, cudaStream_t s);
 
+// Likelihood on all B x B pairs on the tensor cores (BF16 likelihood MLP
+// 16 -> 256 x L -> 1, s' 8, a 2, o 6): out[i * B + j] = l([s'_i; a_i; o_j]).
+bool tc_pairs_supported(const voila_mlp* ell, int d_s, int d_a, int d_o);
+size_t tc_pairs_scratch_bytes(const voila_mlp* ell);
+voila_status tc_likelihood_pairs(const voila_mlp* ell, const float* S, const float* A, const float* Ob, long long B,
+                                 float* out, WsHeader* hdr, void* scratch, cudaStream_t s);
+
 }  // namespace voila

@@ -720,18 +720,29 @@ voila_status voila_distill_step(const voila_mlp* teacher, const voila_mlp* stude
   st = voila_adam_step(master, grads, adam_m, adam_v, np, opt->lr, opt->beta1, opt->beta2, opt->eps, opt->step,
                        stream);
   if (st != VOILA_OK) return st;
+  return voila_mlp_load_flat(student, master, stream);
+}
+
+voila_status voila_mlp_load_flat(const voila_mlp* mlp, const float* flat, voila_stream_t stream) {
+  if (!mlp || !flat || mlp->n_layers < 1 || mlp->n_layers > VOILA_MAX_LAYERS) return VOILA_ERR_ARG;
+  if (mlp->prec != VOILA_FP32 && mlp->prec != VOILA_BF16) return VOILA_ERR_UNSUPPORTED;
+  for (int l = 0; l < mlp->n_layers; ++l)
+    if (!mlp->W[l] || !mlp->b[l]) return VOILA_ERR_ARG;
+  long long off[2 * VOILA_MAX_LAYERS + 1];
+  const long long np = param_layout(mlp, off);
   PublishArgs pa;
   memset(&pa, 0, sizeof(pa));
-  pa.n_layers = student->n_layers;
-  for (int i = 0; i <= 2 * student->n_layers; ++i) pa.off[i] = off[i];
-  for (int l = 0; l < student->n_layers; ++l) {
-    pa.W[l] = const_cast<void*>(student->W[l]);
-    pa.b[l] = const_cast<float*>(student->b[l]);
+  pa.n_layers = mlp->n_layers;
+  for (int i = 0; i <= 2 * mlp->n_layers; ++i) pa.off[i] = off[i];
+  for (int l = 0; l < mlp->n_layers; ++l) {
+    pa.W[l] = const_cast<void*>(mlp->W[l]);
+    pa.b[l] = const_cast<float*>(mlp->b[l]);
   }
-  if (student->prec == VOILA_BF16)
-    publish_kernel<__nv_bfloat16><<<grid_for(np, 256), 256, 0, s>>>(master, pa);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (mlp->prec == VOILA_BF16)
+    publish_kernel<__nv_bfloat16><<<grid_for(np, 256), 256, 0, s>>>(flat, pa);
   else
-    publish_kernel<float><<<grid_for(np, 256), 256, 0, s>>>(master, pa);
+    publish_kernel<float><<<grid_for(np, 256), 256, 0, s>>>(flat, pa);
   return cudaGetLastError() == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
 

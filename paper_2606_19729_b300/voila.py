@@ -106,6 +106,14 @@ _lib_distill_ws = _sig("voila_distill_step_workspace_size", c_int32, POINTER(voi
                        c_int32, c_int32, POINTER(c_size_t))
 _lib_distill = _sig("voila_distill_step", c_int32, POINTER(voila_mlp), POINTER(voila_mlp), POINTER(voila_ddim), _P, _P,
                     _P, POINTER(voila_adam), _P, _P, _P, c_int32, c_int32, c_int32, c_int32, _P, _P, _P, c_size_t, _P)
+_lib_load_flat = _sig("voila_mlp_load_flat", c_int32, POINTER(voila_mlp), _P, _P)
+_lib_backup = _sig("voila_preference_backup", c_int32, _P, _P, c_int32, c_double, _P, _P, _P)
+_lib_nce_ws = _sig("voila_infonce_workspace_size", c_int32, POINTER(voila_mlp), c_int32, POINTER(c_size_t))
+_lib_nce_fwd = _sig("voila_infonce_forward", c_int32, POINTER(voila_mlp), _P, _P, _P, c_int32, c_int32, c_int32,
+                    c_int32, _P, _P, _P, _P, _P, c_size_t, _P)
+_lib_nce_step_ws = _sig("voila_infonce_step_workspace_size", c_int32, POINTER(voila_mlp), c_int32, POINTER(c_size_t))
+_lib_nce_step = _sig("voila_infonce_step", c_int32, POINTER(voila_mlp), _P, _P, _P, POINTER(voila_adam), _P, _P, _P,
+                     c_int32, c_int32, c_int32, c_int32, _P, _P, _P, c_size_t, _P)
 _lib_philox = _sig("voila_philox_fill", c_int32, c_uint64, c_uint32, c_uint32, c_uint32, _P, c_int64, _P)
 _lib_normal = _sig("voila_normal_fill", c_int32, c_uint64, c_uint32, c_uint32, c_uint32, c_uint32, c_int32,
                    _P, c_int64, _P)
@@ -424,3 +432,46 @@ def voila_distill_step(teacher: DeviceMLP, student: DeviceMLP, ddim: voila_ddim,
                         _ptr(omega, torch.float32), B, S.shape[1], A.shape[1], d_x, _ptr(loss_out, torch.float64),
                         _ptr(grad_out, torch.float32), _ptr(workspace), workspace.numel(), _stream(stream)),
            "voila_distill_step")
+
+
+def voila_mlp_load_flat(mlp: DeviceMLP, flat: torch.Tensor, stream=None):
+    _check(_lib_load_flat(ctypes.byref(mlp.desc), _ptr(flat, torch.float32), _stream(stream)), "voila_mlp_load_flat")
+
+
+def voila_preference_backup(J: torch.Tensor, log_pi0: Optional[torch.Tensor], eta: float, V: torch.Tensor,
+                            pi: Optional[torch.Tensor], stream=None):
+    _check(_lib_backup(_ptr(J, torch.float64), _ptr(log_pi0, torch.float64), J.numel(), eta, _ptr(V, torch.float64),
+                       _ptr(pi, torch.float64), _stream(stream)), "voila_preference_backup")
+
+
+def voila_infonce_workspace_size(ell: DeviceMLP, B: int) -> int:
+    n = c_size_t(0)
+    _check(_lib_nce_ws(ctypes.byref(ell.desc), B, ctypes.byref(n)), "voila_infonce_workspace_size")
+    return n.value
+
+
+def voila_infonce_forward(ell: DeviceMLP, S: torch.Tensor, A: torch.Tensor, Ob: torch.Tensor,
+                          L: Optional[torch.Tensor], lse: Optional[torch.Tensor], loss: torch.Tensor,
+                          G: Optional[torch.Tensor], workspace: torch.Tensor, stream=None):
+    B = S.shape[0]
+    _check(_lib_nce_fwd(ctypes.byref(ell.desc), _ptr(S, torch.float32), _ptr(A, torch.float32),
+                        _ptr(Ob, torch.float32), B, S.shape[1], A.shape[1], Ob.shape[1], _ptr(L, torch.float32),
+                        _ptr(lse, torch.float64), _ptr(loss, torch.float64), _ptr(G, torch.float32),
+                        _ptr(workspace), workspace.numel(), _stream(stream)), "voila_infonce_forward")
+
+
+def voila_infonce_step_workspace_size(ell: DeviceMLP, B: int) -> int:
+    n = c_size_t(0)
+    _check(_lib_nce_step_ws(ctypes.byref(ell.desc), B, ctypes.byref(n)), "voila_infonce_step_workspace_size")
+    return n.value
+
+
+def voila_infonce_step(ell: DeviceMLP, master: torch.Tensor, adam_m: torch.Tensor, adam_v: torch.Tensor,
+                       opt: voila_adam, S: torch.Tensor, A: torch.Tensor, Ob: torch.Tensor, loss: torch.Tensor,
+                       grad_out: Optional[torch.Tensor], workspace: torch.Tensor, stream=None):
+    B = S.shape[0]
+    _check(_lib_nce_step(ctypes.byref(ell.desc), _ptr(master, torch.float32), _ptr(adam_m, torch.float32),
+                         _ptr(adam_v, torch.float32), ctypes.byref(opt), _ptr(S, torch.float32),
+                         _ptr(A, torch.float32), _ptr(Ob, torch.float32), B, S.shape[1], A.shape[1], Ob.shape[1],
+                         _ptr(loss, torch.float64), _ptr(grad_out, torch.float32), _ptr(workspace),
+                         workspace.numel(), _stream(stream)), "voila_infonce_step")

@@ -16,6 +16,7 @@ the five workload configurations:
 * ``sweep``       d_s=12, d_a=3, d_omega=16, generator 4x512 SiLU, N=16384, K=2048, H=25
 * ``distill``     teacher 3x512 + 64-d step embedding, student 3x256, B=65536
 * ``batched``     64 planners sharing the mid-size MLPs, uneven N, K, H
+* ``infonce``     likelihood 16->256x3->1 on B=1024 tuples (B^2 pairs)
 """
 from __future__ import annotations
 
@@ -182,6 +183,35 @@ def distill(seed: int = 3, B: int = 65536, teacher_prec: int = PREC_FP32) -> Dis
     A = round_to(rng.uniform(-1.0, 1.0, size=(B, d_a)), PREC_FP32)
     omega = round_to(rng.normal(0.0, 1.0, size=(B, d_x)), PREC_FP32)
     return DistillWorkload("distill", d_s, d_a, d_x, B, 32, 1e-4, 0.02, emb, seed, teacher, student, S, A, omega)
+
+
+
+@dataclass
+class InfoNCEWorkload:
+    """Likelihood-model objective (Eq. 6) on B synthetic tuples (s'_i, a_i, o_i)."""
+    name: str
+    d_s: int
+    d_a: int
+    d_o: int
+    B: int
+    seed: int
+    ell: MLPSpec
+    S: np.ndarray                  # [B, d_s] ~ N(0, I)
+    A: np.ndarray                  # [B, d_a] ~ U[-1, 1]
+    O: np.ndarray                  # [B, d_o] = s'[:d_o] + 0.1 N(0, I)
+    lr: float = 1e-3
+
+
+def infonce(seed: int = 5, B: int = 1024, prec: int = PREC_BF16) -> InfoNCEWorkload:
+    """Likelihood 16->256x3->1 SiLU (the planning shapes: s' 8, a 2, o 6); the
+    observation of tuple i is the first 6 state coordinates plus N(0, 0.1^2)."""
+    rng = np.random.default_rng(seed)
+    d_s, d_a, d_o = 8, 2, 6
+    ell = xavier_mlp(rng, [d_s + d_a + d_o, 256, 256, 256, 1], ACT_SILU, prec)
+    S = round_to(rng.normal(0.0, 1.0, size=(B, d_s)), PREC_FP32)
+    A = round_to(rng.uniform(-1.0, 1.0, size=(B, d_a)), PREC_FP32)
+    O = round_to(S[:, :d_o] + rng.normal(0.0, 0.1, size=(B, d_o)), PREC_FP32)
+    return InfoNCEWorkload("infonce", d_s, d_a, d_o, B, seed, ell, S, A, O)
 
 
 def batched_planners(seed: int = 4, P: int = 64):
