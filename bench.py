@@ -4,7 +4,8 @@
 One step = one SIR belief update (N particles: propose with g_T, weight with
 the likelihood MLP, normalise, resample) followed by the Monte-Carlo rollout
 of the updated belief over K action sequences x H steps with the generator
-and reward MLPs, the per-sequence return reduction and the argmax.
+and reward MLPs, the per-sequence return reduction and the argmax, and the
+PORPP log-sum-exp backup of the returns (value and policy).
 
 Default workload ("mid_bf16"): state 8, action 2, observation 6, latent 8;
 3x256 SiLU MLPs with BF16 weights; N=4096, K=1024, H=20, gamma=0.98; all
@@ -39,7 +40,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mid_bf16", "mid_fp32", "small_fp32", "batched", "sweep", "distill"], default="mid_bf16")
+    ap.add_argument("--workload", choices=["mid_bf16", "mid_fp32", "small_fp32", "batched", "sweep", "distill", "infonce"], default="mid_bf16")
     ap.add_argument("--cpu-seqs", type=int, default=8, help="action sequences in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-seqs", type=int, default=16, help="sequences for the FP32-form comparison (0: skip)")
@@ -573,6 +574,102 @@ def run_distill(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_infonce(args, rank, world, local):
+    """InfoNCE objective of the likelihood model (Eq. 6) on B=1024 tuples: the
+    16-256-256-256-1 SiLU likelihood (BF16) on all B^2 = 1,048,576 pairs on the
+    tensor cores, row log-sum-exp, loss and dloss/dL; then the likelihood's
+    training step (FP32 arithmetic, hand-written backward, Adam) timed beside it."""
+    import torch
+    from paper_2606_19729_b300 import voila as V
+    from paper_2606_19729_b300 import workloads as WL
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = WL.infonce(B=args.B or 1024)
+    B = wl.B
+    stream = torch.cuda.current_stream()
+    ell = V.DeviceMLP.from_spec(wl.ell)
+    S, A, Ob = (torch.from_numpy(x).float().cuda() for x in (wl.S, wl.A, wl.O))
+    L = torch.empty(B, B, device="cuda")
+    G = torch.empty(B, B, device="cuda")
+    lse = torch.empty(B, dtype=torch.float64, device="cuda")
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    ws = V.alloc_workspace(V.voila_infonce_workspace_size(ell, B))
+
+    def fwd():
+        V.voila_infonce_forward(ell, S, A, Ob, L, lse, loss, G, ws)
+
+    for _ in range(args.warmup):
+        fwd()
+    torch.cuda.synchronize()
+    reps = max(args.steps, 20)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    with Clocks(local) as clk:
+        for e0, e1 in ev:
+            e0.record(stream)
+            fwd()
+            e1.record(stream)
+        torch.cuda.synchronize()
+    assert V.workspace_status(ws) == V.OK
+    fwd_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / reps
+    sec = max_over_ranks(fwd_s * reps, world, torch.device("cuda", local))
+    pairs = B * B
+    value = aggregate_rate(pairs * reps, world, sec)
+    fpp = sum(2 * w.shape[0] * w.shape[1] for w in wl.ell.W)
+    achieved = fpp * pairs / fwd_s / 1e12
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = peaks.get("bf16_tflops_sustained", 1400.0)
+    # training step of the likelihood (CUDA cores), a few steps
+    master = torch.cat([torch.cat([w.float().reshape(-1), b.reshape(-1)]) for w, b in zip(ell.W, ell.b)])
+    m, v = torch.zeros_like(master), torch.zeros_like(master)
+    sws = V.alloc_workspace(V.voila_infonce_step_workspace_size(ell, B))
+    step_losses = torch.empty(3, dtype=torch.float64, device="cuda")
+    sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+    for i, (e0, e1) in enumerate(sev):
+        e0.record(stream)
+        V.voila_infonce_step(ell, master, m, v, V.voila_adam(wl.lr, 0.9, 0.999, 1e-8, i + 1), S, A, Ob,
+                             step_losses[i:i + 1], None, sws)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in sev]
+    line = {"metric": "InfoNCE pair evaluations/s", "value": value, "unit": "pairs/s", "n_gpus": world,
+            "steps": reps, "warmup": args.warmup, "ms_per_step": 1e3 * fwd_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic (seeded tuples, random-init likelihood)",
+            "config": {"workload": f"infonce: B={B} tuples (B^2={pairs} pairs), likelihood 16x256x256x256x1 SiLU "
+                                   "BF16 on the tensor cores; row log-sum-exp, loss, dloss/dL"},
+            "loss": loss.item(),
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "voila_infonce_forward (weight pack + pair kernel + row LSE + loss)",
+                         "peak_kind": "measured bf16 sustained"},
+            "train_step": {"ms": statistics.median(step_ms), "loss_first": float(step_losses[0].item()),
+                           "loss_last": float(step_losses[-1].item()),
+                           "note": "FP32 CUDA-core training forward and backward over all B^2 pair rows"},
+            "gpu_launches": 4 * reps, "clocks": clk.summary()}
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import voila_oracle as O
+        rows = 256  # tuples i of the sample: their B-pair rows of logits and log-sum-exp
+        t0 = time.perf_counter()
+        X = O.infonce_pairs(wl.S, wl.A, wl.O).reshape(B, B, -1)[:rows].reshape(-1, wl.ell.dims[0])
+        Lo = O.mlp_forward(O.MLP(wl.ell.W, wl.ell.b, wl.ell.act), X)[:, 0].reshape(rows, B)
+        mo = Lo.max(axis=1, keepdims=True)
+        _ = mo[:, 0] + np.log(np.exp(Lo - mo).sum(axis=1))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": rows * B / dt, "unit": "pairs/s", "cores": blas_threads(), "kind": "oracle",
+                                "sample": f"FP64 oracle logits and row log-sum-exp of {rows} of {B} rows "
+                                          f"({rows * B} pairs) in {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -589,6 +686,9 @@ def main():
         return
     if args.workload == "distill":
         run_distill(args, rank, world, local)
+        return
+    if args.workload == "infonce":
+        run_infonce(args, rank, world, local)
         return
 
     import torch
@@ -632,6 +732,9 @@ def main():
     p_new = torch.empty_like(particles)
     J = torch.empty(K, dtype=torch.float64, device=dev)
     best = torch.empty(1, dtype=torch.int32, device=dev)
+    Vb = torch.empty(1, dtype=torch.float64, device=dev)
+    pi = torch.empty(K, dtype=torch.float64, device=dev)
+    eta = 1.0
     ws_b = V.alloc_workspace(V.voila_belief_update_workspace_size(g, lik, N))
     ws_r = V.alloc_workspace(V.voila_rollout_workspace_size(g, R, N, K, H))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -640,13 +743,14 @@ def main():
         V.voila_belief_update(g, lik, p_in, None, a0, obs_t, wl.d_omega, wl.lam, wl.seed, 1, planner, p_new, None,
                               None, None, None, ws_b)
         V.voila_rollout(g, R, p_new, None, act_seq, wl.d_omega, wl.gamma, wl.seed, planner, J, None, best, ws_r)
+        V.voila_preference_backup(J, None, eta, Vb, pi)
 
     for _ in range(args.warmup):
         step(particles, obs, actions, action)
     torch.cuda.synchronize()
     assert V.workspace_status(ws_b) == V.OK and V.workspace_status(ws_r) == V.OK
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -660,11 +764,13 @@ def main():
             V.voila_rollout(g, R, p_new, None, actions, wl.d_omega, wl.gamma, wl.seed, planner, J, None, best,
                             ws_r)
             ev[i][2].record(stream)
+            V.voila_preference_backup(J, None, eta, Vb, pi)
+            ev[i][3].record(stream)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     roll_ms = [e[1].elapsed_time(e[2]) for e in ev]
     total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
     assert V.workspace_status(ws_b) == V.OK and V.workspace_status(ws_r) == V.OK
@@ -677,11 +783,12 @@ def main():
     h_obs = obs.cpu().pin_memory()
     h_J = torch.empty(K, dtype=torch.float64).pin_memory()
     h_best = torch.empty(1, dtype=torch.int32).pin_memory()
+    h_V = torch.empty(1, dtype=torch.float64).pin_memory()
     d_particles = torch.empty_like(particles)
     d_actions = torch.empty_like(actions)
     d_obs = torch.empty_like(obs)
     h2d = h_particles.numel() * 4 + h_actions.numel() * 4 + h_obs.numel() * 4
-    d2h = K * 8 + 4
+    d2h = K * 8 + 4 + 8
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
     for i in range(args.steps + 1):
@@ -694,6 +801,7 @@ def main():
         step(d_particles, d_obs, d_actions, d_actions[0, 0])
         h_J.copy_(J, non_blocking=True)
         h_best.copy_(best, non_blocking=True)
+        h_V.copy_(Vb, non_blocking=True)
         if i > 0:
             e2e_ev[i - 1][1].record(stream)
         torch.cuda.synchronize()
@@ -744,7 +852,7 @@ def main():
                 [e[0].elapsed_time(e[1]) for e in ev]),
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 6 * args.steps,
+            "gpu_launches": 7 * args.steps,
             "clocks": clk.summary()}
     J8 = None
     if wl.prec == 1 and rank == 0 and not args.no_forms:
