@@ -591,3 +591,103 @@ def infonce_loss_and_grad(ell: MLP, s_next, a, o):
     loss, lse, G = infonce_loss(L)
     _, dW, db = mlp_backward(ell, X, G.reshape(-1, 1))
     return loss, lse, dW, db
+
+
+# ---------------------------------------------------------------------------
+# Vectorised progressive widening of the observation branches (Sec. 4.3):
+# simulations are grouped by their parent action node; an action node a gets
+# a new observation branch, sampled by f_Z (Eq. 5), when
+#     |C(a)| < k_o N(a)^alpha_o,
+# otherwise the simulation joins an existing branch. The successor states of
+# each (action node, branch) are then weighted by exp(l(s', a, o_branch)/lambda)
+# and resampled.
+# Readings (the paper leaves these open):
+# * within a node, simulations are taken in batch order; the m-th one of the
+#   node sees the visit count N(a) + m + 1 and the branch count left by the
+#   earlier ones; a branch cap C_max bounds |C(a)|;
+# * the threshold k_o n^alpha_o is evaluated in FP64 as k_o * pow(n, alpha_o);
+# * a simulation that does not widen joins branch floor(u |C(a)|), u the
+#   24-bit uniform of word 0 of Philox at counter (m, step, 0, stream 6);
+# * omega_Z of simulation m is drawn at counter (m, 0, step) of stream 3;
+# * each (node, branch) group is resampled as the SIR step does (log-sum-exp
+#   normalisation, 2^-52 quantisation, systematic resampling), with u0 from
+#   counter (node, branch, step, stream 2 block 1).
+# ---------------------------------------------------------------------------
+STREAM_PW_BRANCH = 6
+
+
+@dataclass
+class PWTree:
+    """The action-node tensors the widening reads and updates."""
+    act: np.ndarray    # [n_nodes, d_a] action of each action node
+    N: np.ndarray      # [n_nodes] visit counts
+    C: np.ndarray      # [n_nodes] observation-branch counts
+    obs: np.ndarray    # [n_nodes, C_max, d_o] branch observations
+
+
+@dataclass
+class PWResult:
+    branch: np.ndarray     # [M] branch of each simulation
+    widened: np.ndarray    # [M] bool: the simulation created its branch
+    ell: np.ndarray        # [M] l(s'_m, a, o_branch)
+    w: np.ndarray          # [M] quantised weight within its (node, branch) group
+    idx: np.ndarray        # [M] simulation whose successor state fills slot m
+    s_out: np.ndarray      # [M, d_s] resampled successor states
+
+
+def pw_branch_uniform(seed: int, m, step: int, planner: int):
+    k0, k1 = seed_key(seed)
+    m = np.asarray(m, dtype=np.uint64)
+    w0, _, _, _ = philox4x32_10(m, 0, step, counter_word3(STREAM_PW_BRANCH, planner, 0), k0, k1)
+    return uniform24(w0)
+
+
+def pw_group_uniform(seed: int, node: int, branch: int, step: int, planner: int) -> float:
+    k0, k1 = seed_key(seed)
+    w0, w1, _, _ = philox4x32_10(node, branch, step, counter_word3(STREAM_RESAMPLE, planner, 1), k0, k1)
+    return float(uniform53(w0, w1))
+
+
+def progressive_widening(tree: PWTree, node: np.ndarray, s_next: np.ndarray, g_Z: MLP, L: Likelihood,
+                         d_omega: int, k_o: float, alpha_o: float, lam: float, seed: int, step: int,
+                         planner: int = 0) -> PWResult:
+    """Updates `tree` in place (N, C, obs) and returns the per-simulation results."""
+    node = np.asarray(node, np.int64)
+    s_next = np.asarray(s_next, np.float64)
+    M = node.shape[0]
+    C_max = tree.obs.shape[1]
+    branch = np.zeros(M, np.int64)
+    widened = np.zeros(M, bool)
+    for a in np.unique(node):
+        ms = np.nonzero(node == a)[0]          # ascending simulation index
+        C = int(tree.C[a])
+        n0 = int(tree.N[a])
+        for r, m in enumerate(ms):
+            n = n0 + r + 1
+            if C < C_max and C < k_o * math.pow(n, alpha_o):
+                branch[m] = C
+                widened[m] = True
+                x = [s_next[m], tree.act[a]]
+                if d_omega > 0:
+                    x.append(np.reshape(normals(seed, m, 0, step, STREAM_OBS_OMEGA, planner, d_omega), -1))
+                tree.obs[a, C] = mlp_forward(g_Z, np.concatenate(x)[None, :])[0]
+                C += 1
+            else:
+                u = float(pw_branch_uniform(seed, m, step, planner))
+                branch[m] = min(C - 1, int(math.floor(u * C)))
+        tree.N[a] = n0 + len(ms)
+        tree.C[a] = C
+    ell = np.empty(M)
+    for m in range(M):
+        ell[m] = likelihood(L, s_next[m:m + 1], np.asarray(tree.act[node[m]], np.float64),
+                            np.asarray(tree.obs[node[m], branch[m]], np.float64))[0]
+    w = np.zeros(M)
+    idx = np.zeros(M, np.int64)
+    for key in sorted(set(zip(node.tolist(), branch.tolist()))):
+        ms = np.nonzero((node == key[0]) & (branch == key[1]))[0]
+        wg, _ = log_normalise(ell[ms] / lam)
+        q = quantise_weights(wg)
+        u0 = pw_group_uniform(seed, key[0], key[1], step, planner)
+        w[ms] = q
+        idx[ms] = ms[systematic_resample(q, u0)]
+    return PWResult(branch, widened, ell, w, idx, s_next[idx])

@@ -544,3 +544,80 @@ def test_infonce_weight_gradient_finite_differences():
         fp = O.infonce_loss(O.infonce_logits(O.MLP(ell.W, bp, ell.act), s, a, o))[0]
         fm = O.infonce_loss(O.infonce_logits(O.MLP(ell.W, bm, ell.act), s, a, o))[0]
         assert math.isclose(db[l][0], (fp - fm) / (2 * h), rel_tol=1e-5, abs_tol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Progressive widening (Sec. 4.3): branch counts against the closed form
+# ceil(k n^alpha), batch-split invariance of the widening decisions, and the
+# Gaussian-likelihood weights of a two-simulation group.
+# --------------------------------------------------------------------------
+def _pw_setup(n_nodes, C_max, d_s=4, d_a=2, d_o=3, seed=31):
+    rng = np.random.default_rng(seed)
+    tree = O.PWTree(rng.uniform(-1, 1, (n_nodes, d_a)), np.zeros(n_nodes, np.int64), np.zeros(n_nodes, np.int64),
+                    np.zeros((n_nodes, C_max, d_o)))
+    g_Z = O.MLP([rng.standard_normal((8, d_s + d_a + 2)) * 0.5, rng.standard_normal((d_o, 8)) * 0.5],
+                [np.zeros(8), np.zeros(d_o)], O.ACT_TANH)
+    return rng, tree, g_Z
+
+
+def test_pw_branch_count_closed_form():
+    # k = 1, alpha = 1/2: the threshold grows by at most 1 per visit, so after n
+    # visits |C| = ceil(sqrt(n)) (capped), whatever the batching
+    for C_max in (100, 7):
+        rng, tree, g_Z = _pw_setup(1, C_max)
+        M = 200
+        s = rng.standard_normal((M, 4))
+        res = O.progressive_widening(tree, np.zeros(M, np.int64), s, g_Z, O.Likelihood(O.LIK_GAUSSIAN, sigma=1.0),
+                                     2, 1.0, 0.5, 1.0, seed=3, step=0)
+        expect = [min(C_max, math.ceil(math.sqrt(n))) for n in range(1, M + 1)]
+        assert tree.C[0] == expect[-1] and tree.N[0] == M
+        grew = np.diff([0] + expect) > 0
+        np.testing.assert_array_equal(res.widened, grew)
+        assert np.all(res.branch < tree.C[0]) and np.all(res.branch >= 0)
+    # alpha = 1, k = 1: every visit widens until the cap
+    rng, tree, g_Z = _pw_setup(1, 5)
+    res = O.progressive_widening(tree, np.zeros(9, np.int64), rng.standard_normal((9, 4)), g_Z,
+                                 O.Likelihood(O.LIK_GAUSSIAN, sigma=1.0), 2, 1.0, 1.0, 1.0, seed=3, step=0)
+    np.testing.assert_array_equal(res.widened, [True] * 5 + [False] * 4)
+    np.testing.assert_array_equal(res.branch[:5], np.arange(5))
+
+
+def test_pw_widening_is_batch_split_invariant():
+    rng, tree_a, g_Z = _pw_setup(6, 16)
+    _, tree_b, _ = _pw_setup(6, 16)
+    M = 120
+    node = rng.integers(0, 6, M)
+    s = rng.standard_normal((M, 4))
+    lik = O.Likelihood(O.LIK_GAUSSIAN, sigma=0.7)
+    ra = O.progressive_widening(tree_a, node, s, g_Z, lik, 2, 1.3, 0.6, 1.0, seed=5, step=2)
+    rb1 = O.progressive_widening(tree_b, node[:50], s[:50], g_Z, lik, 2, 1.3, 0.6, 1.0, seed=5, step=2)
+    rb2 = O.progressive_widening(tree_b, node[50:], s[50:], g_Z, lik, 2, 1.3, 0.6, 1.0, seed=5, step=3)
+    np.testing.assert_array_equal(ra.widened, np.concatenate([rb1.widened, rb2.widened]))
+    np.testing.assert_array_equal(tree_a.N, tree_b.N)
+    np.testing.assert_array_equal(tree_a.C, tree_b.C)
+    np.testing.assert_array_equal(tree_a.N, np.bincount(node, minlength=6))
+
+
+def test_pw_group_weights_gaussian_closed_form():
+    # two simulations of one node, k = 0.9 and alpha small: the first widens
+    # (0 < 0.9), the second joins branch 0 (1 >= 0.9 * 2^0.001); weights are the normalised Gaussian densities
+    rng, tree, g_Z = _pw_setup(1, 4)
+    s = np.array([[0.1, -0.2, 0.3, 0.0], [0.5, 0.4, -0.1, 0.2]])
+    sigma, lam = 0.8, 1.25
+    res = O.progressive_widening(tree, np.zeros(2, np.int64), s, g_Z, O.Likelihood(O.LIK_GAUSSIAN, sigma=sigma),
+                                 2, 0.9, 1e-3, lam, seed=9, step=1)
+    np.testing.assert_array_equal(res.widened, [True, False])
+    np.testing.assert_array_equal(res.branch, [0, 0])
+    o = tree.obs[0, 0]
+    d2 = np.sum((o[None, :] - s[:, :3]) ** 2, axis=1)
+    p = np.exp(-d2 / (2 * sigma ** 2 * lam))
+    np.testing.assert_allclose(res.w, p / p.sum(), atol=2 ** -52)
+    assert set(res.idx.tolist()) <= {0, 1}
+    np.testing.assert_array_equal(res.s_out, s[res.idx])
+
+
+def test_pw_join_choice_is_uniform():
+    u = O.pw_branch_uniform(11, np.arange(40000), 0, 0)
+    counts = np.bincount(np.floor(u * 5).astype(int), minlength=5)
+    chi2 = np.sum((counts - 8000.0) ** 2 / 8000.0)
+    assert chi2 < 20.5   # 4 degrees of freedom, p ~ 4e-4
