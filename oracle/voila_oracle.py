@@ -638,7 +638,7 @@ class PWResult:
 def pw_branch_uniform(seed: int, m, step: int, planner: int):
     k0, k1 = seed_key(seed)
     m = np.asarray(m, dtype=np.uint64)
-    w0, _, _, _ = philox4x32_10(m, 0, step, counter_word3(STREAM_PW_BRANCH, planner, 0), k0, k1)
+    w0, _, _, _ = philox4x32_10(m, step, 0, counter_word3(STREAM_PW_BRANCH, planner, 0), k0, k1)
     return uniform24(w0)
 
 
@@ -650,11 +650,17 @@ def pw_group_uniform(seed: int, node: int, branch: int, step: int, planner: int)
 
 def progressive_widening(tree: PWTree, node: np.ndarray, s_next: np.ndarray, g_Z: MLP, L: Likelihood,
                          d_omega: int, k_o: float, alpha_o: float, lam: float, seed: int, step: int,
-                         planner: int = 0) -> PWResult:
-    """Updates `tree` in place (N, C, obs) and returns the per-simulation results."""
+                         planner: int = 0, sim_index: Optional[np.ndarray] = None) -> PWResult:
+    """Updates `tree` in place (N, C, obs) and returns the per-simulation results.
+
+    sim_index: the batch index of each given simulation (default 0 .. M-1), so
+    that the simulations of a subset of nodes can be replayed with their own
+    random counters; idx holds batch indices too.
+    """
     node = np.asarray(node, np.int64)
     s_next = np.asarray(s_next, np.float64)
     M = node.shape[0]
+    gid = np.arange(M) if sim_index is None else np.asarray(sim_index, np.int64)
     C_max = tree.obs.shape[1]
     branch = np.zeros(M, np.int64)
     widened = np.zeros(M, bool)
@@ -669,11 +675,11 @@ def progressive_widening(tree: PWTree, node: np.ndarray, s_next: np.ndarray, g_Z
                 widened[m] = True
                 x = [s_next[m], tree.act[a]]
                 if d_omega > 0:
-                    x.append(np.reshape(normals(seed, m, 0, step, STREAM_OBS_OMEGA, planner, d_omega), -1))
+                    x.append(np.reshape(normals(seed, gid[m], 0, step, STREAM_OBS_OMEGA, planner, d_omega), -1))
                 tree.obs[a, C] = mlp_forward(g_Z, np.concatenate(x)[None, :])[0]
                 C += 1
             else:
-                u = float(pw_branch_uniform(seed, m, step, planner))
+                u = float(pw_branch_uniform(seed, gid[m], step, planner))
                 branch[m] = min(C - 1, int(math.floor(u * C)))
         tree.N[a] = n0 + len(ms)
         tree.C[a] = C
@@ -690,4 +696,4 @@ def progressive_widening(tree: PWTree, node: np.ndarray, s_next: np.ndarray, g_Z
         u0 = pw_group_uniform(seed, key[0], key[1], step, planner)
         w[ms] = q
         idx[ms] = ms[systematic_resample(q, u0)]
-    return PWResult(branch, widened, ell, w, idx, s_next[idx])
+    return PWResult(branch, widened, ell, w, gid[idx], s_next[idx])
