@@ -74,7 +74,8 @@ enum {
   VOILA_STREAM_ROLLOUT_OMEGA = 0,
   VOILA_STREAM_BELIEF_OMEGA = 1,
   VOILA_STREAM_RESAMPLE = 2,
-  VOILA_STREAM_OBS_OMEGA = 3
+  VOILA_STREAM_OBS_OMEGA = 3,
+  VOILA_STREAM_PW_BRANCH = 6   /* progressive widening: choice of an existing branch */
 };
 
 #define VOILA_MAX_LAYERS 8
@@ -503,6 +504,63 @@ voila_status voila_infonce_step(const voila_mlp* ell, float* master, float* adam
                                 const float* Ob, int32_t B, int32_t d_s, int32_t d_a, int32_t d_o,
                                 double* loss_out, float* grad_out, void* workspace,
                                 size_t ws_bytes, voila_stream_t stream);
+
+/*
+ * Action-node tensors of the belief tree that progressive widening reads and
+ * updates (device memory, caller-owned).
+ *   act [n_nodes][d_a] float   action of each action node
+ *   N   [n_nodes] int64        visit counts N(a)            (updated)
+ *   C   [n_nodes] int32        observation-branch counts    (updated)
+ *   obs [n_nodes][C_max][d_o] float  branch observations    (appended)
+ * n_nodes < 2^24, 1 <= C_max <= 65535.
+ */
+typedef struct {
+  int32_t n_nodes, d_a, d_o, C_max;
+  const float* act;
+  int64_t* N;
+  int32_t* C;
+  float* obs;
+} voila_pw_tree;
+
+/* Workspace of voila_progressive_widening for M simulations, in bytes. */
+voila_status voila_progressive_widening_workspace_size(int32_t M, size_t* bytes);
+
+/*
+ * Vectorised progressive widening (Sec. 4.3) for a batch of M simulations:
+ * simulation m reached action node node[m] with successor state s_next[m].
+ *  1. Simulations are grouped by action node, each group in batch order. The
+ *     r-th simulation of node a sees n = N(a) + r + 1 visits; it WIDENS when
+ *     C(a) < C_max and C(a) < k_o * pow(n, alpha_o) (FP64): it gets branch
+ *     C(a), whose observation f_Z([s'; act[a]; omega_Z]) (Eq. 5, omega_Z at
+ *     counter (m, 0, step) of VOILA_STREAM_OBS_OMEGA) is stored in obs[a][C(a)],
+ *     and C(a) grows by one. Otherwise it JOINS branch floor(u * C(a)), u the
+ *     24-bit uniform of word 0 at counter (m, step, 0) of
+ *     VOILA_STREAM_PW_BRANCH. N(a) grows by the group size.
+ *  2. l_m = l(s'_m, act[a], obs[a][branch_m]) (Sec. 4.2.3).
+ *  3. Each (node, branch) group is resampled as voila_belief_update does:
+ *     weights exp(l / lambda) normalised by log-sum-exp, quantised to
+ *     multiples of 2^-52, exact prefix sum, systematic resampling with u0
+ *     from counter (node, branch, step) of VOILA_STREAM_RESAMPLE (block 1);
+ *     slot j of a group (its j-th simulation in batch order) receives the
+ *     successor state of simulation idx_out[slot].
+ *   node [M] int32 in [0, n_nodes) (others set VOILA_ERR_ARG in the status
+ *        word and are skipped); s_next [M][d_s] float; M < 2^24.
+ *   g_Z  dims [d_s + d_a + d_omega] -> ... -> d_o, FP32 or BF16 weights
+ *        (FP32 arithmetic); ell: MLP of [s'; a; o] or GAUSSIAN (d_o <= d_s).
+ *   branch_out [M] int32, s_out [M][d_s] float: required.
+ *   widened_out [M] uint8, ell_out [M] float, w_out [M] double, idx_out [M]
+ *   int32: optional (NULL).
+ *   workspace  device, 256-byte aligned; starts with the status word
+ *              (VOILA_ERR_ARG, VOILA_ERR_NONFINITE, VOILA_ERR_DEGENERATE).
+ */
+voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t* node,
+                                        const float* s_next, int32_t M, int32_t d_s,
+                                        const voila_mlp* g_Z, const voila_likelihood* ell,
+                                        int32_t d_omega, double k_o, double alpha_o, float lambda,
+                                        uint64_t seed, uint32_t step, uint32_t planner_id,
+                                        int32_t* branch_out, uint8_t* widened_out, float* ell_out,
+                                        double* w_out, int32_t* idx_out, float* s_out,
+                                        void* workspace, size_t ws_bytes, voila_stream_t stream);
 
 /*
  * Raw Philox4x32-10 words: out[4 i + j] = word j of counter (i, c1, c2, c3),

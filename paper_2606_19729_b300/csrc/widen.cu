@@ -1,0 +1,538 @@
+// Vectorised progressive widening of observation branches (Sec. 4.3).
+//
+// A batch of M simulations, each with the action node it reached and its
+// successor state s', is processed in five phases, all on the GPU:
+//   1. group by action node: bitonic sort of the unique 64-bit keys
+//      node << 32 | m (so each node's simulations keep batch order);
+//   2. one thread per node group walks its simulations in order: the r-th
+//      one widens when C < C_max and C < k_o (N + r + 1)^alpha_o (FP64),
+//      creating branch C; otherwise it joins branch floor(u C), u the 24-bit
+//      Philox uniform of counter (m, step, 0, stream 6); N and C are updated;
+//   3. the observation sampler f_Z (Eq. 5) fills the new branches:
+//      o = f_Z([s'; a; omega_Z]), omega_Z at counter (m, 0, step, stream 3);
+//   4. the likelihood l(s', a, o_branch) of every simulation;
+//   5. group by (node, branch) (a second sort, keys node << 40 | branch << 24
+//      | m) and, one warp per group, the SIR step: log-sum-exp normalisation
+//      of l / lambda, 2^-52 quantisation, exact prefix sum, systematic
+//      resampling with u0 from counter (node, branch, step, stream 2 block 1).
+#include <math.h>
+#include <string.h>
+
+#include "../../include/voila.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "simt_mlp.cuh"
+
+namespace voila {
+namespace {
+
+constexpr int kSortChunk = 2048;  // keys sorted in shared memory by one 1024-thread CTA
+
+__global__ void pw_keys_node_kernel(const int32_t* __restrict__ node, int M, int n_pad, int n_nodes,
+                                    unsigned long long* __restrict__ keys, WsHeader* hdr) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x) {
+    unsigned long long k = ~0ull;
+    if (i < M) {
+      const int a = node[i];
+      if (a < 0 || a >= n_nodes) {
+        set_status(hdr, VOILA_ERR_ARG, 60);
+        k = 0xffffffffull << 32 | (unsigned)i;  // sorts after every valid node; skipped later
+      } else {
+        k = (unsigned long long)a << 32 | (unsigned)i;
+      }
+    }
+    keys[i] = k;
+  }
+}
+
+__global__ void pw_keys_branch_kernel(const unsigned long long* __restrict__ keys_node, const int32_t* __restrict__ branch,
+                                      int M, int n_pad, unsigned long long* __restrict__ keys) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += gridDim.x * blockDim.x) {
+    unsigned long long k = ~0ull;
+    if (p < M) {
+      const unsigned long long kn = keys_node[p];
+      const unsigned a = (unsigned)(kn >> 32), m = (unsigned)(kn & 0xffffffffu);
+      k = a == 0xffffffffu ? ~0ull : ((unsigned long long)a << 40 | (unsigned long long)branch[m] << 24 | m);
+    }
+    keys[p] = k;
+  }
+}
+
+// Bitonic compare-exchange at distance j >= kSortChunk of merge size k.
+__global__ void bitonic_global_kernel(unsigned long long* keys, int n, int j, int k) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = i ^ j;
+  if (i < n && l > i) {
+    const unsigned long long a = keys[i], b = keys[l];
+    const bool up = (i & k) == 0;
+    if ((a > b) == up) {
+      keys[i] = b;
+      keys[l] = a;
+    }
+  }
+}
+
+// Merge sizes k = k_first .. k_last (powers of two), distances from j_first
+// (first k) or k / 2 (later ones) down to 1, inside chunks of kSortChunk keys.
+__global__ void __launch_bounds__(1024) bitonic_shared_kernel(unsigned long long* keys, int n, int k_first,
+                                                              int k_last, int j_first) {
+  __shared__ unsigned long long s[kSortChunk];
+  const int base = blockIdx.x * kSortChunk;
+  for (int t = threadIdx.x; t < kSortChunk; t += blockDim.x) s[t] = base + t < n ? keys[base + t] : ~0ull;
+  __syncthreads();
+  for (int k = k_first; k <= k_last; k <<= 1) {
+    for (int j = (k == k_first ? j_first : k >> 1); j > 0; j >>= 1) {
+      const int t = threadIdx.x;  // pair t of the 1024 in the chunk
+      const int i = (t / j) * 2 * j + (t % j), l = i + j;
+      const bool up = ((base + i) & k) == 0;
+      const unsigned long long a = s[i], b = s[l];
+      if ((a > b) == up) {
+        s[i] = b;
+        s[l] = a;
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < kSortChunk; t += blockDim.x)
+    if (base + t < n) keys[base + t] = s[t];
+}
+
+cudaError_t bitonic_sort(unsigned long long* keys, int n, cudaStream_t s) {
+  // n is a power of two
+  const int chunks = (n + kSortChunk - 1) / kSortChunk;
+  const int k_top = n < kSortChunk ? n : kSortChunk;
+  bitonic_shared_kernel<<<chunks, 1024, 0, s>>>(keys, n, 2, k_top, 1);
+  for (int k = 2 * kSortChunk; k <= n; k <<= 1) {
+    for (int j = k >> 1; j >= kSortChunk; j >>= 1)
+      bitonic_global_kernel<<<(n + 255) / 256, 256, 0, s>>>(keys, n, j, k);
+    bitonic_shared_kernel<<<chunks, 1024, 0, s>>>(keys, n, k, k, kSortChunk / 2);
+  }
+  return cudaGetLastError();
+}
+
+struct PwArgs {
+  int M, n_nodes, d_s, d_a, d_o, C_max, d_omega;
+  double k_o, alpha;
+  float lambda, sigma;
+  int lik_kind;
+  uint32_t key0, key1, step, planner;
+  const float* act;
+  long long* N;
+  int32_t* C;
+  float* obs;
+  const float* s_next;
+  int32_t* branch;
+  uint8_t* widened;
+  float* ell;
+  double* w;
+  int32_t* idx;
+  float* s_out;
+  double* cw;
+  int32_t* list;
+  int32_t* count;
+  WsHeader* hdr;
+};
+
+// Phase 2: one thread per node group, simulations in batch order. The
+// widened simulations are appended to `list` (slots reserved atomically; the
+// order of the list does not matter, each entry fills its own branch).
+__global__ void pw_widen_kernel(const unsigned long long* __restrict__ keys, PwArgs p) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= p.M) return;
+  const unsigned a = (unsigned)(keys[q] >> 32);
+  if (a == 0xffffffffu) return;
+  if (q > 0 && (unsigned)(keys[q - 1] >> 32) == a) return;  // not the first of its group
+  const long long n0 = p.N[a];
+  int C = p.C[a];
+  int r = 0, nw = 0;
+  for (int e = q; e < p.M && (unsigned)(keys[e] >> 32) == a; ++e, ++r) {
+    const unsigned m = (unsigned)(keys[e] & 0xffffffffu);
+    const double thr = p.k_o * pow((double)(n0 + r + 1), p.alpha);
+    if (C < p.C_max && (double)C < thr) {
+      p.branch[m] = C;
+      p.widened[m] = 1;
+      ++C;
+      ++nw;
+    } else {
+      const uint4 x = philox(make_uint4(m, p.step, 0u, ctr_word3(6u, p.planner, 0u)), p.key0, p.key1);
+      const int b = (int)floor((double)uniform24(x.x) * (double)C);  // exact: 24-bit fraction x integer
+      p.branch[m] = b < C - 1 ? b : C - 1;
+      p.widened[m] = 0;
+    }
+  }
+  p.N[a] = n0 + r;
+  p.C[a] = C;
+  if (nw) {
+    int slot = atomicAdd(p.count, nw);
+    for (int e = q; e < q + r; ++e) {
+      const unsigned m = (unsigned)(keys[e] & 0xffffffffu);
+      if (p.widened[m]) p.list[slot++] = (int32_t)m;
+    }
+  }
+}
+
+MlpDev mlp_dev(const voila_mlp* M) {
+  MlpDev m;
+  memset(&m, 0, sizeof(m));
+  m.n_layers = M->n_layers;
+  m.act = M->act;
+  m.prec = M->prec;
+  for (int l = 0; l <= VOILA_MAX_LAYERS; ++l) m.dims[l] = M->dims[l];
+  for (int l = 0; l < M->n_layers; ++l) {
+    m.W[l] = M->W[l];
+    m.b[l] = M->b[l];
+  }
+  return m;
+}
+
+// Phase 3b: o = f_Z([s'_m; a; omega_Z(m)]) for the listed simulations -> obs[a][branch_m].
+template <typename TW>
+__global__ void __launch_bounds__(kSimtThreads) pw_observe_kernel(MlpDev gz, const int32_t* __restrict__ node, PwArgs p,
+                                                                  int ld) {
+  extern __shared__ __align__(16) float sm[];
+  float* bufA = sm;
+  float* bufB = bufA + kSimtRows * ld;
+  __shared__ int rows_m[kSimtRows];
+  const int cnt = *p.count;
+  const int din = p.d_s + p.d_a + p.d_omega;
+  for (int t0 = blockIdx.x * kSimtRows; t0 < cnt; t0 += gridDim.x * kSimtRows) {
+    const int nr = min(kSimtRows, cnt - t0);
+    __syncthreads();
+    if (threadIdx.x < kSimtRows) rows_m[threadIdx.x] = threadIdx.x < nr ? p.list[t0 + threadIdx.x] : 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < kSimtRows * din; e += blockDim.x) {
+      const int r = e / din, c = e % din;
+      float v = 0.0f;
+      if (r < nr && c < p.d_s + p.d_a) {
+        const int m = rows_m[r];
+        v = c < p.d_s ? p.s_next[(size_t)m * p.d_s + c] : p.act[(size_t)node[m] * p.d_a + c - p.d_s];
+      }
+      bufA[r * ld + c] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * ((p.d_omega + 3) / 4); e += blockDim.x) {
+      const int r = e / ((p.d_omega + 3) / 4), b = e % ((p.d_omega + 3) / 4);
+      const float4 z = normal4(p.key0, p.key1, (uint32_t)rows_m[r], 0u, p.step, VOILA_STREAM_OBS_OMEGA, p.planner,
+                               (uint32_t)b);
+      const float zz[4] = {z.x, z.y, z.z, z.w};
+      for (int i = 0; i < 4 && 4 * b + i < p.d_omega; ++i) bufA[r * ld + p.d_s + p.d_a + 4 * b + i] = zz[i];
+    }
+    const float* y = simt_mlp<TW>(gz, bufA, bufB, ld, nr);
+    for (int e = threadIdx.x; e < nr * p.d_o; e += blockDim.x) {
+      const int r = e / p.d_o, c = e % p.d_o;
+      const int m = rows_m[r];
+      p.obs[((size_t)node[m] * p.C_max + p.branch[m]) * p.d_o + c] = y[r * ld + c];
+    }
+  }
+}
+
+// Phase 4: l(s'_m, a, o_branch) for every simulation (MLP on the CUDA cores,
+// or the analytic Gaussian kind).
+template <typename TW>
+__global__ void __launch_bounds__(kSimtThreads) pw_likelihood_kernel(MlpDev lm, const int32_t* __restrict__ node,
+                                                                     PwArgs p, int ld) {
+  extern __shared__ __align__(16) float sm[];
+  float* bufA = sm;
+  float* bufB = bufA + kSimtRows * ld;
+  const int din = p.d_s + p.d_a + p.d_o;
+  for (int t0 = blockIdx.x * kSimtRows; t0 < p.M; t0 += gridDim.x * kSimtRows) {
+    const int nr = min(kSimtRows, p.M - t0);
+    if (p.lik_kind == VOILA_LIK_GAUSSIAN) {
+      for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        const int m = t0 + r, a = node[m];
+        float l = 0.0f;
+        if (a >= 0 && a < p.n_nodes) {
+          const float* o = p.obs + ((size_t)a * p.C_max + p.branch[m]) * p.d_o;
+          float acc = 0.0f;
+          for (int d = 0; d < p.d_o; ++d) {
+            const float df = o[d] - p.s_next[(size_t)m * p.d_s + d];
+            acc = fmaf(df, df, acc);
+          }
+          l = -acc / (2.0f * p.sigma * p.sigma);
+        }
+        p.ell[m] = l;
+      }
+      continue;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kSimtRows * din; e += blockDim.x) {
+      const int r = e / din, c = e % din;
+      float v = 0.0f;
+      if (r < nr) {
+        const int m = t0 + r, a = node[m];
+        if (a >= 0 && a < p.n_nodes) {
+          if (c < p.d_s) v = p.s_next[(size_t)m * p.d_s + c];
+          else if (c < p.d_s + p.d_a) v = p.act[(size_t)a * p.d_a + c - p.d_s];
+          else v = p.obs[((size_t)a * p.C_max + p.branch[m]) * p.d_o + c - p.d_s - p.d_a];
+        }
+      }
+      bufA[r * ld + c] = v;
+    }
+    const float* y = simt_mlp<TW>(lm, bufA, bufB, ld, nr);
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) p.ell[t0 + r] = y[r * ld];
+  }
+}
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double wmax(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Phase 5: one warp per (node, branch) group of the sorted keys.
+__global__ void __launch_bounds__(256) pw_resample_kernel(const unsigned long long* __restrict__ keys, PwArgs p) {
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (q >= p.M) return;
+  const unsigned long long g = keys[q] >> 24;
+  if (keys[q] == ~0ull) return;
+  if (q > 0 && (keys[q - 1] >> 24) == g) return;
+  int n = 0;  // group size
+  while (true) {
+    const int e = q + n + lane;
+    const bool same = e < p.M && (keys[e] >> 24) == g;
+    const unsigned ball = __ballot_sync(0xffffffffu, same);
+    if (ball == 0xffffffffu) {
+      n += 32;
+      continue;
+    }
+    n += __popc(~ball) == 32 ? 0 : __ffs(~ball) - 1;
+    break;
+  }
+  const unsigned a = (unsigned)(g >> 16), br = (unsigned)(g & 0xffffu);
+  auto sim = [&](int i) { return (int)(keys[q + i] & 0xffffffull); };
+  double mx = -INFINITY;
+  bool bad = false;
+  for (int i = lane; i < n; i += 32) {
+    const double lw = (double)p.ell[sim(i)] / (double)p.lambda;
+    if (isnan(lw) || lw == INFINITY) bad = true;
+    mx = fmax(mx, lw);
+  }
+  mx = wmax(mx);
+  if (__any_sync(0xffffffffu, bad)) {
+    if (lane == 0) set_status(p.hdr, VOILA_ERR_NONFINITE, 61);
+    return;
+  }
+  if (mx == -INFINITY) {
+    if (lane == 0) set_status(p.hdr, VOILA_ERR_DEGENERATE, 62);
+    return;
+  }
+  double Z = 0.0;
+  for (int i = lane; i < n; i += 32) Z += exp((double)p.ell[sim(i)] / (double)p.lambda - mx);
+  Z = wsum(Z);
+  // quantised weights and their inclusive prefix sum (exact in any order)
+  double carry = 0.0;
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int i = i0 + lane;
+    double qv = 0.0;
+    if (i < n) {
+      const double wv = exp((double)p.ell[sim(i)] / (double)p.lambda - mx) / Z;
+      qv = rint(wv * 4503599627370496.0) * 2.220446049250313e-16;
+      p.w[sim(i)] = qv;
+    }
+    double inc = qv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (i < n) p.cw[q + i] = carry + inc;
+    carry += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  __syncwarp();
+  const uint4 x = philox(make_uint4(a, br, p.step, ctr_word3(VOILA_STREAM_RESAMPLE, p.planner, 1u)), p.key0, p.key1);
+  const double u0 = uniform53(x.x, x.y);
+  const double total = p.cw[q + n - 1];
+  for (int j = lane; j < n; j += 32) {
+    const double pj = __ddiv_rn(__dmul_rn(u0 + (double)j, total), (double)n);
+    int lo = 0, hi = n;  // first i with cw[i] > pj
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (p.cw[q + mid] > pj) hi = mid;
+      else lo = mid + 1;
+    }
+    const int src = lo < n ? lo : n - 1;
+    const int mj = sim(j), ms = sim(src);
+    if (p.idx) p.idx[mj] = ms;
+    for (int d = 0; d < p.d_s; ++d) p.s_out[(size_t)mj * p.d_s + d] = p.s_next[(size_t)ms * p.d_s + d];
+  }
+}
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int pow2_at_least(int m) {
+  int n = 2;
+  while (n < m) n <<= 1;
+  return n;
+}
+
+// Workspace: header | keys by node [n_pad] | keys by branch [n_pad] | cw [M] f64 |
+// list [M] i32 | count | widened [M] u8 | ell [M] f32 | w [M] f64
+struct PwLayout {
+  size_t keys1, keys2, cw, list, count, widened, ell, w, total;
+};
+
+PwLayout pw_layout(int M) {
+  PwLayout L;
+  const size_t n_pad = (size_t)pow2_at_least(M < 2 ? 2 : M);
+  size_t o = 1024;
+  L.keys1 = o; o += a256(n_pad * 8);
+  L.keys2 = o; o += a256(n_pad * 8);
+  L.cw = o; o += a256((size_t)M * 8);
+  L.list = o; o += a256((size_t)M * 4);
+  L.count = o; o += 256;
+  L.widened = o; o += a256((size_t)M);
+  L.ell = o; o += a256((size_t)M * 4);
+  L.w = o; o += a256((size_t)M * 8);
+  L.total = o;
+  return L;
+}
+
+int grid_of(long long n, int per) {
+  long long g = (n + per - 1) / per;
+  if (g > 148 * 16) g = 148 * 16;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+}  // namespace voila
+
+using namespace voila;
+
+extern "C" {
+
+voila_status voila_progressive_widening_workspace_size(int32_t M, size_t* bytes) {
+  if (M < 0 || M > (1 << 24) || !bytes) return VOILA_ERR_ARG;
+  *bytes = pw_layout(M).total;
+  return VOILA_OK;
+}
+
+voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t* node, const float* s_next,
+                                        int32_t M, int32_t d_s, const voila_mlp* g_Z, const voila_likelihood* ell,
+                                        int32_t d_omega, double k_o, double alpha_o, float lambda, uint64_t seed,
+                                        uint32_t step, uint32_t planner_id, int32_t* branch_out,
+                                        uint8_t* widened_out, float* ell_out, double* w_out, int32_t* idx_out,
+                                        float* s_out, void* workspace, size_t ws_bytes, voila_stream_t stream) {
+  if (!tree || !g_Z || !ell || M < 0 || M > (1 << 24) || d_s < 1 || d_omega < 0 || !(k_o > 0.0) ||
+      !(alpha_o > 0.0) || !(lambda > 0.0f) || planner_id >= 65536)
+    return VOILA_ERR_ARG;
+  if (tree->n_nodes < 1 || tree->n_nodes >= (1 << 24) || tree->C_max < 1 || tree->C_max > 65535 || tree->d_a < 0 ||
+      tree->d_o < 1 || !tree->N || !tree->C || !tree->obs || (tree->d_a && !tree->act))
+    return VOILA_ERR_ARG;
+  if (g_Z->n_layers < 1 || g_Z->n_layers > VOILA_MAX_LAYERS || (g_Z->prec != VOILA_FP32 && g_Z->prec != VOILA_BF16))
+    return VOILA_ERR_UNSUPPORTED;
+  if (g_Z->dims[0] != d_s + tree->d_a + d_omega || g_Z->dims[g_Z->n_layers] != tree->d_o) return VOILA_ERR_SHAPE;
+  if (ell->kind == VOILA_LIK_MLP) {
+    const voila_mlp* lm = ell->mlp;
+    if (!lm || lm->n_layers < 1 || lm->n_layers > VOILA_MAX_LAYERS) return VOILA_ERR_ARG;
+    if (lm->prec != VOILA_FP32 && lm->prec != VOILA_BF16) return VOILA_ERR_UNSUPPORTED;
+    if (lm->dims[0] != d_s + tree->d_a + tree->d_o || lm->dims[lm->n_layers] != 1) return VOILA_ERR_SHAPE;
+  } else if (ell->kind == VOILA_LIK_GAUSSIAN) {
+    if (!(ell->sigma > 0.0f) || tree->d_o > d_s) return VOILA_ERR_ARG;
+  } else {
+    return VOILA_ERR_ARG;
+  }
+  const PwLayout L = pw_layout(M);
+  if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 255)) return VOILA_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  if (cudaMemsetAsync(ws, 0, sizeof(WsHeader), s) != cudaSuccess) return VOILA_ERR_CUDA;
+  if (M == 0) return VOILA_OK;
+  if (!node || !s_next || !branch_out || !s_out) return VOILA_ERR_ARG;
+
+  PwArgs p;
+  memset(&p, 0, sizeof(p));
+  p.M = M;
+  p.n_nodes = tree->n_nodes;
+  p.d_s = d_s;
+  p.d_a = tree->d_a;
+  p.d_o = tree->d_o;
+  p.C_max = tree->C_max;
+  p.d_omega = d_omega;
+  p.k_o = k_o;
+  p.alpha = alpha_o;
+  p.lambda = lambda;
+  p.sigma = ell->sigma;
+  p.lik_kind = ell->kind;
+  p.key0 = (uint32_t)(seed & 0xffffffffu);
+  p.key1 = (uint32_t)(seed >> 32);
+  p.step = step;
+  p.planner = planner_id;
+  p.act = tree->act;
+  p.N = (long long*)tree->N;
+  p.C = tree->C;
+  p.obs = tree->obs;
+  p.s_next = s_next;
+  p.branch = branch_out;
+  p.widened = (uint8_t*)(ws + L.widened);
+  p.ell = ell_out ? ell_out : (float*)(ws + L.ell);
+  p.w = w_out ? w_out : (double*)(ws + L.w);
+  p.idx = idx_out;
+  p.s_out = s_out;
+  p.cw = (double*)(ws + L.cw);
+  p.list = (int32_t*)(ws + L.list);
+  p.count = (int32_t*)(ws + L.count);
+  p.hdr = (WsHeader*)ws;
+  unsigned long long* keys1 = (unsigned long long*)(ws + L.keys1);
+  unsigned long long* keys2 = (unsigned long long*)(ws + L.keys2);
+  const int n_pad = pow2_at_least(M < 2 ? 2 : M);
+
+  // 1. group by node
+  pw_keys_node_kernel<<<grid_of(n_pad, 256), 256, 0, s>>>(node, M, n_pad, tree->n_nodes, keys1, p.hdr);
+  if (cudaGetLastError() != cudaSuccess || bitonic_sort(keys1, n_pad, s) != cudaSuccess) return VOILA_ERR_CUDA;
+  // 2. widening decisions
+  if (cudaMemsetAsync(p.count, 0, sizeof(int32_t), s) != cudaSuccess) return VOILA_ERR_CUDA;
+  pw_widen_kernel<<<(M + 255) / 256, 256, 0, s>>>(keys1, p);
+  if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
+  // 3. observations of the new branches
+  {
+    const MlpDev gz = mlp_dev(g_Z);
+    int wmax = 0;
+    for (int l = 0; l <= g_Z->n_layers; ++l) wmax = g_Z->dims[l] > wmax ? g_Z->dims[l] : wmax;
+    if (wmax > VOILA_MAX_WIDTH) return VOILA_ERR_SHAPE;
+    const int ld = (wmax % 2 == 0) ? wmax + 1 : wmax;
+    const size_t smem = (size_t)2 * kSimtRows * ld * sizeof(float);
+    auto k = g_Z->prec == VOILA_BF16 ? pw_observe_kernel<__nv_bfloat16> : pw_observe_kernel<float>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return VOILA_ERR_CUDA;
+    k<<<grid_of(M, kSimtRows), kSimtThreads, smem, s>>>(gz, node, p, ld);
+    if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
+  }
+  // 4. likelihood of every simulation against its branch's observation
+  {
+    MlpDev lm;
+    memset(&lm, 0, sizeof(lm));
+    int ld = 1;
+    size_t smem = 0;
+    bool bf16 = false;
+    if (ell->kind == VOILA_LIK_MLP) {
+      lm = mlp_dev(ell->mlp);
+      int wmax = 0;
+      for (int l = 0; l <= ell->mlp->n_layers; ++l) wmax = ell->mlp->dims[l] > wmax ? ell->mlp->dims[l] : wmax;
+      if (wmax > VOILA_MAX_WIDTH) return VOILA_ERR_SHAPE;
+      ld = (wmax % 2 == 0) ? wmax + 1 : wmax;
+      smem = (size_t)2 * kSimtRows * ld * sizeof(float);
+      bf16 = ell->mlp->prec == VOILA_BF16;
+    }
+    auto k = bf16 ? pw_likelihood_kernel<__nv_bfloat16> : pw_likelihood_kernel<float>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem < 16 ? 16 : smem)) !=
+        cudaSuccess)
+      return VOILA_ERR_CUDA;
+    k<<<grid_of(M, kSimtRows), kSimtThreads, smem, s>>>(lm, node, p, ld);
+    if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
+  }
+  // 5. group by (node, branch) and resample each group
+  pw_keys_branch_kernel<<<grid_of(n_pad, 256), 256, 0, s>>>(keys1, branch_out, M, n_pad, keys2);
+  if (cudaGetLastError() != cudaSuccess || bitonic_sort(keys2, n_pad, s) != cudaSuccess) return VOILA_ERR_CUDA;
+  pw_resample_kernel<<<(int)(((long long)M * 32 + 255) / 256), 256, 0, s>>>(keys2, p);
+  if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
+  if (widened_out && cudaMemcpyAsync(widened_out, p.widened, (size_t)M, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return VOILA_ERR_CUDA;
+  return VOILA_OK;
+}
+
+}  // extern "C"

@@ -60,6 +60,11 @@ class voila_adam(ctypes.Structure):
     _fields_ = [("lr", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float), ("step", c_int32)]
 
 
+class voila_pw_tree(ctypes.Structure):
+    _fields_ = [("n_nodes", c_int32), ("d_a", c_int32), ("d_o", c_int32), ("C_max", c_int32), ("act", c_void_p),
+                ("N", c_void_p), ("C", c_void_p), ("obs", c_void_p)]
+
+
 def _sig(name, res, *args):
     f = getattr(_lib, name)
     f.restype = res
@@ -114,6 +119,10 @@ _lib_nce_fwd = _sig("voila_infonce_forward", c_int32, POINTER(voila_mlp), _P, _P
 _lib_nce_step_ws = _sig("voila_infonce_step_workspace_size", c_int32, POINTER(voila_mlp), c_int32, POINTER(c_size_t))
 _lib_nce_step = _sig("voila_infonce_step", c_int32, POINTER(voila_mlp), _P, _P, _P, POINTER(voila_adam), _P, _P, _P,
                      c_int32, c_int32, c_int32, c_int32, _P, _P, _P, c_size_t, _P)
+_lib_pw_ws = _sig("voila_progressive_widening_workspace_size", c_int32, c_int32, POINTER(c_size_t))
+_lib_pw = _sig("voila_progressive_widening", c_int32, POINTER(voila_pw_tree), _P, _P, c_int32, c_int32,
+               POINTER(voila_mlp), POINTER(voila_likelihood), c_int32, c_double, c_double, c_float, c_uint64,
+               c_uint32, c_uint32, _P, _P, _P, _P, _P, _P, _P, c_size_t, _P)
 _lib_philox = _sig("voila_philox_fill", c_int32, c_uint64, c_uint32, c_uint32, c_uint32, _P, c_int64, _P)
 _lib_normal = _sig("voila_normal_fill", c_int32, c_uint64, c_uint32, c_uint32, c_uint32, c_uint32, c_int32,
                    _P, c_int64, _P)
@@ -475,3 +484,42 @@ def voila_infonce_step(ell: DeviceMLP, master: torch.Tensor, adam_m: torch.Tenso
                          _ptr(A, torch.float32), _ptr(Ob, torch.float32), B, S.shape[1], A.shape[1], Ob.shape[1],
                          _ptr(loss, torch.float64), _ptr(grad_out, torch.float32), _ptr(workspace),
                          workspace.numel(), _stream(stream)), "voila_infonce_step")
+
+
+class PWTree:
+    """Device action-node tensors for progressive widening (act, N, C, obs)."""
+
+    def __init__(self, act: torch.Tensor, N: torch.Tensor, C: torch.Tensor, obs: torch.Tensor):
+        self.act = act.to(device="cuda", dtype=torch.float32).contiguous()
+        self.N = N.to(device="cuda", dtype=torch.int64).contiguous()
+        self.C = C.to(device="cuda", dtype=torch.int32).contiguous()
+        self.obs = obs.to(device="cuda", dtype=torch.float32).contiguous()
+        self.desc = voila_pw_tree()
+        self.desc.n_nodes = self.act.shape[0]
+        self.desc.d_a = self.act.shape[1]
+        self.desc.d_o = self.obs.shape[2]
+        self.desc.C_max = self.obs.shape[1]
+        self.desc.act = self.act.data_ptr()
+        self.desc.N = self.N.data_ptr()
+        self.desc.C = self.C.data_ptr()
+        self.desc.obs = self.obs.data_ptr()
+
+
+def voila_progressive_widening_workspace_size(M: int) -> int:
+    n = c_size_t(0)
+    _check(_lib_pw_ws(M, ctypes.byref(n)), "voila_progressive_widening_workspace_size")
+    return n.value
+
+
+def voila_progressive_widening(tree: PWTree, node: torch.Tensor, s_next: torch.Tensor, g_Z: DeviceMLP,
+                               ell: voila_likelihood, d_omega: int, k_o: float, alpha_o: float, lam: float, seed: int,
+                               step: int, planner_id: int, branch: torch.Tensor, s_out: torch.Tensor,
+                               workspace: torch.Tensor, widened: Optional[torch.Tensor] = None,
+                               ell_out: Optional[torch.Tensor] = None, w: Optional[torch.Tensor] = None,
+                               idx: Optional[torch.Tensor] = None, stream=None):
+    M, d_s = s_next.shape
+    _check(_lib_pw(ctypes.byref(tree.desc), _ptr(node, torch.int32), _ptr(s_next, torch.float32), M, d_s,
+                   ctypes.byref(g_Z.desc), ctypes.byref(ell), d_omega, k_o, alpha_o, lam, seed, step, planner_id,
+                   _ptr(branch, torch.int32), _ptr(widened, torch.uint8), _ptr(ell_out, torch.float32),
+                   _ptr(w, torch.float64), _ptr(idx, torch.int32), _ptr(s_out, torch.float32), _ptr(workspace),
+                   workspace.numel(), _stream(stream)), "voila_progressive_widening")

@@ -17,6 +17,7 @@ the five workload configurations:
 * ``distill``     teacher 3x512 + 64-d step embedding, student 3x256, B=65536
 * ``batched``     64 planners sharing the mid-size MLPs, uneven N, K, H
 * ``infonce``     likelihood 16->256x3->1 on B=1024 tuples (B^2 pairs)
+* ``pw``          progressive widening: 65536 simulations over 4096 action nodes
 """
 from __future__ import annotations
 
@@ -212,6 +213,53 @@ def infonce(seed: int = 5, B: int = 1024, prec: int = PREC_BF16) -> InfoNCEWorkl
     A = round_to(rng.uniform(-1.0, 1.0, size=(B, d_a)), PREC_FP32)
     O = round_to(S[:, :d_o] + rng.normal(0.0, 0.1, size=(B, d_o)), PREC_FP32)
     return InfoNCEWorkload("infonce", d_s, d_a, d_o, B, seed, ell, S, A, O)
+
+
+
+@dataclass
+class PWWorkload:
+    """A batch of simulations at the action nodes of a belief tree (Sec. 4.3)."""
+    name: str
+    d_s: int
+    d_a: int
+    d_o: int
+    d_omega: int
+    M: int
+    n_nodes: int
+    C_max: int
+    k_o: float
+    alpha_o: float
+    lam: float
+    seed: int
+    g_Z: MLPSpec
+    ell: MLPSpec
+    act: np.ndarray       # [n_nodes, d_a] ~ U[-1, 1]
+    N0: np.ndarray        # [n_nodes] prior visit counts
+    C0: np.ndarray        # [n_nodes] = min(C_max, ceil(k_o N0^alpha_o))
+    obs0: np.ndarray      # [n_nodes, C_max, d_o]: existing branches ~ N(0, I), the rest 0
+    node: np.ndarray      # [M] action node of each simulation
+    s_next: np.ndarray    # [M, d_s] ~ N(0, I)
+
+
+def pw(seed: int = 6, M: int = 65536, n_nodes: int = 4096, C_max: int = 32, prec: int = PREC_BF16,
+       k_o: float = 2.1, alpha_o: float = 0.3) -> PWWorkload:
+    """Planning shapes (s' 8, a 2, o 6, omega_Z 8; f_Z 18->256x3->6 and l 16->256x3->1
+    SiLU). Node visits are skewed: node = floor(n_nodes u^2), so a few nodes hold
+    many simulations; prior visit counts are uniform on 0..200."""
+    rng = np.random.default_rng(seed)
+    d_s, d_a, d_o, d_w = 8, 2, 6, 8
+    g_Z = xavier_mlp(rng, [d_s + d_a + d_w, 256, 256, 256, d_o], ACT_SILU, prec)
+    ell = xavier_mlp(rng, [d_s + d_a + d_o, 256, 256, 256, 1], ACT_SILU, prec)
+    act = round_to(rng.uniform(-1.0, 1.0, size=(n_nodes, d_a)), PREC_FP32)
+    N0 = rng.integers(0, 201, size=n_nodes).astype(np.int64)
+    C0 = np.minimum(C_max, np.ceil(k_o * np.power(N0.astype(np.float64), alpha_o))).astype(np.int64)
+    obs0 = np.zeros((n_nodes, C_max, d_o))
+    for a in range(n_nodes):
+        obs0[a, :C0[a]] = round_to(rng.normal(0.0, 1.0, size=(C0[a], d_o)), PREC_FP32)
+    node = np.minimum(n_nodes - 1, np.floor(n_nodes * rng.uniform(0.0, 1.0, size=M) ** 2)).astype(np.int64)
+    s_next = round_to(rng.normal(0.0, 1.0, size=(M, d_s)), PREC_FP32)
+    return PWWorkload("pw", d_s, d_a, d_o, d_w, M, n_nodes, C_max, k_o, alpha_o, 1.0, seed, g_Z, ell, act, N0, C0,
+                      obs0, node, s_next)
 
 
 def batched_planners(seed: int = 4, P: int = 64):
