@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -40,7 +41,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mid_bf16", "mid_fp32", "small_fp32", "batched", "sweep", "distill", "infonce"], default="mid_bf16")
+    ap.add_argument("--workload", choices=["mid_bf16", "mid_fp32", "small_fp32", "batched", "sweep", "distill", "infonce", "pw"], default="mid_bf16")
     ap.add_argument("--cpu-seqs", type=int, default=8, help="action sequences in the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-seqs", type=int, default=16, help="sequences for the FP32-form comparison (0: skip)")
@@ -670,6 +671,103 @@ def run_infonce(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_pw(args, rank, world, local):
+    """Progressive widening (Sec. 4.3) of 65536 simulations over 4096 action nodes:
+    grouping, widening decisions, f_Z observations of the new branches, branch
+    likelihoods (16-256-256-256-1, BF16 weights, FP32 arithmetic), per-branch SIR
+    resampling. The tree is restored before every call so each call does the same work."""
+    import torch
+    from paper_2606_19729_b300 import voila as V
+    from paper_2606_19729_b300 import workloads as WL
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = WL.pw(M=args.B or 65536)
+    M = wl.M
+    stream = torch.cuda.current_stream()
+    tree = V.PWTree(torch.from_numpy(wl.act), torch.from_numpy(wl.N0), torch.from_numpy(wl.C0),
+                    torch.from_numpy(wl.obs0))
+    N0, C0, obs0 = tree.N.clone(), tree.C.clone(), tree.obs.clone()
+    g_Z = V.DeviceMLP.from_spec(wl.g_Z)
+    ell = V.DeviceMLP.from_spec(wl.ell)
+    lik = V.mlp_likelihood(ell)
+    node = torch.from_numpy(wl.node).to(device="cuda", dtype=torch.int32)
+    s_next = torch.from_numpy(wl.s_next).float().cuda()
+    branch = torch.empty(M, dtype=torch.int32, device="cuda")
+    s_out = torch.empty_like(s_next)
+    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(M))
+
+    def call():
+        V.voila_progressive_widening(tree, node, s_next, g_Z, lik, wl.d_omega, wl.k_o, wl.alpha_o, wl.lam, wl.seed,
+                                     0, rank, branch, s_out, ws)
+
+    def restore():
+        tree.N.copy_(N0)
+        tree.C.copy_(C0)
+        tree.obs.copy_(obs0)
+
+    for _ in range(args.warmup):
+        restore()
+        call()
+    torch.cuda.synchronize()
+    assert V.workspace_status(ws) == V.OK
+    reps = max(args.steps, 20)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    with Clocks(local) as clk:
+        for e0, e1 in ev:
+            restore()
+            e0.record(stream)
+            call()
+            e1.record(stream)
+        torch.cuda.synchronize()
+    assert V.workspace_status(ws) == V.OK
+    call_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / reps
+    sec = max_over_ranks(call_s * reps, world, torch.device("cuda", local))
+    widened = int((tree.C - C0).sum().item())
+    fz = sum(2 * w.shape[0] * w.shape[1] for w in wl.g_Z.W)
+    fl = sum(2 * w.shape[0] * w.shape[1] for w in wl.ell.W)
+    flops = fl * M + fz * widened
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = nsm * 128 * 2 * 2032e6 / 1e12
+    line = {"metric": "progressive-widening simulations/s", "value": aggregate_rate(M * reps, world, sec),
+            "unit": "simulations/s", "n_gpus": world, "steps": reps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * call_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded tree and simulations, random-init f_Z and likelihood)",
+            "config": {"workload": f"pw: M={M} simulations over {wl.n_nodes} action nodes (skewed), C_max={wl.C_max}, "
+                                   f"k_o={wl.k_o}, alpha_o={wl.alpha_o}; f_Z 18x256x256x256x6 and likelihood "
+                                   "16x256x256x256x1 SiLU, BF16 weights, FP32 arithmetic"},
+            "widened_per_call": widened,
+            "roofline": {"bound": "alu", "achieved": flops / call_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / call_s / 1e12 / peak, "traffic": None,
+                         "kernel": "voila_progressive_widening (whole call; likelihood MLP dominates the FLOPs)",
+                         "peak_kind": "FP32 FMA lanes x max SM clock (derived)"},
+            "gpu_launches": None, "clocks": clk.summary()}
+    n_pad = 2
+    while n_pad < M:
+        n_pad *= 2
+    sort_launches = 1 + sum(int(math.log2(k)) - 10 for k in (2 ** e for e in range(12, int(math.log2(n_pad)) + 1)))
+    # keys, sort, widen, observe, likelihood, keys, sort, resample
+    line["gpu_launches"] = reps * (6 + 2 * sort_launches)
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import voila_oracle as O
+        counts = np.bincount(wl.node, minlength=wl.n_nodes)
+        nodes = np.nonzero(counts)[0][:64]
+        sel = np.isin(wl.node, nodes)
+        tree_o = O.PWTree(wl.act.copy(), wl.N0.copy(), wl.C0.copy(), wl.obs0.copy())
+        t0 = time.perf_counter()
+        O.progressive_widening(tree_o, wl.node[sel], wl.s_next[sel], O.MLP(wl.g_Z.W, wl.g_Z.b, wl.g_Z.act),
+                               O.Likelihood(O.LIK_MLP, mlp=O.MLP(wl.ell.W, wl.ell.b, wl.ell.act)), wl.d_omega,
+                               wl.k_o, wl.alpha_o, wl.lam, wl.seed, 0, sim_index=np.nonzero(sel)[0])
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": int(sel.sum()) / dt, "unit": "simulations/s", "cores": blas_threads(),
+                                "kind": "oracle", "sample": f"FP64 oracle widening of the {int(sel.sum())} simulations "
+                                                            f"of the first 64 visited nodes in {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -689,6 +787,9 @@ def main():
         return
     if args.workload == "infonce":
         run_infonce(args, rank, world, local)
+        return
+    if args.workload == "pw":
+        run_pw(args, rank, world, local)
         return
 
     import torch
