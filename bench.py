@@ -697,7 +697,7 @@ def run_pw(args, rank, world, local):
     s_next = torch.from_numpy(wl.s_next).float().cuda()
     branch = torch.empty(M, dtype=torch.int32, device="cuda")
     s_out = torch.empty_like(s_next)
-    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(M))
+    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(lik, M))
 
     def call():
         V.voila_progressive_widening(tree, node, s_next, g_Z, lik, wl.d_omega, wl.k_o, wl.alpha_o, wl.lam, wl.seed,
@@ -734,10 +734,10 @@ def run_pw(args, rank, world, local):
     line = {"metric": "progressive-widening simulations/s", "value": aggregate_rate(M * reps, world, sec),
             "unit": "simulations/s", "n_gpus": world, "steps": reps, "warmup": args.warmup,
             "ms_per_step": 1e3 * call_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic (seeded tree and simulations, random-init f_Z and likelihood)",
+            "dtype": "bf16", "data": "synthetic (seeded tree and simulations, random-init f_Z and likelihood)",
             "config": {"workload": f"pw: M={M} simulations over {wl.n_nodes} action nodes (skewed), C_max={wl.C_max}, "
-                                   f"k_o={wl.k_o}, alpha_o={wl.alpha_o}; f_Z 18x256x256x256x6 and likelihood "
-                                   "16x256x256x256x1 SiLU, BF16 weights, FP32 arithmetic"},
+                                   f"k_o={wl.k_o}, alpha_o={wl.alpha_o}; f_Z 18x256x256x256x6 (BF16 weights, FP32 "
+                                   "CUDA cores) and likelihood 16x256x256x256x1 SiLU (BF16, tensor cores)"},
             "widened_per_call": widened,
             "roofline": {"bound": "alu", "achieved": flops / call_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                          "frac": flops / call_s / 1e12 / peak, "traffic": None,
@@ -748,13 +748,11 @@ def run_pw(args, rank, world, local):
     while n_pad < M:
         n_pad *= 2
     sort_launches = 1 + sum(int(math.log2(k)) - 10 for k in (2 ** e for e in range(12, int(math.log2(n_pad)) + 1)))
-    # keys, sort, widen, observe, likelihood, keys, sort, resample
-    line["gpu_launches"] = reps * (6 + 2 * sort_launches)
+    # keys, sort, widen, join, observe, likelihood (pack + pair kernel), keys, sort, resample
+    line["gpu_launches"] = reps * (8 + 2 * sort_launches)
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import voila_oracle as O
-        counts = np.bincount(wl.node, minlength=wl.n_nodes)
-        nodes = np.nonzero(counts)[0][:64]
-        sel = np.isin(wl.node, nodes)
+        sel = np.ones(M, bool)
         tree_o = O.PWTree(wl.act.copy(), wl.N0.copy(), wl.C0.copy(), wl.obs0.copy())
         t0 = time.perf_counter()
         O.progressive_widening(tree_o, wl.node[sel], wl.s_next[sel], O.MLP(wl.g_Z.W, wl.g_Z.b, wl.g_Z.act),
@@ -762,8 +760,8 @@ def run_pw(args, rank, world, local):
                                wl.k_o, wl.alpha_o, wl.lam, wl.seed, 0, sim_index=np.nonzero(sel)[0])
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": int(sel.sum()) / dt, "unit": "simulations/s", "cores": blas_threads(),
-                                "kind": "oracle", "sample": f"FP64 oracle widening of the {int(sel.sum())} simulations "
-                                                            f"of the first 64 visited nodes in {dt:.1f} s"}
+                                "kind": "oracle", "sample": f"FP64 oracle widening of all {int(sel.sum())} simulations "
+                                                            f"(one call) in {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -522,8 +522,9 @@ typedef struct {
   float* obs;
 } voila_pw_tree;
 
-/* Workspace of voila_progressive_widening for M simulations, in bytes. */
-voila_status voila_progressive_widening_workspace_size(int32_t M, size_t* bytes);
+/* Workspace of voila_progressive_widening for M simulations and likelihood ell, in bytes. */
+voila_status voila_progressive_widening_workspace_size(const voila_likelihood* ell, int32_t M,
+                                                       size_t* bytes);
 
 /*
  * Vectorised progressive widening (Sec. 4.3) for a batch of M simulations:
@@ -547,11 +548,15 @@ voila_status voila_progressive_widening_workspace_size(int32_t M, size_t* bytes)
  *        word and are skipped); s_next [M][d_s] float; M < 2^24.
  *   g_Z  dims [d_s + d_a + d_omega] -> ... -> d_o, FP32 or BF16 weights
  *        (FP32 arithmetic); ell: MLP of [s'; a; o] or GAUSSIAN (d_o <= d_s).
+ *        A BF16 likelihood of the planning shapes (s' 8, a 2, o 6, hidden
+ *        widths multiples of 64 up to 256) runs on the tensor cores (BF16
+ *        activations, FP32 accumulation); any other on the CUDA cores in FP32.
  *   branch_out [M] int32, s_out [M][d_s] float: required.
  *   widened_out [M] uint8, ell_out [M] float, w_out [M] double, idx_out [M]
  *   int32: optional (NULL).
- *   workspace  device, 256-byte aligned; starts with the status word
- *              (VOILA_ERR_ARG, VOILA_ERR_NONFINITE, VOILA_ERR_DEGENERATE).
+ *   workspace  device, 1024-byte aligned; starts with the status word
+ *              (VOILA_ERR_ARG, VOILA_ERR_NONFINITE, VOILA_ERR_DEGENERATE,
+ *              VOILA_ERR_TIMEOUT).
  */
 voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t* node,
                                         const float* s_next, int32_t M, int32_t d_s,

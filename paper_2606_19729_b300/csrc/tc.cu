@@ -117,12 +117,17 @@ struct TcParams {
   float* ddim_y;
   float ddim_cx[64];
   float ddim_cv[64];
-  // likelihood pairs: row i * B + j evaluates l([s'_i (8); a_i (2); o_j (6)]) -> out[row]
+  // likelihood pairs: row i * B + j evaluates l([s'_i (8); a_i (2); o_j (6)]) -> out[row];
+  // gather form (gather_node != null): row m evaluates
+  // l([s'_m; act[node_m]; obs[node_m][branch_m]]) for rows m < pair_B
   const float* pair_s;
   const float* pair_a;
   const float* pair_o;
   long long pair_B;
   float* pair_out;
+  const int32_t* gather_node;
+  const int32_t* gather_branch;
+  int gather_n_nodes, gather_C_max;
 };
 
 __device__ __forceinline__ int item_planner(const TcParams& p, long long it) {
@@ -573,14 +578,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         }
       } else if constexpr (PAIRS) {
         if (owner) {
-          const long long pi = valid ? row / p.pair_B : 0, pj = valid ? row % p.pair_B : 0;
+          long long pi, pa, po;  // rows of s', a and o
+          bool in = valid;
+          if (p.gather_node) {
+            const int a = valid ? __ldg(p.gather_node + row) : -1;
+            in = a >= 0 && a < p.gather_n_nodes;
+            pi = row;
+            pa = in ? a : 0;
+            po = in ? (long long)a * p.gather_C_max + __ldg(p.gather_branch + row) : 0;
+          } else {
+            pi = valid ? row / p.pair_B : 0;
+            pa = pi;
+            po = valid ? row % p.pair_B : 0;
+          }
           float x[16];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) x[i] = valid ? __ldg(p.pair_s + pi * 8 + i) : 0.0f;
-          x[8] = valid ? __ldg(p.pair_a + pi * 2) : 0.0f;
-          x[9] = valid ? __ldg(p.pair_a + pi * 2 + 1) : 0.0f;
+          for (int i = 0; i < 8; ++i) x[i] = in ? __ldg(p.pair_s + pi * 8 + i) : 0.0f;
+          x[8] = in ? __ldg(p.pair_a + pa * 2) : 0.0f;
+          x[9] = in ? __ldg(p.pair_a + pa * 2 + 1) : 0.0f;
 #pragma unroll
-          for (int i = 0; i < 6; ++i) x[10 + i] = valid ? __ldg(p.pair_o + pj * 6 + i) : 0.0f;
+          for (int i = 0; i < 6; ++i) x[10 + i] = in ? __ldg(p.pair_o + po * 6 + i) : 0.0f;
           store_row<16>(A, r, x);
         }
       } else if (owner) {
@@ -1168,6 +1185,12 @@ size_t tc_pairs_scratch_bytes(const voila_mlp* ell) {
 
 voila_status tc_likelihood_pairs(const voila_mlp* ell, const float* S, const float* A, const float* Ob, long long B,
                                  float* out, WsHeader* hdr, void* scratch, cudaStream_t s) {
+  return tc_likelihood_rows(ell, S, A, Ob, B, nullptr, nullptr, 0, 0, out, hdr, scratch, s);
+}
+
+voila_status tc_likelihood_rows(const voila_mlp* ell, const float* S, const float* A, const float* Ob, long long B,
+                                const int32_t* node, const int32_t* branch, int n_nodes, int C_max, float* out,
+                                WsHeader* hdr, void* scratch, cudaStream_t s) {
   Plan pl = make_plan(ell, nullptr);
   if (!pl.ok || pl.wide) return VOILA_ERR_UNSUPPORTED;
   if ((uintptr_t)scratch % 1024) return VOILA_ERR_WORKSPACE;
@@ -1176,7 +1199,7 @@ voila_status tc_likelihood_pairs(const voila_mlp* ell, const float* S, const flo
   q.particles = S;  // unused by the pair rows
   q.actions = A;
   q.G = nullptr;
-  q.rows = B * B;
+  q.rows = node ? B : B * B;
   q.N = 1;
   q.H = 1;
   q.planner = 0;
@@ -1215,6 +1238,10 @@ voila_status tc_likelihood_pairs(const voila_mlp* ell, const float* S, const flo
   p.pair_o = Ob;
   p.pair_B = B;
   p.pair_out = out;
+  p.gather_node = node;
+  p.gather_branch = branch;
+  p.gather_n_nodes = n_nodes;
+  p.gather_C_max = C_max;
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

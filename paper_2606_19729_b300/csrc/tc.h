@@ -51,5 +51,10 @@ bool tc_pairs_supported(const voila_mlp* ell, int d_s, int d_a, int d_o);
 size_t tc_pairs_scratch_bytes(const voila_mlp* ell);
 voila_status tc_likelihood_pairs(const voila_mlp* ell, const float* S, const float* A, const float* Ob, long long B,
                                  float* out, WsHeader* hdr, void* scratch, cudaStream_t s);
+// Gather form: out[m] = l([S[m]; A[node[m]]; Ob[node[m] * C_max + branch[m]]]) for m < M
+// (node outside [0, n_nodes): zero input row).
+voila_status tc_likelihood_rows(const voila_mlp* ell, const float* S, const float* A, const float* Ob, long long M,
+                                const int32_t* node, const int32_t* branch, int n_nodes, int C_max, float* out,
+                                WsHeader* hdr, void* scratch, cudaStream_t s);
 
 }  // namespace voila

@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "simt_mlp.cuh"
+#include "tc.h"
 
 namespace voila {
 namespace {
@@ -130,45 +131,79 @@ struct PwArgs {
   double* cw;
   int32_t* list;
   int32_t* count;
+  int32_t* cbefore;
   WsHeader* hdr;
 };
 
-// Phase 2: one thread per node group, simulations in batch order. The
-// widened simulations are appended to `list` (slots reserved atomically; the
-// order of the list does not matter, each entry fills its own branch).
+// The rank (0-based, from r_from) of the next simulation of a node group of g
+// that widens while the node has C branches: the smallest visit count
+// n >= n0 + r_from + 1 with k_o * pow(n, alpha) > C, found from the inverse
+// (C / k_o)^(1 / alpha) and confirmed with the same FP64 expression the
+// per-simulation rule evaluates; g when none does (or C has reached C_max).
+__device__ int pw_next_widen(long long n0, int C, int r_from, int g, const PwArgs& p) {
+  if (C >= p.C_max || r_from >= g) return g;
+  const long long lo = n0 + r_from + 1, hi = n0 + g;
+  const double est = pow((double)C / p.k_o, 1.0 / p.alpha);  // k n^alpha = C at n = est
+  if (!(est < (double)(hi + 3))) return g;
+  long long n = (long long)floor(est) - 2;
+  if (n < lo) n = lo;
+  while (n <= hi && !((double)C < p.k_o * pow((double)n, p.alpha))) ++n;
+  return n <= hi ? (int)(n - n0 - 1) : g;
+}
+
+// Phase 2: one thread per node group, simulations in batch order: records the
+// branch count each simulation sees (cbefore) and which ones widen, jumping
+// from one widening to the next. The widened simulations are appended to
+// `list` (slots reserved atomically; each entry fills its own branch, so the
+// order does not matter).
 __global__ void pw_widen_kernel(const unsigned long long* __restrict__ keys, PwArgs p) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= p.M) return;
   const unsigned a = (unsigned)(keys[q] >> 32);
   if (a == 0xffffffffu) return;
   if (q > 0 && (unsigned)(keys[q - 1] >> 32) == a) return;  // not the first of its group
+  int g = 1;
+  while (q + g < p.M && (unsigned)(keys[q + g] >> 32) == a) ++g;
   const long long n0 = p.N[a];
   int C = p.C[a];
-  int r = 0, nw = 0;
-  for (int e = q; e < p.M && (unsigned)(keys[e] >> 32) == a; ++e, ++r) {
-    const unsigned m = (unsigned)(keys[e] & 0xffffffffu);
-    const double thr = p.k_o * pow((double)(n0 + r + 1), p.alpha);
-    if (C < p.C_max && (double)C < thr) {
+  int next = pw_next_widen(n0, C, 0, g, p);
+  int nw = 0;
+  for (int r = 0; r < g; ++r) {
+    const unsigned m = (unsigned)(keys[q + r] & 0xffffffffu);
+    p.cbefore[m] = C;
+    if (r == next) {
       p.branch[m] = C;
       p.widened[m] = 1;
       ++C;
       ++nw;
+      next = pw_next_widen(n0, C, r + 1, g, p);
     } else {
-      const uint4 x = philox(make_uint4(m, p.step, 0u, ctr_word3(6u, p.planner, 0u)), p.key0, p.key1);
-      const int b = (int)floor((double)uniform24(x.x) * (double)C);  // exact: 24-bit fraction x integer
-      p.branch[m] = b < C - 1 ? b : C - 1;
       p.widened[m] = 0;
     }
   }
-  p.N[a] = n0 + r;
+  p.N[a] = n0 + g;
   p.C[a] = C;
   if (nw) {
     int slot = atomicAdd(p.count, nw);
-    for (int e = q; e < q + r; ++e) {
-      const unsigned m = (unsigned)(keys[e] & 0xffffffffu);
+    for (int r = 0; r < g; ++r) {
+      const unsigned m = (unsigned)(keys[q + r] & 0xffffffffu);
       if (p.widened[m]) p.list[slot++] = (int32_t)m;
     }
   }
+}
+
+// Phase 2b: a simulation that did not widen joins branch floor(u C) of the C
+// branches it saw, u the 24-bit uniform of Philox counter (m, step, 0, stream 6)
+// (u C is exact in FP64: a 24-bit fraction times an integer).
+__global__ void pw_join_kernel(const int32_t* __restrict__ node, PwArgs p) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= p.M) return;
+  const int a = node[m];
+  if (a < 0 || a >= p.n_nodes || p.widened[m]) return;
+  const int C = p.cbefore[m];
+  const uint4 x = philox(make_uint4((uint32_t)m, p.step, 0u, ctr_word3(6u, p.planner, 0u)), p.key0, p.key1);
+  const int b = (int)floor((double)uniform24(x.x) * (double)C);
+  p.branch[m] = b < C - 1 ? b : C - 1;
 }
 
 MlpDev mlp_dev(const voila_mlp* M) {
@@ -370,16 +405,23 @@ int pow2_at_least(int m) {
   return n;
 }
 
-// Workspace: header | keys by node [n_pad] | keys by branch [n_pad] | cw [M] f64 |
-// list [M] i32 | count | widened [M] u8 | ell [M] f32 | w [M] f64
+// Workspace: header | tensor-core scratch (packed likelihood) | keys by node
+// [n_pad] | keys by branch [n_pad] | cw [M] f64 | list [M] i32 | count |
+// widened [M] u8 | ell [M] f32 | w [M] f64 | cbefore [M] i32
 struct PwLayout {
-  size_t keys1, keys2, cw, list, count, widened, ell, w, total;
+  size_t tc, keys1, keys2, cw, list, count, widened, ell, w, cbefore, total;
 };
 
-PwLayout pw_layout(int M) {
+bool pw_tc_likelihood(const voila_likelihood* ell, int d_s, int d_a, int d_o) {
+  return ell && ell->kind == VOILA_LIK_MLP && ell->mlp && tc_pairs_supported(ell->mlp, d_s, d_a, d_o);
+}
+
+PwLayout pw_layout(const voila_likelihood* ell, int M) {
   PwLayout L;
   const size_t n_pad = (size_t)pow2_at_least(M < 2 ? 2 : M);
   size_t o = 1024;
+  L.tc = o;
+  if (ell && ell->kind == VOILA_LIK_MLP && ell->mlp) o += (tc_pairs_scratch_bytes(ell->mlp) + 1023) / 1024 * 1024;
   L.keys1 = o; o += a256(n_pad * 8);
   L.keys2 = o; o += a256(n_pad * 8);
   L.cw = o; o += a256((size_t)M * 8);
@@ -388,6 +430,7 @@ PwLayout pw_layout(int M) {
   L.widened = o; o += a256((size_t)M);
   L.ell = o; o += a256((size_t)M * 4);
   L.w = o; o += a256((size_t)M * 8);
+  L.cbefore = o; o += a256((size_t)M * 4);
   L.total = o;
   return L;
 }
@@ -405,9 +448,9 @@ using namespace voila;
 
 extern "C" {
 
-voila_status voila_progressive_widening_workspace_size(int32_t M, size_t* bytes) {
-  if (M < 0 || M > (1 << 24) || !bytes) return VOILA_ERR_ARG;
-  *bytes = pw_layout(M).total;
+voila_status voila_progressive_widening_workspace_size(const voila_likelihood* ell, int32_t M, size_t* bytes) {
+  if (!ell || M < 0 || M > (1 << 24) || !bytes) return VOILA_ERR_ARG;
+  *bytes = pw_layout(ell, M).total;
   return VOILA_OK;
 }
 
@@ -436,8 +479,8 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   } else {
     return VOILA_ERR_ARG;
   }
-  const PwLayout L = pw_layout(M);
-  if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 255)) return VOILA_ERR_WORKSPACE;
+  const PwLayout L = pw_layout(ell, M);
+  if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 1023)) return VOILA_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   if (cudaMemsetAsync(ws, 0, sizeof(WsHeader), s) != cudaSuccess) return VOILA_ERR_CUDA;
@@ -476,6 +519,7 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   p.cw = (double*)(ws + L.cw);
   p.list = (int32_t*)(ws + L.list);
   p.count = (int32_t*)(ws + L.count);
+  p.cbefore = (int32_t*)(ws + L.cbefore);
   p.hdr = (WsHeader*)ws;
   unsigned long long* keys1 = (unsigned long long*)(ws + L.keys1);
   unsigned long long* keys2 = (unsigned long long*)(ws + L.keys2);
@@ -487,6 +531,7 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   // 2. widening decisions
   if (cudaMemsetAsync(p.count, 0, sizeof(int32_t), s) != cudaSuccess) return VOILA_ERR_CUDA;
   pw_widen_kernel<<<(M + 255) / 256, 256, 0, s>>>(keys1, p);
+  pw_join_kernel<<<(M + 255) / 256, 256, 0, s>>>(node, p);
   if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   // 3. observations of the new branches
   {
@@ -503,7 +548,11 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
     if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   }
   // 4. likelihood of every simulation against its branch's observation
-  {
+  if (pw_tc_likelihood(ell, d_s, tree->d_a, tree->d_o)) {
+    const voila_status st = tc_likelihood_rows(ell->mlp, s_next, tree->act, tree->obs, M, node, branch_out,
+                                               tree->n_nodes, tree->C_max, p.ell, p.hdr, ws + L.tc, s);
+    if (st != VOILA_OK) return st;
+  } else {
     MlpDev lm;
     memset(&lm, 0, sizeof(lm));
     int ld = 1;
