@@ -233,6 +233,49 @@ __device__ __forceinline__ void epi_cols32(float* u, const float* bl, const floa
   }
 }
 
+// 16 accumulator columns [16b, 16b + 16) of row r, as epi_cols32 (layers whose
+// quarter of the columns is 16 wide).
+template <bool SCALE, bool OUT_FP8>
+__device__ __forceinline__ void epi_cols16(float* u, const float* bl, const float* sl, int b, int act,
+                                           uint8_t* A, int r) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float4 bb = *reinterpret_cast<const float4*>(bl + 16 * b + 4 * j);
+    if (SCALE) {
+      const float4 sc = *reinterpret_cast<const float4*>(sl + 16 * b + 4 * j);
+      u[4 * j + 0] = fmaf(u[4 * j + 0], sc.x, bb.x);
+      u[4 * j + 1] = fmaf(u[4 * j + 1], sc.y, bb.y);
+      u[4 * j + 2] = fmaf(u[4 * j + 2], sc.z, bb.z);
+      u[4 * j + 3] = fmaf(u[4 * j + 3], sc.w, bb.w);
+    } else {
+      u[4 * j + 0] += bb.x;
+      u[4 * j + 1] += bb.y;
+      u[4 * j + 2] += bb.z;
+      u[4 * j + 3] += bb.w;
+    }
+  }
+  if (!OUT_FP8) {
+    uint8_t* slab = A + (b >> 2) * (128 * 128);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      uint4 o;
+      o.x = act_pair(u[8 * j + 0], u[8 * j + 1], act);
+      o.y = act_pair(u[8 * j + 2], u[8 * j + 3], act);
+      o.z = act_pair(u[8 * j + 4], u[8 * j + 5], act);
+      o.w = act_pair(u[8 * j + 6], u[8 * j + 7], act);
+      *reinterpret_cast<uint4*>(slab + r * 128 + ((((b & 3) * 2 + j) ^ (r & 7)) << 4)) = o;
+    }
+  } else {
+    uint8_t* slab = A + (b >> 3) * (128 * 128);
+    uint4 o;
+    o.x = ptx::pack_e4m3x4(act_value(u[0], act), act_value(u[1], act), act_value(u[2], act), act_value(u[3], act));
+    o.y = ptx::pack_e4m3x4(act_value(u[4], act), act_value(u[5], act), act_value(u[6], act), act_value(u[7], act));
+    o.z = ptx::pack_e4m3x4(act_value(u[8], act), act_value(u[9], act), act_value(u[10], act), act_value(u[11], act));
+    o.w = ptx::pack_e4m3x4(act_value(u[12], act), act_value(u[13], act), act_value(u[14], act), act_value(u[15], act));
+    *reinterpret_cast<uint4*>(slab + r * 128 + (((b & 7) ^ (r & 7)) << 4)) = o;
+  }
+}
+
 // Byte address of 16-byte chunk j (8 BF16 columns) of row r in a 128B-swizzled
 // K-major slab: the chunk index is XORed with r mod 8.
 __device__ __forceinline__ uint8_t* a_chunk(uint8_t* slab, int r, int j) {
@@ -355,8 +398,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     }
     for (int g = 0; g < 2; ++g) {
       ptx::mbar_init(ptx::smem_u32(&accf[g]), 1);
-      // every epilogue warp of both CTAs (of one tile, or of both groups in the wide kernel)
-      ptx::mbar_init(ptx::smem_u32(&ready[g]), (WIDE ? 4 : 2) * kEpiWarpsPerTile);
+      // every epilogue warp of both CTAs
+      ptx::mbar_init(ptx::smem_u32(&ready[g]), 4 * kEpiWarpsPerTile);
     }
     ptx::mbar_init(ptx::smem_u32(drain), 1);
     *abort_flag = 0;
@@ -536,11 +579,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       while (!ptx::mbar_try_wait(ptx::smem_u32(drain), 0) && clock64() - t0 < kSpinLimit) {
       }
     }
-  } else {
-    // ------------------------------------------------------------ epilogue
-    // Eight warps per tile: warp w may read TMEM lanes 32*(w % 4) .. +31 (its
-    // rows); the two warps of a lane quadrant split the hidden columns. The
-    // "sub 0" warps also own the row state (s_t, omega, reward, G).
+  } else if constexpr (WIDE) {
+    // ------------------------------------------------------------ epilogue (wide)
+    // One tile per CTA and work item: the sixteen warps form two column groups
+    // of eight; warp w may read TMEM lanes 32*(w % 4) .. +31 (its rows); the two
+    // warps of a lane quadrant split a group's columns. The group-0 "sub 0"
+    // warps also own the row state.
     const int e = warp - 2;
     const int g = e >> 3;                   // tile of this warp (wide kernel: column group)
     const int sub = (e >> 2) & 1;           // column half of the hidden layers
@@ -723,6 +767,182 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         }
       } else if (owner && valid && ok) {
         PL.G[row] = Gacc;
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (two tiles)
+    // All sixteen warps serve each tile in turn, in the order the MMA warp
+    // issues them (tile 0 of a layer, then tile 1), so one tile's epilogue
+    // runs while the other tile's MMAs do. Warp w reads TMEM lanes
+    // 32*(w % 4) .. +31 (its rows of the tile) and a quarter of the columns
+    // (slice (w - 2) / 4); the slice-0 warps hold the row state of tile 0 (s_t,
+    // omega, reward, G), the slice-1 warps that of tile 1.
+    const int e = warp - 2;
+    const int slice = e >> 2;
+    const int q = warp & 3;
+    const int r = 32 * q + lane;
+    const bool owner = slice < 2;
+    const int og = slice & 1;  // the tile whose rows an owner holds
+    uint8_t* Aown = Abuf[og];
+    const uint32_t tq = (uint32_t)(32 * q) << 16;
+    const uint32_t ready_remote0 = ptx::mapa_shared(ptx::smem_u32(&ready[0]), 0);  // even CTA's
+    const uint32_t ready_remote1 = ptx::mapa_shared(ptx::smem_u32(&ready[1]), 0);
+    uint32_t nacc[2] = {0u, 0u};
+    bool ok = true;
+    for (long long it = cl; it < p.total_items && ok; it += ncl) {
+      const int pq = item_planner(p, it);
+      const long long sp = it - (pq ? p.item_end[pq - 1] : 0);
+      const TcPlanner& PL = p.pl[pq];
+      const int H = PL.H;
+      const long long row = sp * kSuperRows + og * (2 * kTileRows) + (long long)rank * kTileRows + r;
+      const bool valid = row < PL.rows;
+      const uint32_t n = valid ? (uint32_t)(row % PL.N) : 0u;
+      const uint32_t k = valid ? (uint32_t)(row / PL.N) : 0u;
+      const float* act_row = PL.actions + (size_t)k * H * DA;
+      float s[DS], a[DA];
+      if constexpr (PAIRS) {
+        if (owner) {
+          long long pi, pa, po;  // rows of s', a and o
+          bool in = valid;
+          if (p.gather_node) {
+            const int an = valid ? __ldg(p.gather_node + row) : -1;
+            in = an >= 0 && an < p.gather_n_nodes;
+            pi = row;
+            pa = in ? an : 0;
+            po = in ? (long long)an * p.gather_C_max + __ldg(p.gather_branch + row) : 0;
+          } else {
+            pi = valid ? row / p.pair_B : 0;
+            pa = pi;
+            po = valid ? row % p.pair_B : 0;
+          }
+          float x[16];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) x[i] = in ? __ldg(p.pair_s + pi * 8 + i) : 0.0f;
+          x[8] = in ? __ldg(p.pair_a + pa * 2) : 0.0f;
+          x[9] = in ? __ldg(p.pair_a + pa * 2 + 1) : 0.0f;
+#pragma unroll
+          for (int i = 0; i < 6; ++i) x[10 + i] = in ? __ldg(p.pair_o + po * 6 + i) : 0.0f;
+          store_row<16>(Aown, r, x);
+        }
+      } else if (owner) {
+#pragma unroll
+        for (int i = 0; i < DS; ++i) s[i] = valid ? __ldg(PL.particles + (size_t)n * DS + i) : 0.0f;
+#pragma unroll
+        for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + i);
+        write_gen_input<DS, DA, DW>(Aown, r, s, a, p.key0, p.key1, n, k, 0, PL.planner);
+      }
+      ptx::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        ptx::mbar_arrive_cluster(ready_remote0);
+        ptx::mbar_arrive_cluster(ready_remote1);
+      }
+      double Gacc = 0.0, disc = 1.0;
+      for (int t = 0; t < H && ok; ++t) {
+        for (int l = 0; l < p.n_total && ok; ++l) {
+          const TcLayer& L = p.layers[l];
+          const float* bl = bias_s + L.bias_off;  // shared memory (L1 loads measured slower)
+          // no A operand follows the final layer of the final step
+          const bool arrive = !(t == H - 1 && l == p.n_total - 1);
+          for (int g = 0; g < 2; ++g) {
+            if (!bounded_wait(ptx::smem_u32(&accf[g]), nacc[g] & 1, abort_flag, p.hdr, 30 + g)) {
+              ok = false;
+              break;
+            }
+            ++nacc[g];
+            ptx::tc_fence_after();
+            uint8_t* A = Abuf[g];
+            const uint32_t tm = tmem_base + (uint32_t)(g * 256) + tq;
+            if (L.act >= 0) {
+              // hidden layer: this warp's quarter of the columns, 32 per TMEM load
+              const int per = L.Npad >> 2;
+              if (per >= 32) {
+                const int c0 = slice * (per >> 5);
+                for (int c = c0; c < c0 + (per >> 5); ++c) {
+                  float v[32];
+                  ptx::tmem_ld32(tm + 32 * c, v);
+                  ptx::tmem_wait_ld32(v);
+                  if (!F8) {
+                    epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
+                  } else if (L.out_fp8) {
+                    if (L.fp8) epi_cols32<true, true>(v, bl, scale_s + L.scale_off, c, L.act, A, r);
+                    else epi_cols32<false, true>(v, bl, nullptr, c, L.act, A, r);
+                  } else {
+                    if (L.fp8) epi_cols32<true, false>(v, bl, scale_s + L.scale_off, c, L.act, A, r);
+                    else epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
+                  }
+                }
+              } else {
+                float v[16];
+                ptx::tmem_ld16(tm + 16 * slice, v);
+                ptx::tmem_wait_ld();
+                if (!F8) {
+                  epi_cols16<false, false>(v, bl, nullptr, slice, L.act, A, r);
+                } else if (L.out_fp8) {
+                  if (L.fp8) epi_cols16<true, true>(v, bl, scale_s + L.scale_off, slice, L.act, A, r);
+                  else epi_cols16<false, true>(v, bl, nullptr, slice, L.act, A, r);
+                } else {
+                  if (L.fp8) epi_cols16<true, false>(v, bl, scale_s + L.scale_off, slice, L.act, A, r);
+                  else epi_cols16<false, false>(v, bl, nullptr, slice, L.act, A, r);
+                }
+              }
+            } else if (owner && og == g) {
+              if constexpr (PAIRS) {
+                float v[16];
+                ptx::tmem_ld16(tm, v);
+                ptx::tmem_wait_ld();
+                if (valid) p.pair_out[row] = v[0] + bl[0];
+              } else if (l == p.n_gen - 1) {
+                // generator output: s_{t+1} (FP32, kept in registers)
+                float v[32];
+                ptx::tmem_ld16(tm, v);
+                if (DS > 16) ptx::tmem_ld16(tm + 16, v + 16);
+                ptx::tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < DS; ++i) s[i] = v[i] + bl[i];
+                if (p.reward_kind == VOILA_REWARD_GOAL) {
+                  float acc = 0.0f;
+#pragma unroll
+                  for (int i = 0; i < VOILA_MAX_GOAL; ++i)
+                    if (i < p.goal_dims && i < DS) {
+                      const float d = s[i] - p.goal[i];
+                      acc = fmaf(d, d, acc);
+                    }
+                  Gacc += disc * (double)(-acc);
+                  disc *= p.gamma;
+                  if (t + 1 < H) {
+#pragma unroll
+                    for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + (t + 1) * DA + i);
+                    write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
+                  }
+                } else {
+                  write_rew_input<DS, DA>(A, r, s, a);
+                }
+              } else {
+                // reward output r_t: G += gamma^t r_t in FP64
+                float v[16];
+                ptx::tmem_ld16(tm, v);
+                ptx::tmem_wait_ld();
+                Gacc += disc * (double)(v[0] + bl[0]);
+                disc *= p.gamma;
+                if (t + 1 < H) {
+#pragma unroll
+                  for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + (t + 1) * DA + i);
+                  write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
+                }
+              }
+            }
+            ptx::tc_fence_before();
+            if (arrive) {
+              ptx::fence_proxy_async_smem();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive_cluster(g ? ready_remote1 : ready_remote0);
+            }
+          }
+        }
+      }
+      if constexpr (!PAIRS) {
+        if (owner && valid && ok) PL.G[row] = Gacc;
       }
     }
   }
