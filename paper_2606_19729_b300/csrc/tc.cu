@@ -76,6 +76,9 @@ struct TcLayer {
   int box_rows;     // rows of one CTA's TMA box: min(Npad, 256) / 2
   uint32_t idesc;
   int row0;         // first row of chunk 0 in the [rows][64] weight tensor
+  int fuse_out;     // 1: a scalar output layer follows, computed in this layer's epilogue on CUDA cores
+  int fuse_off;     // its weights (fuse_K floats) and bias in the fused-output vector
+  int fuse_K;
 };
 
 // One independent planning problem of a (batched) launch.
@@ -96,6 +99,7 @@ struct TcParams {
   const float* bias_all;
   int bias_total;   // floats, multiple of 4
   int scale_total;  // floats after the biases in the same vector (FP8 channel scales)
+  int fuse_total;   // floats after the scales: fused scalar-output weights and biases
   double gamma;
   uint32_t key0, key1;
   int reward_kind, goal_dims;
@@ -276,6 +280,33 @@ __device__ __forceinline__ void epi_cols16(float* u, const float* bl, const floa
   }
 }
 
+// The columns [W c, W c + W) of row r of a layer followed by a fused scalar
+// output: (channel scale) + bias + activation, dotted in FP32 with the output
+// weights wf (the activations are not rounded to BF16: a BF16 round trip per
+// value costs a conversion on the MUFU pipe, which bounds this epilogue).
+template <bool SCALE, int W>
+__device__ __forceinline__ float fuse_cols(const float* u, const float* bl, const float* sl, int c, int act,
+                                           const float* wf, float part) {
+#pragma unroll
+  for (int j = 0; j < W; j += 4) {
+    const float4 b = *reinterpret_cast<const float4*>(bl + W * c + j);
+    const float4 w = *reinterpret_cast<const float4*>(wf + W * c + j);
+    float x0 = u[j] + b.x, x1 = u[j + 1] + b.y, x2 = u[j + 2] + b.z, x3 = u[j + 3] + b.w;
+    if (SCALE) {
+      const float4 sc = *reinterpret_cast<const float4*>(sl + W * c + j);
+      x0 = fmaf(u[j], sc.x, b.x);
+      x1 = fmaf(u[j + 1], sc.y, b.y);
+      x2 = fmaf(u[j + 2], sc.z, b.z);
+      x3 = fmaf(u[j + 3], sc.w, b.w);
+    }
+    part = fmaf(act_value(x0, act), w.x, part);
+    part = fmaf(act_value(x1, act), w.y, part);
+    part = fmaf(act_value(x2, act), w.z, part);
+    part = fmaf(act_value(x3, act), w.w, part);
+  }
+  return part;
+}
+
 // Byte address of 16-byte chunk j (8 BF16 columns) of row r in a 128B-swizzled
 // K-major slab: the chunk index is XORed with r mod 8.
 __device__ __forceinline__ uint8_t* a_chunk(uint8_t* slab, int r, int j) {
@@ -379,7 +410,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
   uint8_t* ring = smem + 2 * kABytes;
   float* bias_s = reinterpret_cast<float*>(ring + kStages * kSlotBytes);
   float* scale_s = bias_s + p.bias_total;  // FP8 channel scales follow the biases
-  uint64_t* bars = reinterpret_cast<uint64_t*>(scale_s + p.scale_total);
+  float* fuse_s = scale_s + p.scale_total;  // fused scalar-output weights and biases
+  float* red_s = fuse_s + p.fuse_total;     // [2 tiles][4 column slices][128 rows] partial sums
+  uint64_t* bars = reinterpret_cast<uint64_t*>(red_s + (p.fuse_total ? 1024 : 0));
   uint64_t* full = bars;
   uint64_t* empty = bars + kStages;
   uint64_t* accf = bars + 2 * kStages;      // [2]
@@ -405,7 +438,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
-  for (int i = threadIdx.x; i < p.bias_total + p.scale_total; i += blockDim.x) bias_s[i] = p.bias_all[i];
+  for (int i = threadIdx.x; i < p.bias_total + p.scale_total + p.fuse_total; i += blockDim.x)
+    bias_s[i] = p.bias_all[i];
   if (warp == 1) {
     ptx::tmem_alloc_pair(ptx::smem_u32(tmem_holder), 512);
     ptx::tmem_relinquish_pair();
@@ -853,7 +887,49 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
             ptx::tc_fence_after();
             uint8_t* A = Abuf[g];
             const uint32_t tm = tmem_base + (uint32_t)(g * 256) + tq;
-            if (L.act >= 0) {
+            if (L.act >= 0 && L.fuse_out) {
+              // last hidden layer before a scalar output: the output is computed here on
+              // the CUDA cores (each warp's quarter of the columns, then the row owner
+              // adds the four partial sums and the bias in a fixed order)
+              const int per = L.Npad >> 2;
+              const float* wf = fuse_s + L.fuse_off;
+              const float* sl = scale_s + L.scale_off;
+              float part = 0.0f;
+              if (per >= 32) {
+                const int c0 = slice * (per >> 5);
+                for (int c = c0; c < c0 + (per >> 5); ++c) {
+                  float v[32];
+                  ptx::tmem_ld32(tm + 32 * c, v);
+                  ptx::tmem_wait_ld32(v);
+                  part = (F8 && L.fp8) ? fuse_cols<true, 32>(v, bl, sl, c, L.act, wf, part)
+                                       : fuse_cols<false, 32>(v, bl, sl, c, L.act, wf, part);
+                }
+              } else {
+                float v[16];
+                ptx::tmem_ld16(tm + 16 * slice, v);
+                ptx::tmem_wait_ld();
+                part = (F8 && L.fp8) ? fuse_cols<true, 16>(v, bl, sl, slice, L.act, wf, part)
+                                     : fuse_cols<false, 16>(v, bl, sl, slice, L.act, wf, part);
+              }
+              red_s[(g * 4 + slice) * 128 + r] = part;
+              asm volatile("bar.sync %0, 128;" ::"r"(1 + q) : "memory");  // the four warps of quadrant q
+              if (owner && og == g) {
+                float val = wf[L.fuse_K];
+#pragma unroll
+                for (int sl4 = 0; sl4 < 4; ++sl4) val += red_s[(g * 4 + sl4) * 128 + r];
+                if constexpr (PAIRS) {
+                  if (valid) p.pair_out[row] = val;
+                } else {
+                  Gacc += disc * (double)val;
+                  disc *= p.gamma;
+                  if (t + 1 < H) {
+#pragma unroll
+                    for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + (t + 1) * DA + i);
+                    write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
+                  }
+                }
+              }
+            } else if (L.act >= 0) {
               // hidden layer: this warp's quarter of the columns, 32 per TMEM load
               const int per = L.Npad >> 2;
               if (per >= 32) {
@@ -970,6 +1046,11 @@ struct PackTable {
   int ldk[kMaxTcLayers];   // row stride of W[l] (its input width)
   int colmap_layer;        // layer whose packed column kg reads W column colmap[kg] (-1: none)
   short colmap[128];       // -1: zero column
+  // fused scalar output layers: weights (FP32 copies) and bias at fuse_base + fuseoff
+  int fuse_n, fuse_base;
+  const __nv_bfloat16* fuseW[2];
+  const float* fuseb[2];
+  int fuseK[2], fuseoff[2];
   int n;
   uint8_t* wout;
   float* bout;   // biases, then channel scales
@@ -1025,6 +1106,14 @@ __global__ void pack_kernel(const __grid_constant__ PackTable t) {
   }
 }
 
+__global__ void fuse_pack_kernel(const __grid_constant__ PackTable t) {
+  for (int f = 0; f < t.fuse_n; ++f) {
+    float* dst = t.bout + t.fuse_base + t.fuseoff[f];
+    for (int i = threadIdx.x; i < t.fuseK[f]; i += blockDim.x) dst[i] = __bfloat162float(t.fuseW[f][i]);
+    if (threadIdx.x == 0) dst[t.fuseK[f]] = t.fuseb[f][0];
+  }
+}
+
 struct Plan {
   TcParams p;
   PackTable pack;
@@ -1045,13 +1134,33 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R, bool ddim = false) {
   pl.ok = false;
   pl.pack.colmap_layer = -1;
   const voila_mlp* mlps[2] = {g, R && R->kind == VOILA_REWARD_MLP ? R->mlp : nullptr};
-  int nl = 0, boff = 0, rows = 0;
+  int nl = 0, boff = 0, rows = 0, foff = 0;
   long long elems = 0;
+  bool any_wide = false;  // a layer wider than 256: the wide kernel, which has no fused outputs
+  for (int m = 0; m < 2; ++m)
+    if (mlps[m])
+      for (int l = 0; l <= mlps[m]->n_layers; ++l) any_wide = any_wide || mlps[m]->dims[l] > 256;
   for (int m = 0; m < 2; ++m) {
     const voila_mlp* M = mlps[m];
     if (!M) continue;
     if ((M->prec != VOILA_BF16 && M->prec != VOILA_FP8E4M3) || M->n_layers < 2) return pl;
+    // a scalar output layer is computed in the previous layer's epilogue
+    const bool fuse = !ddim && !any_wide && M->dims[M->n_layers] == 1;
     for (int l = 0; l < M->n_layers; ++l) {
+      if (fuse && l == M->n_layers - 1) {
+        TcLayer& P = pl.p.layers[nl - 1];
+        P.fuse_out = 1;
+        P.fuse_off = foff;
+        P.fuse_K = M->dims[l];
+        PackTable& T = pl.pack;
+        T.fuseW[T.fuse_n] = (const __nv_bfloat16*)M->W[l];
+        T.fuseb[T.fuse_n] = M->b[l];
+        T.fuseK[T.fuse_n] = M->dims[l];
+        T.fuseoff[T.fuse_n] = foff;
+        ++T.fuse_n;
+        foff += round_up(M->dims[l] + 1, 4);
+        continue;
+      }
       if (nl >= kMaxTcLayers) return pl;
       const int K = (ddim && l == 0) ? 96 : M->dims[l], N = M->dims[l + 1];
       const bool last = l == M->n_layers - 1;
@@ -1115,9 +1224,11 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R, bool ddim = false) {
     if (pl.p.layers[l].fp8) soff += pl.p.layers[l].Npad;
   }
   pl.p.scale_total = soff;
+  pl.p.fuse_total = foff;
+  pl.pack.fuse_base = boff + soff;
   pl.total_rows = rows;
   pl.wbytes = (size_t)rows * 128;
-  pl.bias_bytes = (size_t)(boff + soff) * sizeof(float);
+  pl.bias_bytes = (size_t)(boff + soff + foff) * sizeof(float);
   pl.total = (pl.wbytes + 1023) / 1024 * 1024 + (pl.bias_bytes + 255) / 256 * 256;
   pl.ok = true;
   return pl;
@@ -1250,6 +1361,7 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
       scale_kernel<<<(srows * 32 + 255) / 256, 256, 0, s>>>(pl.pack);
     }
     pack_kernel<<<(int)blocks, 256, 0, s>>>(pl.pack);
+    if (pl.pack.fuse_n > 0) fuse_pack_kernel<<<1, 256, 0, s>>>(pl.pack);
     if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   }
   // one tensor map per layer over the [rows][64] BF16 weight tensor
@@ -1279,7 +1391,7 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   long long nclusters = items < nsm / 2 ? items : nsm / 2;
   if (max_clusters > 0 && nclusters > max_clusters) nclusters = max_clusters;
-  const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total);
+  const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total + p.fuse_total + (p.fuse_total ? 1024 : 0));
   const bool f8 = p.scale_total > 0;
   cudaError_t e;
   if (dims_a)
@@ -1353,6 +1465,7 @@ voila_status tc_ddim_sample(const voila_mlp* teacher, const float* S, const floa
     long long blocks = (total + 255) / 256;
     if (blocks > 148 * 8) blocks = 148 * 8;
     pack_kernel<<<(int)blocks, 256, 0, s>>>(pl.pack);
+    if (pl.pack.fuse_n > 0) fuse_pack_kernel<<<1, 256, 0, s>>>(pl.pack);
     EmbFreq fr;
     for (int i = 0; i < 32; ++i) fr.f[i] = (float)freq[i];
     ddim_emb_kernel<<<T, 64, 0, s>>>(fr, T, emb);
@@ -1386,7 +1499,7 @@ voila_status tc_ddim_sample(const voila_mlp* teacher, const float* S, const floa
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const long long nclusters = p.total_items < nsm / 2 ? p.total_items : nsm / 2;
-  const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total);
+  const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total + p.fuse_total + (p.fuse_total ? 1024 : 0));
   const cudaError_t e = launch_tc<8, 10, 0, false, true, kModeDdim>(p, smem, nclusters, s);
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
@@ -1435,6 +1548,7 @@ voila_status tc_likelihood_rows(const voila_mlp* ell, const float* S, const floa
     long long blocks = (total + 255) / 256;
     if (blocks > 148 * 8) blocks = 148 * 8;
     pack_kernel<<<(int)blocks, 256, 0, s>>>(pl.pack);
+    if (pl.pack.fuse_n > 0) fuse_pack_kernel<<<1, 256, 0, s>>>(pl.pack);
     if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   }
   PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
@@ -1466,7 +1580,7 @@ voila_status tc_likelihood_rows(const voila_mlp* ell, const float* S, const floa
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const long long nclusters = p.total_items < nsm / 2 ? p.total_items : nsm / 2;
-  const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total);
+  const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total + p.fuse_total + (p.fuse_total ? 1024 : 0));
   const cudaError_t e = launch_tc<8, 2, 6, false, false, kModePairs>(p, smem, nclusters, s);
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
