@@ -653,7 +653,7 @@ def run_infonce(args, rank, world, local):
                          "peak_kind": "measured bf16 sustained"},
             "train_step": {"ms": statistics.median(step_ms), "loss_first": float(step_losses[0].item()),
                            "loss_last": float(step_losses[-1].item()),
-                           "note": "FP32 CUDA-core training forward and backward over all B^2 pair rows"},
+                           "note": "BF16 likelihood: tensor-core training forward and backward over all B^2 pair rows"},
             "gpu_launches": 4 * reps, "clocks": clk.summary()}
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import voila_oracle as O

@@ -429,6 +429,10 @@ voila_status voila_distill_step_workspace_size(const voila_mlp* teacher, const v
  *            bytes; its first bytes are the teacher sampler's workspace, so
  *            voila_workspace_status(workspace) reports the sampler's status.
  * Deterministic: every reduction runs in a fixed order.
+ * A BF16 student (hidden widths multiples of 16 up to 256) trains on the
+ * tensor cores: BF16 operands, activations and deltas, FP32 accumulation,
+ * weight gradients as split-K GEMMs over the batch; an FP32 student on the
+ * CUDA cores in FP32 (voila_generator_fwd_train / voila_generator_bwd).
  */
 voila_status voila_distill_step(const voila_mlp* teacher, const voila_mlp* student,
                                 const voila_ddim* ddim, float* master, float* adam_m,
@@ -489,15 +493,16 @@ voila_status voila_infonce_step_workspace_size(const voila_mlp* ell, int32_t B, 
 
 /*
  * One training step of the likelihood model on Eq. 6: the training forward
- * over the B^2 pair rows (CUDA cores, FP32 arithmetic on the MLP's FP32 or
- * BF16 weights), the loss and dloss/dL as voila_infonce_forward, the
- * hand-written backward, voila_adam_step on `master` (flat FP32 layout of
+ * over the B^2 pair rows, the loss and dloss/dL as voila_infonce_forward,
+ * the hand-written backward, voila_adam_step on `master` (flat FP32 layout of
  * voila_mlp_load_flat) and voila_mlp_load_flat(ell, master).
  *   loss_out  device double (the loss before the update); grad_out [n_params]
  *             float or NULL.
- *   workspace device, 1024-byte aligned. The batch of B^2 rows saves its
- *             hidden pre-activations: about 4 B^2 (d_in + 3 + 3 sum of hidden
- *             widths) bytes.
+ *   workspace device, 1024-byte aligned. The batch of B^2 rows keeps its
+ *             activations for the backward: on the order of 10 B^2 times the
+ *             sum of the hidden widths bytes.
+ * A BF16 likelihood trains on the tensor cores (as voila_distill_step's BF16
+ * student), an FP32 one on the CUDA cores.
  */
 voila_status voila_infonce_step(const voila_mlp* ell, float* master, float* adam_m, float* adam_v,
                                 const voila_adam* opt, const float* S, const float* A,

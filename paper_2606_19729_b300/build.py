@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIB_DIR, "libvoila.so")
-SOURCES = ["api.cu", "simt.cu", "belief.cu", "tc.cu", "noalloc.cu", "train.cu", "objective.cu", "widen.cu"]
+SOURCES = ["api.cu", "simt.cu", "belief.cu", "tc.cu", "noalloc.cu", "train.cu", "objective.cu", "widen.cu", "gemm.cu", "train_tc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-cudart", "shared",

@@ -1,0 +1,329 @@
+// BF16 tensor-core GEMM with the epilogues of MLP training (tcgen05, TMA).
+//
+// D[M][N] = A[M][K] . B[N][K]^T, A and B BF16 K-major (row-major [rows][K]),
+// FP32 accumulation in TMEM; one CTA computes a 128-row tile over all N <= 256
+// columns and a range of K (split-K over blockIdx.y). Warp 0 streams A and B
+// K-chunks of 64 (128-byte rows, 128B swizzle) into a 4-stage ring with TMA,
+// warp 1 issues the MMAs (M = 128, N, K = 16) from one thread, warps 2-5 read
+// the accumulator (warp w owns TMEM lanes 32 (w mod 4) .. +31, one row per
+// thread) and run one of the epilogues:
+//   kFwdHidden  z = acc + b;  H = act(z), AD = act'(z) row-major, H^T via
+//               a shared-memory transpose (BF16);
+//   kFwdOut     Y = acc + b (FP32, the first n_real columns);
+//   kBwd        delta = acc * AD_in;  D row-major and D^T (BF16);
+//   kPartial    P[split][m][n] = acc (FP32), summed later in split order.
+// Every wait is bounded; on expiry the kernel records VOILA_ERR_TIMEOUT,
+// waits (bounded) for its copies, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <math.h>
+#include <string.h>
+
+#include "../../include/voila.h"
+#include "common.cuh"
+#include "gemm.h"
+#include "tc_ptx.cuh"
+
+namespace voila {
+namespace {
+
+constexpr int kGThreads = 192;
+constexpr int kGStages = 4;
+constexpr int kGABytes = 128 * 128;  // 128 rows x 64 BF16
+constexpr int kGBBytes = 256 * 128;  // up to 256 rows x 64 BF16
+constexpr long long kGSpin = 4000000000LL;
+
+struct GemmParams {
+  CUtensorMap ta, tb;
+  int M, N;           // rows of A (valid rows), columns of D (MMA N, multiple of 16, <= 256)
+  int n_real;         // columns stored by kFwdOut / kPartial-transposed users
+  int kchunks;        // K chunks of 64 per CTA
+  int mode, act;
+  uint32_t bbytes;    // bytes of one B chunk (N rows x 128 B)
+  const float* bias;
+  __nv_bfloat16* H;   // [M][N]
+  __nv_bfloat16* AD;  // [M][N]
+  __nv_bfloat16* HT;  // [N][ldT]
+  const __nv_bfloat16* AD_in;
+  float* Y;
+  int ldY;
+  float* P;           // [splits][M][N]
+  int ldT;
+  WsHeader* hdr;
+};
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool gwait(uint32_t bar, uint32_t parity, volatile int* abort_flag, WsHeader* hdr,
+                                      int where) {
+  if (ptx::mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (ptx::mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kGSpin) {
+      *abort_flag = 1;
+      set_status(hdr, VOILA_ERR_TIMEOUT, where);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void act_and_grad(float z, int act, float& h, float& d) {
+  if (act == VOILA_ACT_SILU) {
+    const float sg = 1.0f / (1.0f + __expf(-z));
+    h = z * sg;
+    d = sg * (1.0f + z * (1.0f - sg));
+  } else if (act == VOILA_ACT_TANH) {
+    h = tanhf(z);
+    d = 1.0f - h * h;
+  } else {
+    h = z;
+    d = 1.0f;
+  }
+}
+
+__device__ __forceinline__ uint32_t bf2(float lo, float hi) { return ptx::pack_bf16x2(lo, hi); }
+
+__global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_constant__ GemmParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* ringA = smem;
+  uint8_t* ringB = smem + kGStages * kGABytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ringB + kGStages * kGBBytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kGStages;
+  uint64_t* accf = bars + 2 * kGStages;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kGStages + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * 128;
+  const int kc0 = blockIdx.y * p.kchunks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kGStages; ++s) {
+      ptx::mbar_init(ptx::smem_u32(&full[s]), 1);
+      ptx::mbar_init(ptx::smem_u32(&empty[s]), 1);
+    }
+    ptx::mbar_init(ptx::smem_u32(accf), 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(ptx::smem_u32(tmem_holder), 256);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      ptx::prefetch_tmap(&p.ta);
+      ptx::prefetch_tmap(&p.tb);
+      int last[kGStages];
+      for (int s = 0; s < kGStages; ++s) last[s] = -1;
+      bool ok = true;
+      for (int c = 0; c < p.kchunks && ok; ++c) {
+        const int slot = c % kGStages;
+        const uint32_t phase = (uint32_t)(c / kGStages) & 1u;
+        if (!gwait(ptx::smem_u32(&empty[slot]), phase ^ 1u, abort_flag, p.hdr, 70)) {
+          ok = false;
+          break;
+        }
+        const uint32_t fb = ptx::smem_u32(&full[slot]);
+        ptx::mbar_arrive_expect_tx(fb, (uint32_t)kGABytes + p.bbytes);
+        tma_load_2d(ptx::smem_u32(ringA + slot * kGABytes), &p.ta, (kc0 + c) * 64, m0, fb);
+        tma_load_2d(ptx::smem_u32(ringB + slot * kGBBytes), &p.tb, (kc0 + c) * 64, 0, fb);
+        last[slot] = (int)phase;
+      }
+      if (!ok) {  // loads still in flight complete before shared memory goes away
+        for (int s = 0; s < kGStages; ++s)
+          if (last[s] >= 0) {
+            const long long t0 = clock64();
+            while (!ptx::mbar_try_wait(ptx::smem_u32(&full[s]), (uint32_t)last[s]) && clock64() - t0 < kGSpin) {
+            }
+          }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = ptx::idesc_bf16(128, p.N);
+      bool ok = true;
+      for (int c = 0; c < p.kchunks && ok; ++c) {
+        const int slot = c % kGStages;
+        const uint32_t phase = (uint32_t)(c / kGStages) & 1u;
+        if (!gwait(ptx::smem_u32(&full[slot]), phase, abort_flag, p.hdr, 71)) {
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint64_t ad = ptx::smem_desc(ptx::smem_u32(ringA + slot * kGABytes), 1024, ptx::kSwizzle128B);
+        const uint64_t bd = ptx::smem_desc(ptx::smem_u32(ringB + slot * kGBBytes), 1024, ptx::kSwizzle128B);
+        const uint32_t ahi = (uint32_t)(ad >> 32), alo = (uint32_t)ad;
+        const uint32_t bhi = (uint32_t)(bd >> 32), blo = (uint32_t)bd;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)  // K = 16 per MMA: +32 bytes (+2 in the address field)
+          ptx::mma_bf16(tmem, ptx::desc_with_lo(ahi, alo + 2 * kk), ptx::desc_with_lo(bhi, blo + 2 * kk), idesc,
+                        (c | kk) ? 1u : 0u);
+        ptx::mma_commit(ptx::smem_u32(&empty[slot]));
+      }
+      ptx::mma_commit(ptx::smem_u32(accf));  // every MMA above (or none) has completed
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const int r = 32 * q + lane;
+    const int m = m0 + r;
+    const bool valid = m < p.M;
+    const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
+    const bool ok = gwait(ptx::smem_u32(accf), 0, abort_flag, p.hdr, 72);
+    ptx::tc_fence_after();
+    // staging for transposed stores: the ring is free once the MMAs are done
+    __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(smem);  // [N][128]
+    if (ok) {
+      for (int cb = 0; cb < p.N; cb += 16) {
+        float v[16];
+        ptx::tmem_ld16(tq + cb, v);
+        ptx::tmem_wait_ld();
+        if (p.mode == kGemmFwdHidden || p.mode == kGemmBwd) {
+          float h[16], d[16];
+          if (p.mode == kGemmFwdHidden) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) act_and_grad(v[j] + p.bias[cb + j], p.act, h[j], d[j]);
+          } else {
+            float a[16];
+            if (valid) {
+              const uint4* src = reinterpret_cast<const uint4*>(p.AD_in + (size_t)m * p.N + cb);
+              const uint4 w0 = src[0], w1 = src[1];
+              const uint32_t ws[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                a[2 * j] = __uint_as_float(ws[j] << 16);
+                a[2 * j + 1] = __uint_as_float(ws[j] & 0xffff0000u);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) a[j] = 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) h[j] = v[j] * a[j];
+          }
+          if (valid) {
+            uint4* dst = reinterpret_cast<uint4*>(p.H + (size_t)m * p.N + cb);
+            dst[0] = make_uint4(bf2(h[0], h[1]), bf2(h[2], h[3]), bf2(h[4], h[5]), bf2(h[6], h[7]));
+            dst[1] = make_uint4(bf2(h[8], h[9]), bf2(h[10], h[11]), bf2(h[12], h[13]), bf2(h[14], h[15]));
+            if (p.mode == kGemmFwdHidden) {
+              uint4* dd = reinterpret_cast<uint4*>(p.AD + (size_t)m * p.N + cb);
+              dd[0] = make_uint4(bf2(d[0], d[1]), bf2(d[2], d[3]), bf2(d[4], d[5]), bf2(d[6], d[7]));
+              dd[1] = make_uint4(bf2(d[8], d[9]), bf2(d[10], d[11]), bf2(d[12], d[13]), bf2(d[14], d[15]));
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) stage[(cb + j) * 128 + r] = __float2bfloat16_rn(valid ? h[j] : 0.0f);
+        } else if (p.mode == kGemmFwdOut) {
+          if (valid)
+            for (int j = 0; j < 16; ++j)
+              if (cb + j < p.n_real) p.Y[(size_t)m * p.ldY + cb + j] = v[j] + p.bias[cb + j];
+        } else {  // kGemmPartial
+          if (valid) {
+            float4* dst = reinterpret_cast<float4*>(p.P + ((size_t)blockIdx.y * p.M + m) * p.N + cb);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          }
+        }
+      }
+    }
+    if (p.mode == kGemmFwdHidden || p.mode == kGemmBwd) {
+      // transposed copy: stage [N][128] -> HT[n][m0 .. m0 + 127], 16 bytes per store
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (ok) {
+        const int per_row = 16;  // 128 BF16 = 16 x 16 bytes
+        for (int e = threadIdx.x - 64; e < p.N * per_row; e += 128) {
+          const int n = e / per_row, j = e % per_row;
+          const int mm = m0 + 8 * j;
+          if (mm + 8 <= p.ldT)
+            *reinterpret_cast<uint4*>(p.HT + (size_t)n * p.ldT + mm) =
+                *reinterpret_cast<const uint4*>(stage + n * 128 + 8 * j);
+        }
+      }
+    }
+  }
+
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  if (warp == 1) ptx::tmem_dealloc(tmem, 256);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &qr) ==
+            cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+// [rows][K] BF16 with row stride ld elements; box = 64 K x box_rows rows, 128B swizzle, zero fill.
+bool make_map(CUtensorMap* map, const __nv_bfloat16* base, long long K, long long rows, long long ld, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+  if (!enc || ((uintptr_t)base & 15) || (ld * 2) % 16 || K < 1 || rows < 1) return false;
+  const cuuint64_t gdim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)(ld * 2)};
+  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  const cuuint32_t estride[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, gdim, gstride, box, estride,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t tc_gemm_smem_bytes() { return 1024 + kGStages * (kGABytes + kGBBytes) + (2 * kGStages + 2) * 8 + 16; }
+
+cudaError_t tc_gemm(const TcGemm& g, cudaStream_t s) {
+  if (g.N < 16 || g.N > 256 || g.N % 16 || g.M < 1 || g.K < 1 || g.splits < 1) return cudaErrorInvalidValue;
+  GemmParams p;
+  memset(&p, 0, sizeof(p));
+  if (!make_map(&p.ta, g.A, g.K, g.M, g.lda, 128)) return cudaErrorInvalidValue;
+  if (!make_map(&p.tb, g.B, g.K, g.N, g.ldb, g.N)) return cudaErrorInvalidValue;
+  const int kchunks_total = (int)((g.K + 63) / 64);
+  p.M = g.M;
+  p.N = g.N;
+  p.n_real = g.n_real;
+  p.kchunks = (kchunks_total + g.splits - 1) / g.splits;
+  p.mode = g.mode;
+  p.act = g.act;
+  p.bbytes = (uint32_t)g.N * 128u;
+  p.bias = g.bias;
+  p.H = g.H;
+  p.AD = g.AD;
+  p.HT = g.HT;
+  p.AD_in = g.AD_in;
+  p.Y = g.Y;
+  p.ldY = g.ldY;
+  p.P = g.P;
+  p.ldT = g.ldT;
+  p.hdr = g.hdr;
+  const size_t smem = tc_gemm_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int splits = (kchunks_total + p.kchunks - 1) / p.kchunks;
+  dim3 grid((unsigned)((g.M + 127) / 128), (unsigned)splits);
+  gemm_tc_kernel<<<grid, kGThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace voila

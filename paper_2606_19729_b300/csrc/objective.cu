@@ -9,8 +9,9 @@
 // of the planning shapes) or on the CUDA cores (any other), then one CTA per
 // row for lse_i = log sum_j exp(L_ij) and dloss/dL_ij = (exp(L_ij - lse_i) -
 // [i == j]) / B, and one CTA for loss = -(1/B) sum_i (L_ii - lse_i). The
-// training step runs the FP32 training forward and the hand-written backward
-// over the B^2 pair rows, then Adam.
+// training step runs the training forward and the hand-written backward over
+// the B^2 pair rows (tensor cores for a BF16 likelihood, CUDA cores in FP32
+// otherwise), then Adam.
 #include <math.h>
 #include <string.h>
 
@@ -20,6 +21,7 @@
 #include "reduce.cuh"
 #include "simt_mlp.cuh"
 #include "tc.h"
+#include "train_tc.h"
 
 namespace voila {
 namespace {
@@ -247,6 +249,7 @@ static size_t step_hidden(const voila_mlp* m) {
 
 struct StepLayout {
   size_t x, L, saved, G, grads, diag, scratch, total;
+  bool tc;  // BF16 likelihood: training forward/backward on the tensor cores
 };
 
 static StepLayout step_layout(const voila_mlp* ell, int B) {
@@ -257,8 +260,9 @@ static StepLayout step_layout(const voila_mlp* ell, int B) {
   o += a1024(rows * ell->dims[0] * 4);
   S.L = o;
   o += a1024(rows * 4);
+  S.tc = tc_train_supported(ell);
   S.saved = o;
-  o += a1024(rows * step_hidden(ell) * 4);
+  o += S.tc ? 0 : a1024(rows * step_hidden(ell) * 4);
   S.G = o;
   o += a1024(rows * 4);
   S.grads = o;
@@ -267,7 +271,8 @@ static StepLayout step_layout(const voila_mlp* ell, int B) {
   o += a1024((size_t)B * 8);
   S.scratch = o;
   size_t bwd = 0;
-  voila_generator_bwd_workspace_size(ell, (int32_t)rows, &bwd);
+  if (S.tc) bwd = tc_train_bytes(ell, (long long)rows);
+  else voila_generator_bwd_workspace_size(ell, (int32_t)rows, &bwd);
   o += a1024(bwd);
   S.total = o;
   return S;
@@ -304,7 +309,8 @@ voila_status voila_infonce_step(const voila_mlp* ell, float* master, float* adam
   const size_t scratch_bytes = L.total - L.scratch;
   pairs_input_kernel<<<grid_for((long long)rows * ell->dims[0], 256), 256, 0, s>>>(S, A, Ob, B, d_s, d_a, d_o, X);
   if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
-  st = voila_generator_fwd_train(ell, X, rows, Lm, saved, scratch, scratch_bytes, stream);
+  if (L.tc) st = tc_train_forward(ell, X, rows, Lm, scratch, (WsHeader*)ws, s);
+  else st = voila_generator_fwd_train(ell, X, rows, Lm, saved, scratch, scratch_bytes, stream);
   if (st != VOILA_OK) return st;
   st = lse_and_loss(Lm, B, nullptr, diag, G, loss_out, s);
   if (st != VOILA_OK) return st;
@@ -317,7 +323,8 @@ voila_status voila_infonce_step(const voila_mlp* ell, float* master, float* adam
     db[l] = grads + off;
     off += ell->dims[l + 1];
   }
-  st = voila_generator_bwd(ell, X, saved, G, rows, nullptr, dW, db, scratch, scratch_bytes, stream);
+  if (L.tc) st = tc_train_backward(ell, G, rows, grads, scratch, (WsHeader*)ws, s);
+  else st = voila_generator_bwd(ell, X, saved, G, rows, nullptr, dW, db, scratch, scratch_bytes, stream);
   if (st != VOILA_OK) return st;
   st = voila_adam_step(master, grads, adam_m, adam_v, (int64_t)off, opt->lr, opt->beta1, opt->beta2, opt->eps,
                        opt->step, stream);

@@ -16,6 +16,7 @@
 #include "kernels.h"
 #include "simt_mlp.cuh"
 #include "tc.h"
+#include "train_tc.h"
 
 namespace voila {
 
@@ -486,6 +487,7 @@ size_t ddim_ws_bytes(const voila_mlp* teacher, int T) {
 // [kLossBlocks] (FP64), scratch (bwd).
 struct DistillLayout {
   size_t ddim, s_hat, x, y, dy, saved, grads, part, scratch, total;
+  bool tc;  // BF16 student: the training forward/backward run on the tensor cores (scratch)
 };
 
 DistillLayout distill_layout(const voila_mlp* teacher, const voila_mlp* st, int B, int d_x, int T) {
@@ -498,10 +500,12 @@ DistillLayout distill_layout(const voila_mlp* teacher, const voila_mlp* st, int 
   L.x = o;     o += align256((size_t)B * st->dims[0] * 4);
   L.y = o;     o += align256((size_t)B * d_x * 4);
   L.dy = o;    o += align256((size_t)B * d_x * 4);
-  L.saved = o; o += align256((size_t)B * hidden_total(st) * 4);
+  L.saved = o; o += tc_train_supported(st) ? 0 : align256((size_t)B * hidden_total(st) * 4);
   L.grads = o; o += align256((size_t)np * 4);
   L.part = o;  o += align256(kLossBlocks * 8);
-  L.scratch = o; o += align256(bwd_ws_bytes(st, B));
+  L.tc = tc_train_supported(st);
+  o = (o + 1023) & ~(size_t)1023;
+  L.scratch = o; o += L.tc ? tc_train_bytes(st, B) : align256(bwd_ws_bytes(st, B));
   L.total = o;
   return L;
 }
@@ -699,7 +703,8 @@ voila_status voila_distill_step(const voila_mlp* teacher, const voila_mlp* stude
   concat_input_kernel<<<grid_for((long long)B * student->dims[0], 256), 256, 0, s>>>(S, A, omega, B, d_s, d_a,
                                                                                      d_x, X);
   if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
-  st = voila_generator_fwd_train(student, X, B, Y, saved, scratch, scratch_bytes, stream);
+  if (L.tc) st = tc_train_forward(student, X, B, Y, scratch, (WsHeader*)ws, s);
+  else st = voila_generator_fwd_train(student, X, B, Y, saved, scratch, scratch_bytes, stream);
   if (st != VOILA_OK) return st;
   // 3. loss (1/B) sum ||f - s_hat||^2 and dL/dY = 2 (f - s_hat) / B
   mse_kernel<<<kLossBlocks, 256, 0, s>>>(Y, s_hat, (long long)B * d_x, 2.0f / (float)B, dY, part);
@@ -714,7 +719,8 @@ voila_status voila_distill_step(const voila_mlp* teacher, const voila_mlp* stude
     dW[l] = grads + off[2 * l];
     db[l] = grads + off[2 * l + 1];
   }
-  st = voila_generator_bwd(student, X, saved, dY, B, nullptr, dW, db, scratch, scratch_bytes, stream);
+  if (L.tc) st = tc_train_backward(student, dY, B, grads, scratch, (WsHeader*)ws, s);
+  else st = voila_generator_bwd(student, X, saved, dY, B, nullptr, dW, db, scratch, scratch_bytes, stream);
   if (st != VOILA_OK) return st;
   // 5. Adam on the FP32 master weights, then the forward copy
   st = voila_adam_step(master, grads, adam_m, adam_v, np, opt->lr, opt->beta1, opt->beta2, opt->eps, opt->step,
