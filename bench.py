@@ -552,9 +552,12 @@ def run_distill(args, rank, world, local):
                     "h2d_bytes_per_step": int(sum(x.numel() * 4 for x in (hS, hA, hO))), "d2h_bytes_per_step": 8},
             "gpu_launches": None, "clocks": clk.summary()}
     n_layers = len(wl.student.W)
-    # per step: sampler 3 (pack, embeddings, kernel), concat 1, fwd L, mse 2,
-    # bwd (L x 3 + (L-1) delta), adam 1, publish 1
-    line["gpu_launches"] = args.steps * (3 + 1 + n_layers + 2 + 3 * n_layers + (n_layers - 1) + 2)
+    # per step (BF16 student, tensor cores): sampler 3 (pack, embeddings, kernel),
+    # concat 1, forward (input prep, 2 padded weights, L-1 transposed weights,
+    # L GEMMs), loss 2, backward (delta prep, bias sum of the output, L-1 delta
+    # GEMMs, L weight GEMMs, L partial sums, L-1 bias sums), adam 1, publish 1
+    L_ = n_layers
+    line["gpu_launches"] = args.steps * (3 + 1 + (1 + 2 + (L_ - 1) + L_) + 2 + (2 + (L_ - 1) + 3 * L_ + (L_ - 1)) + 2)
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import voila_oracle as O
         rows = args.distill_cpu_rows
@@ -951,7 +954,7 @@ def main():
                 [e[0].elapsed_time(e[1]) for e in ev]),
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 7 * args.steps,
+            "gpu_launches": 8 * args.steps,  # propose, resample, pack, fused-output pack, rollout, reduce, argmax, backup
             "clocks": clk.summary()}
     J8 = None
     if wl.prec == 1 and rank == 0 and not args.no_forms:
