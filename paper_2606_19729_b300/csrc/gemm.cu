@@ -4,9 +4,10 @@
 // FP32 accumulation in TMEM; one CTA computes a 128-row tile over all N <= 256
 // columns and a range of K (split-K over blockIdx.y). Warp 0 streams A and B
 // K-chunks of 64 (128-byte rows, 128B swizzle) into a 4-stage ring with TMA,
-// warp 1 issues the MMAs (M = 128, N, K = 16) from one thread, warps 2-5 read
+// warp 1 issues the MMAs (M = 128, N, K = 16) from one thread, warps 2-17 read
 // the accumulator (warp w owns TMEM lanes 32 (w mod 4) .. +31, one row per
-// thread) and run one of the epilogues:
+// thread; the four warps of a lane quadrant split the columns) and run one of
+// the epilogues:
 //   kFwdHidden  z = acc + b;  H = act(z), AD = act'(z) row-major, H^T via
 //               a shared-memory transpose (BF16);
 //   kFwdOut     Y = acc + b (FP32, the first n_real columns);
@@ -27,7 +28,8 @@
 namespace voila {
 namespace {
 
-constexpr int kGThreads = 192;
+constexpr int kGThreads = 576;  // producer warp, MMA warp, 16 epilogue warps
+constexpr int kGEpiThreads = 512;
 constexpr int kGStages = 4;
 constexpr int kGABytes = 128 * 128;  // 128 rows x 64 BF16
 constexpr int kGBBytes = 256 * 128;  // up to 256 rows x 64 BF16
@@ -77,7 +79,7 @@ __device__ __forceinline__ bool gwait(uint32_t bar, uint32_t parity, volatile in
 
 __device__ __forceinline__ void act_and_grad(float z, int act, float& h, float& d) {
   if (act == VOILA_ACT_SILU) {
-    const float sg = 1.0f / (1.0f + __expf(-z));
+    const float sg = __fdividef(1.0f, 1.0f + __expf(-z));
     h = z * sg;
     d = sg * (1.0f + z * (1.0f - sg));
   } else if (act == VOILA_ACT_TANH) {
@@ -180,16 +182,19 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_cons
   } else {
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;
+    const int slice = (warp - 2) >> 2;  // column quarter of this warp
     const int r = 32 * q + lane;
     const int m = m0 + r;
     const bool valid = m < p.M;
     const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
+    const int cps = p.N >= 64 ? p.N / 4 : 16;  // columns per slice (multiples of 16)
+    const int c_lo = slice * cps, c_hi = c_lo + cps < p.N ? c_lo + cps : p.N;
     const bool ok = gwait(ptx::smem_u32(accf), 0, abort_flag, p.hdr, 72);
     ptx::tc_fence_after();
     // staging for transposed stores: the ring is free once the MMAs are done
     __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(smem);  // [N][128]
     if (ok) {
-      for (int cb = 0; cb < p.N; cb += 16) {
+      for (int cb = c_lo; cb < c_hi; cb += 16) {
         float v[16];
         ptx::tmem_ld16(tq + cb, v);
         ptx::tmem_wait_ld();
@@ -243,10 +248,10 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_cons
     }
     if (p.mode == kGemmFwdHidden || p.mode == kGemmBwd) {
       // transposed copy: stage [N][128] -> HT[n][m0 .. m0 + 127], 16 bytes per store
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, 512;" ::: "memory");
       if (ok) {
         const int per_row = 16;  // 128 BF16 = 16 x 16 bytes
-        for (int e = threadIdx.x - 64; e < p.N * per_row; e += 128) {
+        for (int e = threadIdx.x - 64; e < p.N * per_row; e += kGEpiThreads) {
           const int n = e / per_row, j = e % per_row;
           const int mm = m0 + 8 * j;
           if (mm + 8 <= p.ldT)

@@ -23,6 +23,8 @@
 namespace voila {
 namespace {
 
+constexpr int kColsumBlocks = 148;  // row blocks of the output-bias gradient
+
 int r16(int v) { return (v + 15) / 16 * 16; }
 size_t a1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
 
@@ -30,7 +32,7 @@ struct TrainLayout {
   int L, d[VOILA_MAX_LAYERS + 1], K0p, NLp;
   long long M, ldT;
   size_t xb, xt, h[VOILA_MAX_LAYERS], ht[VOILA_MAX_LAYERS], ad[VOILA_MAX_LAYERS], dl, dlt;
-  size_t dd[VOILA_MAX_LAYERS], ddt[VOILA_MAX_LAYERS], w1p, wlp, wt[VOILA_MAX_LAYERS + 1], part, total;
+  size_t dd[VOILA_MAX_LAYERS], ddt[VOILA_MAX_LAYERS], w1p, wlp, wt[VOILA_MAX_LAYERS + 1], part, colpart, total;
   int splits_max;
 };
 
@@ -64,6 +66,7 @@ TrainLayout train_layout(const voila_mlp* m, long long M) {
   }
   T.splits_max = 148;
   T.part = o; o += a1k((size_t)T.splits_max * 256 * 256 * sizeof(float));
+  T.colpart = o; o += a1k((size_t)kColsumBlocks * 256 * sizeof(double));
   T.total = o;
   return T;
 }
@@ -123,25 +126,46 @@ __global__ void reduce_partials_kernel(const float* __restrict__ P, int S, int R
   }
 }
 
-// out[n] = sum_m DT[n][m], m < M (one CTA per n, fixed order).
+// out[n] = sum_m DT[n][m], m < M (one CTA per n, eight values per 16-byte
+// load and the tail of M element by element, in a fixed order).
 __global__ void __launch_bounds__(256) rowsum_bf16_kernel(const __nv_bfloat16* __restrict__ DT, long long M,
                                                           long long ldT, float* __restrict__ out) {
   __shared__ double red[33];
   const __nv_bfloat16* row = DT + (size_t)blockIdx.x * ldT;
-  double a = 0.0;
-  for (long long m = threadIdx.x; m < M; m += blockDim.x) a += (double)__bfloat162float(row[m]);
-  a = block_sum(a, red);
-  if (threadIdx.x == 0) out[blockIdx.x] = (float)a;
+  const long long groups = M / 8;
+  float a = 0.0f;
+  for (long long gi = threadIdx.x; gi < groups; gi += blockDim.x) {
+    const uint4 w = *reinterpret_cast<const uint4*>(row + 8 * gi);
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a += __uint_as_float(ws[j] << 16) + __uint_as_float(ws[j] & 0xffff0000u);
+  }
+  for (long long m = 8 * groups + threadIdx.x; m < M; m += blockDim.x) a += __bfloat162float(row[m]);
+  const double t = block_sum((double)a, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = (float)t;
 }
 
-// out[c] = sum_m dY[m][c] (one CTA per column, fixed order).
-__global__ void __launch_bounds__(256) colsum_kernel(const float* __restrict__ dY, long long M, int dL,
-                                                     float* __restrict__ out) {
+// part[b][c] = sum over the rows of block b of dY[m][c] (contiguous row ranges,
+// fixed order), then out[c] = sum_b part[b][c] in block order.
+__global__ void __launch_bounds__(256) colsum_partial_kernel(const float* __restrict__ dY, long long M, int dL,
+                                                             double* __restrict__ part) {
   __shared__ double red[33];
+  const long long per = (M + gridDim.x - 1) / gridDim.x;
+  const long long m0 = blockIdx.x * per, m1 = m0 + per < M ? m0 + per : M;
+  for (int c = 0; c < dL; ++c) {
+    double a = 0.0;
+    for (long long m = m0 + threadIdx.x; m < m1; m += blockDim.x) a += (double)dY[m * dL + c];
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * dL + c] = a;
+  }
+}
+
+__global__ void colsum_final_kernel(const double* __restrict__ part, int nb, int dL, float* __restrict__ out) {
+  const int c = threadIdx.x;
+  if (c >= dL) return;
   double a = 0.0;
-  for (long long m = threadIdx.x; m < M; m += blockDim.x) a += (double)dY[m * dL + blockIdx.x];
-  a = block_sum(a, red);
-  if (threadIdx.x == 0) out[blockIdx.x] = (float)a;
+  for (int b = 0; b < nb; ++b) a += part[(size_t)b * dL + c];
+  out[c] = (float)a;
 }
 
 int grid_of(long long n) {
@@ -238,7 +262,8 @@ voila_status tc_train_backward(const voila_mlp* m, const float* dY, long long M,
   }
   prep_dy_kernel<<<grid_of(M * T.NLp), 256, 0, s>>>(dY, M, T.d[L], T.NLp, T.ldT, at<bf>(scratch, T.dl),
                                                     at<bf>(scratch, T.dlt));
-  colsum_kernel<<<T.d[L], 256, 0, s>>>(dY, M, T.d[L], grads + goff[L][1]);
+  colsum_partial_kernel<<<kColsumBlocks, 256, 0, s>>>(dY, M, T.d[L], at<double>(scratch, T.colpart));
+  colsum_final_kernel<<<1, 256, 0, s>>>(at<double>(scratch, T.colpart), kColsumBlocks, T.d[L], grads + goff[L][1]);
   if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   // deltas of the hidden layers
   for (int l = L; l >= 2; --l) {
