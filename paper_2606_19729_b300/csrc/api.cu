@@ -6,6 +6,7 @@
 
 #include "../../include/voila.h"
 #include "kernels.h"
+#include "simt_mlp.cuh"
 #include "tc.h"
 
 using namespace voila;
@@ -35,7 +36,6 @@ int max_width(const voila_mlp* m) {
   return w;
 }
 
-int simt_ld(int maxw) { return (maxw % 2 == 0) ? maxw + 1 : maxw; }
 
 MlpDev to_dev(const voila_mlp* m) {
   MlpDev d;

@@ -221,7 +221,7 @@ voila_status voila_infonce_forward(const voila_mlp* ell, const float* S, const f
       m.b[l] = ell->b[l];
     }
     const int wmax = widest_of(ell);
-    const int ld = (wmax % 2 == 0) ? wmax + 1 : wmax;
+    const int ld = simt_ld(wmax);
     const size_t smem = (size_t)2 * kSimtRows * ld * sizeof(float);
     auto k = ell->prec == VOILA_BF16 ? pairs_simt_kernel<__nv_bfloat16> : pairs_simt_kernel<float>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)

@@ -7,9 +7,36 @@
 
 namespace voila {
 
+// Row stride of the [rows][ld] activation buffers for layers up to maxw wide:
+// a multiple of 4 (16-byte rows for float4 loads) that is 4 mod 32, so the
+// rows that different threads of a warp read start in different banks.
+inline int simt_ld(int maxw) { return (maxw + 31) / 32 * 32 + 4; }
+
+// Four consecutive weights W[k .. k + 3] (16 or 8 bytes, aligned when K % 4 == 0).
+template <typename TW>
+__device__ __forceinline__ void ldw4(const TW* p, float* w);
+template <>
+__device__ __forceinline__ void ldw4<float>(const float* p, float* w) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  w[0] = v.x;
+  w[1] = v.y;
+  w[2] = v.z;
+  w[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void ldw4<__nv_bfloat16>(const __nv_bfloat16* p, float* w) {
+  const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+  w[0] = __uint_as_float(v.x << 16);
+  w[1] = __uint_as_float(v.x & 0xffff0000u);
+  w[2] = __uint_as_float(v.y << 16);
+  w[3] = __uint_as_float(v.y & 0xffff0000u);
+}
+
 // One layer on a tile held in shared memory. Threads are split into
 // `ng` row groups x `cpp` columns; a thread owns column j (stride cpp) and
-// rows rg, rg+ng, ... so narrow layers still keep most threads busy.
+// rows rg, rg+ng, ... so narrow layers still keep most threads busy. When K
+// is a multiple of 4, four K values are read per 16-byte shared load and
+// four weights per global load (four FMAs per row and load).
 template <typename TW>
 __device__ void simt_layer(const float* __restrict__ in, float* __restrict__ out, int ld,
                            int nrows, int K, int Nout, const TW* __restrict__ W,
@@ -28,7 +55,23 @@ __device__ void simt_layer(const float* __restrict__ in, float* __restrict__ out
 #pragma unroll
     for (int i = 0; i < kSimtRows; ++i) acc[i] = bj;
     const TW* wj = W + (size_t)j * K;
-    for (int k = 0; k < K; ++k) {
+    int k = 0;
+    if ((K & 3) == 0) {
+      for (; k < K; k += 4) {
+        float w[4];
+        ldw4<TW>(wj + k, w);
+#pragma unroll
+        for (int i = 0; i < kSimtRows; ++i)
+          if (i < nr) {
+            const float4 x = *reinterpret_cast<const float4*>(in + (rg + i * ng) * ld + k);
+            acc[i] = fmaf(x.x, w[0], acc[i]);
+            acc[i] = fmaf(x.y, w[1], acc[i]);
+            acc[i] = fmaf(x.z, w[2], acc[i]);
+            acc[i] = fmaf(x.w, w[3], acc[i]);
+          }
+      }
+    }
+    for (; k < K; ++k) {
       const float wv = ldw<TW>(wj + k);
 #pragma unroll
       for (int i = 0; i < kSimtRows; ++i)

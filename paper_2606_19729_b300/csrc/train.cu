@@ -629,7 +629,7 @@ voila_status voila_ddim_sample(const voila_mlp* teacher, const float* S, const f
   for (int i = 0; i < emb_dim / 2; ++i) a.freq[i] = (float)pow(10000.0, -(double)i / (emb_dim / 2));
   a.Y = Y;
   const int wmax = widest(teacher);
-  a.ld = (wmax % 2 == 0) ? wmax + 1 : wmax;
+  a.ld = simt_ld(wmax);
   const size_t smem = (size_t)2 * kSimtRows * a.ld * sizeof(float) + kSimtRows * 16 * sizeof(float);
   auto k = teacher->prec == VOILA_BF16 ? ddim_kernel<__nv_bfloat16> : ddim_kernel<float>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)

@@ -539,7 +539,7 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
     int wmax = 0;
     for (int l = 0; l <= g_Z->n_layers; ++l) wmax = g_Z->dims[l] > wmax ? g_Z->dims[l] : wmax;
     if (wmax > VOILA_MAX_WIDTH) return VOILA_ERR_SHAPE;
-    const int ld = (wmax % 2 == 0) ? wmax + 1 : wmax;
+    const int ld = simt_ld(wmax);
     const size_t smem = (size_t)2 * kSimtRows * ld * sizeof(float);
     auto k = g_Z->prec == VOILA_BF16 ? pw_observe_kernel<__nv_bfloat16> : pw_observe_kernel<float>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -563,7 +563,7 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
       int wmax = 0;
       for (int l = 0; l <= ell->mlp->n_layers; ++l) wmax = ell->mlp->dims[l] > wmax ? ell->mlp->dims[l] : wmax;
       if (wmax > VOILA_MAX_WIDTH) return VOILA_ERR_SHAPE;
-      ld = (wmax % 2 == 0) ? wmax + 1 : wmax;
+      ld = simt_ld(wmax);
       smem = (size_t)2 * kSimtRows * ld * sizeof(float);
       bf16 = ell->mlp->prec == VOILA_BF16;
     }
