@@ -700,7 +700,7 @@ def run_pw(args, rank, world, local):
     s_next = torch.from_numpy(wl.s_next).float().cuda()
     branch = torch.empty(M, dtype=torch.int32, device="cuda")
     s_out = torch.empty_like(s_next)
-    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(lik, M))
+    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(tree, lik, M))
 
     def call():
         V.voila_progressive_widening(tree, node, s_next, g_Z, lik, wl.d_omega, wl.k_o, wl.alpha_o, wl.lam, wl.seed,
@@ -751,8 +751,9 @@ def run_pw(args, rank, world, local):
     while n_pad < M:
         n_pad *= 2
     sort_launches = 1 + sum(int(math.log2(k)) - 10 for k in (2 ** e for e in range(12, int(math.log2(n_pad)) + 1)))
-    # keys, sort, widen, join, observe, likelihood (pack + pair kernel), keys, sort, resample
-    line["gpu_launches"] = reps * (8 + 2 * sort_launches)
+    # keys, sort, group bounds, widen, assign, observe, likelihood (pack, fused-output
+    # pack, pair kernel), keys, sort, resample
+    line["gpu_launches"] = reps * (10 + 2 * sort_launches)
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import voila_oracle as O
         sel = np.ones(M, bool)

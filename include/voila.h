@@ -527,8 +527,10 @@ typedef struct {
   float* obs;
 } voila_pw_tree;
 
-/* Workspace of voila_progressive_widening for M simulations and likelihood ell, in bytes. */
-voila_status voila_progressive_widening_workspace_size(const voila_likelihood* ell, int32_t M,
+/* Workspace of voila_progressive_widening for the tree, likelihood ell and M
+ * simulations, in bytes. */
+voila_status voila_progressive_widening_workspace_size(const voila_pw_tree* tree,
+                                                       const voila_likelihood* ell, int32_t M,
                                                        size_t* bytes);
 
 /*

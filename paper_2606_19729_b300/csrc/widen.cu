@@ -131,7 +131,11 @@ struct PwArgs {
   double* cw;
   int32_t* list;
   int32_t* count;
-  int32_t* cbefore;
+  int32_t* gstart;  // [n_nodes] first sorted position of the node's group, -1 if absent
+  int32_t* gend;    // [n_nodes]
+  int32_t* c0;      // [n_nodes] branch count before the batch
+  int32_t* nwid;    // [n_nodes] widenings in the batch
+  int32_t* wpos;    // [n_nodes][C_max] group ranks of the widening simulations
   WsHeader* hdr;
 };
 
@@ -151,59 +155,69 @@ __device__ int pw_next_widen(long long n0, int C, int r_from, int g, const PwArg
   return n <= hi ? (int)(n - n0 - 1) : g;
 }
 
-// Phase 2: one thread per node group, simulations in batch order: records the
-// branch count each simulation sees (cbefore) and which ones widen, jumping
-// from one widening to the next. The widened simulations are appended to
-// `list` (slots reserved atomically; each entry fills its own branch, so the
-// order does not matter).
-__global__ void pw_widen_kernel(const unsigned long long* __restrict__ keys, PwArgs p) {
+// Phase 2a: first and one-past-last sorted position of every node's group.
+__global__ void pw_bounds_kernel(const unsigned long long* __restrict__ keys, PwArgs p) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= p.M) return;
   const unsigned a = (unsigned)(keys[q] >> 32);
   if (a == 0xffffffffu) return;
-  if (q > 0 && (unsigned)(keys[q - 1] >> 32) == a) return;  // not the first of its group
-  int g = 1;
-  while (q + g < p.M && (unsigned)(keys[q + g] >> 32) == a) ++g;
+  if (q == 0 || (unsigned)(keys[q - 1] >> 32) != a) p.gstart[a] = q;
+  if (q == p.M - 1 || (unsigned)(keys[q + 1] >> 32) != a) p.gend[a] = q + 1;
+}
+
+// Phase 2b: one thread per visited node finds the ranks of the simulations
+// that widen (jumping from one widening to the next), updates N and C, and
+// lists the widened simulations for the observation sampler (slots reserved
+// atomically; each entry fills its own branch, so their order does not matter).
+__global__ void pw_widen_kernel(const unsigned long long* __restrict__ keys, PwArgs p) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= p.n_nodes) return;
+  const int q = p.gstart[a];
+  if (q < 0) return;
+  const int g = p.gend[a] - q;
   const long long n0 = p.N[a];
-  int C = p.C[a];
-  int next = pw_next_widen(n0, C, 0, g, p);
-  int nw = 0;
-  for (int r = 0; r < g; ++r) {
-    const unsigned m = (unsigned)(keys[q + r] & 0xffffffffu);
-    p.cbefore[m] = C;
-    if (r == next) {
-      p.branch[m] = C;
-      p.widened[m] = 1;
-      ++C;
-      ++nw;
-      next = pw_next_widen(n0, C, r + 1, g, p);
-    } else {
-      p.widened[m] = 0;
-    }
+  const int C0 = p.C[a];
+  int C = C0, nw = 0;
+  int* wpos = p.wpos + (size_t)a * p.C_max;
+  for (int r = pw_next_widen(n0, C, 0, g, p); r < g; r = pw_next_widen(n0, C, r + 1, g, p)) {
+    wpos[nw++] = r;
+    ++C;
   }
+  p.c0[a] = C0;
+  p.nwid[a] = nw;
   p.N[a] = n0 + g;
   p.C[a] = C;
   if (nw) {
-    int slot = atomicAdd(p.count, nw);
-    for (int r = 0; r < g; ++r) {
-      const unsigned m = (unsigned)(keys[q + r] & 0xffffffffu);
-      if (p.widened[m]) p.list[slot++] = (int32_t)m;
-    }
+    const int slot = atomicAdd(p.count, nw);
+    for (int i = 0; i < nw; ++i) p.list[slot + i] = (int32_t)(keys[q + wpos[i]] & 0xffffffffu);
   }
 }
 
-// Phase 2b: a simulation that did not widen joins branch floor(u C) of the C
-// branches it saw, u the 24-bit uniform of Philox counter (m, step, 0, stream 6)
-// (u C is exact in FP64: a 24-bit fraction times an integer).
-__global__ void pw_join_kernel(const int32_t* __restrict__ node, PwArgs p) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= p.M) return;
-  const int a = node[m];
-  if (a < 0 || a >= p.n_nodes || p.widened[m]) return;
-  const int C = p.cbefore[m];
-  const uint4 x = philox(make_uint4((uint32_t)m, p.step, 0u, ctr_word3(6u, p.planner, 0u)), p.key0, p.key1);
-  const int b = (int)floor((double)uniform24(x.x) * (double)C);
-  p.branch[m] = b < C - 1 ? b : C - 1;
+// Phase 2c: one thread per simulation. Its rank r in the node group gives the
+// branch count it saw (C0 + the widenings ranked before it); a widening
+// simulation takes the new branch, the others join branch floor(u C), u the
+// 24-bit uniform of Philox counter (m, step, 0, stream 6) (u C is exact in FP64:
+// a 24-bit fraction times an integer).
+__global__ void pw_assign_kernel(const unsigned long long* __restrict__ keys, PwArgs p) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= p.M) return;
+  const unsigned a = (unsigned)(keys[q] >> 32);
+  if (a == 0xffffffffu) return;
+  const unsigned m = (unsigned)(keys[q] & 0xffffffffu);
+  const int r = q - p.gstart[a], nw = p.nwid[a];
+  const int* wpos = p.wpos + (size_t)a * p.C_max;
+  int cnt = 0;
+  while (cnt < nw && wpos[cnt] < r) ++cnt;
+  const int C = p.c0[a] + cnt;
+  if (cnt < nw && wpos[cnt] == r) {
+    p.branch[m] = C;
+    p.widened[m] = 1;
+  } else {
+    const uint4 x = philox(make_uint4(m, p.step, 0u, ctr_word3(6u, p.planner, 0u)), p.key0, p.key1);
+    const int b = (int)floor((double)uniform24(x.x) * (double)C);
+    p.branch[m] = b < C - 1 ? b : C - 1;
+    p.widened[m] = 0;
+  }
 }
 
 MlpDev mlp_dev(const voila_mlp* M) {
@@ -407,16 +421,17 @@ int pow2_at_least(int m) {
 
 // Workspace: header | tensor-core scratch (packed likelihood) | keys by node
 // [n_pad] | keys by branch [n_pad] | cw [M] f64 | list [M] i32 | count |
-// widened [M] u8 | ell [M] f32 | w [M] f64 | cbefore [M] i32
+// widened [M] u8 | ell [M] f32 | w [M] f64 | per node: gstart, gend, c0, nwid
+// [n_nodes] i32 and wpos [n_nodes][C_max] i32
 struct PwLayout {
-  size_t tc, keys1, keys2, cw, list, count, widened, ell, w, cbefore, total;
+  size_t tc, keys1, keys2, cw, list, count, widened, ell, w, gstart, gend, c0, nwid, wpos, total;
 };
 
 bool pw_tc_likelihood(const voila_likelihood* ell, int d_s, int d_a, int d_o) {
   return ell && ell->kind == VOILA_LIK_MLP && ell->mlp && tc_pairs_supported(ell->mlp, d_s, d_a, d_o);
 }
 
-PwLayout pw_layout(const voila_likelihood* ell, int M) {
+PwLayout pw_layout(const voila_pw_tree* tree, const voila_likelihood* ell, int M) {
   PwLayout L;
   const size_t n_pad = (size_t)pow2_at_least(M < 2 ? 2 : M);
   size_t o = 1024;
@@ -430,7 +445,12 @@ PwLayout pw_layout(const voila_likelihood* ell, int M) {
   L.widened = o; o += a256((size_t)M);
   L.ell = o; o += a256((size_t)M * 4);
   L.w = o; o += a256((size_t)M * 8);
-  L.cbefore = o; o += a256((size_t)M * 4);
+  const size_t nn = (size_t)tree->n_nodes;
+  L.gstart = o; o += a256(nn * 4);
+  L.gend = o; o += a256(nn * 4);
+  L.c0 = o; o += a256(nn * 4);
+  L.nwid = o; o += a256(nn * 4);
+  L.wpos = o; o += a256(nn * (size_t)tree->C_max * 4);
   L.total = o;
   return L;
 }
@@ -448,9 +468,12 @@ using namespace voila;
 
 extern "C" {
 
-voila_status voila_progressive_widening_workspace_size(const voila_likelihood* ell, int32_t M, size_t* bytes) {
-  if (!ell || M < 0 || M > (1 << 24) || !bytes) return VOILA_ERR_ARG;
-  *bytes = pw_layout(ell, M).total;
+voila_status voila_progressive_widening_workspace_size(const voila_pw_tree* tree, const voila_likelihood* ell,
+                                                       int32_t M, size_t* bytes) {
+  if (!tree || !ell || M < 0 || M > (1 << 24) || !bytes || tree->n_nodes < 1 || tree->n_nodes >= (1 << 24) ||
+      tree->C_max < 1 || tree->C_max > 65535)
+    return VOILA_ERR_ARG;
+  *bytes = pw_layout(tree, ell, M).total;
   return VOILA_OK;
 }
 
@@ -479,7 +502,7 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   } else {
     return VOILA_ERR_ARG;
   }
-  const PwLayout L = pw_layout(ell, M);
+  const PwLayout L = pw_layout(tree, ell, M);
   if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 1023)) return VOILA_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   char* ws = (char*)workspace;
@@ -519,7 +542,11 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   p.cw = (double*)(ws + L.cw);
   p.list = (int32_t*)(ws + L.list);
   p.count = (int32_t*)(ws + L.count);
-  p.cbefore = (int32_t*)(ws + L.cbefore);
+  p.gstart = (int32_t*)(ws + L.gstart);
+  p.gend = (int32_t*)(ws + L.gend);
+  p.c0 = (int32_t*)(ws + L.c0);
+  p.nwid = (int32_t*)(ws + L.nwid);
+  p.wpos = (int32_t*)(ws + L.wpos);
   p.hdr = (WsHeader*)ws;
   unsigned long long* keys1 = (unsigned long long*)(ws + L.keys1);
   unsigned long long* keys2 = (unsigned long long*)(ws + L.keys2);
@@ -530,8 +557,11 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   if (cudaGetLastError() != cudaSuccess || bitonic_sort(keys1, n_pad, s) != cudaSuccess) return VOILA_ERR_CUDA;
   // 2. widening decisions
   if (cudaMemsetAsync(p.count, 0, sizeof(int32_t), s) != cudaSuccess) return VOILA_ERR_CUDA;
-  pw_widen_kernel<<<(M + 255) / 256, 256, 0, s>>>(keys1, p);
-  pw_join_kernel<<<(M + 255) / 256, 256, 0, s>>>(node, p);
+  if (cudaMemsetAsync(p.gstart, 0xff, (size_t)tree->n_nodes * sizeof(int32_t), s) != cudaSuccess)
+    return VOILA_ERR_CUDA;
+  pw_bounds_kernel<<<(M + 255) / 256, 256, 0, s>>>(keys1, p);
+  pw_widen_kernel<<<(tree->n_nodes + 127) / 128, 128, 0, s>>>(keys1, p);
+  pw_assign_kernel<<<(M + 255) / 256, 256, 0, s>>>(keys1, p);
   if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   // 3. observations of the new branches
   {

@@ -47,7 +47,7 @@ def _run(V, wl, node, s_next, tree, lik_dev, step, planner=0):
     w = torch.empty(M, dtype=torch.float64, device="cuda")
     idx = torch.empty(M, dtype=torch.int32, device="cuda")
     s_out = torch.empty(M, wl.d_s, device="cuda")
-    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(lik_dev, M))
+    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(tree, lik_dev, M))
     V.voila_progressive_widening(tree, cuda(node, torch.int32), cuda(s_next), g_Z, lik_dev, wl.d_omega, wl.k_o,
                                  wl.alpha_o, wl.lam, wl.seed, step, planner, branch, s_out, ws, widened, ell, w, idx)
     torch.cuda.synchronize()
