@@ -167,6 +167,21 @@ __device__ __forceinline__ float act_value(float u, int act) {
   return u;
 }
 
+// SiLU (folded form above) of the pair (x0, x1) = z + b, or = z * sc + b for
+// an E4M3 layer's channel scale, in packed FP32x2 arithmetic; returns the
+// activations as a packed pair.
+__device__ __forceinline__ uint64_t silu2(uint64_t x) {
+  float u0, u1;
+  ptx::f2_unpack(x, u0, u1);
+  return ptx::f2_fma(x, ptx::f2_pack(ptx::tanh_approx(u0), ptx::tanh_approx(u1)), x);
+}
+
+__device__ __forceinline__ uint32_t silu2_bf16(uint64_t x) {
+  float y0, y1;
+  ptx::f2_unpack(silu2(x), y0, y1);
+  return ptx::pack_bf16x2(y0, y1);
+}
+
 __device__ __forceinline__ uint32_t act_pair(float u0, float u1, int act) {
   if (act == VOILA_ACT_SILU)
     return ptx::pack_bf16x2(fmaf(u0, ptx::tanh_approx(u0), u0), fmaf(u1, ptx::tanh_approx(u1), u1));
@@ -187,39 +202,61 @@ __device__ __forceinline__ void epi_cols32(float* u, const float* bl, const floa
       const float4 b0 = *reinterpret_cast<const float4*>(bl + 32 * c + 8 * j);
       const float4 b1 = *reinterpret_cast<const float4*>(bl + 32 * c + 8 * j + 4);
       uint4 o;
-      o.x = act_pair(u[8 * j + 0] + b0.x, u[8 * j + 1] + b0.y, act);
-      o.y = act_pair(u[8 * j + 2] + b0.z, u[8 * j + 3] + b0.w, act);
-      o.z = act_pair(u[8 * j + 4] + b1.x, u[8 * j + 5] + b1.y, act);
-      o.w = act_pair(u[8 * j + 6] + b1.z, u[8 * j + 7] + b1.w, act);
+      if (act == VOILA_ACT_SILU) {
+        using ptx::f2_add;
+        using ptx::f2_pack;
+        o.x = silu2_bf16(f2_add(f2_pack(u[8 * j + 0], u[8 * j + 1]), f2_pack(b0.x, b0.y)));
+        o.y = silu2_bf16(f2_add(f2_pack(u[8 * j + 2], u[8 * j + 3]), f2_pack(b0.z, b0.w)));
+        o.z = silu2_bf16(f2_add(f2_pack(u[8 * j + 4], u[8 * j + 5]), f2_pack(b1.x, b1.y)));
+        o.w = silu2_bf16(f2_add(f2_pack(u[8 * j + 6], u[8 * j + 7]), f2_pack(b1.z, b1.w)));
+      } else {
+        o.x = act_pair(u[8 * j + 0] + b0.x, u[8 * j + 1] + b0.y, act);
+        o.y = act_pair(u[8 * j + 2] + b0.z, u[8 * j + 3] + b0.w, act);
+        o.z = act_pair(u[8 * j + 4] + b1.x, u[8 * j + 5] + b1.y, act);
+        o.w = act_pair(u[8 * j + 6] + b1.z, u[8 * j + 7] + b1.w, act);
+      }
       *reinterpret_cast<uint4*>(slab + r * 128 + ((((c & 1) * 4 + j) ^ (r & 7)) << 4)) = o;
     }
     return;
   }
+  using ptx::f2_pack;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {  // transformed in place (register pressure)
     const float4 b = *reinterpret_cast<const float4*>(bl + 32 * c + 4 * j);
+    uint64_t x01, x23;
     if (SCALE) {
       const float4 sc = *reinterpret_cast<const float4*>(sl + 32 * c + 4 * j);
-      u[4 * j + 0] = fmaf(u[4 * j + 0], sc.x, b.x);
-      u[4 * j + 1] = fmaf(u[4 * j + 1], sc.y, b.y);
-      u[4 * j + 2] = fmaf(u[4 * j + 2], sc.z, b.z);
-      u[4 * j + 3] = fmaf(u[4 * j + 3], sc.w, b.w);
+      x01 = ptx::f2_fma(f2_pack(u[4 * j + 0], u[4 * j + 1]), f2_pack(sc.x, sc.y), f2_pack(b.x, b.y));
+      x23 = ptx::f2_fma(f2_pack(u[4 * j + 2], u[4 * j + 3]), f2_pack(sc.z, sc.w), f2_pack(b.z, b.w));
     } else {
-      u[4 * j + 0] += b.x;
-      u[4 * j + 1] += b.y;
-      u[4 * j + 2] += b.z;
-      u[4 * j + 3] += b.w;
+      x01 = ptx::f2_add(f2_pack(u[4 * j + 0], u[4 * j + 1]), f2_pack(b.x, b.y));
+      x23 = ptx::f2_add(f2_pack(u[4 * j + 2], u[4 * j + 3]), f2_pack(b.z, b.w));
+    }
+    if (act == VOILA_ACT_SILU) {
+      x01 = silu2(x01);
+      x23 = silu2(x23);
+      ptx::f2_unpack(x01, u[4 * j + 0], u[4 * j + 1]);
+      ptx::f2_unpack(x23, u[4 * j + 2], u[4 * j + 3]);
+    } else {
+      float y0, y1, y2, y3;
+      ptx::f2_unpack(x01, y0, y1);
+      ptx::f2_unpack(x23, y2, y3);
+      u[4 * j + 0] = act_value(y0, act);
+      u[4 * j + 1] = act_value(y1, act);
+      u[4 * j + 2] = act_value(y2, act);
+      u[4 * j + 3] = act_value(y3, act);
     }
   }
+  // u now holds the activations
   if (!OUT_FP8) {
     uint8_t* slab = A + (c >> 1) * (128 * 128);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       uint4 o;
-      o.x = act_pair(u[8 * j + 0], u[8 * j + 1], act);
-      o.y = act_pair(u[8 * j + 2], u[8 * j + 3], act);
-      o.z = act_pair(u[8 * j + 4], u[8 * j + 5], act);
-      o.w = act_pair(u[8 * j + 6], u[8 * j + 7], act);
+      o.x = ptx::pack_bf16x2(u[8 * j + 0], u[8 * j + 1]);
+      o.y = ptx::pack_bf16x2(u[8 * j + 2], u[8 * j + 3]);
+      o.z = ptx::pack_bf16x2(u[8 * j + 4], u[8 * j + 5]);
+      o.w = ptx::pack_bf16x2(u[8 * j + 6], u[8 * j + 7]);
       *reinterpret_cast<uint4*>(slab + r * 128 + ((((c & 1) * 4 + j) ^ (r & 7)) << 4)) = o;
     }
   } else {
@@ -228,10 +265,10 @@ __device__ __forceinline__ void epi_cols32(float* u, const float* bl, const floa
     for (int j = 0; j < 2; ++j) {
       const float* y = u + 16 * j;
       uint4 o;
-      o.x = ptx::pack_e4m3x4(act_value(y[0], act), act_value(y[1], act), act_value(y[2], act), act_value(y[3], act));
-      o.y = ptx::pack_e4m3x4(act_value(y[4], act), act_value(y[5], act), act_value(y[6], act), act_value(y[7], act));
-      o.z = ptx::pack_e4m3x4(act_value(y[8], act), act_value(y[9], act), act_value(y[10], act), act_value(y[11], act));
-      o.w = ptx::pack_e4m3x4(act_value(y[12], act), act_value(y[13], act), act_value(y[14], act), act_value(y[15], act));
+      o.x = ptx::pack_e4m3x4(y[0], y[1], y[2], y[3]);
+      o.y = ptx::pack_e4m3x4(y[4], y[5], y[6], y[7]);
+      o.z = ptx::pack_e4m3x4(y[8], y[9], y[10], y[11]);
+      o.w = ptx::pack_e4m3x4(y[12], y[13], y[14], y[15]);
       *reinterpret_cast<uint4*>(slab + r * 128 + ((((c & 3) * 2 + j) ^ (r & 7)) << 4)) = o;
     }
   }
@@ -282,27 +319,38 @@ __device__ __forceinline__ void epi_cols16(float* u, const float* bl, const floa
 
 // The columns [W c, W c + W) of row r of a layer followed by a fused scalar
 // output: (channel scale) + bias + activation, dotted in FP32 with the output
-// weights wf (the activations are not rounded to BF16: a BF16 round trip per
-// value costs a conversion on the MUFU pipe, which bounds this epilogue).
+// weights wf (the activations are not rounded to BF16). The dot product runs
+// as two interleaved partial sums (even and odd columns) in one FP32x2
+// register; the caller adds the two halves.
 template <bool SCALE, int W>
-__device__ __forceinline__ float fuse_cols(const float* u, const float* bl, const float* sl, int c, int act,
-                                           const float* wf, float part) {
+__device__ __forceinline__ uint64_t fuse_cols(const float* u, const float* bl, const float* sl, int c, int act,
+                                              const float* wf, uint64_t part) {
+  using ptx::f2_pack;
 #pragma unroll
   for (int j = 0; j < W; j += 4) {
     const float4 b = *reinterpret_cast<const float4*>(bl + W * c + j);
     const float4 w = *reinterpret_cast<const float4*>(wf + W * c + j);
-    float x0 = u[j] + b.x, x1 = u[j + 1] + b.y, x2 = u[j + 2] + b.z, x3 = u[j + 3] + b.w;
+    uint64_t x01, x23;
     if (SCALE) {
       const float4 sc = *reinterpret_cast<const float4*>(sl + W * c + j);
-      x0 = fmaf(u[j], sc.x, b.x);
-      x1 = fmaf(u[j + 1], sc.y, b.y);
-      x2 = fmaf(u[j + 2], sc.z, b.z);
-      x3 = fmaf(u[j + 3], sc.w, b.w);
+      x01 = ptx::f2_fma(f2_pack(u[j], u[j + 1]), f2_pack(sc.x, sc.y), f2_pack(b.x, b.y));
+      x23 = ptx::f2_fma(f2_pack(u[j + 2], u[j + 3]), f2_pack(sc.z, sc.w), f2_pack(b.z, b.w));
+    } else {
+      x01 = ptx::f2_add(f2_pack(u[j], u[j + 1]), f2_pack(b.x, b.y));
+      x23 = ptx::f2_add(f2_pack(u[j + 2], u[j + 3]), f2_pack(b.z, b.w));
     }
-    part = fmaf(act_value(x0, act), w.x, part);
-    part = fmaf(act_value(x1, act), w.y, part);
-    part = fmaf(act_value(x2, act), w.z, part);
-    part = fmaf(act_value(x3, act), w.w, part);
+    if (act == VOILA_ACT_SILU) {
+      x01 = silu2(x01);
+      x23 = silu2(x23);
+    } else {
+      float y0, y1, y2, y3;
+      ptx::f2_unpack(x01, y0, y1);
+      ptx::f2_unpack(x23, y2, y3);
+      x01 = f2_pack(act_value(y0, act), act_value(y1, act));
+      x23 = f2_pack(act_value(y2, act), act_value(y3, act));
+    }
+    part = ptx::f2_fma(x01, f2_pack(w.x, w.y), part);
+    part = ptx::f2_fma(x23, f2_pack(w.z, w.w), part);
   }
   return part;
 }
@@ -362,6 +410,83 @@ __device__ __forceinline__ void write_rew_input(uint8_t* A, int r, const float* 
 #pragma unroll
   for (int i = 0; i < DA; ++i) x[DS + i] = a[i];
   store_row<KP>(A, r, x);
+}
+
+// The two-tile epilogue keeps a row's generator inputs as packed BF16 words
+// (every one of them is rounded to BF16 where it enters an MMA): the state
+// s_t as DS / 2 words and the tail [a_t; omega_T(n, k, t)] as
+// (DA + DW + 1) / 2 words (an odd last word has a zero high half).
+template <int KP>
+__device__ __forceinline__ void store_words(uint8_t* A, int r, const uint32_t* x) {
+#pragma unroll
+  for (int j = 0; j < KP / 8; ++j)
+    *reinterpret_cast<uint4*>(a_chunk(A, r, j)) = make_uint4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+}
+
+template <int DS>
+__device__ __forceinline__ void pack_state(uint32_t* s_pk, const float* s) {
+#pragma unroll
+  for (int i = 0; i < DS / 2; ++i) s_pk[i] = ptx::pack_bf16x2(s[2 * i], s[2 * i + 1]);
+}
+
+// [a_t; omega_T(n, k, t)] of one row, packed: a_t = act[0 .. DA), the noise
+// from stream VOILA_STREAM_ROLLOUT_OMEGA at counter (n, k, t).
+template <int DA, int DW>
+__device__ __forceinline__ void draw_tail(uint32_t* tail, const float* act, uint32_t k0, uint32_t k1, uint32_t n,
+                                          uint32_t k, uint32_t t, uint32_t planner) {
+  constexpr int TE = 2 * ((DA + DW + 1) / 2);
+  float e[TE];
+#pragma unroll
+  for (int i = 0; i < TE; ++i) e[i] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < DA; ++i) e[i] = __ldg(act + i);
+#pragma unroll
+  for (int b = 0; b < (DW + 3) / 4; ++b) {
+    const float4 z = normal4(k0, k1, n, k, t, VOILA_STREAM_ROLLOUT_OMEGA, planner, (uint32_t)b);
+    if (4 * b + 0 < DW) e[DA + 4 * b + 0] = z.x;
+    if (4 * b + 1 < DW) e[DA + 4 * b + 1] = z.y;
+    if (4 * b + 2 < DW) e[DA + 4 * b + 2] = z.z;
+    if (4 * b + 3 < DW) e[DA + 4 * b + 3] = z.w;
+  }
+#pragma unroll
+  for (int j = 0; j < TE / 2; ++j) tail[j] = ptx::pack_bf16x2(e[2 * j], e[2 * j + 1]);
+}
+
+// The a_t words of a tail (the odd last one with its high half cleared).
+template <int DA>
+__device__ __forceinline__ void tail_actions(uint32_t* a_pk, const uint32_t* tail) {
+#pragma unroll
+  for (int i = 0; i < DA / 2; ++i) a_pk[i] = tail[i];
+  if (DA & 1) a_pk[DA / 2] = tail[DA / 2] & 0xFFFFu;
+}
+
+// Generator input row [s_t; a_t; omega_T(n, k, t)], zero padded.
+template <int DS, int DA, int DW>
+__device__ __forceinline__ void write_gen_row(uint8_t* A, int r, const uint32_t* s_pk, const uint32_t* tail) {
+  static_assert(DS % 2 == 0, "the state fills whole BF16 pairs");
+  constexpr int KP = (DS + DA + DW + 15) / 16 * 16;
+  uint32_t x[KP / 2];
+#pragma unroll
+  for (int i = 0; i < KP / 2; ++i) x[i] = 0u;
+#pragma unroll
+  for (int i = 0; i < DS / 2; ++i) x[i] = s_pk[i];
+#pragma unroll
+  for (int i = 0; i < (DA + DW + 1) / 2; ++i) x[DS / 2 + i] = tail[i];
+  store_words<KP>(A, r, x);
+}
+
+// Reward-head input row [s_{t+1}; a_t], zero padded.
+template <int DS, int DA>
+__device__ __forceinline__ void write_rew_row(uint8_t* A, int r, const uint32_t* s_pk, const uint32_t* a_pk) {
+  constexpr int KP = (DS + DA + 15) / 16 * 16;
+  uint32_t x[KP / 2];
+#pragma unroll
+  for (int i = 0; i < KP / 2; ++i) x[i] = 0u;
+#pragma unroll
+  for (int i = 0; i < DS / 2; ++i) x[i] = s_pk[i];
+#pragma unroll
+  for (int i = 0; i < (DA + 1) / 2; ++i) x[DS / 2 + i] = a_pk[i];
+  store_words<KP>(A, r, x);
 }
 
 // Teacher input row of the DDIM sampler, in the column order the packed first
@@ -464,7 +589,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         const int H = p.pl[item_planner(p, it)].H;
         for (int t = 0; t < H && ok; ++t)
           for (int l = 0; l < p.n_total && ok; ++l)
-            for (int g = 0; g < (WIDE ? p.layers[l].ngroups : 2) && ok; ++g) {
+            // two-tile kernel: a chunk is loaded once and serves both tiles' MMAs
+            for (int g = 0; g < (WIDE ? p.layers[l].ngroups : 1) && ok; ++g) {
               const TcLayer& L = p.layers[l];
               // rows of this CTA's half of the chunk (wide: of column group g)
               const int rowoff = (WIDE ? g * 256 : 0) + (int)rank * L.box_rows;
@@ -522,7 +648,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
               const int kpc = 4 * p.layers[l].spc;  // K steps per chunk
               const uint32_t slab16 = (uint32_t)p.layers[l].slab_bytes >> 4;
               const uint32_t idesc = p.layers[l].idesc;
+              // two-tile kernel: tile 1 reuses the slots tile 0 read (the chunks of
+              // a layer, at most four, stay in the ring until tile 1's MMAs on them
+              // complete), so every weight chunk crosses from L2 once per layer
+              const int slot0 = slot;
+              const uint32_t phase0 = phase;
               for (int g = 0; g < (WIDE ? p.layers[l].ngroups : 2) && ok; ++g) {
+                if (!WIDE) {
+                  slot = slot0;
+                  phase = phase0;
+                }
                 // both CTAs' A operands of tile g are written and their accumulators read
                 // (wide: the whole layer input, once per layer)
                 const uint32_t nr = g ? nready1 : nready0;
@@ -596,7 +731,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                                          ptx::desc_with_lo(bd_hi, b_lo + (kk >> 2) * slab16 + 2 * (kk & 3)), idesc,
                                          (c | kk) ? 1u : 0u);
                   }
-                  ptx::mma_commit_pair(ptx::smem_u32(&empty[slot]), 0x3);
+                  if (WIDE || g == 1) ptx::mma_commit_pair(ptx::smem_u32(&empty[slot]), 0x3);
                   if (c == nch - 1) ptx::mma_commit_pair(ptx::smem_u32(&accf[g]), 0x3);
                   if (++slot == kStages) {
                     slot = 0;
@@ -833,7 +968,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       const uint32_t n = valid ? (uint32_t)(row % PL.N) : 0u;
       const uint32_t k = valid ? (uint32_t)(row / PL.N) : 0u;
       const float* act_row = PL.actions + (size_t)k * H * DA;
-      float s[DS], a[DA];
+      // row state of an owner, as packed BF16 words: s_t, a_t, and the tail
+      // [a_{t+1}; omega_T(n, k, t + 1)] drawn ahead of the step's end
+      uint32_t s_pk[DS / 2], a_pk[(DA + 1) / 2], tn[(DA + DW + 1) / 2];
+      float r_pend = 0.0f;  // r_t, added to G in FP64 during the next step
       if constexpr (PAIRS) {
         if (owner) {
           long long pi, pa, po;  // rows of s', a and o
@@ -859,11 +997,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           store_row<16>(Aown, r, x);
         }
       } else if (owner) {
+        float s0[DS];
 #pragma unroll
-        for (int i = 0; i < DS; ++i) s[i] = valid ? __ldg(PL.particles + (size_t)n * DS + i) : 0.0f;
-#pragma unroll
-        for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + i);
-        write_gen_input<DS, DA, DW>(Aown, r, s, a, p.key0, p.key1, n, k, 0, PL.planner);
+        for (int i = 0; i < DS; ++i) s0[i] = valid ? __ldg(PL.particles + (size_t)n * DS + i) : 0.0f;
+        pack_state<DS>(s_pk, s0);
+        draw_tail<DA, DW>(tn, act_row, p.key0, p.key1, n, k, 0u, PL.planner);
+        write_gen_row<DS, DA, DW>(Aown, r, s_pk, tn);
+        tail_actions<DA>(a_pk, tn);
       }
       ptx::fence_proxy_async_smem();
       __syncwarp();
@@ -872,6 +1012,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         ptx::mbar_arrive_cluster(ready_remote1);
       }
       double Gacc = 0.0, disc = 1.0;
+      // with a reward head the owner prepares the next step's input while it
+      // waits for the other tile's generator output, so the reward output
+      // only has to store it
+      const bool ahead = !PAIRS && p.reward_kind == VOILA_REWARD_MLP;
       for (int t = 0; t < H && ok; ++t) {
         for (int l = 0; l < p.n_total && ok; ++l) {
           const TcLayer& L = p.layers[l];
@@ -879,6 +1023,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           // no A operand follows the final layer of the final step
           const bool arrive = !(t == H - 1 && l == p.n_total - 1);
           for (int g = 0; g < 2; ++g) {
+            if (ahead && owner && g != og && l == p.n_gen - 1) {
+              if (t > 0) {  // r_{t-1}, in step order
+                Gacc += disc * (double)r_pend;
+                disc *= p.gamma;
+              }
+              if (t + 1 < H)
+                draw_tail<DA, DW>(tn, act_row + (t + 1) * DA, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
+            }
             if (!bounded_wait(ptx::smem_u32(&accf[g]), nacc[g] & 1, abort_flag, p.hdr, 30 + g)) {
               ok = false;
               break;
@@ -894,24 +1046,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
               const int per = L.Npad >> 2;
               const float* wf = fuse_s + L.fuse_off;
               const float* sl = scale_s + L.scale_off;
-              float part = 0.0f;
+              uint64_t part2 = 0ull;  // (even, odd) column partial sums, both +0.0f
               if (per >= 32) {
                 const int c0 = slice * (per >> 5);
                 for (int c = c0; c < c0 + (per >> 5); ++c) {
                   float v[32];
                   ptx::tmem_ld32(tm + 32 * c, v);
                   ptx::tmem_wait_ld32(v);
-                  part = (F8 && L.fp8) ? fuse_cols<true, 32>(v, bl, sl, c, L.act, wf, part)
-                                       : fuse_cols<false, 32>(v, bl, sl, c, L.act, wf, part);
+                  part2 = (F8 && L.fp8) ? fuse_cols<true, 32>(v, bl, sl, c, L.act, wf, part2)
+                                        : fuse_cols<false, 32>(v, bl, sl, c, L.act, wf, part2);
                 }
               } else {
                 float v[16];
                 ptx::tmem_ld16(tm + 16 * slice, v);
                 ptx::tmem_wait_ld();
-                part = (F8 && L.fp8) ? fuse_cols<true, 16>(v, bl, sl, slice, L.act, wf, part)
-                                     : fuse_cols<false, 16>(v, bl, sl, slice, L.act, wf, part);
+                part2 = (F8 && L.fp8) ? fuse_cols<true, 16>(v, bl, sl, slice, L.act, wf, part2)
+                                      : fuse_cols<false, 16>(v, bl, sl, slice, L.act, wf, part2);
               }
-              red_s[(g * 4 + slice) * 128 + r] = part;
+              float pe, po;
+              ptx::f2_unpack(part2, pe, po);
+              red_s[(g * 4 + slice) * 128 + r] = pe + po;
               asm volatile("bar.sync %0, 128;" ::"r"(1 + q) : "memory");  // the four warps of quadrant q
               if (owner && og == g) {
                 float val = wf[L.fuse_K];
@@ -919,14 +1073,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 for (int sl4 = 0; sl4 < 4; ++sl4) val += red_s[(g * 4 + sl4) * 128 + r];
                 if constexpr (PAIRS) {
                   if (valid) p.pair_out[row] = val;
+                } else if (t + 1 < H) {
+                  r_pend = val;
+                  write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
+                  tail_actions<DA>(a_pk, tn);
                 } else {
                   Gacc += disc * (double)val;
-                  disc *= p.gamma;
-                  if (t + 1 < H) {
-#pragma unroll
-                    for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + (t + 1) * DA + i);
-                    write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
-                  }
                 }
               }
             } else if (L.act >= 0) {
@@ -969,42 +1121,45 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 ptx::tmem_wait_ld();
                 if (valid) p.pair_out[row] = v[0] + bl[0];
               } else if (l == p.n_gen - 1) {
-                // generator output: s_{t+1} (FP32, kept in registers)
+                // generator output: s_{t+1} (FP32 here; BF16 words from here on)
                 float v[32];
                 ptx::tmem_ld16(tm, v);
                 if (DS > 16) ptx::tmem_ld16(tm + 16, v + 16);
                 ptx::tmem_wait_ld();
+                float s1[DS];
 #pragma unroll
-                for (int i = 0; i < DS; ++i) s[i] = v[i] + bl[i];
+                for (int i = 0; i < DS; ++i) s1[i] = v[i] + bl[i];
+                pack_state<DS>(s_pk, s1);
                 if (p.reward_kind == VOILA_REWARD_GOAL) {
                   float acc = 0.0f;
 #pragma unroll
                   for (int i = 0; i < VOILA_MAX_GOAL; ++i)
                     if (i < p.goal_dims && i < DS) {
-                      const float d = s[i] - p.goal[i];
+                      const float d = s1[i] - p.goal[i];
                       acc = fmaf(d, d, acc);
                     }
                   Gacc += disc * (double)(-acc);
                   disc *= p.gamma;
                   if (t + 1 < H) {
-#pragma unroll
-                    for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + (t + 1) * DA + i);
-                    write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
+                    draw_tail<DA, DW>(tn, act_row + (t + 1) * DA, p.key0, p.key1, n, k, (uint32_t)(t + 1),
+                                      PL.planner);
+                    write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
                   }
                 } else {
-                  write_rew_input<DS, DA>(A, r, s, a);
+                  write_rew_row<DS, DA>(A, r, s_pk, a_pk);
                 }
               } else {
-                // reward output r_t: G += gamma^t r_t in FP64
+                // reward output r_t: G += gamma^t r_t in FP64 (during the next step)
                 float v[16];
                 ptx::tmem_ld16(tm, v);
                 ptx::tmem_wait_ld();
-                Gacc += disc * (double)(v[0] + bl[0]);
-                disc *= p.gamma;
+                const float val = v[0] + bl[0];
                 if (t + 1 < H) {
-#pragma unroll
-                  for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + (t + 1) * DA + i);
-                  write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
+                  r_pend = val;
+                  write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
+                  tail_actions<DA>(a_pk, tn);
+                } else {
+                  Gacc += disc * (double)val;
                 }
               }
             }
@@ -1215,6 +1370,10 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R, bool ddim = false) {
                         : (c >= 32 && c < 96) ? (short)(c - 14) : (short)-1;
   }
   pl.p.n_total = nl;
+  // the two-tile kernel keeps a layer's chunks in the ring for both tiles
+  if (!pl.wide)
+    for (int l = 0; l < nl; ++l)
+      if (pl.p.layers[l].nchunks >= kStages) return pl;
   pl.pack.n = nl;
   pl.p.bias_total = boff;
   int soff = 0;  // channel scales follow the biases in the same vector

@@ -273,6 +273,28 @@ __device__ __forceinline__ float tanh_approx(float x) {
   return y;
 }
 
+// Packed FP32x2 arithmetic (two IEEE round-to-nearest operations per
+// instruction, the same results as the scalar forms): the epilogue's bias
+// adds and SiLU FMAs take half the issue slots.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // Waits for this thread's tcgen05.ld operations and ties the 32 destination
 // registers to the wait, so no use of them can be scheduled before it.
 __device__ __forceinline__ void tmem_wait_ld32(float* v) {
