@@ -374,45 +374,7 @@ __device__ __forceinline__ void store_row(uint8_t* A, int r, const float* x) {
   }
 }
 
-// x = [s; a; omega_T(n, k, t)] zero-padded to a multiple of 16, as BF16.
-template <int DS, int DA, int DW>
-__device__ __forceinline__ void write_gen_input(uint8_t* A, int r, const float* s, const float* a,
-                                                uint32_t k0, uint32_t k1, uint32_t n, uint32_t k,
-                                                uint32_t t, uint32_t planner) {
-  constexpr int KP = (DS + DA + DW + 15) / 16 * 16;
-  float x[KP];
-#pragma unroll
-  for (int i = 0; i < KP; ++i) x[i] = 0.0f;
-#pragma unroll
-  for (int i = 0; i < DS; ++i) x[i] = s[i];
-#pragma unroll
-  for (int i = 0; i < DA; ++i) x[DS + i] = a[i];
-#pragma unroll
-  for (int b = 0; b < (DW + 3) / 4; ++b) {
-    const float4 z = normal4(k0, k1, n, k, t, VOILA_STREAM_ROLLOUT_OMEGA, planner, (uint32_t)b);
-    if (4 * b + 0 < DW) x[DS + DA + 4 * b + 0] = z.x;
-    if (4 * b + 1 < DW) x[DS + DA + 4 * b + 1] = z.y;
-    if (4 * b + 2 < DW) x[DS + DA + 4 * b + 2] = z.z;
-    if (4 * b + 3 < DW) x[DS + DA + 4 * b + 3] = z.w;
-  }
-  store_row<KP>(A, r, x);
-}
-
-// x = [s_{t+1}; a_t] zero-padded, as BF16 (reward-head input).
-template <int DS, int DA>
-__device__ __forceinline__ void write_rew_input(uint8_t* A, int r, const float* s, const float* a) {
-  constexpr int KP = (DS + DA + 15) / 16 * 16;
-  float x[KP];
-#pragma unroll
-  for (int i = 0; i < KP; ++i) x[i] = 0.0f;
-#pragma unroll
-  for (int i = 0; i < DS; ++i) x[i] = s[i];
-#pragma unroll
-  for (int i = 0; i < DA; ++i) x[DS + i] = a[i];
-  store_row<KP>(A, r, x);
-}
-
-// The two-tile epilogue keeps a row's generator inputs as packed BF16 words
+// The rollout epilogues keep a row's generator inputs as packed BF16 words
 // (every one of them is rounded to BF16 where it enters an MMA): the state
 // s_t as DS / 2 words and the tail [a_t; omega_T(n, k, t)] as
 // (DA + DW + 1) / 2 words (an odd last word has a zero high half).
@@ -778,7 +740,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       const uint32_t n = valid ? (uint32_t)(row % PL.N) : 0u;
       const uint32_t k = valid ? (uint32_t)(row / PL.N) : 0u;
       const float* act_row = PL.actions + (size_t)k * H * DA;
-      float s[DS], a[DA];
+      float s[DS], a[DA];  // sampler mode: x_t and the conditioning [s; a]
+      // rollout mode: the row state as packed BF16 words (s_t, a_t and the
+      // next step's tail [a_{t+1}; omega_T(n, k, t + 1)], drawn while the
+      // generator's output layer is on the tensor cores)
+      uint32_t s_pk[DS / 2], a_pk[(DA + 1) / 2], tn[(DA + DW + 1) / 2];
       if constexpr (DDIM) {
         if (owner) {  // s holds x_t, a the conditioning [s; a] of the row
 #pragma unroll
@@ -816,9 +782,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       } else if (owner) {
 #pragma unroll
         for (int i = 0; i < DS; ++i) s[i] = valid ? __ldg(PL.particles + (size_t)n * DS + i) : 0.0f;
-#pragma unroll
-        for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + i);
-        write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, 0, PL.planner);
+        pack_state<DS>(s_pk, s);
+        draw_tail<DA, DW>(tn, act_row, p.key0, p.key1, n, k, 0u, PL.planner);
+        write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
+        tail_actions<DA>(a_pk, tn);
       }
       ptx::fence_proxy_async_smem();
       __syncwarp();
@@ -827,6 +794,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       for (int t = 0; t < H && ok; ++t) {
         for (int l = 0; l < p.n_total; ++l) {
           const TcLayer& L = p.layers[l];
+          if constexpr (!DDIM && !PAIRS) {
+            if (owner && l == p.n_gen - 1 && t + 1 < H)
+              draw_tail<DA, DW>(tn, act_row + (t + 1) * DA, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
+          }
           if (!bounded_wait(acc_bar, nacc & 1, abort_flag, p.hdr, 30 + g)) {
             ok = false;
             break;
@@ -881,14 +852,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
             for (int i = 0; i < DS; ++i) s[i] = fmaf(cx, s[i], cv * (v[i] + bl[i]));
             if (t + 1 < H) write_ddim_input(A, r, s, a, p.ddim_emb + (size_t)(t + 1) * 8);
           } else if (owner && l == p.n_gen - 1) {
-            // generator output: s_{t+1} (FP32, kept in registers)
+            // generator output: s_{t+1} (FP32 here; BF16 words from here on)
             float v[32];
             ptx::tmem_ld16(tm, v);
             if (DS > 16) ptx::tmem_ld16(tm + 16, v + 16);
             ptx::tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < DS; ++i) s[i] = v[i] + bl[i];
+            pack_state<DS>(s_pk, s);
             if (p.reward_kind == VOILA_REWARD_GOAL) {
+              if (t + 1 < H) write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
               float acc = 0.0f;
 #pragma unroll
               for (int i = 0; i < VOILA_MAX_GOAL; ++i)
@@ -898,26 +871,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 }
               Gacc += disc * (double)(-acc);
               disc *= p.gamma;
-              if (t + 1 < H) {
-#pragma unroll
-                for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + (t + 1) * DA + i);
-                write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
-              }
             } else {
-              write_rew_input<DS, DA>(A, r, s, a);
+              write_rew_row<DS, DA>(A, r, s_pk, a_pk);
             }
           } else if (owner) {
             // reward output r_t: G += gamma^t r_t in FP64
             float v[16];
             ptx::tmem_ld16(tm, v);
             ptx::tmem_wait_ld();
+            if (t + 1 < H) {
+              write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
+              tail_actions<DA>(a_pk, tn);
+            }
             Gacc += disc * (double)(v[0] + bl[0]);
             disc *= p.gamma;
-            if (t + 1 < H) {
-#pragma unroll
-              for (int i = 0; i < DA; ++i) a[i] = __ldg(act_row + (t + 1) * DA + i);
-              write_gen_input<DS, DA, DW>(A, r, s, a, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
-            }
           }
           ptx::tc_fence_before();
           if (arrive) {
