@@ -474,6 +474,33 @@ __device__ __forceinline__ void write_ddim_input(uint8_t* A, int r, const float*
   for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4*>(a_chunk(A + 128 * 128, r, j)) = __ldg(emb_row + 4 + j);
 }
 
+// Likelihood-pair input row [s'_i; a_i; o_j] of pair row `row` (row = i B + j),
+// or in the gather form [s'_m; act[node_m]; obs[node_m][branch_m]] (row = m),
+// as BF16; zeros for rows past the end or out-of-range indices.
+__device__ __forceinline__ void write_pair_row(const TcParams& p, uint8_t* A, int r, long long row, bool valid) {
+  long long pi, pa, po;  // rows of s', a and o
+  bool in = valid;
+  if (p.gather_node) {
+    const int an = valid ? __ldg(p.gather_node + row) : -1;
+    in = an >= 0 && an < p.gather_n_nodes;
+    pi = row;
+    pa = in ? an : 0;
+    po = in ? (long long)an * p.gather_C_max + __ldg(p.gather_branch + row) : 0;
+  } else {
+    pi = valid ? row / p.pair_B : 0;
+    pa = pi;
+    po = valid ? row % p.pair_B : 0;
+  }
+  float x[16];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = in ? __ldg(p.pair_s + pi * 8 + i) : 0.0f;
+  x[8] = in ? __ldg(p.pair_a + pa * 2) : 0.0f;
+  x[9] = in ? __ldg(p.pair_a + pa * 2 + 1) : 0.0f;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) x[10 + i] = in ? __ldg(p.pair_o + po * 6 + i) : 0.0f;
+  store_row<16>(A, r, x);
+}
+
 // F8: the MLPs contain E4M3 layers (a separate instantiation keeps the BF16
 // form free of the FP8 code paths).
 // WIDE: layers up to 512 wide. Each CTA owns one 128-row tile per work item
@@ -756,29 +783,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           write_ddim_input(A, r, s, a, p.ddim_emb);
         }
       } else if constexpr (PAIRS) {
-        if (owner) {
-          long long pi, pa, po;  // rows of s', a and o
-          bool in = valid;
-          if (p.gather_node) {
-            const int a = valid ? __ldg(p.gather_node + row) : -1;
-            in = a >= 0 && a < p.gather_n_nodes;
-            pi = row;
-            pa = in ? a : 0;
-            po = in ? (long long)a * p.gather_C_max + __ldg(p.gather_branch + row) : 0;
-          } else {
-            pi = valid ? row / p.pair_B : 0;
-            pa = pi;
-            po = valid ? row % p.pair_B : 0;
-          }
-          float x[16];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) x[i] = in ? __ldg(p.pair_s + pi * 8 + i) : 0.0f;
-          x[8] = in ? __ldg(p.pair_a + pa * 2) : 0.0f;
-          x[9] = in ? __ldg(p.pair_a + pa * 2 + 1) : 0.0f;
-#pragma unroll
-          for (int i = 0; i < 6; ++i) x[10 + i] = in ? __ldg(p.pair_o + po * 6 + i) : 0.0f;
-          store_row<16>(A, r, x);
-        }
+        if (owner) write_pair_row(p, A, r, row, valid);
       } else if (owner) {
 #pragma unroll
         for (int i = 0; i < DS; ++i) s[i] = valid ? __ldg(PL.particles + (size_t)n * DS + i) : 0.0f;
@@ -939,30 +944,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       // [a_{t+1}; omega_T(n, k, t + 1)] drawn ahead of the step's end
       uint32_t s_pk[DS / 2], a_pk[(DA + 1) / 2], tn[(DA + DW + 1) / 2];
       float r_pend = 0.0f;  // r_t, added to G in FP64 during the next step
+      // pair mode: the next item's input rows are written (and announced) by
+      // the last layer's epilogue of this item, one tile at a time, so the
+      // next item's first MMA does not wait for the end of this item
+      const bool first_item = it == cl;
+      const bool has_next = PAIRS && it + ncl < p.total_items;
+      const long long row_next = (it + ncl) * kSuperRows + og * (2 * kTileRows) + (long long)rank * kTileRows + r;
       if constexpr (PAIRS) {
-        if (owner) {
-          long long pi, pa, po;  // rows of s', a and o
-          bool in = valid;
-          if (p.gather_node) {
-            const int an = valid ? __ldg(p.gather_node + row) : -1;
-            in = an >= 0 && an < p.gather_n_nodes;
-            pi = row;
-            pa = in ? an : 0;
-            po = in ? (long long)an * p.gather_C_max + __ldg(p.gather_branch + row) : 0;
-          } else {
-            pi = valid ? row / p.pair_B : 0;
-            pa = pi;
-            po = valid ? row % p.pair_B : 0;
-          }
-          float x[16];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) x[i] = in ? __ldg(p.pair_s + pi * 8 + i) : 0.0f;
-          x[8] = in ? __ldg(p.pair_a + pa * 2) : 0.0f;
-          x[9] = in ? __ldg(p.pair_a + pa * 2 + 1) : 0.0f;
-#pragma unroll
-          for (int i = 0; i < 6; ++i) x[10 + i] = in ? __ldg(p.pair_o + po * 6 + i) : 0.0f;
-          store_row<16>(Aown, r, x);
-        }
+        if (owner && first_item) write_pair_row(p, Aown, r, row, valid);
       } else if (owner) {
         float s0[DS];
 #pragma unroll
@@ -972,11 +961,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         write_gen_row<DS, DA, DW>(Aown, r, s_pk, tn);
         tail_actions<DA>(a_pk, tn);
       }
-      ptx::fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) {
-        ptx::mbar_arrive_cluster(ready_remote0);
-        ptx::mbar_arrive_cluster(ready_remote1);
+      if (!PAIRS || first_item) {
+        ptx::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          ptx::mbar_arrive_cluster(ready_remote0);
+          ptx::mbar_arrive_cluster(ready_remote1);
+        }
       }
       double Gacc = 0.0, disc = 1.0;
       // with a reward head the owner prepares the next step's input while it
@@ -987,8 +978,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         for (int l = 0; l < p.n_total && ok; ++l) {
           const TcLayer& L = p.layers[l];
           const float* bl = bias_s + L.bias_off;  // shared memory (L1 loads measured slower)
-          // no A operand follows the final layer of the final step
-          const bool arrive = !(t == H - 1 && l == p.n_total - 1);
+          // no A operand follows the final layer of the final step (pair mode:
+          // unless the next item's input was written in its epilogue)
+          const bool arrive = !(t == H - 1 && l == p.n_total - 1) || has_next;
           for (int g = 0; g < 2; ++g) {
             if (ahead && owner && g != og && l == p.n_gen - 1) {
               if (t > 0) {  // r_{t-1}, in step order
@@ -1040,6 +1032,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 for (int sl4 = 0; sl4 < 4; ++sl4) val += red_s[(g * 4 + sl4) * 128 + r];
                 if constexpr (PAIRS) {
                   if (valid) p.pair_out[row] = val;
+                  if (has_next && t == H - 1) write_pair_row(p, A, r, row_next, row_next < PL.rows);
                 } else if (t + 1 < H) {
                   r_pend = val;
                   write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
@@ -1087,6 +1080,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 ptx::tmem_ld16(tm, v);
                 ptx::tmem_wait_ld();
                 if (valid) p.pair_out[row] = v[0] + bl[0];
+                if (has_next && t == H - 1) write_pair_row(p, A, r, row_next, row_next < PL.rows);
               } else if (l == p.n_gen - 1) {
                 // generator output: s_{t+1} (FP32 here; BF16 words from here on)
                 float v[32];
