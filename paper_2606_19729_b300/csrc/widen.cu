@@ -4,10 +4,12 @@
 // successor state s', is processed in five phases, all on the GPU:
 //   1. group by action node: bitonic sort of the unique 64-bit keys
 //      node << 32 | m (so each node's simulations keep batch order);
-//   2. one thread per node group walks its simulations in order: the r-th
-//      one widens when C < C_max and C < k_o (N + r + 1)^alpha_o (FP64),
-//      creating branch C; otherwise it joins branch floor(u C), u the 24-bit
-//      Philox uniform of counter (m, step, 0, stream 6); N and C are updated;
+//   2. widening decisions: the r-th simulation of a node group widens when
+//      C < C_max and C < k_o (N + r + 1)^alpha_o (FP64), creating branch C;
+//      otherwise it joins branch floor(u C), u the 24-bit Philox uniform of
+//      counter (m, step, 0, stream 6); N and C are updated. One warp per node
+//      finds all of its widenings at once (the rule is monotone in N), one
+//      thread per simulation then takes its branch;
 //   3. the observation sampler f_Z (Eq. 5) fills the new branches:
 //      o = f_Z([s'; a; omega_Z]), omega_Z at counter (m, 0, step, stream 3);
 //   4. the likelihood l(s', a, o_branch) of every simulation;
@@ -139,14 +141,15 @@ struct PwArgs {
   WsHeader* hdr;
 };
 
-// The rank (0-based, from r_from) of the next simulation of a node group of g
-// that widens while the node has C branches: the smallest visit count
-// n >= n0 + r_from + 1 with k_o * pow(n, alpha) > C, found from the inverse
-// (C / k_o)^(1 / alpha) and confirmed with the same FP64 expression the
-// per-simulation rule evaluates; g when none does (or C has reached C_max).
-__device__ int pw_next_widen(long long n0, int C, int r_from, int g, const PwArgs& p) {
-  if (C >= p.C_max || r_from >= g) return g;
-  const long long lo = n0 + r_from + 1, hi = n0 + g;
+// The first rank r in [0, g) of a node group at which a node holding C
+// branches widens, i.e. the smallest visit count n = n0 + r + 1 with
+// C < k_o * pow(n, alpha) (the per-simulation rule, same FP64 expression),
+// found from the inverse (C / k_o)^(1 / alpha); g when there is none in the
+// batch or C has reached C_max. The rule is monotone in n, so the ranks of
+// the successive widenings follow from these thresholds (see pw_widen_kernel).
+__device__ int pw_threshold_rank(long long n0, int C, int g, const PwArgs& p) {
+  if (C >= p.C_max || g <= 0) return g;
+  const long long lo = n0 + 1, hi = n0 + g;
   const double est = pow((double)C / p.k_o, 1.0 / p.alpha);  // k n^alpha = C at n = est
   if (!(est < (double)(hi + 3))) return g;
   long long n = (long long)floor(est) - 2;
@@ -165,31 +168,52 @@ __global__ void pw_bounds_kernel(const unsigned long long* __restrict__ keys, Pw
   if (q == p.M - 1 || (unsigned)(keys[q + 1] >> 32) != a) p.gend[a] = q + 1;
 }
 
-// Phase 2b: one thread per visited node finds the ranks of the simulations
-// that widen (jumping from one widening to the next), updates N and C, and
-// lists the widened simulations for the observation sampler (slots reserved
-// atomically; each entry fills its own branch, so their order does not matter).
+// Phase 2b: one warp per visited node. The j-th widening of the batch (branch
+// count C0 + j before it) happens at rank r_j = max(r_{j-1} + 1, t_j), t_j the
+// threshold rank of C0 + j; so r_j = j + max_{i <= j} (t_i - i): the lanes
+// find the thresholds of 32 consecutive branch counts at once and a prefix
+// maximum gives the ranks. The warp updates N and C and lists the widened
+// simulations for the observation sampler (slots reserved atomically; each
+// entry fills its own branch, so their order does not matter).
 __global__ void pw_widen_kernel(const unsigned long long* __restrict__ keys, PwArgs p) {
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (a >= p.n_nodes) return;
   const int q = p.gstart[a];
   if (q < 0) return;
   const int g = p.gend[a] - q;
   const long long n0 = p.N[a];
   const int C0 = p.C[a];
-  int C = C0, nw = 0;
   int* wpos = p.wpos + (size_t)a * p.C_max;
-  for (int r = pw_next_widen(n0, C, 0, g, p); r < g; r = pw_next_widen(n0, C, r + 1, g, p)) {
-    wpos[nw++] = r;
-    ++C;
+  int nw = 0, carry = 0;  // widenings found; running max of t_i - i
+  for (int base = 0; base < p.C_max - C0; base += 32) {
+    const int j = base + lane;
+    const int t = j < p.C_max - C0 ? pw_threshold_rank(n0, C0 + j, g, p) : g;
+    int m = t - j;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, m, o);
+      if (lane >= o) m = max(m, v);
+    }
+    m = max(m, carry);
+    const int r = j + m;  // strictly increasing in j
+    const bool w = j < p.C_max - C0 && r < g;
+    if (w) wpos[j] = r;
+    nw += __popc(__ballot_sync(0xffffffffu, w));
+    carry = __shfl_sync(0xffffffffu, m, 31);
+    if (!__shfl_sync(0xffffffffu, w, 31)) break;  // the later ones fall past the batch
   }
-  p.c0[a] = C0;
-  p.nwid[a] = nw;
-  p.N[a] = n0 + g;
-  p.C[a] = C;
+  if (lane == 0) {
+    p.c0[a] = C0;
+    p.nwid[a] = nw;
+    p.N[a] = n0 + g;
+    p.C[a] = C0 + nw;
+  }
   if (nw) {
-    const int slot = atomicAdd(p.count, nw);
-    for (int i = 0; i < nw; ++i) p.list[slot + i] = (int32_t)(keys[q + wpos[i]] & 0xffffffffu);
+    int slot = 0;
+    if (lane == 0) slot = atomicAdd(p.count, nw);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    __syncwarp();
+    for (int i = lane; i < nw; i += 32) p.list[slot + i] = (int32_t)(keys[q + wpos[i]] & 0xffffffffu);
   }
 }
 
@@ -354,10 +378,13 @@ __global__ void __launch_bounds__(256) pw_resample_kernel(const unsigned long lo
   }
   const unsigned a = (unsigned)(g >> 16), br = (unsigned)(g & 0xffffu);
   auto sim = [&](int i) { return (int)(keys[q + i] & 0xffffffull); };
+  // FP64 is scarce on this part: l / lambda as a product with 1 / lambda, one
+  // exp per weight (kept in w between the passes), a product with 1 / Z
+  const double inv_lam = 1.0 / (double)p.lambda;
   double mx = -INFINITY;
   bool bad = false;
   for (int i = lane; i < n; i += 32) {
-    const double lw = (double)p.ell[sim(i)] / (double)p.lambda;
+    const double lw = (double)p.ell[sim(i)] * inv_lam;
     if (isnan(lw) || lw == INFINITY) bad = true;
     mx = fmax(mx, lw);
   }
@@ -371,15 +398,20 @@ __global__ void __launch_bounds__(256) pw_resample_kernel(const unsigned long lo
     return;
   }
   double Z = 0.0;
-  for (int i = lane; i < n; i += 32) Z += exp((double)p.ell[sim(i)] / (double)p.lambda - mx);
+  for (int i = lane; i < n; i += 32) {
+    const double e = exp((double)p.ell[sim(i)] * inv_lam - mx);
+    p.w[sim(i)] = e;  // read back by this lane below
+    Z += e;
+  }
   Z = wsum(Z);
+  const double inv_z = 1.0 / Z;
   // quantised weights and their inclusive prefix sum (exact in any order)
   double carry = 0.0;
   for (int i0 = 0; i0 < n; i0 += 32) {
     const int i = i0 + lane;
     double qv = 0.0;
     if (i < n) {
-      const double wv = exp((double)p.ell[sim(i)] / (double)p.lambda - mx) / Z;
+      const double wv = p.w[sim(i)] * inv_z;
       qv = rint(wv * 4503599627370496.0) * 2.220446049250313e-16;
       p.w[sim(i)] = qv;
     }
@@ -560,7 +592,7 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   if (cudaMemsetAsync(p.gstart, 0xff, (size_t)tree->n_nodes * sizeof(int32_t), s) != cudaSuccess)
     return VOILA_ERR_CUDA;
   pw_bounds_kernel<<<(M + 255) / 256, 256, 0, s>>>(keys1, p);
-  pw_widen_kernel<<<(tree->n_nodes + 127) / 128, 128, 0, s>>>(keys1, p);
+  pw_widen_kernel<<<(int)(((long long)tree->n_nodes * 32 + 255) / 256), 256, 0, s>>>(keys1, p);
   pw_assign_kernel<<<(M + 255) / 256, 256, 0, s>>>(keys1, p);
   if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   // 3. observations of the new branches
