@@ -138,24 +138,63 @@ struct PwArgs {
   int32_t* c0;      // [n_nodes] branch count before the batch
   int32_t* nwid;    // [n_nodes] widenings in the batch
   int32_t* wpos;    // [n_nodes][C_max] group ranks of the widening simulations
+  long long* thr;   // [C_max] T(C): the smallest visit count n with C < k_o n^alpha_o
   WsHeader* hdr;
 };
 
-// The first rank r in [0, g) of a node group at which a node holding C
-// branches widens, i.e. the smallest visit count n = n0 + r + 1 with
-// C < k_o * pow(n, alpha) (the per-simulation rule, same FP64 expression),
-// found from the inverse (C / k_o)^(1 / alpha); g when there is none in the
-// batch or C has reached C_max. The rule is monotone in n, so the ranks of
-// the successive widenings follow from these thresholds (see pw_widen_kernel).
-__device__ int pw_threshold_rank(long long n0, int C, int g, const PwArgs& p) {
-  if (C >= p.C_max || g <= 0) return g;
-  const long long lo = n0 + 1, hi = n0 + g;
-  const double est = pow((double)C / p.k_o, 1.0 / p.alpha);  // k n^alpha = C at n = est
-  if (!(est < (double)(hi + 3))) return g;
-  long long n = (long long)floor(est) - 2;
-  if (n < lo) n = lo;
-  while (n <= hi && !((double)C < p.k_o * pow((double)n, p.alpha))) ++n;
-  return n <= hi ? (int)(n - n0 - 1) : g;
+constexpr long long kNever = 0x7fffffffffffffffLL;  // a threshold no visit count reaches
+
+// Phase 2 set-up: T(C) for every branch count C < C_max, the smallest visit
+// count n >= 1 with C < k_o * pow(n, alpha_o) (the per-simulation rule, same
+// FP64 expression). The rule is monotone in n, so a node holding C branches
+// widens at its first visit with count >= T(C), whatever node it is: one FP64
+// search per branch count per call instead of one per node. The search starts
+// two below the inverse (C / k_o)^(1 / alpha_o) and walks to the exact
+// boundary in either direction.
+__global__ void pw_thresholds_kernel(PwArgs p) {
+  const int C = blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= p.C_max) return;
+  constexpr long long kCap = 4000000000000000000LL;
+  auto pred = [&](long long n) { return (double)C < p.k_o * pow((double)n, p.alpha); };
+  const double est = pow((double)C / p.k_o, 1.0 / p.alpha);
+  long long T = kNever;
+  if (est < 1.0e18) {
+    // bracket the boundary (lo: rule false or 0, hi: rule true) by doubling
+    // steps from the estimate, then bisect: bounded whatever the estimate's error
+    long long n = (long long)floor(est) - 2, lo, hi;
+    if (n < 1) n = 1;
+    bool found = true;
+    if (pred(n)) {
+      hi = n;
+      long long d = 1;
+      lo = n - d;
+      while (lo >= 1 && pred(lo)) {
+        hi = lo;
+        d <<= 1;
+        lo = n - d;
+      }
+      if (lo < 1) lo = 0;
+    } else {
+      lo = n;
+      long long d = 1;
+      hi = n + d;
+      while (hi < kCap && !pred(hi)) {
+        lo = hi;
+        d <<= 1;
+        hi = n + d;
+      }
+      found = hi < kCap;
+    }
+    if (found) {
+      while (hi - lo > 1) {
+        const long long mid = lo + (hi - lo) / 2;
+        if (pred(mid)) hi = mid;
+        else lo = mid;
+      }
+      T = hi;
+    }
+  }
+  p.thr[C] = T;
 }
 
 // Phase 2a: first and one-past-last sorted position of every node's group.
@@ -170,8 +209,8 @@ __global__ void pw_bounds_kernel(const unsigned long long* __restrict__ keys, Pw
 
 // Phase 2b: one warp per visited node. The j-th widening of the batch (branch
 // count C0 + j before it) happens at rank r_j = max(r_{j-1} + 1, t_j), t_j the
-// threshold rank of C0 + j; so r_j = j + max_{i <= j} (t_i - i): the lanes
-// find the thresholds of 32 consecutive branch counts at once and a prefix
+// rank at which the visit count reaches T(C0 + j); so r_j = j + max_{i <= j}
+// (t_i - i): the lanes take 32 consecutive branch counts at once and a prefix
 // maximum gives the ranks. The warp updates N and C and lists the widened
 // simulations for the observation sampler (slots reserved atomically; each
 // entry fills its own branch, so their order does not matter).
@@ -187,7 +226,12 @@ __global__ void pw_widen_kernel(const unsigned long long* __restrict__ keys, PwA
   int nw = 0, carry = 0;  // widenings found; running max of t_i - i
   for (int base = 0; base < p.C_max - C0; base += 32) {
     const int j = base + lane;
-    const int t = j < p.C_max - C0 ? pw_threshold_rank(n0, C0 + j, g, p) : g;
+    // threshold rank of branch count C0 + j: the rank whose visit count n0 + r + 1 reaches T
+    int t = g;
+    if (j < p.C_max - C0) {
+      const long long T = p.thr[C0 + j];
+      if (T <= n0 + g) t = T > n0 + 1 ? (int)(T - n0 - 1) : 0;
+    }
     int m = t - j;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -456,7 +500,7 @@ int pow2_at_least(int m) {
 // widened [M] u8 | ell [M] f32 | w [M] f64 | per node: gstart, gend, c0, nwid
 // [n_nodes] i32 and wpos [n_nodes][C_max] i32
 struct PwLayout {
-  size_t tc, keys1, keys2, cw, list, count, widened, ell, w, gstart, gend, c0, nwid, wpos, total;
+  size_t tc, keys1, keys2, cw, list, count, widened, ell, w, gstart, gend, c0, nwid, wpos, thr, total;
 };
 
 bool pw_tc_likelihood(const voila_likelihood* ell, int d_s, int d_a, int d_o) {
@@ -483,6 +527,7 @@ PwLayout pw_layout(const voila_pw_tree* tree, const voila_likelihood* ell, int M
   L.c0 = o; o += a256(nn * 4);
   L.nwid = o; o += a256(nn * 4);
   L.wpos = o; o += a256(nn * (size_t)tree->C_max * 4);
+  L.thr = o; o += a256((size_t)tree->C_max * 8);
   L.total = o;
   return L;
 }
@@ -579,6 +624,7 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   p.c0 = (int32_t*)(ws + L.c0);
   p.nwid = (int32_t*)(ws + L.nwid);
   p.wpos = (int32_t*)(ws + L.wpos);
+  p.thr = (long long*)(ws + L.thr);
   p.hdr = (WsHeader*)ws;
   unsigned long long* keys1 = (unsigned long long*)(ws + L.keys1);
   unsigned long long* keys2 = (unsigned long long*)(ws + L.keys2);
@@ -591,6 +637,7 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   if (cudaMemsetAsync(p.count, 0, sizeof(int32_t), s) != cudaSuccess) return VOILA_ERR_CUDA;
   if (cudaMemsetAsync(p.gstart, 0xff, (size_t)tree->n_nodes * sizeof(int32_t), s) != cudaSuccess)
     return VOILA_ERR_CUDA;
+  pw_thresholds_kernel<<<(tree->C_max + 127) / 128, 128, 0, s>>>(p);
   pw_bounds_kernel<<<(M + 255) / 256, 256, 0, s>>>(keys1, p);
   pw_widen_kernel<<<(int)(((long long)tree->n_nodes * 32 + 255) / 256), 256, 0, s>>>(keys1, p);
   pw_assign_kernel<<<(M + 255) / 256, 256, 0, s>>>(keys1, p);
