@@ -700,7 +700,7 @@ def run_pw(args, rank, world, local):
     s_next = torch.from_numpy(wl.s_next).float().cuda()
     branch = torch.empty(M, dtype=torch.int32, device="cuda")
     s_out = torch.empty_like(s_next)
-    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(tree, lik, M))
+    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(tree, g_Z, lik, M))
 
     def call():
         V.voila_progressive_widening(tree, node, s_next, g_Z, lik, wl.d_omega, wl.k_o, wl.alpha_o, wl.lam, wl.seed,

@@ -527,9 +527,10 @@ typedef struct {
   float* obs;
 } voila_pw_tree;
 
-/* Workspace of voila_progressive_widening for the tree, likelihood ell and M
- * simulations, in bytes. */
-voila_status voila_progressive_widening_workspace_size(const voila_pw_tree* tree,
+/* Workspace of voila_progressive_widening for the tree, observation sampler
+ * g_Z (may be NULL: no room for its tensor-core form, which the call then does
+ * not use), likelihood ell and M simulations, in bytes. */
+voila_status voila_progressive_widening_workspace_size(const voila_pw_tree* tree, const voila_mlp* g_Z,
                                                        const voila_likelihood* ell, int32_t M,
                                                        size_t* bytes);
 

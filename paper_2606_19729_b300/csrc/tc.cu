@@ -57,7 +57,9 @@ constexpr long long kSpinLimit = 4000000000LL;  // ~2 s of SM clock per wait
 // What the rows of a launch are: rollout rows (n, k) over H planning steps;
 // DDIM teacher samples over the sampler's steps; likelihood pairs (i, j) of
 // the InfoNCE objective (one evaluation, H = 1).
-constexpr int kModeRollout = 0, kModeDdim = 1, kModePairs = 2;
+// ... and the observation sampler of progressive widening (rows = the listed
+// widened simulations, one evaluation of f_Z, outputs scattered to the tree).
+constexpr int kModeRollout = 0, kModeDdim = 1, kModePairs = 2, kModeObserve = 3;
 
 struct TcLayer {
   int Kp;           // input width rounded up to 16 (MMA K steps of 16)
@@ -132,6 +134,16 @@ struct TcParams {
   const int32_t* gather_node;
   const int32_t* gather_branch;
   int gather_n_nodes, gather_C_max;
+  // observation sampler (Eq. 5) of progressive widening: row i (i < *obs_count)
+  // is simulation m = obs_list[i], input [s'_m (pair_s); act[node_m] (pair_a);
+  // omega_Z] with omega_Z the normals of stream VOILA_STREAM_OBS_OMEGA at
+  // counter (m, 0, obs_step); f_Z's output goes to obs_out[node_m][branch_m]
+  // (obs_d values). Simulation indices are < pair_B.
+  const int32_t* obs_list;
+  const int32_t* obs_count;
+  float* obs_out;
+  int obs_d;
+  uint32_t obs_step, obs_planner;
 };
 
 __device__ __forceinline__ int item_planner(const TcParams& p, long long it) {
@@ -516,8 +528,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     rollout_tc_kernel(const __grid_constant__ TcParams p) {
   constexpr bool DDIM = MODE == kModeDdim;
   constexpr bool PAIRS = MODE == kModePairs;
+  constexpr bool OBS = MODE == kModeObserve;
   static_assert(!DDIM || (WIDE && !F8 && DS == 8 && DA == 10 && DW == 0), "DDIM sampler layout");
   static_assert(!PAIRS || (!WIDE && !F8 && DS == 8 && DA == 2 && DW == 6), "likelihood pair layout");
+  static_assert(!OBS || (!WIDE && !F8), "observation rows use the two-tile kernel");
+  // work items of the launch: the observation rows are counted on the device
+  long long total_items = p.total_items;
+  if constexpr (OBS) {
+    const int cnt = *reinterpret_cast<const volatile int*>(p.obs_count);
+    const long long need = cnt > 0 ? ((long long)cnt + kSuperRows - 1) / kSuperRows : 0;
+    if (need < total_items) total_items = need;
+  }
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* Abuf[2] = {smem, smem + kABytes};
@@ -574,7 +595,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       bool ok = true;
       int last_round[kStages];
       for (int s = 0; s < kStages; ++s) last_round[s] = -1;
-      for (long long it = cl; it < p.total_items && ok; it += ncl) {
+      for (long long it = cl; it < total_items && ok; it += ncl) {
         const int H = p.pl[item_planner(p, it)].H;
         for (int t = 0; t < H && ok; ++t)
           for (int l = 0; l < p.n_total && ok; ++l)
@@ -628,7 +649,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         const uint64_t adesc0 = ptx::smem_desc(ptx::smem_u32(Abuf[0]), 1024, ptx::kSwizzle128B);
         const uint64_t adesc1 = ptx::smem_desc(ptx::smem_u32(Abuf[1]), 1024, ptx::kSwizzle128B);
         const uint64_t bdesc0 = ptx::smem_desc(ring_addr, 1024, ptx::kSwizzle128B);
-        for (long long it = cl; it < p.total_items && ok; it += ncl) {
+        for (long long it = cl; it < total_items && ok; it += ncl) {
           const int H = p.pl[item_planner(p, it)].H;
           for (int t = 0; t < H && ok; ++t)
             for (int l = 0; l < p.n_total && ok; ++l) {
@@ -756,7 +777,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     const uint32_t acc_bar1 = ptx::smem_u32(&accf[1]);
     uint32_t nacc = 0, nacc1 = 0;
     bool ok = true;
-    for (long long it = cl; it < p.total_items && ok; it += ncl) {
+    for (long long it = cl; it < total_items && ok; it += ncl) {
       const int q = item_planner(p, it);
       const long long sp = it - (q ? p.item_end[q - 1] : 0);
       const TcPlanner& PL = p.pl[q];
@@ -930,7 +951,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     const uint32_t ready_remote1 = ptx::mapa_shared(ptx::smem_u32(&ready[1]), 0);
     uint32_t nacc[2] = {0u, 0u};
     bool ok = true;
-    for (long long it = cl; it < p.total_items && ok; it += ncl) {
+    for (long long it = cl; it < total_items && ok; it += ncl) {
       const int pq = item_planner(p, it);
       const long long sp = it - (pq ? p.item_end[pq - 1] : 0);
       const TcPlanner& PL = p.pl[pq];
@@ -948,10 +969,45 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       // the last layer's epilogue of this item, one tile at a time, so the
       // next item's first MMA does not wait for the end of this item
       const bool first_item = it == cl;
-      const bool has_next = PAIRS && it + ncl < p.total_items;
+      const bool has_next = PAIRS && it + ncl < total_items;
       const long long row_next = (it + ncl) * kSuperRows + og * (2 * kTileRows) + (long long)rank * kTileRows + r;
+      int obs_m = -1, obs_a = 0;  // observation mode: this row's simulation and node
       if constexpr (PAIRS) {
         if (owner && first_item) write_pair_row(p, Aown, r, row, valid);
+      } else if constexpr (OBS) {
+        if (owner) {
+          const int cnt = *reinterpret_cast<const volatile int*>(p.obs_count);
+          if (row < cnt) {
+            const int m = __ldg(p.obs_list + row);
+            const int a = (m >= 0 && m < p.pair_B) ? __ldg(p.gather_node + m) : -1;
+            if (a >= 0 && a < p.gather_n_nodes) {
+              obs_m = m;
+              obs_a = a;
+            }
+          }
+          float s0[DS], e[2 * ((DA + DW + 1) / 2)];
+#pragma unroll
+          for (int i = 0; i < DS; ++i) s0[i] = obs_m >= 0 ? __ldg(p.pair_s + (size_t)obs_m * DS + i) : 0.0f;
+#pragma unroll
+          for (int i = 0; i < 2 * ((DA + DW + 1) / 2); ++i) e[i] = 0.0f;
+#pragma unroll
+          for (int i = 0; i < DA; ++i) e[i] = obs_m >= 0 ? __ldg(p.pair_a + (size_t)obs_a * DA + i) : 0.0f;
+          if (obs_m >= 0) {
+#pragma unroll
+            for (int b = 0; b < (DW + 3) / 4; ++b) {
+              const float4 z = normal4(p.key0, p.key1, (uint32_t)obs_m, 0u, p.obs_step, VOILA_STREAM_OBS_OMEGA,
+                                       p.obs_planner, (uint32_t)b);
+              if (4 * b + 0 < DW) e[DA + 4 * b + 0] = z.x;
+              if (4 * b + 1 < DW) e[DA + 4 * b + 1] = z.y;
+              if (4 * b + 2 < DW) e[DA + 4 * b + 2] = z.z;
+              if (4 * b + 3 < DW) e[DA + 4 * b + 3] = z.w;
+            }
+          }
+          pack_state<DS>(s_pk, s0);
+#pragma unroll
+          for (int j = 0; j < (DA + DW + 1) / 2; ++j) tn[j] = ptx::pack_bf16x2(e[2 * j], e[2 * j + 1]);
+          write_gen_row<DS, DA, DW>(Aown, r, s_pk, tn);
+        }
       } else if (owner) {
         float s0[DS];
 #pragma unroll
@@ -1081,6 +1137,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 ptx::tmem_wait_ld();
                 if (valid) p.pair_out[row] = v[0] + bl[0];
                 if (has_next && t == H - 1) write_pair_row(p, A, r, row_next, row_next < PL.rows);
+              } else if (OBS && l == p.n_gen - 1) {
+                float v[32];
+                ptx::tmem_ld16(tm, v);
+                ptx::tmem_ld16(tm + 16, v + 16);
+                ptx::tmem_wait_ld();
+                if (obs_m >= 0) {
+                  const int br = __ldg(p.gather_branch + obs_m);
+                  if (br >= 0 && br < p.gather_C_max)
+                    for (int i = 0; i < p.obs_d; ++i)
+                      p.obs_out[((size_t)obs_a * p.gather_C_max + br) * p.obs_d + i] = v[i] + bl[i];
+                }
               } else if (l == p.n_gen - 1) {
                 // generator output: s_{t+1} (FP32 here; BF16 words from here on)
                 float v[32];
@@ -1134,7 +1201,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         }
       }
       if constexpr (!PAIRS) {
-        if (owner && valid && ok) PL.G[row] = Gacc;
+        if (!OBS && owner && valid && ok) PL.G[row] = Gacc;
       }
     }
   }
@@ -1702,6 +1769,89 @@ voila_status tc_likelihood_rows(const voila_mlp* ell, const float* S, const floa
   const long long nclusters = p.total_items < nsm / 2 ? p.total_items : nsm / 2;
   const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total + p.fuse_total + (p.fuse_total ? 1024 : 0));
   const cudaError_t e = launch_tc<8, 2, 6, false, false, kModePairs>(p, smem, nclusters, s);
+  return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
+}
+
+bool tc_observe_supported(const voila_mlp* g_Z, int d_s, int d_a, int d_omega, int d_o) {
+  if (!g_Z || g_Z->prec != VOILA_BF16 || d_s != 8 || d_a != 2 || d_omega != 8 || d_o < 1 || d_o > 32) return false;
+  if (g_Z->dims[0] != d_s + d_a + d_omega || g_Z->dims[g_Z->n_layers] != d_o) return false;
+  Plan pl = make_plan(g_Z, nullptr);
+  return pl.ok && !pl.wide && pl.p.n_total == pl.p.n_gen;
+}
+
+size_t tc_observe_scratch_bytes(const voila_mlp* g_Z) {
+  Plan pl = make_plan(g_Z, nullptr);
+  return pl.ok ? pl.total : 0;
+}
+
+voila_status tc_observe_rows(const voila_mlp* g_Z, const float* S, const float* act, const int32_t* list,
+                             const int32_t* count, long long M, const int32_t* node, const int32_t* branch,
+                             int n_nodes, int C_max, float* obs, int d_o, uint32_t key0, uint32_t key1,
+                             uint32_t step, uint32_t planner, WsHeader* hdr, void* scratch, cudaStream_t s) {
+  Plan pl = make_plan(g_Z, nullptr);
+  if (!pl.ok || pl.wide || pl.p.n_total != pl.p.n_gen) return VOILA_ERR_UNSUPPORTED;
+  if ((uintptr_t)scratch % 1024) return VOILA_ERR_WORKSPACE;
+  TcParams& p = pl.p;
+  TcPlanner& q = p.pl[0];
+  q.particles = S;
+  q.actions = act;
+  q.G = nullptr;
+  q.rows = M;  // at most M listed rows; the kernel reads the count
+  q.N = 1;
+  q.H = 1;
+  q.planner = planner;
+  p.P = 1;
+  p.total_items = (M + kSuperRows - 1) / kSuperRows;
+  p.item_end[0] = p.total_items;
+  if (p.total_items == 0) return VOILA_OK;
+  uint8_t* wst = (uint8_t*)scratch;
+  float* bias_all = (float*)(wst + (pl.wbytes + 1023) / 1024 * 1024);
+  pl.pack.wout = wst;
+  pl.pack.bout = bias_all;
+  {
+    const long long total = pl.pack.elems_end[pl.pack.n - 1];
+    long long blocks = (total + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    pack_kernel<<<(int)blocks, 256, 0, s>>>(pl.pack);
+    if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return VOILA_ERR_CUDA;
+  for (int l = 0; l < p.n_total; ++l) {
+    const cuuint64_t gdim[2] = {128, (cuuint64_t)pl.total_rows};  // bytes
+    const cuuint64_t gstride[1] = {128};
+    const cuuint32_t box[2] = {128, (cuuint32_t)p.layers[l].box_rows};
+    const cuuint32_t estride[2] = {1, 1};
+    if (encode(&p.tmap[l], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)wst, gdim, gstride, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return VOILA_ERR_CUDA;
+  }
+  p.bias_all = bias_all;
+  p.reward_kind = VOILA_REWARD_GOAL;
+  p.goal_dims = 0;
+  p.key0 = key0;
+  p.key1 = key1;
+  p.hdr = hdr;
+  p.pair_s = S;
+  p.pair_a = act;
+  p.pair_B = M;
+  p.gather_node = node;
+  p.gather_branch = branch;
+  p.gather_n_nodes = n_nodes;
+  p.gather_C_max = C_max;
+  p.obs_list = list;
+  p.obs_count = count;
+  p.obs_out = obs;
+  p.obs_d = d_o;
+  p.obs_step = step;
+  p.obs_planner = planner;
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long nclusters = p.total_items < nsm / 2 ? p.total_items : nsm / 2;
+  const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total + p.fuse_total + (p.fuse_total ? 1024 : 0));
+  const cudaError_t e = launch_tc<8, 2, 8, false, false, kModeObserve>(p, smem, nclusters, s);
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
 

@@ -57,4 +57,16 @@ voila_status tc_likelihood_rows(const voila_mlp* ell, const float* S, const floa
                                 const int32_t* node, const int32_t* branch, int n_nodes, int C_max, float* out,
                                 WsHeader* hdr, void* scratch, cudaStream_t s);
 
+// Observation sampler of progressive widening on the tensor cores (BF16 f_Z
+// 18 -> 256 x L -> d_o, s' 8, a 2, omega 8): for the first *count entries m of
+// list, obs[node[m] * C_max + branch[m]][0 .. d_o) = f_Z([S[m]; act[node[m]];
+// omega_Z(m)]), omega_Z the normals of stream VOILA_STREAM_OBS_OMEGA at counter
+// (m, 0, step); at most M rows (the count is read on the device).
+bool tc_observe_supported(const voila_mlp* g_Z, int d_s, int d_a, int d_omega, int d_o);
+size_t tc_observe_scratch_bytes(const voila_mlp* g_Z);
+voila_status tc_observe_rows(const voila_mlp* g_Z, const float* S, const float* act, const int32_t* list,
+                             const int32_t* count, long long M, const int32_t* node, const int32_t* branch,
+                             int n_nodes, int C_max, float* obs, int d_o, uint32_t key0, uint32_t key1,
+                             uint32_t step, uint32_t planner, WsHeader* hdr, void* scratch, cudaStream_t s);
+
 }  // namespace voila

@@ -500,19 +500,24 @@ int pow2_at_least(int m) {
 // widened [M] u8 | ell [M] f32 | w [M] f64 | per node: gstart, gend, c0, nwid
 // [n_nodes] i32 and wpos [n_nodes][C_max] i32
 struct PwLayout {
-  size_t tc, keys1, keys2, cw, list, count, widened, ell, w, gstart, gend, c0, nwid, wpos, thr, total;
+  size_t tc, tcz, keys1, keys2, cw, list, count, widened, ell, w, gstart, gend, c0, nwid, wpos, thr, total;
 };
 
 bool pw_tc_likelihood(const voila_likelihood* ell, int d_s, int d_a, int d_o) {
   return ell && ell->kind == VOILA_LIK_MLP && ell->mlp && tc_pairs_supported(ell->mlp, d_s, d_a, d_o);
 }
 
-PwLayout pw_layout(const voila_pw_tree* tree, const voila_likelihood* ell, int M) {
+PwLayout pw_layout(const voila_pw_tree* tree, const voila_mlp* g_Z, const voila_likelihood* ell, int M) {
   PwLayout L;
   const size_t n_pad = (size_t)pow2_at_least(M < 2 ? 2 : M);
   size_t o = 1024;
   L.tc = o;
   if (ell && ell->kind == VOILA_LIK_MLP && ell->mlp) o += (tc_pairs_scratch_bytes(ell->mlp) + 1023) / 1024 * 1024;
+  L.tcz = 0;  // packed f_Z weights of the tensor-core observation sampler (0: none)
+  if (g_Z && tc_observe_supported(g_Z, 8, tree->d_a, g_Z->dims[0] - 8 - tree->d_a, tree->d_o)) {
+    L.tcz = o;
+    o += (tc_observe_scratch_bytes(g_Z) + 1023) / 1024 * 1024;
+  }
   L.keys1 = o; o += a256(n_pad * 8);
   L.keys2 = o; o += a256(n_pad * 8);
   L.cw = o; o += a256((size_t)M * 8);
@@ -545,12 +550,13 @@ using namespace voila;
 
 extern "C" {
 
-voila_status voila_progressive_widening_workspace_size(const voila_pw_tree* tree, const voila_likelihood* ell,
+voila_status voila_progressive_widening_workspace_size(const voila_pw_tree* tree, const voila_mlp* g_Z,
+                                                       const voila_likelihood* ell,
                                                        int32_t M, size_t* bytes) {
   if (!tree || !ell || M < 0 || M > (1 << 24) || !bytes || tree->n_nodes < 1 || tree->n_nodes >= (1 << 24) ||
       tree->C_max < 1 || tree->C_max > 65535)
     return VOILA_ERR_ARG;
-  *bytes = pw_layout(tree, ell, M).total;
+  *bytes = pw_layout(tree, g_Z, ell, M).total;
   return VOILA_OK;
 }
 
@@ -579,7 +585,7 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   } else {
     return VOILA_ERR_ARG;
   }
-  const PwLayout L = pw_layout(tree, ell, M);
+  const PwLayout L = pw_layout(tree, g_Z, ell, M);
   if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 1023)) return VOILA_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   char* ws = (char*)workspace;
@@ -642,8 +648,14 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   pw_widen_kernel<<<(int)(((long long)tree->n_nodes * 32 + 255) / 256), 256, 0, s>>>(keys1, p);
   pw_assign_kernel<<<(M + 255) / 256, 256, 0, s>>>(keys1, p);
   if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
-  // 3. observations of the new branches
-  {
+  // 3. observations of the new branches (tensor cores for a BF16 f_Z of the
+  // generator's shape, else CUDA cores)
+  if (L.tcz && tc_observe_supported(g_Z, d_s, tree->d_a, d_omega, tree->d_o)) {
+    const voila_status st = tc_observe_rows(g_Z, s_next, tree->act, p.list, p.count, M, node, branch_out,
+                                            tree->n_nodes, tree->C_max, tree->obs, tree->d_o, p.key0, p.key1, step,
+                                            planner_id, p.hdr, ws + L.tcz, s);
+    if (st != VOILA_OK) return st;
+  } else {
     const MlpDev gz = mlp_dev(g_Z);
     int wmax = 0;
     for (int l = 0; l <= g_Z->n_layers; ++l) wmax = g_Z->dims[l] > wmax ? g_Z->dims[l] : wmax;

@@ -119,7 +119,7 @@ _lib_nce_fwd = _sig("voila_infonce_forward", c_int32, POINTER(voila_mlp), _P, _P
 _lib_nce_step_ws = _sig("voila_infonce_step_workspace_size", c_int32, POINTER(voila_mlp), c_int32, POINTER(c_size_t))
 _lib_nce_step = _sig("voila_infonce_step", c_int32, POINTER(voila_mlp), _P, _P, _P, POINTER(voila_adam), _P, _P, _P,
                      c_int32, c_int32, c_int32, c_int32, _P, _P, _P, c_size_t, _P)
-_lib_pw_ws = _sig("voila_progressive_widening_workspace_size", c_int32, POINTER(voila_pw_tree),
+_lib_pw_ws = _sig("voila_progressive_widening_workspace_size", c_int32, POINTER(voila_pw_tree), _P,
                   POINTER(voila_likelihood), c_int32, POINTER(c_size_t))
 _lib_pw = _sig("voila_progressive_widening", c_int32, POINTER(voila_pw_tree), _P, _P, c_int32, c_int32,
                POINTER(voila_mlp), POINTER(voila_likelihood), c_int32, c_double, c_double, c_float, c_uint64,
@@ -506,9 +506,11 @@ class PWTree:
         self.desc.obs = self.obs.data_ptr()
 
 
-def voila_progressive_widening_workspace_size(tree: "PWTree", ell: voila_likelihood, M: int) -> int:
+def voila_progressive_widening_workspace_size(tree: "PWTree", g_Z: Optional[DeviceMLP], ell: voila_likelihood,
+                                              M: int) -> int:
     n = c_size_t(0)
-    _check(_lib_pw_ws(ctypes.byref(tree.desc), ctypes.byref(ell), M, ctypes.byref(n)),
+    gz = ctypes.cast(ctypes.byref(g_Z.desc), ctypes.c_void_p) if g_Z is not None else None
+    _check(_lib_pw_ws(ctypes.byref(tree.desc), gz, ctypes.byref(ell), M, ctypes.byref(n)),
            "voila_progressive_widening_workspace_size")
     return n.value
 

@@ -89,14 +89,14 @@ def test_widening_empty_batch_and_errors(V):
     N0 = tree.N.clone()
     g_Z = V.DeviceMLP.from_spec(wl.g_Z)
     lik = V.gaussian_likelihood(1.0)
-    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(tree, lik, 0))
+    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(tree, g_Z, lik, 0))
     V.voila_progressive_widening(tree, torch.empty(0, dtype=torch.int32, device="cuda"),
                                  torch.empty(0, wl.d_s, device="cuda"), g_Z, lik, wl.d_omega, wl.k_o, wl.alpha_o,
                                  wl.lam, wl.seed, 0, 0, torch.empty(0, dtype=torch.int32, device="cuda"),
                                  torch.empty(0, wl.d_s, device="cuda"), ws)
     torch.cuda.synchronize()
     assert torch.equal(tree.N, N0)  # no simulations, no visits
-    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(tree, lik, 64))
+    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(tree, g_Z, lik, 64))
     branch = torch.empty(64, dtype=torch.int32, device="cuda")
     s_out = torch.empty(64, wl.d_s, device="cuda")
     node = cuda(wl.node, torch.int32)
@@ -109,7 +109,7 @@ def test_widening_empty_batch_and_errors(V):
     assert _code(V, V.voila_progressive_widening, tree, node, s, bad, lik, wl.d_omega, wl.k_o, wl.alpha_o, wl.lam,
                  wl.seed, 0, 0, branch, s_out, ws) == V.ERR_SHAPE
     # a workspace sized for fewer simulations
-    small = V.alloc_workspace(V.voila_progressive_widening_workspace_size(tree, lik, 8))
+    small = V.alloc_workspace(V.voila_progressive_widening_workspace_size(tree, g_Z, lik, 8))
     assert _code(V, V.voila_progressive_widening, tree, node, s, g_Z, lik, wl.d_omega, wl.k_o, wl.alpha_o, wl.lam,
                  wl.seed, 0, 0, branch, s_out, small) == V.ERR_WORKSPACE
 

@@ -4,10 +4,11 @@ Integer results are bit-exact: widening decisions, branch choices, visit and
 branch counts (the threshold k_o n^alpha_o is evaluated in FP64 on both sides;
 each test first checks that no threshold lies within 1e-9 of an integer, so
 the last-bit differences of pow cannot flip a decision). New observations and
-likelihood values are FP32 CUDA-core arithmetic (1e-5 normwise relative, the
-FP32 tolerance; BF16 weights are the stored values on both sides), except the
-BF16 likelihood of the planning shapes, which runs on the tensor cores with
-BF16 activations (2e-2, the BF16 tolerance of the rollout). Resampling
+likelihood values of FP32 models are FP32 CUDA-core arithmetic (1e-5
+normwise relative, the FP32 tolerance); a BF16 f_Z or likelihood of the
+planning shapes runs on the tensor cores with BF16 activations (2e-2, the
+BF16 tolerance of the rollout; the likelihood then inherits the observations'
+error). Resampling
 indices are checked as the function of the device's own quantised weights and
 the group's u0 (several index vectors are valid up to rounding of the weights).
 """
@@ -47,7 +48,7 @@ def _run(V, wl, node, s_next, tree, lik_dev, step, planner=0):
     w = torch.empty(M, dtype=torch.float64, device="cuda")
     idx = torch.empty(M, dtype=torch.int32, device="cuda")
     s_out = torch.empty(M, wl.d_s, device="cuda")
-    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(tree, lik_dev, M))
+    ws = V.alloc_workspace(V.voila_progressive_widening_workspace_size(tree, g_Z, lik_dev, M))
     V.voila_progressive_widening(tree, cuda(node, torch.int32), cuda(s_next), g_Z, lik_dev, wl.d_omega, wl.k_o,
                                  wl.alpha_o, wl.lam, wl.seed, step, planner, branch, s_out, ws, widened, ell, w, idx)
     torch.cuda.synchronize()
@@ -63,7 +64,7 @@ def _trees(V, wl):
     return dev, ora
 
 
-def _check(wl, got, res, tree_dev, tree_o, node, s_next, step, nodes=None, planner=0, tol_ell=TOL):
+def _check(wl, got, res, tree_dev, tree_o, node, s_next, step, nodes=None, planner=0, tol_ell=TOL, tol_obs=TOL):
     sel = np.ones(node.shape[0], bool) if nodes is None else np.isin(node, nodes)
     np.testing.assert_array_equal(got["branch"][sel], res.branch)
     np.testing.assert_array_equal(got["widened"][sel].astype(bool), res.widened)
@@ -73,7 +74,7 @@ def _check(wl, got, res, tree_dev, tree_o, node, s_next, step, nodes=None, plann
     keep = np.arange(wl.n_nodes) if nodes is None else np.asarray(nodes)
     np.testing.assert_array_equal(N[keep], tree_o.N[keep])
     np.testing.assert_array_equal(C[keep], tree_o.C[keep])
-    assert rel_err(obs[keep], tree_o.obs[keep]) < TOL
+    assert rel_err(obs[keep], tree_o.obs[keep]) < tol_obs
     assert rel_err(got["ell"][sel], res.ell) < tol_ell
     if tol_ell <= TOL:
         assert np.max(np.abs(got["w"][sel] - res.w)) < TOL
@@ -118,7 +119,8 @@ def test_pw_gaussian_two_steps_and_cap(V):
         assert status == V.OK
         res = O.progressive_widening(tree_o, node, s, oracle_mlp(wl.g_Z), lik, wl.d_omega, wl.k_o, wl.alpha_o,
                                      wl.lam, wl.seed, step)
-        _check(wl, got, res, tree_dev, tree_o, node, s, step)
+        # BF16 f_Z of the planning shapes: tensor-core observations
+        _check(wl, got, res, tree_dev, tree_o, node, s, step, tol_ell=TOL_BF16, tol_obs=TOL_BF16)
     assert tree_dev.C.cpu().numpy().max() <= 5
 
 
@@ -143,8 +145,9 @@ def test_pw_full_batch_sampled_nodes(V):
     res = O.progressive_widening(tree_o, wl.node[sel], wl.s_next[sel], oracle_mlp(wl.g_Z),
                                  O.Likelihood(O.LIK_MLP, mlp=oracle_mlp(wl.ell)), wl.d_omega, wl.k_o, wl.alpha_o,
                                  wl.lam, wl.seed, 7, sim_index=np.nonzero(sel)[0])
-    # BF16 likelihood of the planning shapes: tensor cores, BF16 activations
-    _check(wl, got, res, tree_dev, tree_o, wl.node, wl.s_next, 7, nodes=nodes, tol_ell=TOL_BF16)
+    # BF16 f_Z and likelihood of the planning shapes: tensor cores, BF16 activations
+    # (about 2150 widened simulations: five observation items, the last one ragged)
+    _check(wl, got, res, tree_dev, tree_o, wl.node, wl.s_next, 7, nodes=nodes, tol_ell=TOL_BF16, tol_obs=TOL_BF16)
 
 
 def test_pw_tensor_core_likelihood_small(V):
@@ -158,7 +161,27 @@ def test_pw_tensor_core_likelihood_small(V):
     res = O.progressive_widening(tree_o, wl.node, wl.s_next, oracle_mlp(wl.g_Z),
                                  O.Likelihood(O.LIK_MLP, mlp=oracle_mlp(wl.ell)), wl.d_omega, wl.k_o, wl.alpha_o,
                                  wl.lam, wl.seed, 2)
-    _check(wl, got, res, tree_dev, tree_o, wl.node, wl.s_next, 2, tol_ell=TOL_BF16)
+    _check(wl, got, res, tree_dev, tree_o, wl.node, wl.s_next, 2, tol_ell=TOL_BF16, tol_obs=TOL_BF16)
+
+
+def test_pw_tensor_core_observations_many_items(V):
+    # fresh nodes that widen on most visits: thousands of widened simulations,
+    # several 512-row observation items on the tensor cores and a ragged tail;
+    # every node's observations are compared
+    wl = WL.pw(M=3000, n_nodes=600, C_max=8, prec=WL.PREC_BF16, k_o=1.7, alpha_o=0.45)
+    assert _no_ties(wl.k_o, wl.alpha_o, 3000)
+    wl.N0[:] = 0
+    wl.C0[:] = 0
+    wl.obs0[:] = 0.0
+    tree_dev, tree_o = _trees(V, wl)
+    ell_dev = V.DeviceMLP.from_spec(wl.ell)
+    status, got = _run(V, wl, wl.node, wl.s_next, tree_dev, V.mlp_likelihood(ell_dev), step=5)
+    assert status == V.OK
+    assert got["widened"].sum() > 3 * 512
+    res = O.progressive_widening(tree_o, wl.node, wl.s_next, oracle_mlp(wl.g_Z),
+                                 O.Likelihood(O.LIK_MLP, mlp=oracle_mlp(wl.ell)), wl.d_omega, wl.k_o, wl.alpha_o,
+                                 wl.lam, wl.seed, 5)
+    _check(wl, got, res, tree_dev, tree_o, wl.node, wl.s_next, 5, tol_ell=TOL_BF16, tol_obs=TOL_BF16)
 
 
 def test_pw_invalid_node_sets_status(V):
