@@ -2,8 +2,8 @@
 //
 // A batch of M simulations, each with the action node it reached and its
 // successor state s', is processed in five phases, all on the GPU:
-//   1. group by action node: bitonic sort of the unique 64-bit keys
-//      node << 32 | m (so each node's simulations keep batch order);
+//   1. group by action node: stable radix sort of the 64-bit keys
+//      node << 32 | m on the node (each node's simulations keep batch order);
 //   2. widening decisions: the r-th simulation of a node group widens when
 //      C < C_max and C < k_o (N + r + 1)^alpha_o (FP64), creating branch C;
 //      otherwise it joins branch floor(u C), u the 24-bit Philox uniform of
@@ -13,8 +13,8 @@
 //   3. the observation sampler f_Z (Eq. 5) fills the new branches:
 //      o = f_Z([s'; a; omega_Z]), omega_Z at counter (m, 0, step, stream 3);
 //   4. the likelihood l(s', a, o_branch) of every simulation;
-//   5. group by (node, branch) (a second sort, keys node << 40 | branch << 24
-//      | m) and, one warp per group, the SIR step: log-sum-exp normalisation
+//   5. group by (node, branch) (a second stable radix sort, keys node << 40 |
+//      branch << 24 | m) and, one warp per group, the SIR step: log-sum-exp normalisation
 //      of l / lambda, 2^-52 quantisation, exact prefix sum, systematic
 //      resampling with u0 from counter (node, branch, step, stream 2 block 1).
 #include <math.h>
@@ -28,8 +28,6 @@
 
 namespace voila {
 namespace {
-
-constexpr int kSortChunk = 2048;  // keys sorted in shared memory by one 1024-thread CTA
 
 __global__ void pw_keys_node_kernel(const int32_t* __restrict__ node, int M, int n_pad, int n_nodes,
                                     unsigned long long* __restrict__ keys, WsHeader* hdr) {
@@ -61,56 +59,135 @@ __global__ void pw_keys_branch_kernel(const unsigned long long* __restrict__ key
   }
 }
 
-// Bitonic compare-exchange at distance j >= kSortChunk of merge size k.
-__global__ void bitonic_global_kernel(unsigned long long* keys, int n, int j, int k) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int l = i ^ j;
-  if (i < n && l > i) {
-    const unsigned long long a = keys[i], b = keys[l];
-    const bool up = (i & k) == 0;
-    if ((a > b) == up) {
-      keys[i] = b;
-      keys[l] = a;
-    }
+// Stable LSD radix sort of the 64-bit grouping keys on a derived sort value
+// (8-bit digits; each pass: per-tile digit counts, one exclusive scan over
+// [digit][tile], a stable scatter). Sort value of a key:
+//   by node:          node, invalid or padding keys n_nodes (last);
+//   by (node, branch): node * C_max + branch, invalid or padding n_nodes * C_max.
+// Keys enter in the order whose ties must be kept (batch order for the first
+// sort, node-then-batch order for the second), so the result is ordered by
+// (value, input position).
+constexpr int kRadixWarps = 8, kRadixThreads = 32 * kRadixWarps;
+constexpr int kRadixPerWarp = 256, kRadixTile = kRadixWarps * kRadixPerWarp;  // keys per tile (one CTA)
+
+struct SortSpec {
+  int by_branch;  // 0: by node, 1: by (node, branch)
+  int n_nodes, C_max;
+};
+
+__device__ __forceinline__ unsigned long long sort_value(unsigned long long k, const SortSpec& sp) {
+  if (!sp.by_branch) {
+    const unsigned a = (unsigned)(k >> 32);
+    return a >= (unsigned)sp.n_nodes ? (unsigned long long)sp.n_nodes : (unsigned long long)a;
   }
+  if (k == ~0ull) return (unsigned long long)sp.n_nodes * (unsigned long long)sp.C_max;
+  return (k >> 40) * (unsigned long long)sp.C_max + ((k >> 24) & 0xffffull);
 }
 
-// Merge sizes k = k_first .. k_last (powers of two), distances from j_first
-// (first k) or k / 2 (later ones) down to 1, inside chunks of kSortChunk keys.
-__global__ void __launch_bounds__(1024) bitonic_shared_kernel(unsigned long long* keys, int n, int k_first,
-                                                              int k_last, int j_first) {
-  __shared__ unsigned long long s[kSortChunk];
-  const int base = blockIdx.x * kSortChunk;
-  for (int t = threadIdx.x; t < kSortChunk; t += blockDim.x) s[t] = base + t < n ? keys[base + t] : ~0ull;
+__global__ void __launch_bounds__(kRadixThreads) radix_count_kernel(const unsigned long long* __restrict__ keys, int n,
+                                                                   SortSpec sp, int shift, int* __restrict__ hist,
+                                                                   int tiles) {
+  __shared__ int cnt[256];
+  cnt[threadIdx.x] = 0;
   __syncthreads();
-  for (int k = k_first; k <= k_last; k <<= 1) {
-    for (int j = (k == k_first ? j_first : k >> 1); j > 0; j >>= 1) {
-      const int t = threadIdx.x;  // pair t of the 1024 in the chunk
-      const int i = (t / j) * 2 * j + (t % j), l = i + j;
-      const bool up = ((base + i) & k) == 0;
-      const unsigned long long a = s[i], b = s[l];
-      if ((a > b) == up) {
-        s[i] = b;
-        s[l] = a;
-      }
-      __syncthreads();
-    }
+  const int base = blockIdx.x * kRadixTile;
+  for (int i = base + threadIdx.x; i < base + kRadixTile && i < n; i += kRadixThreads) {
+    const unsigned d = (unsigned)(sort_value(keys[i], sp) >> shift) & 255u;
+    const unsigned peers = __match_any_sync(__activemask(), d);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[d], __popc(peers));
   }
-  for (int t = threadIdx.x; t < kSortChunk; t += blockDim.x)
-    if (base + t < n) keys[base + t] = s[t];
+  __syncthreads();
+  hist[threadIdx.x * tiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-cudaError_t bitonic_sort(unsigned long long* keys, int n, cudaStream_t s) {
-  // n is a power of two
-  const int chunks = (n + kSortChunk - 1) / kSortChunk;
-  const int k_top = n < kSortChunk ? n : kSortChunk;
-  bitonic_shared_kernel<<<chunks, 1024, 0, s>>>(keys, n, 2, k_top, 1);
-  for (int k = 2 * kSortChunk; k <= n; k <<= 1) {
-    for (int j = k >> 1; j >= kSortChunk; j >>= 1)
-      bitonic_global_kernel<<<(n + 255) / 256, 256, 0, s>>>(keys, n, j, k);
-    bitonic_shared_kernel<<<chunks, 1024, 0, s>>>(keys, n, k, k, kSortChunk / 2);
+// Exclusive scan of the [digit][tile] counts, one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) radix_scan_kernel(int* __restrict__ hist, int total) {
+  __shared__ int part[1024];
+  const int per = (total + 1023) / 1024;
+  const int lo = threadIdx.x * per, hi = min(total, lo + per);
+  int sum = 0;
+  for (int i = lo; i < hi; ++i) sum += hist[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the per-thread sums
+    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
   }
-  return cudaGetLastError();
+  int run = part[threadIdx.x] - sum;
+  for (int i = lo; i < hi; ++i) {
+    const int v = hist[i];
+    hist[i] = run;
+    run += v;
+  }
+}
+
+// Stable scatter: warp w of tile t takes keys [t * kRadixTile + w * kRadixPerWarp, +kRadixPerWarp)
+// 32 at a time in order; a key's destination is the scanned count of its digit
+// for the tile, plus the keys of that digit in earlier warps of the tile, plus
+// those earlier in its own warp.
+__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(const unsigned long long* __restrict__ in,
+                                                                     unsigned long long* __restrict__ out, int n,
+                                                                     SortSpec sp, int shift,
+                                                                     const int* __restrict__ hist, int tiles) {
+  __shared__ int wcnt[kRadixWarps][256];
+  __shared__ int boff[256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < kRadixWarps * 256; i += kRadixThreads) (&wcnt[0][0])[i] = 0;
+  boff[threadIdx.x] = hist[threadIdx.x * tiles + blockIdx.x];
+  __syncthreads();
+  constexpr int kIt = kRadixPerWarp / 32;
+  const int base = blockIdx.x * kRadixTile + warp * kRadixPerWarp;
+  unsigned long long kk[kIt];
+  int dd[kIt], lr[kIt];
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int i = base + it * 32 + lane;
+    const bool valid = i < n;
+    kk[it] = valid ? in[i] : 0ull;
+    const int d = valid ? (int)((sort_value(kk[it], sp) >> shift) & 255ull) : 256;  // 256: no key
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    dd[it] = d;
+    lr[it] = d < 256 ? wcnt[warp][d] + __popc(peers & lt) : 0;
+    __syncwarp();
+    if (d < 256 && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {  // per digit: keys of that digit in earlier warps of the tile
+    int run = 0;
+    for (int w = 0; w < kRadixWarps; ++w) {
+      const int v = wcnt[w][threadIdx.x];
+      wcnt[w][threadIdx.x] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kIt; ++it)
+    if (dd[it] < 256) out[boff[dd[it]] + wcnt[warp][dd[it]] + lr[it]] = kk[it];
+}
+
+// Sorts keys[0, n) by their sort value; tmp holds n keys and hist 256 * tiles
+// ints. Returns the buffer that holds the result (keys or tmp).
+unsigned long long* radix_sort(unsigned long long* keys, unsigned long long* tmp, int* hist, int n, SortSpec sp,
+                               cudaStream_t s) {
+  const int tiles = (n + kRadixTile - 1) / kRadixTile;
+  const unsigned long long vmax = sp.by_branch ? (unsigned long long)sp.n_nodes * (unsigned long long)sp.C_max
+                                               : (unsigned long long)sp.n_nodes;
+  unsigned long long* a = keys;
+  unsigned long long* b = tmp;
+  for (int shift = 0; shift < 64 && (vmax >> shift) != 0; shift += 8) {
+    radix_count_kernel<<<tiles, kRadixThreads, 0, s>>>(a, n, sp, shift, hist, tiles);
+    radix_scan_kernel<<<1, 1024, 0, s>>>(hist, 256 * tiles);
+    radix_scatter_kernel<<<tiles, kRadixThreads, 0, s>>>(a, b, n, sp, shift, hist, tiles);
+    unsigned long long* c = a;
+    a = b;
+    b = c;
+  }
+  return a;
 }
 
 struct PwArgs {
@@ -500,7 +577,8 @@ int pow2_at_least(int m) {
 // widened [M] u8 | ell [M] f32 | w [M] f64 | per node: gstart, gend, c0, nwid
 // [n_nodes] i32 and wpos [n_nodes][C_max] i32
 struct PwLayout {
-  size_t tc, tcz, keys1, keys2, cw, list, count, widened, ell, w, gstart, gend, c0, nwid, wpos, thr, total;
+  size_t tc, tcz, keys1, keys2, ktmp, hist, cw, list, count, widened, ell, w, gstart, gend, c0, nwid, wpos, thr,
+      total;
 };
 
 bool pw_tc_likelihood(const voila_likelihood* ell, int d_s, int d_a, int d_o) {
@@ -520,6 +598,8 @@ PwLayout pw_layout(const voila_pw_tree* tree, const voila_mlp* g_Z, const voila_
   }
   L.keys1 = o; o += a256(n_pad * 8);
   L.keys2 = o; o += a256(n_pad * 8);
+  L.ktmp = o; o += a256(n_pad * 8);
+  L.hist = o; o += a256((size_t)256 * ((n_pad + kRadixTile - 1) / kRadixTile) * 4);
   L.cw = o; o += a256((size_t)M * 8);
   L.list = o; o += a256((size_t)M * 4);
   L.count = o; o += 256;
@@ -638,7 +718,17 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
 
   // 1. group by node
   pw_keys_node_kernel<<<grid_of(n_pad, 256), 256, 0, s>>>(node, M, n_pad, tree->n_nodes, keys1, p.hdr);
-  if (cudaGetLastError() != cudaSuccess || bitonic_sort(keys1, n_pad, s) != cudaSuccess) return VOILA_ERR_CUDA;
+  unsigned long long* ktmp = (unsigned long long*)(ws + L.ktmp);
+  int* hist = (int*)(ws + L.hist);
+  if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
+  SortSpec by_node;
+  by_node.by_branch = 0;
+  by_node.n_nodes = tree->n_nodes;
+  by_node.C_max = tree->C_max;
+  unsigned long long* spare = keys1;  // the buffer the first sort leaves free
+  keys1 = radix_sort(keys1, ktmp, hist, M, by_node, s);
+  if (keys1 == spare) spare = ktmp;
+  if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   // 2. widening decisions
   if (cudaMemsetAsync(p.count, 0, sizeof(int32_t), s) != cudaSuccess) return VOILA_ERR_CUDA;
   if (cudaMemsetAsync(p.gstart, 0xff, (size_t)tree->n_nodes * sizeof(int32_t), s) != cudaSuccess)
@@ -697,7 +787,11 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   }
   // 5. group by (node, branch) and resample each group
   pw_keys_branch_kernel<<<grid_of(n_pad, 256), 256, 0, s>>>(keys1, branch_out, M, n_pad, keys2);
-  if (cudaGetLastError() != cudaSuccess || bitonic_sort(keys2, n_pad, s) != cudaSuccess) return VOILA_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
+  SortSpec by_branch = by_node;
+  by_branch.by_branch = 1;
+  keys2 = radix_sort(keys2, spare, hist, M, by_branch, s);
+  if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   pw_resample_kernel<<<(int)(((long long)M * 32 + 255) / 256), 256, 0, s>>>(keys2, p);
   if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   if (widened_out && cudaMemcpyAsync(widened_out, p.widened, (size_t)M, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
