@@ -500,7 +500,10 @@ __global__ void __launch_bounds__(256) pw_resample_kernel(const unsigned long lo
   const unsigned a = (unsigned)(g >> 16), br = (unsigned)(g & 0xffffu);
   auto sim = [&](int i) { return (int)(keys[q + i] & 0xffffffull); };
   // FP64 is scarce on this part: l / lambda as a product with 1 / lambda, one
-  // exp per weight (kept in w between the passes), a product with 1 / Z
+  // exponential per weight, exp(l / lambda - max) <= 1 in FP32 (relative error
+  // below 3e-7; a weight under 2^-53 of the group's largest quantises to zero
+  // either way), kept in w between the passes; the sum Z, the normalisation
+  // (a product with 1 / Z), the 2^-52 quantisation and the scan stay FP64
   const double inv_lam = 1.0 / (double)p.lambda;
   double mx = -INFINITY;
   bool bad = false;
@@ -520,7 +523,7 @@ __global__ void __launch_bounds__(256) pw_resample_kernel(const unsigned long lo
   }
   double Z = 0.0;
   for (int i = lane; i < n; i += 32) {
-    const double e = exp((double)p.ell[sim(i)] * inv_lam - mx);
+    const double e = (double)expf((float)((double)p.ell[sim(i)] * inv_lam - mx));
     p.w[sim(i)] = e;  // read back by this lane below
     Z += e;
   }
