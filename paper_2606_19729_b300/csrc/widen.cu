@@ -216,6 +216,8 @@ struct PwArgs {
   int32_t* nwid;    // [n_nodes] widenings in the batch
   int32_t* wpos;    // [n_nodes][C_max] group ranks of the widening simulations
   long long* thr;   // [C_max] T(C): the smallest visit count n with C < k_o n^alpha_o
+  int32_t* big;     // [M] first sorted positions of the (node, branch) groups left to the warp kernel
+  int32_t* big_count;
   WsHeader* hdr;
 };
 
@@ -478,13 +480,83 @@ __device__ __forceinline__ double wmax(double v) {
   return v;
 }
 
-// Phase 5: one warp per (node, branch) group of the sorted keys.
-__global__ void __launch_bounds__(256) pw_resample_kernel(const unsigned long long* __restrict__ keys, PwArgs p) {
-  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+constexpr int kSmallGroup = 16;  // groups up to this size: one thread each
+
+__device__ __forceinline__ double quantise(double w) { return rint(w * 4503599627370496.0) * 2.220446049250313e-16; }
+
+// Phase 5a: one thread per sorted position; the first position of a (node,
+// branch) group of at most kSmallGroup simulations does the group's SIR step
+// alone (FP64 lanes are scarce: a warp per two-element group would leave most
+// of them idle); the start of a larger group is listed for phase 5b. Same
+// arithmetic as 5b: l / lambda as a product, exp(l / lambda - max) in FP32,
+// FP64 sum, normalisation and 2^-52 quantisation, exact running sum, and the
+// systematic positions p_j = (u0 + j) total / n (FP64, as the oracle) merged
+// against the running sum (the first i with cw_i > p_j, else n - 1).
+__global__ void __launch_bounds__(256) pw_resample_small_kernel(const unsigned long long* __restrict__ keys, PwArgs p) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= p.M) return;
-  const unsigned long long g = keys[q] >> 24;
-  if (keys[q] == ~0ull) return;
+  const unsigned long long k0 = keys[q];
+  if (k0 == ~0ull) return;
+  const unsigned long long g = k0 >> 24;
   if (q > 0 && (keys[q - 1] >> 24) == g) return;
+  int n = 1;
+  while (n <= kSmallGroup && q + n < p.M && (keys[q + n] >> 24) == g) ++n;
+  if (n > kSmallGroup) {
+    p.big[atomicAdd(p.big_count, 1)] = q;
+    return;
+  }
+  auto sim = [&](int i) { return (int)(keys[q + i] & 0xffffffull); };
+  const double inv_lam = 1.0 / (double)p.lambda;
+  double mx = -INFINITY;
+  for (int i = 0; i < n; ++i) {
+    const double lw = (double)p.ell[sim(i)] * inv_lam;
+    if (isnan(lw) || lw == INFINITY) {
+      set_status(p.hdr, VOILA_ERR_NONFINITE, 61);
+      return;
+    }
+    mx = fmax(mx, lw);
+  }
+  if (mx == -INFINITY) {
+    set_status(p.hdr, VOILA_ERR_DEGENERATE, 62);
+    return;
+  }
+  double Z = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double e = (double)expf((float)((double)p.ell[sim(i)] * inv_lam - mx));
+    p.w[sim(i)] = e;
+    Z += e;
+  }
+  const double inv_z = 1.0 / Z;
+  double total = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double qv = quantise(p.w[sim(i)] * inv_z);
+    p.w[sim(i)] = qv;
+    total += qv;  // exact: multiples of 2^-52 summing to at most about 1
+  }
+  const unsigned a = (unsigned)(g >> 16), br = (unsigned)(g & 0xffffu);
+  const uint4 x = philox(make_uint4(a, br, p.step, ctr_word3(VOILA_STREAM_RESAMPLE, p.planner, 1u)), p.key0, p.key1);
+  const double u0 = uniform53(x.x, x.y);
+  int i = 0;
+  double c = p.w[sim(0)];  // cw_i
+  for (int j = 0; j < n; ++j) {
+    const double pj = __ddiv_rn(__dmul_rn(u0 + (double)j, total), (double)n);
+    while (i < n - 1 && !(c > pj)) {
+      ++i;
+      c += p.w[sim(i)];
+    }
+    const int mj = sim(j), ms = sim(i);
+    if (p.idx) p.idx[mj] = ms;
+    for (int d = 0; d < p.d_s; ++d) p.s_out[(size_t)mj * p.d_s + d] = p.s_next[(size_t)ms * p.d_s + d];
+  }
+}
+
+// Phase 5b: one warp per listed (node, branch) group (more than kSmallGroup
+// simulations).
+__global__ void __launch_bounds__(256) pw_resample_kernel(const unsigned long long* __restrict__ keys, PwArgs p) {
+  const int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (wi >= *p.big_count) return;
+  const int q = p.big[wi];
+  const unsigned long long g = keys[q] >> 24;
   int n = 0;  // group size
   while (true) {
     const int e = q + n + lane;
@@ -536,7 +608,7 @@ __global__ void __launch_bounds__(256) pw_resample_kernel(const unsigned long lo
     double qv = 0.0;
     if (i < n) {
       const double wv = p.w[sim(i)] * inv_z;
-      qv = rint(wv * 4503599627370496.0) * 2.220446049250313e-16;
+      qv = quantise(wv);
       p.w[sim(i)] = qv;
     }
     double inc = qv;
@@ -581,7 +653,7 @@ int pow2_at_least(int m) {
 // [n_nodes] i32 and wpos [n_nodes][C_max] i32
 struct PwLayout {
   size_t tc, tcz, keys1, keys2, ktmp, hist, cw, list, count, widened, ell, w, gstart, gend, c0, nwid, wpos, thr,
-      total;
+      big, big_count, total;
 };
 
 bool pw_tc_likelihood(const voila_likelihood* ell, int d_s, int d_a, int d_o) {
@@ -616,6 +688,8 @@ PwLayout pw_layout(const voila_pw_tree* tree, const voila_mlp* g_Z, const voila_
   L.nwid = o; o += a256(nn * 4);
   L.wpos = o; o += a256(nn * (size_t)tree->C_max * 4);
   L.thr = o; o += a256((size_t)tree->C_max * 8);
+  L.big = o; o += a256((size_t)M * 4);
+  L.big_count = o; o += 256;
   L.total = o;
   return L;
 }
@@ -714,6 +788,8 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   p.nwid = (int32_t*)(ws + L.nwid);
   p.wpos = (int32_t*)(ws + L.wpos);
   p.thr = (long long*)(ws + L.thr);
+  p.big = (int32_t*)(ws + L.big);
+  p.big_count = (int32_t*)(ws + L.big_count);
   p.hdr = (WsHeader*)ws;
   unsigned long long* keys1 = (unsigned long long*)(ws + L.keys1);
   unsigned long long* keys2 = (unsigned long long*)(ws + L.keys2);
@@ -795,7 +871,10 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   by_branch.by_branch = 1;
   keys2 = radix_sort(keys2, spare, hist, M, by_branch, s);
   if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
-  pw_resample_kernel<<<(int)(((long long)M * 32 + 255) / 256), 256, 0, s>>>(keys2, p);
+  if (cudaMemsetAsync(p.big_count, 0, sizeof(int32_t), s) != cudaSuccess) return VOILA_ERR_CUDA;
+  pw_resample_small_kernel<<<(M + 255) / 256, 256, 0, s>>>(keys2, p);
+  // at most M / (kSmallGroup + 1) large groups
+  pw_resample_kernel<<<(int)(((long long)(M / (kSmallGroup + 1) + 1) * 32 + 255) / 256), 256, 0, s>>>(keys2, p);
   if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
   if (widened_out && cudaMemcpyAsync(widened_out, p.widened, (size_t)M, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return VOILA_ERR_CUDA;
