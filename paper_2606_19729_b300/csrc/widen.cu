@@ -227,53 +227,60 @@ constexpr long long kNever = 0x7fffffffffffffffLL;  // a threshold no visit coun
 // count n >= 1 with C < k_o * pow(n, alpha_o) (the per-simulation rule, same
 // FP64 expression). The rule is monotone in n, so a node holding C branches
 // widens at its first visit with count >= T(C), whatever node it is: one FP64
-// search per branch count per call instead of one per node. The search starts
-// two below the inverse (C / k_o)^(1 / alpha_o) and walks to the exact
-// boundary in either direction.
+// search per branch count per call instead of one per node. One warp per C:
+// the lanes test 32 visit counts around the inverse (C / k_o)^(1 / alpha_o)
+// at once; a boundary outside that window is bracketed and bisected.
 __global__ void pw_thresholds_kernel(PwArgs p) {
-  const int C = blockIdx.x * blockDim.x + threadIdx.x;
+  const int C = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (C >= p.C_max) return;
   constexpr long long kCap = 4000000000000000000LL;
   auto pred = [&](long long n) { return (double)C < p.k_o * pow((double)n, p.alpha); };
   const double est = pow((double)C / p.k_o, 1.0 / p.alpha);
   long long T = kNever;
   if (est < 1.0e18) {
-    // bracket the boundary (lo: rule false or 0, hi: rule true) by doubling
-    // steps from the estimate, then bisect: bounded whatever the estimate's error
-    long long n = (long long)floor(est) - 2, lo, hi;
-    if (n < 1) n = 1;
-    bool found = true;
-    if (pred(n)) {
-      hi = n;
-      long long d = 1;
-      lo = n - d;
-      while (lo >= 1 && pred(lo)) {
-        hi = lo;
-        d <<= 1;
+    // the 32 lanes test the visit counts around the estimate at once
+    long long n0 = (long long)floor(est) - 15;
+    if (n0 < 1) n0 = 1;
+    const unsigned ball = __ballot_sync(0xffffffffu, pred(n0 + lane));
+    if (ball != 0u && ((ball & 1u) == 0u || n0 == 1)) {
+      T = n0 + __ffs(ball) - 1;  // the rule is monotone: false below, true from here
+    } else if (lane == 0) {
+      // not bracketed by the window: bracket by doubling steps from the
+      // estimate, then bisect (bounded whatever the estimate's error)
+      long long n = n0, lo, hi;
+      bool found = true;
+      if (pred(n)) {
+        hi = n;
+        long long d = 1;
         lo = n - d;
-      }
-      if (lo < 1) lo = 0;
-    } else {
-      lo = n;
-      long long d = 1;
-      hi = n + d;
-      while (hi < kCap && !pred(hi)) {
-        lo = hi;
-        d <<= 1;
+        while (lo >= 1 && pred(lo)) {
+          hi = lo;
+          d <<= 1;
+          lo = n - d;
+        }
+        if (lo < 1) lo = 0;
+      } else {
+        lo = n;
+        long long d = 1;
         hi = n + d;
+        while (hi < kCap && !pred(hi)) {
+          lo = hi;
+          d <<= 1;
+          hi = n + d;
+        }
+        found = hi < kCap;
       }
-      found = hi < kCap;
-    }
-    if (found) {
-      while (hi - lo > 1) {
-        const long long mid = lo + (hi - lo) / 2;
-        if (pred(mid)) hi = mid;
-        else lo = mid;
+      if (found) {
+        while (hi - lo > 1) {
+          const long long mid = lo + (hi - lo) / 2;
+          if (pred(mid)) hi = mid;
+          else lo = mid;
+        }
+        T = hi;
       }
-      T = hi;
     }
   }
-  p.thr[C] = T;
+  if (lane == 0) p.thr[C] = T;
 }
 
 // Phase 2a: first and one-past-last sorted position of every node's group.
@@ -812,7 +819,7 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
   if (cudaMemsetAsync(p.count, 0, sizeof(int32_t), s) != cudaSuccess) return VOILA_ERR_CUDA;
   if (cudaMemsetAsync(p.gstart, 0xff, (size_t)tree->n_nodes * sizeof(int32_t), s) != cudaSuccess)
     return VOILA_ERR_CUDA;
-  pw_thresholds_kernel<<<(tree->C_max + 127) / 128, 128, 0, s>>>(p);
+  pw_thresholds_kernel<<<(int)(((long long)tree->C_max * 32 + 255) / 256), 256, 0, s>>>(p);
   pw_bounds_kernel<<<(M + 255) / 256, 256, 0, s>>>(keys1, p);
   pw_widen_kernel<<<(int)(((long long)tree->n_nodes * 32 + 255) / 256), 256, 0, s>>>(keys1, p);
   pw_assign_kernel<<<(M + 255) / 256, 256, 0, s>>>(keys1, p);
