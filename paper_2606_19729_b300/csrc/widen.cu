@@ -60,8 +60,9 @@ __global__ void pw_keys_branch_kernel(const unsigned long long* __restrict__ key
 }
 
 // Stable LSD radix sort of the 64-bit grouping keys on a derived sort value
-// (8-bit digits; each pass: per-tile digit counts, one exclusive scan over
-// [digit][tile], a stable scatter). Sort value of a key:
+// (8-bit digits; each pass: per-tile digit counts, an exclusive scan over
+// [digit][tile] (done by each scatter tile itself when there are few tiles),
+// a stable scatter). Sort value of a key:
 //   by node:          node, invalid or padding keys n_nodes (last);
 //   by (node, branch): node * C_max + branch, invalid or padding n_nodes * C_max.
 // Keys enter in the order whose ties must be kept (batch order for the first
@@ -130,12 +131,36 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(int* __restrict__ hist
 __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(const unsigned long long* __restrict__ in,
                                                                      unsigned long long* __restrict__ out, int n,
                                                                      SortSpec sp, int shift,
-                                                                     const int* __restrict__ hist, int tiles) {
+                                                                     const int* __restrict__ hist, int tiles,
+                                                                     int scanned) {
   __shared__ int wcnt[kRadixWarps][256];
   __shared__ int boff[256];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < kRadixWarps * 256; i += kRadixThreads) (&wcnt[0][0])[i] = 0;
-  boff[threadIdx.x] = hist[threadIdx.x * tiles + blockIdx.x];
+  if (scanned) {
+    boff[threadIdx.x] = hist[threadIdx.x * tiles + blockIdx.x];
+  } else {
+    // few tiles: this tile's offsets straight from the counts (keys of smaller
+    // digits in all tiles, plus keys of its digit in earlier tiles)
+    const int d = threadIdx.x;
+    int tot = 0, pre = 0;
+    for (int t = 0; t < tiles; ++t) {
+      const int v = hist[d * tiles + t];
+      tot += v;
+      if (t < (int)blockIdx.x) pre += v;
+    }
+    boff[d] = tot;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {  // inclusive scan of the digit totals
+      const int v = d >= o ? boff[d - o] : 0;
+      __syncthreads();
+      boff[d] += v;
+      __syncthreads();
+    }
+    const int incl = boff[d];
+    __syncthreads();
+    boff[d] = incl - tot + pre;
+  }
   __syncthreads();
   constexpr int kIt = kRadixPerWarp / 32;
   const int base = blockIdx.x * kRadixTile + warp * kRadixPerWarp;
@@ -181,8 +206,9 @@ unsigned long long* radix_sort(unsigned long long* keys, unsigned long long* tmp
   unsigned long long* b = tmp;
   for (int shift = 0; shift < 64 && (vmax >> shift) != 0; shift += 8) {
     radix_count_kernel<<<tiles, kRadixThreads, 0, s>>>(a, n, sp, shift, hist, tiles);
-    radix_scan_kernel<<<1, 1024, 0, s>>>(hist, 256 * tiles);
-    radix_scatter_kernel<<<tiles, kRadixThreads, 0, s>>>(a, b, n, sp, shift, hist, tiles);
+    const int scanned = tiles > 64;  // else each scatter tile reads the counts itself
+    if (scanned) radix_scan_kernel<<<1, 1024, 0, s>>>(hist, 256 * tiles);
+    radix_scatter_kernel<<<tiles, kRadixThreads, 0, s>>>(a, b, n, sp, shift, hist, tiles, scanned);
     unsigned long long* c = a;
     a = b;
     b = c;

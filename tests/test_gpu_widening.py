@@ -124,8 +124,9 @@ def test_pw_gaussian_two_steps_and_cap(V):
     assert tree_dev.C.cpu().numpy().max() <= 5
 
 
-def test_pw_full_batch_sampled_nodes(V):
-    wl = WL.pw()
+@pytest.mark.parametrize("M", [65536, 150000])  # 150000: more than 64 radix tiles (the separate scan)
+def test_pw_full_batch_sampled_nodes(V, M):
+    wl = WL.pw(M=M)
     assert _no_ties(wl.k_o, wl.alpha_o, 200 + wl.M)
     tree_dev, tree_o = _trees(V, wl)
     ell_dev = V.DeviceMLP.from_spec(wl.ell)
