@@ -139,8 +139,8 @@ def test_pw_full_batch_sampled_nodes(V, M):
     n1 = (wl.N0 + counts).astype(np.float64)
     expect = np.where(counts > 0, np.minimum(wl.C_max, np.ceil(wl.k_o * np.power(n1, wl.alpha_o))), wl.C0)
     np.testing.assert_array_equal(tree_dev.C.cpu().numpy(), expect)
-    # the busiest node, a quiet one and three random ones, replayed by the oracle
-    nodes = sorted({int(np.argmax(counts)), int(np.nonzero(counts == 1)[0][0])}
+    # the busiest node, the quietest visited one and three random ones, replayed by the oracle
+    nodes = sorted({int(np.argmax(counts)), int(np.argmin(np.where(counts > 0, counts, M + 1)))}
                    | set(np.random.default_rng(3).choice(np.nonzero(counts)[0], 3, replace=False).tolist()))
     sel = np.isin(wl.node, nodes)
     res = O.progressive_widening(tree_o, wl.node[sel], wl.s_next[sel], oracle_mlp(wl.g_Z),
