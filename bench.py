@@ -55,6 +55,19 @@ def parse_args():
     return ap.parse_args()
 
 
+def warm_until(fn, seconds: float) -> None:
+    """Repeats fn (at least once) until `seconds` of wall time have passed, so a
+    short timed region starts with the GPU at its working clock (a sub-ms call
+    timed right after an idle GPU otherwise reads up to 2x slow)."""
+    import torch
+    t0 = time.perf_counter()
+    while True:
+        fn()
+        torch.cuda.synchronize()
+        if time.perf_counter() - t0 >= seconds:
+            return
+
+
 def max_over_ranks(value: float, world: int, device) -> float:
     """The slowest rank's time (the whole-job clock) across `world` replicas."""
     if world <= 1:
@@ -607,8 +620,8 @@ def run_infonce(args, rank, world, local):
 
     for _ in range(args.warmup):
         fwd()
-    torch.cuda.synchronize()
-    reps = max(args.steps, 20)
+    warm_until(fwd, 0.3)
+    reps = max(args.steps, 50)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
     with Clocks(local) as clk:
         for e0, e1 in ev:
@@ -630,7 +643,7 @@ def run_infonce(args, rank, world, local):
     except OSError:
         pass
     peak = peaks.get("bf16_tflops_sustained", 1400.0)
-    # training step of the likelihood (CUDA cores), a few steps
+    # training step of the likelihood (tensor cores for the BF16 planning shapes), a few steps
     master = torch.cat([torch.cat([w.float().reshape(-1), b.reshape(-1)]) for w, b in zip(ell.W, ell.b)])
     m, v = torch.zeros_like(master), torch.zeros_like(master)
     sws = V.alloc_workspace(V.voila_infonce_step_workspace_size(ell, B))
@@ -714,9 +727,9 @@ def run_pw(args, rank, world, local):
     for _ in range(args.warmup):
         restore()
         call()
-    torch.cuda.synchronize()
+    warm_until(lambda: (restore(), call()), 0.3)
     assert V.workspace_status(ws) == V.OK
-    reps = max(args.steps, 20)
+    reps = max(args.steps, 100)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
     with Clocks(local) as clk:
         for e0, e1 in ev:
@@ -739,21 +752,26 @@ def run_pw(args, rank, world, local):
             "ms_per_step": 1e3 * call_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16", "data": "synthetic (seeded tree and simulations, random-init f_Z and likelihood)",
             "config": {"workload": f"pw: M={M} simulations over {wl.n_nodes} action nodes (skewed), C_max={wl.C_max}, "
-                                   f"k_o={wl.k_o}, alpha_o={wl.alpha_o}; f_Z 18x256x256x256x6 (BF16 weights, FP32 "
-                                   "CUDA cores) and likelihood 16x256x256x256x1 SiLU (BF16, tensor cores)"},
+                                   f"k_o={wl.k_o}, alpha_o={wl.alpha_o}; f_Z 18x256x256x256x6 and likelihood "
+                                   "16x256x256x256x1 SiLU (BF16, tensor cores)"},
             "widened_per_call": widened,
             "roofline": {"bound": "alu", "achieved": flops / call_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                          "frac": flops / call_s / 1e12 / peak, "traffic": None,
                          "kernel": "voila_progressive_widening (whole call; likelihood MLP dominates the FLOPs)",
                          "peak_kind": "FP32 FMA lanes x max SM clock (derived)"},
             "gpu_launches": None, "clocks": clk.summary()}
-    n_pad = 2
-    while n_pad < M:
-        n_pad *= 2
-    sort_launches = 1 + sum(int(math.log2(k)) - 10 for k in (2 ** e for e in range(12, int(math.log2(n_pad)) + 1)))
-    # keys, sort, group bounds, widen, assign, observe, likelihood (pack, fused-output
-    # pack, pair kernel), keys, sort, resample
-    line["gpu_launches"] = reps * (10 + 2 * sort_launches)
+    def radix_passes(vmax):
+        n = 0
+        while vmax >> (8 * n):
+            n += 1
+        return n
+    tiles = (M + 2047) // 2048
+    per_pass = 2 + (1 if tiles > 64 else 0)  # counts, (scan,) scatter
+    passes = radix_passes(wl.n_nodes) + radix_passes(wl.n_nodes * wl.C_max)
+    # keys, 2 sorts, thresholds, group bounds, widen, assign, observation sampler (pack,
+    # kernel), likelihood (pack, fused-output pack, kernel), keys, small- and large-group
+    # resampling
+    line["gpu_launches"] = reps * (13 + per_pass * passes)
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import voila_oracle as O
         sel = np.ones(M, bool)
