@@ -232,6 +232,55 @@ __device__ __forceinline__ void epi_cols32(float* u, const float* bl, const floa
     return;
   }
   using ptx::f2_pack;
+  if (SCALE && !OUT_FP8 && act == VOILA_ACT_SILU) {  // E4M3 layer, BF16 output: one pass
+    uint8_t* slab = A + (c >> 1) * (128 * 128);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t wv[4];
+#pragma unroll
+      for (int k2 = 0; k2 < 2; ++k2) {
+        const int i = 8 * j + 4 * k2;
+        const float4 b = *reinterpret_cast<const float4*>(bl + 32 * c + i);
+        const float4 sc = *reinterpret_cast<const float4*>(sl + 32 * c + i);
+        wv[2 * k2] = silu2_bf16(ptx::f2_fma(f2_pack(u[i], u[i + 1]), f2_pack(sc.x, sc.y), f2_pack(b.x, b.y)));
+        wv[2 * k2 + 1] =
+            silu2_bf16(ptx::f2_fma(f2_pack(u[i + 2], u[i + 3]), f2_pack(sc.z, sc.w), f2_pack(b.z, b.w)));
+      }
+      *reinterpret_cast<uint4*>(slab + r * 128 + ((((c & 1) * 4 + j) ^ (r & 7)) << 4)) =
+          make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    }
+    return;
+  }
+  if (OUT_FP8 && act == VOILA_ACT_SILU) {
+    // E4M3 output in one pass: (channel scale and) bias, SiLU, four values per
+    // 32-bit word, sixteen per 16-byte chunk (128 K per 128-byte swizzled row)
+    uint8_t* slab = A + (c >> 2) * (128 * 128);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      uint32_t wv[4];
+#pragma unroll
+      for (int k4 = 0; k4 < 4; ++k4) {
+        const int i = 16 * j + 4 * k4;
+        const float4 b = *reinterpret_cast<const float4*>(bl + 32 * c + i);
+        uint64_t x01, x23;
+        if (SCALE) {
+          const float4 sc = *reinterpret_cast<const float4*>(sl + 32 * c + i);
+          x01 = ptx::f2_fma(f2_pack(u[i], u[i + 1]), f2_pack(sc.x, sc.y), f2_pack(b.x, b.y));
+          x23 = ptx::f2_fma(f2_pack(u[i + 2], u[i + 3]), f2_pack(sc.z, sc.w), f2_pack(b.z, b.w));
+        } else {
+          x01 = ptx::f2_add(f2_pack(u[i], u[i + 1]), f2_pack(b.x, b.y));
+          x23 = ptx::f2_add(f2_pack(u[i + 2], u[i + 3]), f2_pack(b.z, b.w));
+        }
+        float y0, y1, y2, y3;
+        ptx::f2_unpack(silu2(x01), y0, y1);
+        ptx::f2_unpack(silu2(x23), y2, y3);
+        wv[k4] = ptx::pack_e4m3x4(y0, y1, y2, y3);
+      }
+      *reinterpret_cast<uint4*>(slab + r * 128 + ((((c & 3) * 2 + j) ^ (r & 7)) << 4)) =
+          make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    }
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < 8; ++j) {  // transformed in place (register pressure)
     const float4 b = *reinterpret_cast<const float4*>(bl + 32 * c + 4 * j);
