@@ -46,7 +46,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-seqs", type=int, default=16, help="sequences for the FP32-form comparison (0: skip)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32/FP8 form comparison")
-    ap.add_argument("--sweep-err-seqs", type=int, default=2, help="sequences of the sweep's FP64 error sample")
+    ap.add_argument("--sweep-err-seqs", type=int, default=64, help="sequences of the sweep's FP64 error subset")
+    ap.add_argument("--sweep-err-N", type=int, default=256, help="particles of the sweep's FP64 error subset")
     ap.add_argument("--distill-cpu-rows", type=int, default=12288, help="rows of the distillation oracle sample")
     ap.add_argument("--B", type=int, default=None, help="override the distillation batch (profiling runs)")
     ap.add_argument("--N", type=int, default=None, help="override particles (profiling runs)")
@@ -388,7 +389,8 @@ def run_sweep(args, rank, world, local):
     """Precision sweep (state 12, action 3, latent 16, 4x512 SiLU generator, GOAL
     reward, 16384 x 2048 x 25): FP32 (CUDA cores, on a slice of sequences), BF16 and
     FP8 (tensor cores, full workload), each form's return error against the FP64
-    oracle on the first `--sweep-err-seqs` sequences."""
+    oracle on a subset: the first `--sweep-err-seqs` sequences and `--sweep-err-N`
+    particles, run by every form and by the oracle as the same smaller problem."""
     import torch
     from paper_2606_19729_b300 import voila as V
     from paper_2606_19729_b300 import workloads as WL
@@ -424,18 +426,27 @@ def run_sweep(args, rank, world, local):
         forms[name] = {"value": wl.N * K * wl.H / sec, "unit": UNIT, "rollout_ms": 1e3 * sec,
                        "achieved_tflops": fpt * wl.N * K * wl.H / sec / 1e12,
                        "sample": f"{K} of {wl.K} sequences x {wl.N} particles x H={wl.H}", "clocks": clk.summary()}
-        Js[name] = J[: args.sweep_err_seqs].cpu().numpy()
+        # the error subset, as its own smaller problem (same counters as the oracle's)
+        Ns, Ks = min(args.sweep_err_N, wl.N), min(args.sweep_err_seqs, wl.K)
+        Jsub = torch.empty(Ks, dtype=torch.float64, device="cuda")
+        wss = V.alloc_workspace(V.voila_rollout_workspace_size(g, R, Ns, Ks, wl.H))
+        V.voila_rollout(g, R, parts[:Ns].contiguous(), None, acts[:Ks].contiguous(), wl.d_omega, wl.gamma, wl.seed, 0,
+                        Jsub, None, None, wss)
+        torch.cuda.synchronize()
+        assert V.workspace_status(wss) == V.OK
+        Js[name] = Jsub.cpu().numpy()
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import voila_oracle as O
-        ks = list(range(args.sweep_err_seqs))
+        Ns, Ks = min(args.sweep_err_N, wl.N), min(args.sweep_err_seqs, wl.K)
         t0 = time.perf_counter()
-        Jo, _ = O.rollout(O.MLP(wl.g_T.W, wl.g_T.b, wl.g_T.act), O.Reward(O.REWARD_GOAL, wl.goal), wl.particles,
-                          wl.actions, wl.d_omega, wl.gamma, wl.seed, k_index=ks)
+        Jo, _ = O.rollout(O.MLP(wl.g_T.W, wl.g_T.b, wl.g_T.act), O.Reward(O.REWARD_GOAL, wl.goal),
+                          wl.particles[:Ns], wl.actions[:Ks], wl.d_omega, wl.gamma, wl.seed)
         dt = time.perf_counter() - t0
         for name in forms:
             forms[name]["err_vs_fp64"] = float(np.max(np.abs(Js[name] - Jo)) / np.max(np.abs(Jo)))
-        cpu = {"value": len(ks) * wl.N * wl.H / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-               "sample": f"FP64 oracle rollout of {len(ks)} sequences x {wl.N} particles x H={wl.H} in {dt:.1f} s"}
+            forms[name]["err_sample"] = f"J of {Ks} sequences x {Ns} particles x H={wl.H}, max abs error / max |J|"
+        cpu = {"value": Ks * Ns * wl.H / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": f"FP64 oracle rollout of {Ks} sequences x {Ns} particles x H={wl.H} in {dt:.1f} s"}
     else:
         cpu = None
     peaks = {}
