@@ -949,6 +949,7 @@ def main():
     fpt = flops_per_transition(wl)
     roll_avg_s = sum(roll_ms) / len(roll_ms) / 1e3
     traffic = None
+    tensor_pipe = None
     try:  # ncu DRAM bytes per launch, valid only for the kernel source they were taken on
         import hashlib
         with open(os.path.join(ROOT, "profiles", "rollout_tc_mid_bf16_traffic.json")) as f:
@@ -958,6 +959,7 @@ def main():
         if (hashlib.sha256(src).hexdigest()[:16] == prof["source_sha16"] and wl.name == "mid_bf16"
                 and (wl.N, wl.K, wl.H) == (4096, 1024, 20)):
             traffic = prof["dram_read_bytes"] + prof["dram_write_bytes"]
+            tensor_pipe = prof.get("tensor_pipe_pct")
     except (OSError, KeyError, ValueError):
         traffic = None
     if wl.prec == 1:
@@ -966,6 +968,7 @@ def main():
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "rollout_tc_kernel (voila_rollout call: weight pack + rollout + return reduction)",
+                "tensor_pipe_pct_ncu": tensor_pipe,
                 "peak_source": "measured bf16 sustained (MEASURED_PEAKS.json)" if peaks else "fallback"}
     else:
         achieved = fpt * trans_per_step / roll_avg_s / 1e12
