@@ -88,28 +88,33 @@ __global__ void __launch_bounds__(kSimtThreads) pairs_simt_kernel(MlpDev m, cons
 }
 
 // Row i: lse_i, diag_i = L_ii - lse_i and (optionally) G_i. = (softmax - e_i) / B.
-__global__ void __launch_bounds__(256) infonce_rows_kernel(const float* __restrict__ L, int B,
-                                                           double* __restrict__ lse_out, double* __restrict__ diag,
-                                                           float* __restrict__ G) {
-  __shared__ double red[33];
-  const int i = blockIdx.x;
+// One warp per row (eight rows per CTA): the maximum in FP32 (exact), the sum
+// of exp(L_ij - max) (FP32 exponentials) in FP64 per lane, then a fixed-order
+// warp reduction, so every row's sum has one order.
+constexpr int kRowsPerCta = 8;
+__global__ void __launch_bounds__(32 * kRowsPerCta) infonce_rows_kernel(const float* __restrict__ L, int B,
+                                                                       double* __restrict__ lse_out,
+                                                                       double* __restrict__ diag,
+                                                                       float* __restrict__ G) {
+  const int i = blockIdx.x * kRowsPerCta + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= B) return;
   const float* Li = L + (size_t)i * B;
-  double m = -INFINITY;
-  for (int j = threadIdx.x; j < B; j += blockDim.x) m = fmax(m, (double)Li[j]);
-  m = block_max(m, red);
-  const float mf = (float)m;  // L is FP32, so its maximum is exact in FP32
+  float mf = -INFINITY;
+  for (int j = lane; j < B; j += 32) mf = fmaxf(mf, Li[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mf = fmaxf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
   double z = 0.0;
-  for (int j = threadIdx.x; j < B; j += blockDim.x) z += (double)expf(Li[j] - mf);
-  z = block_sum(z, red);
-  const double lse = m + log(z);
-  if (threadIdx.x == 0) {
+  for (int j = lane; j < B; j += 32) z += (double)expf(Li[j] - mf);
+  z = warp_sum(z);
+  const double lse = (double)mf + log(z);
+  if (lane == 0) {
     if (lse_out) lse_out[i] = lse;
     diag[i] = (double)Li[i] - lse;
   }
   if (G) {
     const float inv_b = 1.0f / (float)B, lf = (float)lse;
     float* Gi = G + (size_t)i * B;
-    for (int j = threadIdx.x; j < B; j += blockDim.x) Gi[j] = (expf(Li[j] - lf) - (j == i ? 1.0f : 0.0f)) * inv_b;
+    for (int j = lane; j < B; j += 32) Gi[j] = (expf(Li[j] - lf) - (j == i ? 1.0f : 0.0f)) * inv_b;
   }
 }
 
@@ -166,7 +171,7 @@ int grid_for(long long n, int per) {
 
 voila_status lse_and_loss(const float* L, int B, double* lse_out, double* diag, float* G, double* loss,
                           cudaStream_t s) {
-  infonce_rows_kernel<<<B, 256, 0, s>>>(L, B, lse_out, diag, G);
+  infonce_rows_kernel<<<(B + kRowsPerCta - 1) / kRowsPerCta, 32 * kRowsPerCta, 0, s>>>(L, B, lse_out, diag, G);
   infonce_loss_kernel<<<1, 1024, 0, s>>>(diag, B, loss);
   return cudaGetLastError() == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
