@@ -987,7 +987,10 @@ def main():
                 [e[0].elapsed_time(e[1]) for e in ev]),
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 8 * args.steps,  # propose, resample, pack, fused-output pack, rollout, reduce, argmax, backup
+            # BF16: weight pack, fused-output pack, tensor-core proposal, resample (belief update); weight
+            # pack, fused-output pack, rollout, reduce + argmax (rollout); backup. FP32: proposal, resample,
+            # rollout, reduce + argmax, backup
+            "gpu_launches": (10 if wl.prec == 1 else 6) * args.steps,
             "clocks": clk.summary()}
     J8 = None
     if wl.prec == 1 and rank == 0 and not args.no_forms:

@@ -357,6 +357,11 @@ voila_status voila_belief_update_workspace_size(const voila_mlp* g_T, const voil
   off = align_up(off + (size_t)N * d_s * sizeof(float));
   off = align_up(off + (size_t)N * sizeof(double));
   off = align_up(off + (size_t)N * sizeof(double));
+  // BF16 generator and likelihood of the tensor-core proposal's shapes: room
+  // for its packed weights (placed at the next 1024-byte boundary)
+  if (ell && ell->kind == VOILA_LIK_MLP && valid_mlp(ell->mlp) && g_T->dims[0] == 18 && d_s == 8 &&
+      tc_propose_supported(g_T, ell->mlp, 8, 2, 8, 6))
+    off = align_up(off + 1024 + tc_propose_scratch_bytes(g_T, ell->mlp));  // + slack for the alignment
   *bytes = off;
   return VOILA_OK;
 }
@@ -404,7 +409,19 @@ voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* e
   double* ellv = (double*)(ws + off);
   off = align_up(off + (size_t)N * sizeof(double));
   double* C = (double*)(ws + off);
+  off = align_up(off + (size_t)N * sizeof(double));
   if (cudaMemsetAsync(ws, 0, sizeof(WsHeader), s) != cudaSuccess) return VOILA_ERR_CUDA;
+  uint32_t key0, key1;
+  philox_key(seed, key0, key1);
+  // BF16 MLPs of the supported shapes: the proposal runs on the tensor cores
+  // (the generator step and the likelihood in one kernel)
+  const bool use_tc = ell->kind == VOILA_LIK_MLP && tc_propose_supported(g_T, ell->mlp, d_s, d_a, d_omega, d_o);
+  if (use_tc) {
+    char* scratch = (char*)(((uintptr_t)(ws + off) + 1023) & ~(uintptr_t)1023);
+    if (voila_status st = tc_belief_propose(g_T, ell->mlp, particles_in, action, obs, N, key0, key1, step,
+                                            planner_id, s_prop, ellv, (WsHeader*)ws, scratch, s))
+      return st;
+  }
 
   BeliefArgs b;
   memset(&b, 0, sizeof(b));
@@ -426,7 +443,8 @@ voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* e
   b.s_prop = s_prop;
   b.ell = ellv;
   b.ld = simt_ld(maxw);
-  if (cudaError_t e = launch_belief_propose(b, s)) return cuda_status(e);
+  if (!use_tc)
+    if (cudaError_t e = launch_belief_propose(b, s)) return cuda_status(e);
 
   ResampleArgs r;
   memset(&r, 0, sizeof(r));

@@ -59,7 +59,9 @@ constexpr long long kSpinLimit = 4000000000LL;  // ~2 s of SM clock per wait
 // the InfoNCE objective (one evaluation, H = 1).
 // ... and the observation sampler of progressive widening (rows = the listed
 // widened simulations, one evaluation of f_Z, outputs scattered to the tree).
-constexpr int kModeRollout = 0, kModeDdim = 1, kModePairs = 2, kModeObserve = 3;
+// ... and the proposal of the belief update (rows = particles: one generator
+// step, then the likelihood of the proposal, its scalar output fused).
+constexpr int kModeRollout = 0, kModeDdim = 1, kModePairs = 2, kModeObserve = 3, kModePropose = 4;
 
 struct TcLayer {
   int Kp;           // input width rounded up to 16 (MMA K steps of 16)
@@ -144,6 +146,14 @@ struct TcParams {
   float* obs_out;
   int obs_d;
   uint32_t obs_step, obs_planner;
+  // belief proposal (Sec. 3 SIR step): row i = particle i, s'_i = g_T([s_i; a;
+  // omega_T]) with the noise of stream VOILA_STREAM_BELIEF_OMEGA at counter
+  // (i, 0, prop_step), s'_i to prop_s, l([s'_i; a; o]) to prop_ell (the
+  // likelihood is the second MLP, in the reward head's place); o has 6 values
+  const float* prop_obs;
+  float* prop_s;
+  double* prop_ell;
+  uint32_t prop_step;
 };
 
 __device__ __forceinline__ int item_planner(const TcParams& p, long long it) {
@@ -456,7 +466,8 @@ __device__ __forceinline__ void pack_state(uint32_t* s_pk, const float* s) {
 // from stream VOILA_STREAM_ROLLOUT_OMEGA at counter (n, k, t).
 template <int DA, int DW>
 __device__ __forceinline__ void draw_tail(uint32_t* tail, const float* act, uint32_t k0, uint32_t k1, uint32_t n,
-                                          uint32_t k, uint32_t t, uint32_t planner) {
+                                          uint32_t k, uint32_t t, uint32_t planner,
+                                          uint32_t stream = VOILA_STREAM_ROLLOUT_OMEGA) {
   constexpr int TE = 2 * ((DA + DW + 1) / 2);
   float e[TE];
 #pragma unroll
@@ -465,7 +476,7 @@ __device__ __forceinline__ void draw_tail(uint32_t* tail, const float* act, uint
   for (int i = 0; i < DA; ++i) e[i] = __ldg(act + i);
 #pragma unroll
   for (int b = 0; b < (DW + 3) / 4; ++b) {
-    const float4 z = normal4(k0, k1, n, k, t, VOILA_STREAM_ROLLOUT_OMEGA, planner, (uint32_t)b);
+    const float4 z = normal4(k0, k1, n, k, t, stream, planner, (uint32_t)b);
     if (4 * b + 0 < DW) e[DA + 4 * b + 0] = z.x;
     if (4 * b + 1 < DW) e[DA + 4 * b + 1] = z.y;
     if (4 * b + 2 < DW) e[DA + 4 * b + 2] = z.z;
@@ -510,6 +521,25 @@ __device__ __forceinline__ void write_rew_row(uint8_t* A, int r, const uint32_t*
 #pragma unroll
   for (int i = 0; i < (DA + 1) / 2; ++i) x[DS / 2 + i] = a_pk[i];
   store_words<KP>(A, r, x);
+}
+
+// Likelihood input row [s'; a; o] (belief proposal), o as BF16 pairs, zero padded.
+template <int DS, int DA>
+__device__ __forceinline__ void write_lik_row(uint8_t* A, int r, const uint32_t* s_pk, const float* a,
+                                              const float* o) {
+  constexpr int DO = 6;
+  constexpr int KP = (DS + DA + DO + 15) / 16 * 16;
+  float x[KP];
+#pragma unroll
+  for (int i = 0; i < KP; ++i) x[i] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < DA; ++i) x[DS + i] = a[i];
+#pragma unroll
+  for (int i = 0; i < DO; ++i) x[DS + DA + i] = o[i];
+  uint32_t w[KP / 2];
+#pragma unroll
+  for (int i = 0; i < KP / 2; ++i) w[i] = 2 * i < DS ? s_pk[i] : ptx::pack_bf16x2(x[2 * i], x[2 * i + 1]);
+  store_words<KP>(A, r, w);
 }
 
 // Teacher input row of the DDIM sampler, in the column order the packed first
@@ -581,6 +611,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
   static_assert(!DDIM || (WIDE && !F8 && DS == 8 && DA == 10 && DW == 0), "DDIM sampler layout");
   static_assert(!PAIRS || (!WIDE && !F8 && DS == 8 && DA == 2 && DW == 6), "likelihood pair layout");
   static_assert(!OBS || (!WIDE && !F8), "observation rows use the two-tile kernel");
+  constexpr bool PROP = MODE == kModePropose;
+  static_assert(!PROP || (!WIDE && !F8 && DS == 8 && DA == 2 && DW == 8), "belief proposal layout");
   // work items of the launch: the observation rows are counted on the device
   long long total_items = p.total_items;
   if constexpr (OBS) {
@@ -1062,7 +1094,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
 #pragma unroll
         for (int i = 0; i < DS; ++i) s0[i] = valid ? __ldg(PL.particles + (size_t)n * DS + i) : 0.0f;
         pack_state<DS>(s_pk, s0);
-        draw_tail<DA, DW>(tn, act_row, p.key0, p.key1, n, k, 0u, PL.planner);
+        if constexpr (PROP)
+          draw_tail<DA, DW>(tn, act_row, p.key0, p.key1, n, 0u, p.prop_step, PL.planner, VOILA_STREAM_BELIEF_OMEGA);
+        else
+          draw_tail<DA, DW>(tn, act_row, p.key0, p.key1, n, k, 0u, PL.planner);
         write_gen_row<DS, DA, DW>(Aown, r, s_pk, tn);
         tail_actions<DA>(a_pk, tn);
       }
@@ -1138,6 +1173,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 if constexpr (PAIRS) {
                   if (valid) p.pair_out[row] = val;
                   if (has_next && t == H - 1) write_pair_row(p, A, r, row_next, row_next < PL.rows);
+                } else if constexpr (PROP) {
+                  if (valid) p.prop_ell[row] = (double)val;
                 } else if (t + 1 < H) {
                   r_pend = val;
                   write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
@@ -1222,6 +1259,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                                       PL.planner);
                     write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
                   }
+                } else if constexpr (PROP) {
+                  if (valid)
+                    for (int i = 0; i < DS; ++i) p.prop_s[(size_t)row * DS + i] = s1[i];
+                  float av[DA], ov[6];
+#pragma unroll
+                  for (int i = 0; i < DA; ++i) av[i] = __ldg(act_row + i);
+#pragma unroll
+                  for (int i = 0; i < 6; ++i) ov[i] = __ldg(p.prop_obs + i);
+                  write_lik_row<DS, DA>(A, r, s_pk, av, ov);
                 } else {
                   write_rew_row<DS, DA>(A, r, s_pk, a_pk);
                 }
@@ -1250,7 +1296,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         }
       }
       if constexpr (!PAIRS) {
-        if (!OBS && owner && valid && ok) PL.G[row] = Gacc;
+        if (!OBS && !PROP && owner && valid && ok) PL.G[row] = Gacc;
       }
     }
   }
@@ -1901,6 +1947,96 @@ voila_status tc_observe_rows(const voila_mlp* g_Z, const float* S, const float* 
   const long long nclusters = p.total_items < nsm / 2 ? p.total_items : nsm / 2;
   const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total + p.fuse_total + (p.fuse_total ? 1024 : 0));
   const cudaError_t e = launch_tc<8, 2, 8, false, false, kModeObserve>(p, smem, nclusters, s);
+  return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
+}
+
+bool tc_propose_supported(const voila_mlp* g_T, const voila_mlp* ell, int d_s, int d_a, int d_omega, int d_o) {
+  if (!g_T || !ell || g_T->prec != VOILA_BF16 || ell->prec != VOILA_BF16) return false;
+  if (d_s != 8 || d_a != 2 || d_omega != 8 || d_o != 6) return false;
+  if (g_T->dims[0] != 18 || g_T->dims[g_T->n_layers] != 8 || ell->dims[0] != 16 || ell->dims[ell->n_layers] != 1)
+    return false;
+  voila_reward R;
+  memset(&R, 0, sizeof(R));
+  R.kind = VOILA_REWARD_MLP;
+  R.mlp = ell;
+  Plan pl = make_plan(g_T, &R);
+  return pl.ok && !pl.wide && pl.p.layers[pl.p.n_total - 1].fuse_out;
+}
+
+size_t tc_propose_scratch_bytes(const voila_mlp* g_T, const voila_mlp* ell) {
+  voila_reward R;
+  memset(&R, 0, sizeof(R));
+  R.kind = VOILA_REWARD_MLP;
+  R.mlp = ell;
+  Plan pl = make_plan(g_T, &R);
+  return pl.ok ? pl.total : 0;
+}
+
+voila_status tc_belief_propose(const voila_mlp* g_T, const voila_mlp* ell, const float* particles, const float* action,
+                               const float* obs, long long N, uint32_t key0, uint32_t key1, uint32_t step,
+                               uint32_t planner, float* s_prop, double* ell_out, WsHeader* hdr, void* scratch,
+                               cudaStream_t s) {
+  voila_reward R;
+  memset(&R, 0, sizeof(R));
+  R.kind = VOILA_REWARD_MLP;
+  R.mlp = ell;
+  Plan pl = make_plan(g_T, &R);
+  if (!pl.ok || pl.wide) return VOILA_ERR_UNSUPPORTED;
+  if ((uintptr_t)scratch % 1024) return VOILA_ERR_WORKSPACE;
+  if (N <= 0) return VOILA_OK;
+  TcParams& p = pl.p;
+  TcPlanner& q = p.pl[0];
+  q.particles = particles;
+  q.actions = action;  // one action for every row (sequence index 0)
+  q.G = nullptr;
+  q.rows = N;
+  q.N = (int)N;
+  q.H = 1;
+  q.planner = planner;
+  p.P = 1;
+  p.total_items = (N + kSuperRows - 1) / kSuperRows;
+  p.item_end[0] = p.total_items;
+  uint8_t* wst = (uint8_t*)scratch;
+  float* bias_all = (float*)(wst + (pl.wbytes + 1023) / 1024 * 1024);
+  pl.pack.wout = wst;
+  pl.pack.bout = bias_all;
+  {
+    const long long total = pl.pack.elems_end[pl.pack.n - 1];
+    long long blocks = (total + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    pack_kernel<<<(int)blocks, 256, 0, s>>>(pl.pack);
+    if (pl.pack.fuse_n > 0) fuse_pack_kernel<<<1, 256, 0, s>>>(pl.pack);
+    if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return VOILA_ERR_CUDA;
+  for (int l = 0; l < p.n_total; ++l) {
+    const cuuint64_t gdim[2] = {128, (cuuint64_t)pl.total_rows};  // bytes
+    const cuuint64_t gstride[1] = {128};
+    const cuuint32_t box[2] = {128, (cuuint32_t)p.layers[l].box_rows};
+    const cuuint32_t estride[2] = {1, 1};
+    if (encode(&p.tmap[l], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)wst, gdim, gstride, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return VOILA_ERR_CUDA;
+  }
+  p.bias_all = bias_all;
+  p.reward_kind = VOILA_REWARD_MLP;
+  p.goal_dims = 0;
+  p.gamma = 1.0;
+  p.key0 = key0;
+  p.key1 = key1;
+  p.hdr = hdr;
+  p.prop_obs = obs;
+  p.prop_s = s_prop;
+  p.prop_ell = ell_out;
+  p.prop_step = step;
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long nclusters = p.total_items < nsm / 2 ? p.total_items : nsm / 2;
+  const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total + p.fuse_total + (p.fuse_total ? 1024 : 0));
+  const cudaError_t e = launch_tc<8, 2, 8, false, false, kModePropose>(p, smem, nclusters, s);
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
 

@@ -69,4 +69,15 @@ voila_status tc_observe_rows(const voila_mlp* g_Z, const float* S, const float* 
                              int n_nodes, int C_max, float* obs, int d_o, uint32_t key0, uint32_t key1,
                              uint32_t step, uint32_t planner, WsHeader* hdr, void* scratch, cudaStream_t s);
 
+// Belief proposal on the tensor cores (BF16 generator 18 -> 256 x L -> 8 and
+// BF16 likelihood 16 -> 256 x L -> 1): s_prop[i] = g_T([particles[i]; action;
+// omega(i)]), omega the normals of stream VOILA_STREAM_BELIEF_OMEGA at counter
+// (i, 0, step); ell_out[i] = l([s_prop[i]; action; obs]) (FP64 store).
+bool tc_propose_supported(const voila_mlp* g_T, const voila_mlp* ell, int d_s, int d_a, int d_omega, int d_o);
+size_t tc_propose_scratch_bytes(const voila_mlp* g_T, const voila_mlp* ell);
+voila_status tc_belief_propose(const voila_mlp* g_T, const voila_mlp* ell, const float* particles, const float* action,
+                               const float* obs, long long N, uint32_t key0, uint32_t key1, uint32_t step,
+                               uint32_t planner, float* s_prop, double* ell_out, WsHeader* hdr, void* scratch,
+                               cudaStream_t s);
+
 }  // namespace voila
