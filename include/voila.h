@@ -249,8 +249,15 @@ voila_status voila_belief_update_workspace_size(const voila_mlp* g_T, const voil
  *   idx_out [N] int32 or NULL; w_out [N] double (the q_i) or NULL;
  *   logZ_out [1] double = log sum_i exp(lw_i), or NULL; ess_out [1] double =
  *   1 / sum_i q_i^2, or NULL. particles_out must not alias particles_in.
+ * Precision: FP32 and BF16 MLPs of any supported shape run on the CUDA cores;
+ * an MLP likelihood with g_T 18 -> 256 x L -> 8 and l 16 -> 256 x L -> 1
+ * (d_s 8, d_a 2, d_omega 8, d_o 6), each BF16 or FP8 e4m3 (per-channel
+ * scales on the hidden layers), runs on the tensor cores, proposal and
+ * likelihood in one kernel. FP8 e4m3 MLPs of other shapes (or with the
+ * Gaussian likelihood) return VOILA_ERR_UNSUPPORTED before any device work.
  * Device status: VOILA_ERR_NONFINITE if some lw_i is NaN or +inf,
- * VOILA_ERR_DEGENERATE if all are -inf. N <= 262144.
+ * VOILA_ERR_DEGENERATE if all are -inf; VOILA_ERR_TIMEOUT if a wait of the
+ * tensor-core kernel ran out (the kernel then returns early). N <= 262144.
  */
 voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* ell,
                                  const float* particles_in, const double* logw_in,

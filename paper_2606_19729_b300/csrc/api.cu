@@ -380,19 +380,23 @@ voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* e
   if (!(lambda > 0.0f) || planner_id >= 65536u) return VOILA_ERR_ARG;
   if (g_T->dims[0] != d_s + d_a + d_omega || g_T->dims[g_T->n_layers] != d_s)
     return VOILA_ERR_SHAPE;
-  if (g_T->prec == VOILA_FP8E4M3) return VOILA_ERR_UNSUPPORTED;
   int maxw = max_width(g_T);
   if (ell->kind == VOILA_LIK_MLP) {
     if (!valid_mlp(ell->mlp)) return VOILA_ERR_ARG;
     if (ell->mlp->dims[0] != d_s + d_a + d_o || ell->mlp->dims[ell->mlp->n_layers] != 1)
       return VOILA_ERR_SHAPE;
-    if (ell->mlp->prec == VOILA_FP8E4M3) return VOILA_ERR_UNSUPPORTED;
     if (max_width(ell->mlp) > maxw) maxw = max_width(ell->mlp);
   } else if (ell->kind == VOILA_LIK_GAUSSIAN) {
     if (d_o > d_s || !(ell->sigma > 0.0f)) return VOILA_ERR_ARG;
   } else {
     return VOILA_ERR_ARG;
   }
+  // BF16 / E4M3 MLPs of the supported shapes: the proposal runs on the tensor
+  // cores (the generator step and the likelihood in one kernel); E4M3 MLPs
+  // have no CUDA-core form
+  const bool use_tc = ell->kind == VOILA_LIK_MLP && tc_propose_supported(g_T, ell->mlp, d_s, d_a, d_omega, d_o);
+  if (!use_tc && (g_T->prec == VOILA_FP8E4M3 || (ell->kind == VOILA_LIK_MLP && ell->mlp->prec == VOILA_FP8E4M3)))
+    return VOILA_ERR_UNSUPPORTED;
   if (N == 0) return VOILA_OK;
   if (!particles_in || !particles_out || (d_a > 0 && !action) || (d_o > 0 && !obs))
     return VOILA_ERR_ARG;
@@ -413,9 +417,6 @@ voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* e
   if (cudaMemsetAsync(ws, 0, sizeof(WsHeader), s) != cudaSuccess) return VOILA_ERR_CUDA;
   uint32_t key0, key1;
   philox_key(seed, key0, key1);
-  // BF16 MLPs of the supported shapes: the proposal runs on the tensor cores
-  // (the generator step and the likelihood in one kernel)
-  const bool use_tc = ell->kind == VOILA_LIK_MLP && tc_propose_supported(g_T, ell->mlp, d_s, d_a, d_omega, d_o);
   if (use_tc) {
     char* scratch = (char*)(((uintptr_t)(ws + off) + 1023) & ~(uintptr_t)1023);
     if (voila_status st = tc_belief_propose(g_T, ell->mlp, particles_in, action, obs, N, key0, key1, step,

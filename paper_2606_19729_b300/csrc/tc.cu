@@ -612,7 +612,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
   static_assert(!PAIRS || (!WIDE && !F8 && DS == 8 && DA == 2 && DW == 6), "likelihood pair layout");
   static_assert(!OBS || (!WIDE && !F8), "observation rows use the two-tile kernel");
   constexpr bool PROP = MODE == kModePropose;
-  static_assert(!PROP || (!WIDE && !F8 && DS == 8 && DA == 2 && DW == 8), "belief proposal layout");
+  static_assert(!PROP || (!WIDE && DS == 8 && DA == 2 && DW == 8), "belief proposal layout");
   // work items of the launch: the observation rows are counted on the device
   long long total_items = p.total_items;
   if constexpr (OBS) {
@@ -1951,7 +1951,9 @@ voila_status tc_observe_rows(const voila_mlp* g_Z, const float* S, const float* 
 }
 
 bool tc_propose_supported(const voila_mlp* g_T, const voila_mlp* ell, int d_s, int d_a, int d_omega, int d_o) {
-  if (!g_T || !ell || g_T->prec != VOILA_BF16 || ell->prec != VOILA_BF16) return false;
+  if (!g_T || !ell) return false;
+  if ((g_T->prec != VOILA_BF16 && g_T->prec != VOILA_FP8E4M3) || (ell->prec != VOILA_BF16 && ell->prec != VOILA_FP8E4M3))
+    return false;
   if (d_s != 8 || d_a != 2 || d_omega != 8 || d_o != 6) return false;
   if (g_T->dims[0] != 18 || g_T->dims[g_T->n_layers] != 8 || ell->dims[0] != 16 || ell->dims[ell->n_layers] != 1)
     return false;
@@ -2004,6 +2006,12 @@ voila_status tc_belief_propose(const voila_mlp* g_T, const voila_mlp* ell, const
     const long long total = pl.pack.elems_end[pl.pack.n - 1];
     long long blocks = (total + 255) / 256;
     if (blocks > 148 * 8) blocks = 148 * 8;
+    if (p.scale_total > 0) {  // E4M3 hidden layers: per-channel scales first
+      int srows = 0;
+      for (int l = 0; l < pl.pack.n; ++l)
+        if (pl.pack.fp8[l]) srows += pl.pack.Npad[l];
+      scale_kernel<<<(srows * 32 + 255) / 256, 256, 0, s>>>(pl.pack);
+    }
     pack_kernel<<<(int)blocks, 256, 0, s>>>(pl.pack);
     if (pl.pack.fuse_n > 0) fuse_pack_kernel<<<1, 256, 0, s>>>(pl.pack);
     if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
@@ -2036,7 +2044,8 @@ voila_status tc_belief_propose(const voila_mlp* g_T, const voila_mlp* ell, const
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const long long nclusters = p.total_items < nsm / 2 ? p.total_items : nsm / 2;
   const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total + p.fuse_total + (p.fuse_total ? 1024 : 0));
-  const cudaError_t e = launch_tc<8, 2, 8, false, false, kModePropose>(p, smem, nclusters, s);
+  const cudaError_t e = p.scale_total > 0 ? launch_tc<8, 2, 8, true, false, kModePropose>(p, smem, nclusters, s)
+                                          : launch_tc<8, 2, 8, false, false, kModePropose>(p, smem, nclusters, s);
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
 

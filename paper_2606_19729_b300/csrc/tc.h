@@ -69,8 +69,9 @@ voila_status tc_observe_rows(const voila_mlp* g_Z, const float* S, const float* 
                              int n_nodes, int C_max, float* obs, int d_o, uint32_t key0, uint32_t key1,
                              uint32_t step, uint32_t planner, WsHeader* hdr, void* scratch, cudaStream_t s);
 
-// Belief proposal on the tensor cores (BF16 generator 18 -> 256 x L -> 8 and
-// BF16 likelihood 16 -> 256 x L -> 1): s_prop[i] = g_T([particles[i]; action;
+// Belief proposal on the tensor cores (generator 18 -> 256 x L -> 8 and
+// likelihood 16 -> 256 x L -> 1, each BF16 or FP8 e4m3 with per-channel
+// scales on its hidden layers): s_prop[i] = g_T([particles[i]; action;
 // omega(i)]), omega the normals of stream VOILA_STREAM_BELIEF_OMEGA at counter
 // (i, 0, step); ell_out[i] = l([s_prop[i]; action; obs]) (FP64 store).
 bool tc_propose_supported(const voila_mlp* g_T, const voila_mlp* ell, int d_s, int d_a, int d_omega, int d_o);

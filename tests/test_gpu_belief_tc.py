@@ -1,13 +1,15 @@
-"""Parity of the BF16 belief update (SIR step of Sec. 3, weights exp(l / lambda) of
-Sec. 4.2.3) with the FP64 oracle. With BF16 generator and likelihood MLPs of the
-mid-size shapes the proposal runs on the tensor cores: one kernel computes
-s'_i = g_T([s_i; a; omega_T(i, 0, step)]) and l([s'_i; a; o]).
+"""Parity of the tensor-core belief update (SIR step of Sec. 3, weights
+exp(l / lambda) of Sec. 4.2.3) with the FP64 oracle. With BF16 or FP8 e4m3
+generator and likelihood MLPs of the mid-size shapes the proposal runs on the
+tensor cores: one kernel computes s'_i = g_T([s_i; a; omega_T(i, 0, step)]) and
+l([s'_i; a; o]).
 
-Tolerances follow from the BF16 arithmetic: proposals and likelihoods carry the
-2e-2 normwise error of the BF16 rollout (inputs of every layer rounded to
-8-bit mantissas). A likelihood error of at most d = 2e-2 * max|l| moves every
-log-weight by at most 2 d / lambda after normalisation, log Z by at most
-d / lambda and log ESS by at most 4 d / lambda. The resampled indices are
+Tolerances follow from the arithmetic: proposals and likelihoods carry the
+normwise error of the rollout in the same precision (2e-2 BF16: inputs of every
+layer rounded to 8-bit mantissas; 6e-2 FP8 e4m3: hidden activations and weights
+with 4-bit mantissas and per-channel scales). A likelihood error of at most
+d = tol * max|l| moves every log-weight by at most 2 d / lambda after
+normalisation, log Z by at most d / lambda and log ESS by at most 4 d / lambda. The resampled indices are
 compared bit for bit with systematic resampling of the device's own weights,
 and every output particle with the oracle's proposal of its index."""
 import numpy as np
@@ -19,7 +21,7 @@ from paper_2606_19729_b300 import workloads as WL
 from tests.helpers import cuda, oracle_mlp, rel_err
 
 pytestmark = pytest.mark.gpu
-TOL_BF16 = 2e-2
+TOL = {WL.PREC_BF16: 2e-2, WL.PREC_FP8: 6e-2}
 
 
 @pytest.fixture(scope="module")
@@ -30,9 +32,9 @@ def V():
     return voila
 
 
-@pytest.fixture(scope="module")
-def wl():
-    return WL.mid_bf16(N=4096, K=2, H=2)
+@pytest.fixture(scope="module", params=[WL.PREC_BF16, WL.PREC_FP8], ids=["bf16", "fp8"])
+def wl(request):
+    return WL.mid_bf16(N=4096, K=2, H=2, prec=request.param)
 
 
 def _run(V, wl, N, lam, step, logw=None, planner=0):
@@ -56,38 +58,56 @@ def _run(V, wl, N, lam, step, logw=None, planner=0):
     return (out.cpu().numpy(), idx.cpu().numpy(), w.cpu().numpy(), lz.item(), ess.item()), res
 
 
-def _check(got, res, lam):
+def _check(got, res, lam, tol):
     out, idx, w, lz, ess = got
     N = w.shape[0]
     assert abs(np.sum(w) - 1.0) <= N * 2.0 ** -52
     assert np.all(w * 2.0 ** 52 == np.rint(w * 2.0 ** 52))
-    d = TOL_BF16 * max(np.max(np.abs(res.ell)), 1e-3)
+    d = tol * max(np.max(np.abs(res.ell)), 1e-3)
     big = res.w > 1e-9
     assert np.max(np.abs(np.log(w[big]) - np.log(res.w[big]))) <= 2 * d / lam
     assert abs(lz - res.logZ) <= d / lam
     assert abs(np.log(ess) - np.log(res.ess)) <= 4 * d / lam
     assert np.array_equal(idx, O.systematic_resample(w, res.u0))
-    assert rel_err(out, res.s_prop[idx]) < TOL_BF16
+    assert rel_err(out, res.s_prop[idx]) < tol
 
 
 @pytest.mark.parametrize("N", [4096, 1000, 513, 1])
-def test_bf16_belief_update_mlp_likelihood(V, wl, N):
+def test_tc_belief_update_mlp_likelihood(V, wl, N):
     got, res = _run(V, wl, N, 1.0, 3)
-    _check(got, res, 1.0)
+    _check(got, res, 1.0, TOL[wl.prec])
 
 
-def test_bf16_belief_update_tempered_with_prior(V, wl):
+@pytest.mark.parametrize("lam", [0.5, 0.02])
+def test_tc_belief_update_tempered_with_prior(V, wl, lam):
+    # lambda = 0.02 spreads l / lambda over several units (|l| < 0.07 at this
+    # initialisation): uneven weights, an ESS well below N
     N = 700
     logw = np.random.default_rng(5).normal(0.0, 0.5, size=N)
-    got, res = _run(V, wl, N, 0.5, 11, logw=logw, planner=2)
-    _check(got, res, 0.5)
+    got, res = _run(V, wl, N, lam, 11, logw=logw, planner=2)
+    if lam < 0.1:
+        assert res.ess < 0.8 * N
+    _check(got, res, lam, TOL[wl.prec])
 
 
-def test_bf16_belief_update_proposals_match_oracle(V, wl):
+def test_tc_belief_update_proposals_match_oracle(V, wl):
     # at a temperature where the weights are almost flat every proposal is
     # gathered somewhere: the gathered rows cover most of the oracle's proposals
     N = 2048
     got, res = _run(V, wl, N, 1e4, 4)
     out, idx = got[0], got[1]
     assert len(np.unique(idx)) > N // 2
-    assert rel_err(out, res.s_prop[idx]) < TOL_BF16
+    assert rel_err(out, res.s_prop[idx]) < TOL[wl.prec]
+
+
+def test_fp8_belief_update_other_shapes_unsupported(V):
+    # E4M3 MLPs have no CUDA-core form: shapes outside the tensor-core plan are refused
+    rng = np.random.default_rng(3)
+    g = V.DeviceMLP.from_spec(WL.xavier_mlp(rng, [10, 64, 64, 4], WL.ACT_SILU, WL.PREC_FP8))
+    lik = V.gaussian_likelihood(0.5)
+    N = 64
+    out = torch.empty((N, 4), dtype=torch.float32, device="cuda")
+    ws = V.alloc_workspace(V.voila_belief_update_workspace_size(g, lik, N))
+    with pytest.raises(RuntimeError, match="unsupported"):
+        V.voila_belief_update(g, lik, cuda(np.zeros((N, 4))), None, cuda(np.zeros(2)), cuda(np.zeros(2)), 4, 1.0, 0,
+                              0, 0, out, None, None, None, None, ws)
