@@ -987,10 +987,10 @@ def main():
                 [e[0].elapsed_time(e[1]) for e in ev]),
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            # BF16: weight pack, fused-output pack, tensor-core proposal, resample (belief update); weight
-            # pack, fused-output pack, rollout, reduce + argmax (rollout); backup. FP32: proposal, resample,
-            # rollout, reduce + argmax, backup
-            "gpu_launches": (10 if wl.prec == 1 else 6) * args.steps,
+            # BF16: weight pack, fused-output pack, tensor-core proposal, resampling (belief update); weight
+            # pack, fused-output pack, rollout, reduce + argmax (rollout); backup. FP32: proposal, resampling,
+            # rollout, reduce + argmax, backup. Resampling: one launch up to 2048 particles, four above.
+            "gpu_launches": ((9 if wl.prec == 1 else 5) + (1 if N <= 2048 else 4)) * args.steps,
             "clocks": clk.summary()}
     J8 = None
     if wl.prec == 1 and rank == 0 and not args.no_forms:

@@ -282,7 +282,7 @@ voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* e
  * the scratch is one array of VOILA_NOALLOC_SCRATCH_BYTES compiled into the
  * library, which every GPU that loads the library keeps until the process
  * exits. N is accepted while voila_belief_update_workspace_size(g_T, ell, N)
- * fits in that array (N <= 87368 for d_s = 8); larger N returns
+ * fits in that array (N <= 87320 for d_s = 8 with FP32 MLPs); larger N returns
  * VOILA_ERR_WORKSPACE before any device work.
  *   status_out  device int32 or NULL: receives the device-side status
  *               (VOILA_OK, VOILA_ERR_NONFINITE or VOILA_ERR_DEGENERATE),

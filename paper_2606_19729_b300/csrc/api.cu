@@ -357,6 +357,8 @@ voila_status voila_belief_update_workspace_size(const voila_mlp* g_T, const voil
   off = align_up(off + (size_t)N * d_s * sizeof(float));
   off = align_up(off + (size_t)N * sizeof(double));
   off = align_up(off + (size_t)N * sizeof(double));
+  // segment partials of the many-CTA resampling
+  if (N > kResampleSingleCta) off = align_up(off + (size_t)5 * kResampleMaxSegs * sizeof(double));
   // BF16 generator and likelihood of the tensor-core proposal's shapes: room
   // for its packed weights (placed at the next 1024-byte boundary)
   if (ell && ell->kind == VOILA_LIK_MLP && valid_mlp(ell->mlp) && g_T->dims[0] == 18 && d_s == 8 &&
@@ -414,6 +416,11 @@ voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* e
   off = align_up(off + (size_t)N * sizeof(double));
   double* C = (double*)(ws + off);
   off = align_up(off + (size_t)N * sizeof(double));
+  double* part = nullptr;
+  if (N > kResampleSingleCta) {
+    part = (double*)(ws + off);
+    off = align_up(off + (size_t)5 * kResampleMaxSegs * sizeof(double));
+  }
   if (cudaMemsetAsync(ws, 0, sizeof(WsHeader), s) != cudaSuccess) return VOILA_ERR_CUDA;
   uint32_t key0, key1;
   philox_key(seed, key0, key1);
@@ -460,6 +467,7 @@ voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* e
   r.planner = planner_id;
   r.step = step;
   r.C = C;
+  r.part = part;
   r.w_out = w_out;
   r.idx_out = idx_out;
   r.particles_out = particles_out;

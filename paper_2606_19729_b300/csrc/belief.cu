@@ -112,8 +112,181 @@ __global__ void __launch_bounds__(kResampleThreads) belief_resample_kernel(Resam
   }
 }
 
+// ---------------------------------------------------------------------------
+// Many-CTA form (N > kResampleSingleCta; measured faster from 4096 particles
+// up, mostly from the parallel search and gather): segment b = particles
+// [b S, (b + 1) S), S = kResampleSegElems, one CTA each; thread t of a
+// segment owns four consecutive particles. The segment partials (maximum,
+// non-finite flag, sum of exponentials, total of the quantised weights, sum
+// of their squares) go to a.part, and every CTA of a later launch combines
+// them in segment order, so all CTAs see the same m and Z and the result does
+// not depend on scheduling. The prefix sums stay segment-local: the quantised
+// weights are multiples of 2^-52 with partial sums below 2, so
+// C_i = (exclusive segment offset) + (local prefix) is exact, and the search
+// first finds the segment, then the index inside it.
+// ---------------------------------------------------------------------------
+constexpr int kSegThreads = kResampleSegElems / 4;
+enum { kPartMax = 0, kPartBad = 1, kPartZ = 2, kPartTotal = 3, kPartSq = 4 };
+
+__device__ __forceinline__ double part_at(const ResampleArgs& a, int which, int seg) {
+  return a.part[which * kResampleMaxSegs + seg];
+}
+
+// Global maximum and non-finite flag from the segment partials, in segment order.
+__device__ __forceinline__ void combine_max(const ResampleArgs& a, int G, double& m, bool& bad) {
+  m = -INFINITY;
+  bad = false;
+  for (int b = 0; b < G; ++b) {
+    m = fmax(m, part_at(a, kPartMax, b));
+    bad = bad || part_at(a, kPartBad, b) != 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kSegThreads) resample_seg_max_kernel(ResampleArgs a) {
+  __shared__ double red[33];
+  const int b = blockIdx.x;
+  const int s1 = min(a.N, (b + 1) * kResampleSegElems);
+  const int i0 = min(s1, b * kResampleSegElems + 4 * (int)threadIdx.x), i1 = min(s1, i0 + 4);
+  double lmax = -INFINITY, bad = 0.0;
+  for (int i = i0; i < i1; ++i) {
+    double lw = __ddiv_rn(a.ell[i], a.lambda);
+    if (a.logw) lw = __dadd_rn(lw, a.logw[i]);
+    a.C[i] = lw;
+    if (isnan(lw) || lw == INFINITY) bad = 1.0;
+    lmax = fmax(lmax, lw);
+  }
+  const double m = block_max(lmax, red);
+  const double f = block_max(bad, red);
+  if (threadIdx.x == 0) {
+    a.part[kPartMax * kResampleMaxSegs + b] = m;
+    a.part[kPartBad * kResampleMaxSegs + b] = f;
+  }
+}
+
+__global__ void __launch_bounds__(kSegThreads) resample_seg_exp_kernel(ResampleArgs a) {
+  __shared__ double red[33];
+  double m;
+  bool bad;
+  combine_max(a, gridDim.x, m, bad);
+  if (bad || m == -INFINITY) {
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+      set_status(a.hdr, bad ? VOILA_ERR_NONFINITE : VOILA_ERR_DEGENERATE, 1);
+    return;
+  }
+  const int b = blockIdx.x;
+  const int s1 = min(a.N, (b + 1) * kResampleSegElems);
+  const int i0 = min(s1, b * kResampleSegElems + 4 * (int)threadIdx.x), i1 = min(s1, i0 + 4);
+  double zl = 0.0;
+  for (int i = i0; i < i1; ++i) {
+    const double e = exp(a.C[i] - m);
+    a.C[i] = e;
+    zl += e;
+  }
+  const double z = block_sum(zl, red);
+  if (threadIdx.x == 0) a.part[kPartZ * kResampleMaxSegs + b] = z;
+}
+
+__global__ void __launch_bounds__(kSegThreads) resample_seg_scan_kernel(ResampleArgs a) {
+  __shared__ double red[33];
+  double m;
+  bool bad;
+  combine_max(a, gridDim.x, m, bad);
+  if (bad || m == -INFINITY) return;
+  double Z = 0.0;
+  for (int s = 0; s < (int)gridDim.x; ++s) Z += part_at(a, kPartZ, s);
+  const int b = blockIdx.x;
+  const int s1 = min(a.N, (b + 1) * kResampleSegElems);
+  const int i0 = min(s1, b * kResampleSegElems + 4 * (int)threadIdx.x), i1 = min(s1, i0 + 4);
+  double acc = 0.0, q2 = 0.0;
+  for (int i = i0; i < i1; ++i) {
+    const double w = __ddiv_rn(a.C[i], Z);
+    const double q = rint(w * 4503599627370496.0) * 2.220446049250313e-16;
+    if (a.w_out) a.w_out[i] = q;
+    acc += q;
+    q2 += q * q;
+    a.C[i] = acc;
+  }
+  const double off = block_exclusive_scan(acc, red);
+  for (int i = i0; i < i1; ++i) a.C[i] += off;  // segment-local inclusive prefix
+  const double tot = block_sum(acc, red);       // exact: every partial sum is representable
+  const double sq = block_sum(q2, red);
+  if (threadIdx.x == 0) {
+    a.part[kPartTotal * kResampleMaxSegs + b] = tot;
+    a.part[kPartSq * kResampleMaxSegs + b] = sq;
+  }
+}
+
+constexpr int kSearchThreads = 256;
+
+__global__ void __launch_bounds__(kSearchThreads) resample_seg_search_kernel(ResampleArgs a, int G) {
+  __shared__ double segoff[kResampleMaxSegs + 1];  // exclusive offsets; segoff[G] = C_{N-1}
+  __shared__ int stop_s;
+  if (threadIdx.x == 0) {
+    double m;
+    bool bad;
+    combine_max(a, G, m, bad);
+    stop_s = bad || m == -INFINITY;
+    if (!stop_s) {
+      double acc = 0.0;
+      for (int s = 0; s < G; ++s) {
+        segoff[s] = acc;
+        acc += part_at(a, kPartTotal, s);
+      }
+      segoff[G] = acc;
+      if (blockIdx.x == 0) {
+        double Z = 0.0, sq = 0.0;
+        for (int s = 0; s < G; ++s) {
+          Z += part_at(a, kPartZ, s);
+          sq += part_at(a, kPartSq, s);
+        }
+        if (a.logZ_out) *a.logZ_out = m + log(Z);
+        if (a.ess_out) *a.ess_out = 1.0 / sq;
+      }
+    }
+  }
+  __syncthreads();
+  if (stop_s) return;
+  const int N = a.N;
+  const int j = blockIdx.x * kSearchThreads + threadIdx.x;
+  if (j >= N) return;
+  const double total = segoff[G];
+  const uint4 wd = philox(make_uint4(0u, 0u, a.step, ctr_word3(VOILA_STREAM_RESAMPLE, a.planner, 0)),
+                          a.key0, a.key1);
+  const double u0 = uniform53(wd.x, wd.y);
+  const double p = __ddiv_rn(__dmul_rn(__dadd_rn(u0, (double)j), total), (double)N);
+  int lo = 0, hi = G;  // first segment whose end prefix exceeds p
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (segoff[mid + 1] > p) hi = mid;
+    else lo = mid + 1;
+  }
+  int idx = N - 1;
+  if (lo < G) {
+    const double base = segoff[lo];
+    int l2 = lo * kResampleSegElems, h2 = min(N, (lo + 1) * kResampleSegElems);
+    const int end = h2;
+    while (l2 < h2) {  // first i of the segment with base + C_i > p
+      const int mid = (l2 + h2) >> 1;
+      if (base + a.C[mid] > p) h2 = mid;
+      else l2 = mid + 1;
+    }
+    idx = l2 < end ? l2 : N - 1;
+  }
+  if (a.idx_out) a.idx_out[j] = idx;
+  for (int d = 0; d < a.d_s; ++d) a.particles_out[(size_t)j * a.d_s + d] = a.s_prop[(size_t)idx * a.d_s + d];
+}
+
 cudaError_t launch_belief_resample(const ResampleArgs& a, cudaStream_t s) {
-  belief_resample_kernel<<<1, kResampleThreads, 0, s>>>(a);
+  if (a.N <= kResampleSingleCta) {
+    belief_resample_kernel<<<1, kResampleThreads, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  const int G = (a.N + kResampleSegElems - 1) / kResampleSegElems;
+  if (G > kResampleMaxSegs || !a.part) return cudaErrorInvalidValue;
+  resample_seg_max_kernel<<<G, kSegThreads, 0, s>>>(a);
+  resample_seg_exp_kernel<<<G, kSegThreads, 0, s>>>(a);
+  resample_seg_scan_kernel<<<G, kSegThreads, 0, s>>>(a);
+  resample_seg_search_kernel<<<(a.N + kSearchThreads - 1) / kSearchThreads, kSearchThreads, 0, s>>>(a, G);
   return cudaGetLastError();
 }
 

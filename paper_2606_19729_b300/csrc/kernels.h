@@ -42,6 +42,12 @@ struct BeliefArgs {
   int ld;
 };
 
+// Resampling runs in one CTA up to kResampleSingleCta particles, above that
+// in CTAs of kResampleSegElems particles each (at most kResampleMaxSegs).
+constexpr int kResampleSingleCta = 2048;
+constexpr int kResampleSegElems = 4096;
+constexpr int kResampleMaxSegs = 64;
+
 struct ResampleArgs {
   const double* ell;
   const double* logw;
@@ -50,6 +56,7 @@ struct ResampleArgs {
   double lambda;
   uint32_t key0, key1, planner, step;
   double* C;          // [N] workspace
+  double* part;       // [5][kResampleMaxSegs] segment partials (N > kResampleSingleCta)
   double* w_out;      // [N] or null
   int32_t* idx_out;   // [N] or null
   float* particles_out;

@@ -169,11 +169,24 @@ def test_belief_update_with_prior_logw(V):
     _check_belief(got, res, TOL_FP32)
 
 
-def test_belief_update_degenerate_and_nonfinite_status(V):
-    wl = WL.small_fp32(N=64)
+@pytest.mark.parametrize("N", [2048, 2049, 4096, 16385, 70001, 262144])
+def test_belief_update_many_cta_resampling(V, N):
+    # above 2048 particles the resampling runs in CTAs of 4096 particles
+    # (segment partials combined in order, segment-local exact prefix sums)
+    # and one search-and-gather thread per output; 262144 is the largest N
+    # the call takes
+    wl = WL.small_fp32(N=N)
+    logw = np.random.default_rng(N).normal(0.0, 1.0, size=N)
+    got, res = _belief(V, wl, V.gaussian_likelihood(0.3), O.Likelihood(O.LIK_GAUSSIAN, sigma=0.3), logw=logw,
+                       step=5)
+    _check_belief(got, res, TOL_FP32)
+
+
+@pytest.mark.parametrize("N", [64, 20000])
+def test_belief_update_degenerate_and_nonfinite_status(V, N):
+    wl = WL.small_fp32(N=N)
     g = V.DeviceMLP.from_spec(wl.g_T)
     lik = V.gaussian_likelihood(0.5)
-    N = 64
     out = torch.empty((N, wl.d_s), dtype=torch.float32, device="cuda")
     ws = V.alloc_workspace(V.voila_belief_update_workspace_size(g, lik, N))
     a = cuda(wl.actions[0, 0])
@@ -182,7 +195,7 @@ def test_belief_update_degenerate_and_nonfinite_status(V):
     V.voila_belief_update(g, lik, cuda(wl.particles[:N]), logw, a, o, wl.d_omega, 1.0, 0, 0, 0, out, None, None,
                           None, None, ws)
     assert V.workspace_status(ws) == V.ERR_DEGENERATE
-    logw[3] = float("nan")
+    logw[N - 3] = float("nan")
     V.voila_belief_update(g, lik, cuda(wl.particles[:N]), logw, a, o, wl.d_omega, 1.0, 0, 0, 0, out, None, None,
                           None, None, ws)
     assert V.workspace_status(ws) == V.ERR_NONFINITE
