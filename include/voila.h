@@ -138,6 +138,18 @@ voila_status voila_workspace_status(const void* workspace, voila_stream_t stream
 const char* voila_status_string(voila_status s);
 
 /*
+ * Self-test of the device-side failure detection: one thread waits on an
+ * mbarrier that nothing arrives on, through the bounded wait every
+ * tensor-core kernel uses, and gives up after limit_cycles SM clock cycles
+ * (0 .. 4e9; the kernels themselves use ~4e9, about 2 s), recording
+ * VOILA_ERR_TIMEOUT in the status word of `workspace` (device, 256-byte
+ * aligned, at least 256 bytes; its status word is cleared first). The wait
+ * ends by itself and the context stays usable: read the result with
+ * voila_workspace_status. The paper has no counterpart.
+ */
+voila_status voila_selftest_wait_timeout(void* workspace, int64_t limit_cycles, voila_stream_t stream);
+
+/*
  * Workspace bytes for voila_rollout with these sizes (host call, no device work).
  */
 voila_status voila_rollout_workspace_size(const voila_mlp* g_T, const voila_reward* R,

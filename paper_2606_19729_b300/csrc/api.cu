@@ -127,6 +127,14 @@ voila_status voila_workspace_status(const void* workspace, voila_stream_t stream
   return (voila_status)h.status;
 }
 
+voila_status voila_selftest_wait_timeout(void* workspace, int64_t limit_cycles, voila_stream_t stream) {
+  if (!workspace || ((uintptr_t)workspace % kAlign) || limit_cycles < 0 || limit_cycles > 4000000000LL)
+    return VOILA_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), s) != cudaSuccess) return VOILA_ERR_CUDA;
+  return cuda_status(launch_wait_timeout_selftest((WsHeader*)workspace, (long long)limit_cycles, s));
+}
+
 voila_status voila_rollout_workspace_size(const voila_mlp* g_T, const voila_reward* R, int32_t N,
                                           int32_t K, int32_t H, size_t* bytes) {
   if (!bytes || !valid_mlp(g_T) || !R || N < 0 || K < 0 || H < 0) return VOILA_ERR_ARG;

@@ -163,13 +163,13 @@ __device__ __forceinline__ int item_planner(const TcParams& p, long long it) {
 }
 
 __device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                             WsHeader* hdr, int where) {
+                                             WsHeader* hdr, int where, long long limit = kSpinLimit) {
   if (ptx::mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
     if (ptx::mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (clock64() - t0 > kSpinLimit) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       set_status(hdr, VOILA_ERR_TIMEOUT, where);
       return false;
@@ -2060,6 +2060,31 @@ voila_status tc_rollout(const voila_mlp* g_T, const voila_reward* R, const Rollo
   q.H = a.H;
   q.planner = a.planner;
   return tc_rollout_batched(g_T, R, &q, 1, a.d_s, a.d_a, a.d_omega, a.gamma, a.key0, a.key1, 0, 0, hdr, scratch, s);
+}
+
+namespace {
+
+// Self-test of the bounded waits: one thread waits, through the same
+// bounded_wait the tensor-core kernels use, on an mbarrier that nothing
+// arrives on; when `limit` SM cycles have passed it records VOILA_ERR_TIMEOUT
+// (site 99) in the status word and the kernel returns.
+__global__ void wait_timeout_selftest_kernel(WsHeader* hdr, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(ptx::smem_u32(&bar), 1);
+    abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) bounded_wait(ptx::smem_u32(&bar), 0u, &abort_flag, hdr, 99, limit);
+}
+
+}  // namespace
+
+cudaError_t launch_wait_timeout_selftest(WsHeader* hdr, long long limit, cudaStream_t s) {
+  wait_timeout_selftest_kernel<<<1, 32, 0, s>>>(hdr, limit);
+  return cudaGetLastError();
 }
 
 }  // namespace voila

@@ -81,4 +81,7 @@ voila_status tc_belief_propose(const voila_mlp* g_T, const voila_mlp* ell, const
                                uint32_t planner, float* s_prop, double* ell_out, WsHeader* hdr, void* scratch,
                                cudaStream_t s);
 
+// Self-test of the bounded waits (see voila_selftest_wait_timeout).
+cudaError_t launch_wait_timeout_selftest(WsHeader* hdr, long long limit, cudaStream_t s);
+
 }  // namespace voila

@@ -125,6 +125,7 @@ _lib_pw = _sig("voila_progressive_widening", c_int32, POINTER(voila_pw_tree), _P
                POINTER(voila_mlp), POINTER(voila_likelihood), c_int32, c_double, c_double, c_float, c_uint64,
                c_uint32, c_uint32, _P, _P, _P, _P, _P, _P, _P, c_size_t, _P)
 _lib_philox = _sig("voila_philox_fill", c_int32, c_uint64, c_uint32, c_uint32, c_uint32, _P, c_int64, _P)
+_lib_selftest_wait = _sig("voila_selftest_wait_timeout", c_int32, _P, c_int64, _P)
 _lib_normal = _sig("voila_normal_fill", c_int32, c_uint64, c_uint32, c_uint32, c_uint32, c_uint32, c_int32,
                    _P, c_int64, _P)
 
@@ -358,6 +359,11 @@ def voila_generator_fwd_seeded(mlp: DeviceMLP, S: torch.Tensor, A: torch.Tensor,
     _check(_lib_fwd_seeded(ctypes.byref(mlp.desc), _ptr(S, torch.float32), _ptr(A, torch.float32), a_stride,
                            B, d_s, d_a, d_omega, seed, stream_id, step, planner_id, _ptr(Y, torch.float32),
                            _stream(stream)), "voila_generator_fwd_seeded")
+
+
+def voila_selftest_wait_timeout(workspace: torch.Tensor, limit_cycles: int, stream=None):
+    """A bounded wait that nothing completes; afterwards the workspace status is VOILA_ERR_TIMEOUT."""
+    _check(_lib_selftest_wait(_ptr(workspace), limit_cycles, _stream(stream)), "voila_selftest_wait_timeout")
 
 
 def voila_philox_fill(seed: int, c1: int, c2: int, c3: int, out: torch.Tensor, stream=None):

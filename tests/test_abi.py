@@ -42,6 +42,7 @@ def test_status_strings_and_host_validation():
     assert V._lib_rollout(ctypes.byref(m), ctypes.byref(r), None, None, 4, 4, None, 4, 4, 2, 4, 0.9, 0, 0,
                           None, None, None, None, 0, None) == V.ERR_ARG
     assert V._lib_philox(0, 0, 0, 0, None, -1, None) == V.ERR_ARG
+    assert V._lib_selftest_wait(None, 5, None) == V.ERR_ARG
     assert V._lib_normal(0, 0, 0, 0, 0, 0, None, 1, None) == V.ERR_ARG
 
 
