@@ -21,7 +21,7 @@ What it computes (paper sections cited per function):
   operator of Sec. 2.1): proposals from f_T, weights exp(l(s', a, o)/lambda)
   (Sec. 4.2.3, last paragraph), normalisation, systematic resampling.
 
-Readings taken where the paper is silent (all listed in the design doc):
+Readings taken where the paper is silent:
 * the reward scores the post-transition state s_{t+1};
 * resampling happens at every update (no ESS threshold) and is systematic;
 * weights are quantised to multiples of 2^-52 before the prefix sum, so the
