@@ -111,3 +111,46 @@ def test_fp8_belief_update_other_shapes_unsupported(V):
     with pytest.raises(RuntimeError, match="unsupported"):
         V.voila_belief_update(g, lik, cuda(np.zeros((N, 4))), None, cuda(np.zeros(2)), cuda(np.zeros(2)), 4, 1.0, 0,
                               0, 0, out, None, None, None, None, ws)
+
+
+def test_planning_step_in_cuda_graph(V):
+    # one planning step (tensor-core belief update with the many-CTA resampling,
+    # rollout of the updated belief, PORPP backup) captured in a CUDA graph and
+    # replayed: the same bits as the eager calls (every reduction has one order)
+    wl = WL.mid_bf16(N=4096, K=16, H=3)
+    g = V.DeviceMLP.from_spec(wl.g_T)
+    lik = V.mlp_likelihood(V.DeviceMLP.from_spec(wl.ell))
+    R = V.mlp_reward(V.DeviceMLP.from_spec(wl.reward_mlp))
+    N, K, H = wl.N, wl.K, wl.H
+    parts, acts = cuda(wl.particles), cuda(wl.actions)
+    a0, obs = cuda(wl.actions[0, 0]), cuda(np.linspace(-0.6, 0.5, wl.d_o))
+    p_new = torch.empty_like(parts)
+    w = torch.empty(N, dtype=torch.float64, device="cuda")
+    J = torch.empty(K, dtype=torch.float64, device="cuda")
+    best = torch.empty(1, dtype=torch.int32, device="cuda")
+    Vb = torch.empty(1, dtype=torch.float64, device="cuda")
+    ws_b = V.alloc_workspace(V.voila_belief_update_workspace_size(g, lik, N))
+    ws_r = V.alloc_workspace(V.voila_rollout_workspace_size(g, R, N, K, H))
+
+    def step(stream=None):
+        V.voila_belief_update(g, lik, parts, None, a0, obs, wl.d_omega, 0.05, wl.seed, 2, 0, p_new, None, w, None,
+                              None, ws_b, stream=stream)
+        V.voila_rollout(g, R, p_new, None, acts, wl.d_omega, wl.gamma, wl.seed, 0, J, None, best, ws_r,
+                        stream=stream)
+        V.voila_preference_backup(J, None, 1.0, Vb, None, stream=stream)
+
+    step()
+    torch.cuda.synchronize()
+    ref = [t.clone() for t in (p_new, w, J, best, Vb)]
+    for t in (p_new, w, J, Vb):
+        t.zero_()
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            step(stream=s)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert V.workspace_status(ws_b) == V.OK and V.workspace_status(ws_r) == V.OK
+    for got, r in zip((p_new, w, J, best, Vb), ref):
+        assert torch.equal(got, r)
