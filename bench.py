@@ -212,7 +212,44 @@ def cpu_baseline(wl, seqs, particles=None):
     trans = seqs * wl.N * wl.H
     return {"value": trans / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 numpy oracle: 1 belief update of {wl.N} particles + rollout of {seqs} of {wl.K} "
-                      f"sequences x {wl.N} particles x H={wl.H} ({trans} transitions) in {dt:.2f} s"}, J
+                      f"sequences x {wl.N} particles x H={wl.H} ({trans} transitions) in {dt:.2f} s"}, J, res
+
+
+def device_belief_weights(V, g, ell_mlp, wl):
+    """The device belief update on the oracle leg's inputs (prior particles,
+    a = actions[0, 0], o = 0, step 1, planner 0): its normalised weights and the
+    median time of one call (ms)."""
+    import torch
+    lik = V.mlp_likelihood(ell_mlp)
+    N = wl.N
+    parts = torch.from_numpy(wl.particles).float().cuda()
+    a0 = torch.from_numpy(np.ascontiguousarray(wl.actions[0, 0])).float().cuda()
+    obs = torch.zeros(wl.d_o, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(parts)
+    w = torch.empty(N, dtype=torch.float64, device="cuda")
+    ws = V.alloc_workspace(V.voila_belief_update_workspace_size(g, lik, N))
+
+    def call():
+        V.voila_belief_update(g, lik, parts, None, a0, obs, wl.d_omega, wl.lam, wl.seed, 1, 0, out, None, w, None,
+                              None, ws)
+
+    warm_until(call, 0.3)
+    ts = []
+    for _ in range(20):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    assert V.workspace_status(ws) == V.OK
+    return w.cpu().numpy(), statistics.median(ts)
+
+
+def logw_err(w, w_ref):
+    """max |log w - log w_ref| over the weights the reference gives more than 1e-9."""
+    big = w_ref > 1e-9
+    return float(np.max(np.abs(np.log(np.maximum(w[big], 1e-300)) - np.log(w_ref[big]))))
 
 
 def fp32_form(V, wl, seqs, planner, particles, stream):
@@ -278,7 +315,7 @@ def run_reference(args, rank):
     t0 = time.perf_counter()
     last = None
     for _ in range(args.steps):
-        last, _ = cpu_baseline(wl, seqs)
+        last, _, _ = cpu_baseline(wl, seqs)
     dt = time.perf_counter() - t0
     value = args.steps * seqs * wl.N * wl.H / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -1004,7 +1041,7 @@ def main():
                               None, None, None, None, ws_b)
         V.voila_rollout(g, R, p_new, None, actions, wl.d_omega, wl.gamma, wl.seed, planner, J, None, best, ws_r)
         torch.cuda.synchronize()
-        cb, Jo = cpu_baseline(wl, args.cpu_seqs, p_new.cpu().double().numpy())
+        cb, Jo, bres = cpu_baseline(wl, args.cpu_seqs, p_new.cpu().double().numpy())
         line["cpu_baseline"] = cb
         Jd = J[: args.cpu_seqs].cpu().numpy()
         if J8 is not None:
@@ -1014,6 +1051,18 @@ def main():
                                "sample": f"J of {args.cpu_seqs} of {wl.K} sequences (all particles) vs the FP64 oracle "
                                          "from the same resampled particles",
                                "tolerance": 2e-2 if wl.prec == 1 else 1e-5}
+        # belief-update weights of the device forms against the FP64 oracle's (same inputs)
+        ell_lam = wl.lam / max(float(np.max(np.abs(bres.ell))), 1e-300)
+        w_dev, ms_dev = device_belief_weights(V, g, V.DeviceMLP.from_spec(wl.ell), wl)
+        line["err_vs_fp64"]["belief_logw_maxabs"] = logw_err(w_dev, bres.w)
+        line["err_vs_fp64"]["belief_sample"] = (f"max |log w - log w*| over the {wl.N} particles' weights "
+                                                f"(lambda / max|l*| = {ell_lam:.3g})")
+        if wl.prec == 1 and "forms" in line and "fp8_e4m3" in line["forms"]:
+            mk8 = lambda spec: V.DeviceMLP([torch.from_numpy(x) for x in spec.W],  # noqa: E731
+                                           [torch.from_numpy(x) for x in spec.b], spec.act, V.FP8E4M3)
+            w8, ms8 = device_belief_weights(V, mk8(wl.g_T), mk8(wl.ell), wl)
+            line["forms"]["fp8_e4m3"]["belief_update_ms"] = ms8
+            line["forms"]["fp8_e4m3"]["belief_logw_err_vs_fp64"] = logw_err(w8, bres.w)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
