@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-seqs", type=int, default=16, help="sequences for the FP32-form comparison (0: skip)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32/FP8 form comparison")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the compact records of the other configurations in the default run")
     ap.add_argument("--sweep-err-seqs", type=int, default=64, help="sequences of the sweep's FP64 error subset")
     ap.add_argument("--sweep-err-N", type=int, default=256, help="particles of the sweep's FP64 error subset")
     ap.add_argument("--distill-cpu-rows", type=int, default=12288, help="rows of the distillation oracle sample")
@@ -252,6 +254,85 @@ def logw_err(w, w_ref):
     return float(np.max(np.abs(np.log(np.maximum(w[big], 1e-300)) - np.log(w_ref[big]))))
 
 
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# Fallback denominators (no MEASURED_PEAKS.json): one earlier B300 measurement.
+FALLBACK_BF16_BURST, FALLBACK_BF16_SUSTAINED = 1800.0, 1400.0
+
+
+def measure_fp8_peak(n: int = 8192, reps: int = 10):
+    """Dense E4M3 GEMM rate of this GPU: torch._scaled_mm (cuBLASLt) on n^3,
+    2 n^3 FLOP, best of `reps` by CUDA events. None if the call is unavailable."""
+    import torch
+    try:
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        one = torch.ones((), device="cuda")
+        f = lambda: torch._scaled_mm(a, b.t(), scale_a=one, scale_b=one, out_dtype=torch.bfloat16)  # noqa: E731
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        del a, b
+        return 2.0 * n ** 3 / best / 1e12
+    except (RuntimeError, AttributeError, TypeError):
+        return None
+
+
+def fp32_roofline(achieved: float, peaks: dict, clocks, nsm: int) -> dict:
+    """FP32 CUDA-core roofline: SMs x 128 FMA lanes x 2 FLOP x SM clock (the
+    kernel's sampled median clock when known, else the maximum)."""
+    mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    peak = nsm * 128 * 2 * mhz * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": f"FP32 FMA: {nsm} SMs x 128 lanes x 2 FLOP x {mhz:.0f} MHz (derived)"}
+
+
+def tensor_roofline(achieved: float, peaks: dict, clocks: dict, kind: str = "bf16", fp8_peak=None) -> dict:
+    """Roofline block of a tensor-core kernel. The denominator is the measured
+    burst rate of the kernel's operand type (BF16: cuBLAS from MEASURED_PEAKS.json;
+    FP8: the torch._scaled_mm probe of this run, else twice the BF16 burst, the
+    nominal ratio), taken as it stands when the kernel's sampled median SM clock
+    is within 5 % of the maximum and scaled to that median clock otherwise. The
+    ratio to the power-capped sustained BF16 figure is kept as a side field."""
+    burst = peaks.get("bf16_tflops", FALLBACK_BF16_BURST)
+    sustained = peaks.get("bf16_tflops_sustained", FALLBACK_BF16_SUSTAINED)
+    src = "measured (MEASURED_PEAKS.json)" if peaks else "fallback"
+    if kind == "fp8":
+        if fp8_peak:
+            base, basis = fp8_peak, "measured e4m3 burst (torch._scaled_mm 8192^3, best of 10, this run)"
+        else:
+            base, basis = 2.0 * burst, f"bf16 burst x 2 (nominal e4m3/bf16 ratio), bf16 {src}"
+    else:
+        base, basis = burst, f"bf16 burst (cuBLAS 8192^3), {src}"
+    smax = peaks.get("sm_max_mhz", 2032.0)
+    med = (clocks or {}).get("sm_mhz")
+    if med and med < 0.95 * smax:
+        peak = base * med / smax
+        basis += f", scaled to the kernel's median SM clock {med:.0f} of {smax:.0f} MHz"
+    else:
+        peak = base
+        basis += " (the kernel ran within 5% of the maximum SM clock)" if med else " (clock unsampled)"
+    out = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "peak_source": basis}
+    if kind == "bf16":
+        out["frac_vs_sustained_bf16"] = achieved / sustained
+    return out
+
+
 def fp32_form(V, wl, seqs, planner, particles, stream):
     """The plain FP32 CUDA-core form on the same workload, timed on a slice of
     `seqs` action sequences (throughput per transition does not depend on K)."""
@@ -278,9 +359,10 @@ def fp32_form(V, wl, seqs, planner, particles, stream):
             "sample": f"{seqs} of {wl.K} sequences x {wl.N} particles x H={wl.H}, same weights in FP32"}
 
 
-def fp8_form(V, wl, planner, particles, stream):
+def fp8_form(V, wl, planner, particles, stream, peaks=None, fp8_peak=None):
     """The FP8 e4m3 form (hidden layers E4M3 with per-channel scales) on the full
-    workload, same particles and weights; returns its throughput and J."""
+    workload, same particles and weights; returns its throughput, its roofline
+    against the E4M3 tensor rate, and J."""
     import torch
     g8 = V.DeviceMLP([torch.from_numpy(w) for w in wl.g_T.W], [torch.from_numpy(b) for b in wl.g_T.b],
                      wl.g_T.act, V.FP8E4M3)
@@ -292,16 +374,23 @@ def fp8_form(V, wl, planner, particles, stream):
     ws = V.alloc_workspace(V.voila_rollout_workspace_size(g8, R8, wl.N, wl.K, wl.H))
     V.voila_rollout(g8, R8, particles, None, acts, wl.d_omega, wl.gamma, wl.seed, planner, J, None, None, ws)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 3
-    e0.record(stream)
-    for _ in range(reps):
-        V.voila_rollout(g8, R8, particles, None, acts, wl.d_omega, wl.gamma, wl.seed, planner, J, None, None, ws)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    reps = 12
+    with Clocks(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        for _ in range(reps):
+            V.voila_rollout(g8, R8, particles, None, acts, wl.d_omega, wl.gamma, wl.seed, planner, J, None, None, ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
     assert V.workspace_status(ws) == V.OK
     sec = e0.elapsed_time(e1) / 1e3 / reps
+    achieved = flops_per_transition(wl) * wl.N * wl.K * wl.H / sec / 1e12
+    clocks = clk.summary()
     return {"value": wl.N * wl.K * wl.H / sec, "unit": UNIT, "dtype": "e4m3 hidden layers, bf16 first/last",
-            "rollout_ms": 1e3 * sec, "sample": "full workload, same particles and weights"}, J.cpu().numpy()
+            "rollout_ms": 1e3 * sec, "sample": "full workload, same particles and weights",
+            "roofline": dict(tensor_roofline(achieved, peaks or {}, clocks, "fp8", fp8_peak),
+                             kernel="rollout_tc_kernel FP8 instantiation (voila_rollout call)",
+                             flops="algorithmic, as the BF16 line (543,232 per transition)"),
+            "clocks": clocks}, J.cpu().numpy()
 
 
 def run_reference(args, rank):
@@ -328,7 +417,7 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args, rank, world, local):
+def batched_record(args, rank, world, local):
     """64 independent planners (uneven N, K, H from seed 4) sharing the mid-size BF16
     MLPs: one autotuned, graph-captured batched launch per step, against the same
     work as 64 sequential voila_rollout calls."""
@@ -395,15 +484,10 @@ def run_batched(args, rank, world, local):
         torch.cuda.synchronize()
         seq_s = sum(a.elapsed_time(b) for a, b in seq_ev) / 1e3
     same = all(torch.equal(a, it["J"]) for a, it in zip(J_batched, items))
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
+    peaks = load_peaks()
+    clocks = clk.summary()
     fpt = flops_per_transition(wl)
     achieved = fpt * E * args.steps / batched_s / 1e12
-    peak = peaks.get("bf16_tflops_sustained", 1400.0)
     line = {"metric": METRIC, "value": E * args.steps / batched_s, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * batched_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
@@ -415,14 +499,19 @@ def run_batched(args, rank, world, local):
             "schedule": best, "autotune_ms": tune_ms,
             "sequential_64_launches": {"value": E * len(seq_ev) / seq_s, "ms_per_step": 1e3 * seq_s / len(seq_ev)},
             "batched_equals_sequential": same,
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "rollout_tc_kernel (batched)"},
-            "gpu_launches": 4 * args.steps, "clocks": clk.summary()}
+            "roofline": dict(tensor_roofline(achieved, peaks, clocks, "bf16"), traffic=None,
+                             kernel="rollout_tc_kernel (batched)"),
+            "gpu_launches": 4 * args.steps, "clocks": clocks}
+    return line
+
+
+def run_batched(args, rank, world, local):
+    line = batched_record(args, rank, world, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def run_sweep(args, rank, world, local):
+def sweep_record(args, rank, world, local, fp8_peak=None):
     """Precision sweep (state 12, action 3, latent 16, 4x512 SiLU generator, GOAL
     reward, 16384 x 2048 x 25): FP32 (CUDA cores, on a slice of sequences), BF16 and
     FP8 (tensor cores, full workload), each form's return error against the FP64
@@ -435,6 +524,9 @@ def run_sweep(args, rank, world, local):
     torch.cuda.set_device(local)
     wl = WL.sweep()
     stream = torch.cuda.current_stream()
+    peaks = load_peaks()
+    if fp8_peak is None:
+        fp8_peak = measure_fp8_peak()
     parts = torch.from_numpy(wl.particles).float().cuda()
     acts = torch.from_numpy(wl.actions).float().cuda()
     R = V.goal_reward(list(wl.goal))
@@ -460,9 +552,19 @@ def run_sweep(args, rank, world, local):
         assert V.workspace_status(ws) == V.OK
         sec = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3 / reps
         fpt = sum(2 * w.shape[0] * w.shape[1] for w in wl.g_T.W)
+        achieved = fpt * wl.N * K * wl.H / sec / 1e12
+        clocks = clk.summary()
         forms[name] = {"value": wl.N * K * wl.H / sec, "unit": UNIT, "rollout_ms": 1e3 * sec,
-                       "achieved_tflops": fpt * wl.N * K * wl.H / sec / 1e12,
-                       "sample": f"{K} of {wl.K} sequences x {wl.N} particles x H={wl.H}", "clocks": clk.summary()}
+                       "achieved_tflops": achieved,
+                       "sample": f"{K} of {wl.K} sequences x {wl.N} particles x H={wl.H}", "clocks": clocks}
+        if prec == V.FP32:
+            forms[name]["roofline"] = dict(fp32_roofline(achieved, peaks, clocks,
+                                                         torch.cuda.get_device_properties(0).multi_processor_count),
+                                           kernel="rollout_simt_kernel")
+        else:
+            forms[name]["roofline"] = dict(
+                tensor_roofline(achieved, peaks, clocks, "fp8" if prec == V.FP8E4M3 else "bf16", fp8_peak),
+                kernel="rollout_tc_kernel (wide)")
         # the error subset, as its own smaller problem (same counters as the oracle's)
         Ns, Ks = min(args.sweep_err_N, wl.N), min(args.sweep_err_seqs, wl.K)
         Jsub = torch.empty(Ks, dtype=torch.float64, device="cuda")
@@ -486,25 +588,22 @@ def run_sweep(args, rank, world, local):
                "sample": f"FP64 oracle rollout of {Ks} sequences x {Ns} particles x H={wl.H} in {dt:.1f} s"}
     else:
         cpu = None
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    peak = peaks.get("bf16_tflops_sustained", 1400.0)
     b = forms["bf16"]
     line = {"metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": 1, "ms_per_step": b["rollout_ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded inputs, random-init weights)",
             "config": {"workload": "sweep: N=16384 x K=2048 x H=25, d_s=12 d_a=3 d_omega=16, generator 31x512x512x512x512x12 "
                                    "SiLU, GOAL reward; forms FP32 / BF16 / FP8 e4m3 (per-channel scales)"},
-            "forms": forms,
-            "roofline": {"bound": "tensor", "achieved": b["achieved_tflops"], "peak": peak, "unit": "TFLOP/s",
-                         "frac": b["achieved_tflops"] / peak, "traffic": None, "kernel": "rollout_tc_kernel (wide)"},
-            "gpu_launches": 3 * args.steps}
+            "forms": forms, "peaks_this_run": {"e4m3_tflops_burst": fp8_peak},
+            "roofline": dict(b["roofline"], traffic=None),
+            "gpu_launches": 3 * args.steps, "clocks": b["clocks"]}
     if cpu:
         line["cpu_baseline"] = cpu
+    return line
+
+
+def run_sweep(args, rank, world, local):
+    line = sweep_record(args, rank, world, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -520,7 +619,7 @@ def distill_flops(wl):
     return teacher, student * 3
 
 
-def run_distill(args, rank, world, local):
+def distill_record(args, rank, world, local):
     """Distillation training step (Eq. 3), B=65536: teacher DDIM targets (32 steps of
     the 82-512-512-512-8 SiLU denoiser), student 18-256-256-256-8 forward with BF16
     weights, MSE, hand-written backward, Adam on FP32 master weights."""
@@ -530,7 +629,7 @@ def run_distill(args, rank, world, local):
     from paper_2606_19729_b300.distill import Distiller
 
     torch.cuda.set_device(local)
-    if world > 1:
+    if world > 1 and not torch.distributed.is_initialized():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     wl = WL.distill(B=args.B or 65536, teacher_prec=WL.PREC_BF16)
@@ -575,13 +674,8 @@ def run_distill(args, rank, world, local):
     assert V.workspace_status(tws) == V.OK and V.workspace_status(d.ws) == V.OK
     f_teacher, f_student = distill_flops(wl)
     achieved = f_teacher * B / ddim_s / 1e12
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    peak = peaks.get("bf16_tflops_sustained", 1400.0)
+    peaks = load_peaks()
+    clocks = clk.summary()
     # end to end: inputs copied from pinned host memory each step, the loss read back
     hS, hA, hO = (x.cpu().pin_memory() for x in (S, A, om))
     hl = torch.empty(1, dtype=torch.float64).pin_memory()
@@ -604,14 +698,12 @@ def run_distill(args, rank, world, local):
                              "pre-activations, gradients) exceeds L2"},
             "loss": {"first": float(lo[0]), "last": float(lo[-1])},
             "teacher_ms": 1e3 * ddim_s,
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "rollout_tc_kernel (DDIM sampler mode)",
-                         "peak_kind": "measured bf16 sustained",
-                         "flops": "algorithmic: 2 x (82x512 + 512x512 x 2 + 512x8) x 32 steps per sample"},
+            "roofline": dict(tensor_roofline(achieved, peaks, clocks, "bf16"), traffic=None,
+                             kernel="rollout_tc_kernel (DDIM sampler mode)",
+                             flops="algorithmic: 2 x (82x512 + 512x512 x 2 + 512x8) x 32 steps per sample"),
             "e2e": {"value": B * e2e_steps * world / e2e_sec, "unit": "samples/s",
                     "h2d_bytes_per_step": int(sum(x.numel() * 4 for x in (hS, hA, hO))), "d2h_bytes_per_step": 8},
-            "gpu_launches": None, "clocks": clk.summary()}
+            "gpu_launches": None, "clocks": clocks}
     n_layers = len(wl.student.W)
     # per step (BF16 student, tensor cores): sampler 3 (pack, embeddings, kernel),
     # concat 1, forward (input prep, 2 padded weights, L-1 transposed weights,
@@ -635,6 +727,11 @@ def run_distill(args, rank, world, local):
         line["cpu_baseline"] = {"value": rows / dt, "unit": "samples/s", "cores": blas_threads(), "kind": "oracle",
                                 "sample": f"FP64 oracle distillation step on {rows} of {B} rows "
                                           f"(DDIM targets, loss, gradient, Adam) in {dt:.1f} s"}
+    return line
+
+
+def run_distill(args, rank, world, local):
+    line = distill_record(args, rank, world, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -684,13 +781,8 @@ def run_infonce(args, rank, world, local):
     value = aggregate_rate(pairs * reps, world, sec)
     fpp = sum(2 * w.shape[0] * w.shape[1] for w in wl.ell.W)
     achieved = fpp * pairs / fwd_s / 1e12
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    peak = peaks.get("bf16_tflops_sustained", 1400.0)
+    peaks = load_peaks()
+    clocks = clk.summary()
     # training step of the likelihood (tensor cores for the BF16 planning shapes), a few steps
     master = torch.cat([torch.cat([w.float().reshape(-1), b.reshape(-1)]) for w, b in zip(ell.W, ell.b)])
     m, v = torch.zeros_like(master), torch.zeros_like(master)
@@ -711,14 +803,12 @@ def run_infonce(args, rank, world, local):
             "config": {"workload": f"infonce: B={B} tuples (B^2={pairs} pairs), likelihood 16x256x256x256x1 SiLU "
                                    "BF16 on the tensor cores; row log-sum-exp, loss, dloss/dL"},
             "loss": loss.item(),
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "voila_infonce_forward (weight pack + pair kernel + row LSE + loss)",
-                         "peak_kind": "measured bf16 sustained"},
+            "roofline": dict(tensor_roofline(achieved, peaks, clocks, "bf16"), traffic=None,
+                             kernel="voila_infonce_forward (weight pack + pair kernel + row LSE + loss)"),
             "train_step": {"ms": statistics.median(step_ms), "loss_first": float(step_losses[0].item()),
                            "loss_last": float(step_losses[-1].item()),
                            "note": "BF16 likelihood: tensor-core training forward and backward over all B^2 pair rows"},
-            "gpu_launches": 4 * reps, "clocks": clk.summary()}
+            "gpu_launches": 4 * reps, "clocks": clocks}
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import voila_oracle as O
         rows = 256  # tuples i of the sample: their B-pair rows of logits and log-sum-exp
@@ -834,6 +924,110 @@ def run_pw(args, rank, world, local):
                                                             f"(one call) in {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def small_fp32_record(args, local):
+    """The plain FP32 configuration in full (N=256, K=64, H=10, 2x64 tanh MLPs,
+    GOAL reward): one planning step (belief update with the MLP likelihood, then
+    the rollout of the updated belief, reduction and argmax) on the CUDA cores,
+    timed by CUDA events over many steps; J against the FP64 oracle from the same
+    resampled particles."""
+    import torch
+    from paper_2606_19729_b300 import voila as V
+    from paper_2606_19729_b300 import workloads as WL
+    from oracle import voila_oracle as O
+
+    wl = WL.small_fp32()
+    dev = torch.device("cuda", local)
+    g = V.DeviceMLP.from_spec(wl.g_T)
+    lik = V.mlp_likelihood(V.DeviceMLP.from_spec(wl.ell))
+    R = V.goal_reward(list(wl.goal))
+    P = torch.from_numpy(wl.particles).float().to(dev)
+    A = torch.from_numpy(wl.actions).float().to(dev)
+    a0 = A[0, 0].contiguous()
+    # one observation drawn from the samplers: s' = g_T(s_true, a, w), o = g_Z(s', a, w_Z)
+    gz = V.DeviceMLP.from_spec(wl.g_Z)
+    s_true = torch.from_numpy(WL.true_state(wl.seed, wl.d_s, 0.5)).float().to(dev).reshape(1, -1)
+    s_next = torch.empty((1, wl.d_s), device=dev)
+    V.voila_generator_fwd_seeded(g, s_true, a0.reshape(1, -1), 0, wl.d_omega, wl.seed, 5, 0, 0, s_next)
+    obs2 = torch.empty((1, wl.d_o), device=dev)
+    V.voila_generator_fwd_seeded(gz, s_next, a0.reshape(1, -1), 0, wl.d_omega, wl.seed, V.STREAM_OBS_OMEGA, 0, 0,
+                                 obs2)
+    obs = obs2.reshape(-1).contiguous()
+    p_new = torch.empty_like(P)
+    J = torch.empty(wl.K, dtype=torch.float64, device=dev)
+    best = torch.empty(1, dtype=torch.int32, device=dev)
+    ws_b = V.alloc_workspace(V.voila_belief_update_workspace_size(g, lik, wl.N))
+    ws_r = V.alloc_workspace(V.voila_rollout_workspace_size(g, R, wl.N, wl.K, wl.H))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        V.voila_belief_update(g, lik, P, None, a0, obs, wl.d_omega, wl.lam, wl.seed, 1, 0, p_new, None, None,
+                              None, None, ws_b)
+        V.voila_rollout(g, R, p_new, None, A, wl.d_omega, wl.gamma, wl.seed, 0, J, None, best, ws_r)
+
+    warm_until(step, 0.3)
+    reps = 200
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(reps)]
+    with Clocks(local) as clk:
+        for e in ev:
+            e[0].record(stream)
+            V.voila_belief_update(g, lik, P, None, a0, obs, wl.d_omega, wl.lam, wl.seed, 1, 0, p_new, None, None,
+                                  None, None, ws_b)
+            e[1].record(stream)
+            V.voila_rollout(g, R, p_new, None, A, wl.d_omega, wl.gamma, wl.seed, 0, J, None, best, ws_r)
+            e[2].record(stream)
+        torch.cuda.synchronize()
+    assert V.workspace_status(ws_b) == V.OK and V.workspace_status(ws_r) == V.OK
+    step_ms = statistics.median(e[0].elapsed_time(e[2]) for e in ev)
+    roll_ms = statistics.median(e[1].elapsed_time(e[2]) for e in ev)
+    trans = wl.N * wl.K * wl.H
+    clocks = clk.summary()
+    achieved = flops_per_transition(wl) * trans / (roll_ms / 1e3) / 1e12
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    Jo, _ = O.rollout(O.MLP(wl.g_T.W, wl.g_T.b, wl.g_T.act), O.Reward(O.REWARD_GOAL, wl.goal),
+                      p_new.cpu().double().numpy(), wl.actions, wl.d_omega, wl.gamma, wl.seed)
+    Jd = J.cpu().numpy()
+    return {"workload": "small_fp32: N=256 x K=64 x H=10, d_s=4 d_a=2 d_o=4 d_omega=4, 2x64 tanh FP32, GOAL "
+                        "reward; belief update + rollout per step",
+            "value": trans / (step_ms / 1e3), "unit": UNIT, "ms_per_step": step_ms, "rollout_ms": roll_ms,
+            "belief_update_ms": statistics.median(e[0].elapsed_time(e[1]) for e in ev), "dtype": "f32",
+            "roofline": dict(fp32_roofline(achieved, load_peaks(), clocks, nsm), kernel="rollout_simt_kernel",
+                             note="launch-latency bound: 163,840 transitions per launch"),
+            "err_vs_fp64": {"J_normwise": float(np.max(np.abs(Jd - Jo)) / np.max(np.abs(Jo))), "tolerance": 1e-5,
+                            "sample": "all 64 sequences, from the device's resampled particles"},
+            "steps_timed": reps, "clocks": clocks}
+
+
+def config_records(args, rank, world, local, fp8_peak):
+    """Compact records of the other configurations, for the default run's line:
+    the plain FP32 configuration, the precision sweep at full size, the
+    distillation step and the batched planners."""
+    import copy
+    out = {}
+    out["c1_small_fp32"] = small_fp32_record(args, local)
+    a = copy.copy(args)
+    a.steps, a.warmup = 2, 1
+    sw = sweep_record(a, rank, world, local, fp8_peak)
+    out["c3_sweep"] = {"workload": sw["config"]["workload"],
+                       "forms": {k: {kk: v.get(kk) for kk in ("value", "rollout_ms", "roofline", "err_vs_fp64",
+                                                              "err_sample", "sample", "clocks")}
+                                 for k, v in sw["forms"].items()},
+                       "cpu_baseline": sw.get("cpu_baseline")}
+    a = copy.copy(args)
+    a.steps, a.warmup = 10, 3
+    d = distill_record(a, rank, world, local)
+    out["c4_distill"] = {k: d.get(k) for k in ("metric", "value", "unit", "ms_per_step", "teacher_ms", "roofline",
+                                               "loss", "e2e", "cpu_baseline", "clocks")}
+    out["c4_distill"]["workload"] = d["config"]["workload"]
+    a = copy.copy(args)
+    a.steps, a.warmup = 4, 1
+    b = batched_record(a, rank, world, local)
+    out["c5_batched"] = {k: b.get(k) for k in ("value", "unit", "ms_per_step", "schedule", "autotune_ms",
+                                               "sequential_64_launches", "batched_equals_sequential", "roofline",
+                                               "clocks")}
+    out["c5_batched"]["workload"] = b["config"]["workload"]
+    return out
 
 
 def main():
@@ -977,12 +1171,8 @@ def main():
     e2e_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3, world, dev)
     e2e_value = aggregate_rate(trans_per_step * args.steps, world, e2e_s)
 
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
+    peaks = load_peaks()
+    clocks = clk.summary()
     fpt = flops_per_transition(wl)
     roll_avg_s = sum(roll_ms) / len(roll_ms) / 1e3
     traffic = None
@@ -1001,19 +1191,13 @@ def main():
         traffic = None
     if wl.prec == 1:
         achieved = fpt * trans_per_step / roll_avg_s / 1e12
-        peak = peaks.get("bf16_tflops_sustained", 1400.0)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "rollout_tc_kernel (voila_rollout call: weight pack + rollout + return reduction)",
-                "tensor_pipe_pct_ncu": tensor_pipe,
-                "peak_source": "measured bf16 sustained (MEASURED_PEAKS.json)" if peaks else "fallback"}
+        roof = dict(tensor_roofline(achieved, peaks, clocks, "bf16"), traffic=traffic,
+                    kernel="rollout_tc_kernel (voila_rollout call: weight pack + rollout + return reduction)",
+                    tensor_pipe_pct_ncu=tensor_pipe)
     else:
         achieved = fpt * trans_per_step / roll_avg_s / 1e12
-        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak = nsm * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "rollout_simt_kernel",
-                "peak_source": "FP32 FMA: SMs x 128 lanes x 2 FLOP x max SM clock"}
+        roof = fp32_roofline(achieved, peaks, clocks, torch.cuda.get_device_properties(dev).multi_processor_count)
+        roof["kernel"] = "rollout_simt_kernel"
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
@@ -1028,13 +1212,19 @@ def main():
             # pack, fused-output pack, rollout, reduce + argmax (rollout); backup. FP32: proposal, resampling,
             # rollout, reduce + argmax, backup. Resampling: one launch up to 2048 particles, four above.
             "gpu_launches": ((9 if wl.prec == 1 else 5) + (1 if N <= 2048 else 4)) * args.steps,
-            "clocks": clk.summary()}
+            "clocks": clocks}
     J8 = None
     if wl.prec == 1 and rank == 0 and not args.no_forms:
         line["forms"] = {}
         if args.fp32_seqs > 0:
-            line["forms"]["fp32_cuda_cores"] = fp32_form(V, wl, args.fp32_seqs, planner, p_new, stream)
-        line["forms"]["fp8_e4m3"], J8 = fp8_form(V, wl, planner, p_new, stream)
+            f32 = fp32_form(V, wl, args.fp32_seqs, planner, p_new, stream)
+            nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+            f32["roofline"] = fp32_roofline(fpt * f32["value"] / 1e12, peaks, None, nsm)
+            line["forms"]["fp32_cuda_cores"] = f32
+        fp8_peak = measure_fp8_peak()
+        line["peaks_this_run"] = {"e4m3_tflops_burst": fp8_peak,
+                                  "how": "torch._scaled_mm e4m3 x e4m3 -> bf16, 8192^3, best of 10 (CUDA events)"}
+        line["forms"]["fp8_e4m3"], J8 = fp8_form(V, wl, planner, p_new, stream, peaks, fp8_peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the device's resampled particles and J of this exact step, against FP64
         V.voila_belief_update(g, lik, particles, None, action, obs, wl.d_omega, wl.lam, wl.seed, 1, planner, p_new,
@@ -1063,6 +1253,9 @@ def main():
             w8, ms8 = device_belief_weights(V, mk8(wl.g_T), mk8(wl.ell), wl)
             line["forms"]["fp8_e4m3"]["belief_update_ms"] = ms8
             line["forms"]["fp8_e4m3"]["belief_logw_err_vs_fp64"] = logw_err(w8, bres.w)
+    if rank == 0 and world == 1 and wl.prec == 1 and not args.no_configs:
+        line["configs"] = config_records(args, rank, world, local,
+                                         (line.get("peaks_this_run") or {}).get("e4m3_tflops_burst"))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -184,6 +184,35 @@ voila_status voila_rollout(const voila_mlp* g_T, const voila_reward* R,
                            void* workspace, size_t ws_bytes, voila_stream_t stream);
 
 /*
+ * One shard of a rollout split over several calls or GPUs by particles and/or
+ * by action sequences. The simulations of different (particle, sequence)
+ * pairs are independent (Sec. 2.2: the planner runs them side by side), so a
+ * shard computes exactly the rows of the whole problem that it holds.
+ *   particles [N][d_s]: particles n_offset .. n_offset + N - 1 of the whole
+ *     belief of N_total particles; w [N] their weights or NULL (1 / N_total each);
+ *   actions [K][H][d_a]: sequences k_offset .. k_offset + K - 1 of the whole set;
+ *   row (n, k) draws omega_T at counter (n + n_offset, k + k_offset, t), so G of
+ *   a shard equals the matching block of the unsharded call's G bit for bit;
+ *   J [K] (required): the shard's partial value J_k = sum over its particles of
+ *     w_n G[k][n]. With all particles (n_offset = 0, N = N_total) this is the
+ *     unsharded J of those sequences, bit for bit. Over particle shards the full
+ *     J_k is the sum of the shards' partials (FP64; equal to the unsharded J up
+ *     to the order of the additions);
+ *   best_k [1] or NULL: argmax over this shard's J (meaningful when the shard
+ *     holds every particle).
+ * Requires 0 <= n_offset, n_offset + N <= N_total, 0 <= k_offset; the other
+ * arguments, the workspace (voila_rollout_workspace_size(g_T, R, N, K, H)) and
+ * the errors are those of voila_rollout, which is this call with n_offset =
+ * k_offset = 0 and N_total = N.
+ */
+voila_status voila_rollout_shard(const voila_mlp* g_T, const voila_reward* R, const float* particles,
+                                 const double* w, int32_t N, int32_t n_offset, int32_t N_total,
+                                 int32_t d_s, const float* actions, int32_t K, int32_t k_offset,
+                                 int32_t H, int32_t d_a, int32_t d_omega, double gamma, uint64_t seed,
+                                 uint32_t planner_id, double* J, double* G, int32_t* best_k,
+                                 void* workspace, size_t ws_bytes, voila_stream_t stream);
+
+/*
  * One independent planning problem of a batched rollout: its own belief
  * (particles, optional weights), action sequences, horizon and noise stream,
  * sharing the generator and reward of the call. All pointers are device
@@ -297,11 +326,14 @@ voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* e
  * fits in that array (N <= 87320 for d_s = 8 with FP32 MLPs); larger N returns
  * VOILA_ERR_WORKSPACE before any device work.
  *   status_out  device int32 or NULL: receives the device-side status
- *               (VOILA_OK, VOILA_ERR_NONFINITE or VOILA_ERR_DEGENERATE),
- *               asynchronously on `stream`.
+ *               (VOILA_OK, VOILA_ERR_NONFINITE, VOILA_ERR_DEGENERATE, or
+ *               VOILA_ERR_TIMEOUT if a bounded wait of the tensor-core
+ *               proposal expired), asynchronously on `stream`.
  * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture. The call
- * runs on the current device, so `stream` must belong to it.
+ * device current; make that first call before any stream capture. The address
+ * is looked up again when the device's context has changed (after
+ * cudaDeviceReset the library's device image, and the array, are loaded anew).
+ * The call runs on the current device, so `stream` must belong to it.
  * All calls share the one array and it keeps the last call's contents: calls
  * whose work overlaps on the GPU (different streams, or different host
  * threads) race and must be serialised by the caller.

@@ -285,13 +285,15 @@ def likelihood(L: Likelihood, s_next: np.ndarray, a: np.ndarray, o: np.ndarray) 
 def rollout(g_T: MLP, R: Reward, particles: np.ndarray, actions: np.ndarray,
             d_omega: int, gamma: float, seed: int, planner: int = 0,
             w: Optional[np.ndarray] = None, k_index: Optional[Sequence[int]] = None,
-            return_states: bool = False):
+            return_states: bool = False, n_offset: int = 0):
     """Monte-Carlo rollout of every particle under every action sequence.
 
     particles [N, d_s]; actions [K, H, d_a]. omega_T(n, k, t) comes from
     stream STREAM_ROLLOUT_OMEGA at counter (n, k, t). `k_index` restricts the
     evaluation to a subset of sequences (their global indices keep the noise
-    counters of the full problem). Returns J [K'] and G [K', N].
+    counters of the full problem); `n_offset` is the global index of the first
+    particle when `particles` is a block of a larger belief (particle n draws
+    at counter n + n_offset). Returns J [K'] and G [K', N].
     """
     particles = np.asarray(particles, np.float64)
     actions = np.asarray(actions, np.float64)
@@ -301,7 +303,7 @@ def rollout(g_T: MLP, R: Reward, particles: np.ndarray, actions: np.ndarray,
     Kp = ks.shape[0]
     s = np.broadcast_to(particles[None, :, :], (Kp, N, d_s)).copy()
     G = np.zeros((Kp, N))
-    nn = np.arange(N)[None, :]
+    nn = np.arange(N)[None, :] + n_offset
     kk = ks[:, None]
     states = [s.copy()] if return_states else None
     for t in range(H):

@@ -149,9 +149,20 @@ voila_status voila_rollout(const voila_mlp* g_T, const voila_reward* R, const fl
                            uint64_t seed, uint32_t planner_id, double* J, double* G,
                            int32_t* best_k, void* workspace, size_t ws_bytes,
                            voila_stream_t stream) {
+  return voila_rollout_shard(g_T, R, particles, w, N, 0, N, d_s, actions, K, 0, H, d_a, d_omega, gamma, seed,
+                             planner_id, J, G, best_k, workspace, ws_bytes, stream);
+}
+
+voila_status voila_rollout_shard(const voila_mlp* g_T, const voila_reward* R, const float* particles,
+                                 const double* w, int32_t N, int32_t n_offset, int32_t N_total, int32_t d_s,
+                                 const float* actions, int32_t K, int32_t k_offset, int32_t H, int32_t d_a,
+                                 int32_t d_omega, double gamma, uint64_t seed, uint32_t planner_id, double* J,
+                                 double* G, int32_t* best_k, void* workspace, size_t ws_bytes,
+                                 voila_stream_t stream) {
   voila_status st = check_rollout(g_T, R, N, d_s, K, H, d_a, d_omega);
   if (st != VOILA_OK) return st;
   if (planner_id >= 65536u) return VOILA_ERR_ARG;
+  if (n_offset < 0 || k_offset < 0 || (long long)n_offset + N > N_total) return VOILA_ERR_ARG;
   if (N == 0 || K == 0) return VOILA_OK;
   if (!particles || !J || (H > 0 && d_a > 0 && !actions)) return VOILA_ERR_ARG;
   if (!workspace || ((uintptr_t)workspace % kAlign)) return VOILA_ERR_WORKSPACE;
@@ -180,6 +191,8 @@ voila_status voila_rollout(const voila_mlp* g_T, const voila_reward* R, const fl
   a.gamma = gamma;
   philox_key(seed, a.key0, a.key1);
   a.planner = planner_id;
+  a.n_off = (uint32_t)n_offset;
+  a.k_off = (uint32_t)k_offset;
   a.G = Gbuf;
 
   if (g_T->prec != VOILA_FP32) {  // BF16 and FP8 forms: tensor cores
@@ -191,7 +204,7 @@ voila_status voila_rollout(const voila_mlp* g_T, const voila_reward* R, const fl
     a.ld = simt_ld(maxw);
     if (cudaError_t e = launch_rollout_simt(a, s)) return cuda_status(e);
   }
-  return cuda_status(launch_reduce_returns(Gbuf, w, N, K, J, best_k, s));
+  return cuda_status(launch_reduce_returns(Gbuf, w, N, N_total, K, J, best_k, s));
 }
 
 // Batched rollout workspace: [header | tensor-core scratch | G of every planner

@@ -39,6 +39,15 @@ __device__ double block_exclusive_scan(double v, double* red) {
   return warp_off + inc - v;
 }
 
+// Tempered log-weight lw_i = l_i / lambda + logw_i (Sec. 4.2.3) in FP32: the
+// weights' arithmetic runs in FP32; FP64 holds only their sum, the normalised
+// quantised weights and the exact prefix sum that drives the resampling.
+__device__ __forceinline__ float log_weight(const ResampleArgs& a, int i) {
+  float lw = __fdiv_rn((float)a.ell[i], (float)a.lambda);
+  if (a.logw) lw = __fadd_rn(lw, (float)a.logw[i]);
+  return lw;
+}
+
 __global__ void __launch_bounds__(kResampleThreads) belief_resample_kernel(ResampleArgs a) {
   __shared__ double red[33];
   __shared__ int bad_s;
@@ -47,18 +56,17 @@ __global__ void __launch_bounds__(kResampleThreads) belief_resample_kernel(Resam
   const int i0 = min(N, tid * chunk), i1 = min(N, i0 + chunk);
   if (tid == 0) bad_s = 0;
   __syncthreads();
-  // lw_i = l_i / lambda + logw_i
-  double lmax = -INFINITY;
+  // lw_i = l_i / lambda + logw_i (FP32)
+  float lmax = -INFINITY;
   int bad = 0;
   for (int i = i0; i < i1; ++i) {
-    double lw = __ddiv_rn(a.ell[i], a.lambda);
-    if (a.logw) lw = __dadd_rn(lw, a.logw[i]);
-    a.C[i] = lw;
+    const float lw = log_weight(a, i);
+    a.C[i] = (double)lw;
     if (isnan(lw) || lw == INFINITY) bad = 1;
-    lmax = fmax(lmax, lw);
+    lmax = fmaxf(lmax, lw);
   }
   if (bad) atomicOr(&bad_s, 1);
-  const double m = block_max(lmax, red);
+  const double m = block_max((double)lmax, red);  // an FP32 value
   if (bad_s) {
     if (tid == 0) set_status(a.hdr, VOILA_ERR_NONFINITE, 1);
     return;
@@ -67,10 +75,10 @@ __global__ void __launch_bounds__(kResampleThreads) belief_resample_kernel(Resam
     if (tid == 0) set_status(a.hdr, VOILA_ERR_DEGENERATE, 1);
     return;
   }
-  // e_i = exp(lw_i - m), Z = sum e_i
+  // e_i = exp(lw_i - m) in FP32, Z = sum e_i in FP64
   double zl = 0.0;
   for (int i = i0; i < i1; ++i) {
-    const double e = exp(a.C[i] - m);
+    const double e = (double)expf((float)a.C[i] - (float)m);
     a.C[i] = e;
     zl += e;
   }
@@ -147,15 +155,15 @@ __global__ void __launch_bounds__(kSegThreads) resample_seg_max_kernel(ResampleA
   const int b = blockIdx.x;
   const int s1 = min(a.N, (b + 1) * kResampleSegElems);
   const int i0 = min(s1, b * kResampleSegElems + 4 * (int)threadIdx.x), i1 = min(s1, i0 + 4);
-  double lmax = -INFINITY, bad = 0.0;
+  float lmax = -INFINITY;
+  double bad = 0.0;
   for (int i = i0; i < i1; ++i) {
-    double lw = __ddiv_rn(a.ell[i], a.lambda);
-    if (a.logw) lw = __dadd_rn(lw, a.logw[i]);
-    a.C[i] = lw;
+    const float lw = log_weight(a, i);
+    a.C[i] = (double)lw;
     if (isnan(lw) || lw == INFINITY) bad = 1.0;
-    lmax = fmax(lmax, lw);
+    lmax = fmaxf(lmax, lw);
   }
-  const double m = block_max(lmax, red);
+  const double m = block_max((double)lmax, red);
   const double f = block_max(bad, red);
   if (threadIdx.x == 0) {
     a.part[kPartMax * kResampleMaxSegs + b] = m;
@@ -178,7 +186,7 @@ __global__ void __launch_bounds__(kSegThreads) resample_seg_exp_kernel(ResampleA
   const int i0 = min(s1, b * kResampleSegElems + 4 * (int)threadIdx.x), i1 = min(s1, i0 + 4);
   double zl = 0.0;
   for (int i = i0; i < i1; ++i) {
-    const double e = exp(a.C[i] - m);
+    const double e = (double)expf((float)a.C[i] - (float)m);
     a.C[i] = e;
     zl += e;
   }
@@ -290,13 +298,15 @@ cudaError_t launch_belief_resample(const ResampleArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// J_k = sum_n w_n G[k][n]: one CTA per sequence, fixed summation order.
+// J_k = sum_n w_n G[k][n]: one CTA per sequence, fixed summation order;
+// without w every particle weighs 1 / N_total (N_total = N unless the call is
+// one particle shard of a larger problem).
 __global__ void __launch_bounds__(256) reduce_returns_kernel(const double* __restrict__ G,
                                                              const double* __restrict__ w, int N,
-                                                             int K, double* __restrict__ J) {
+                                                             int N_total, int K, double* __restrict__ J) {
   __shared__ double red[33];
   const int k = blockIdx.x;
-  const double invN = 1.0 / (double)N;
+  const double invN = 1.0 / (double)N_total;
   double acc = 0.0;
   const double* g = G + (size_t)k * N;
   for (int n = threadIdx.x; n < N; n += blockDim.x) acc += g[n] * (w ? w[n] : invN);
@@ -426,9 +436,9 @@ cudaError_t launch_reduce_returns_batched(const BatchedReduceArgs& a, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_returns(const double* G, const double* w, int N, int K, double* J,
+cudaError_t launch_reduce_returns(const double* G, const double* w, int N, int N_total, int K, double* J,
                                   int32_t* best_k, cudaStream_t s) {
-  reduce_returns_kernel<<<K, 256, 0, s>>>(G, w, N, K, J);
+  reduce_returns_kernel<<<K, 256, 0, s>>>(G, w, N, N_total, K, J);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !best_k) return e;
   argmax_kernel<<<1, 1024, 0, s>>>(J, K, best_k);

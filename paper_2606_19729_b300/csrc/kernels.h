@@ -23,6 +23,7 @@ struct RolloutArgs {
   int N, K, H, d_s, d_a, d_omega;
   double gamma;
   uint32_t key0, key1, planner;
+  uint32_t n_off, k_off;  // a shard's offsets in the whole problem: noise counters (n + n_off, k + k_off, t)
   double* G;  // [K][N]
   int ld;     // shared-memory row stride (floats)
 };
@@ -83,7 +84,8 @@ cudaError_t launch_rollout_simt(const RolloutArgs& a, cudaStream_t s);
 cudaError_t launch_belief_propose(const BeliefArgs& a, cudaStream_t s);
 cudaError_t launch_belief_resample(const ResampleArgs& a, cudaStream_t s);
 cudaError_t launch_mlp_fwd(const FwdArgs& a, cudaStream_t s);
-cudaError_t launch_reduce_returns(const double* G, const double* w, int N, int K, double* J,
+// J_k = sum_n w_n G[k][n] (w == NULL: the uniform weight 1 / N_total).
+cudaError_t launch_reduce_returns(const double* G, const double* w, int N, int N_total, int K, double* J,
                                   int32_t* best_k, cudaStream_t s);
 // Returns of P planners in one launch: J_q[k] = sum_n w_q[n] G_q[k][n], then argmax per planner.
 struct BatchedReduceArgs {

@@ -1,6 +1,7 @@
 // voila_belief_update_noalloc: the SIR belief update for callers that cannot
 // allocate device memory. Its scratch is one fixed array compiled into the
 // library instead of a caller workspace.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -18,18 +19,43 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[VOILA_NOALLOC_S
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};  // the context the address above belongs to
+
+// The driver's cuCtxGetCurrent through the runtime's entry-point query (the
+// library does not link libcuda itself).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  }
+  return fn;
+}
 
 // Device address of g_noalloc_scratch on the current device. On the host the
 // symbol is only a stand-in for the device array, so the address must come
-// from the runtime: looked up once per device, with that device current.
+// from the runtime: looked up once per device, with that device current, and
+// again if the device's context has changed since (after cudaDeviceReset the
+// library's device image is loaded anew and the array may have moved).
 voila_status scratch_for_current_device(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VOILA_ERR_CUDA;
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get) return VOILA_ERR_CUDA;
+  CUcontext ctx = nullptr;
+  if (get(&ctx) != CUDA_SUCCESS) return VOILA_ERR_CUDA;  // NULL before this thread's first runtime work
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[dev]) {
+  if (!ctx || !g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
+    // the lookup also makes the device's context current in this thread
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return VOILA_ERR_CUDA;
+    if (get(&ctx) != CUDA_SUCCESS || !ctx) return VOILA_ERR_CUDA;
     g_scratch_ptr[dev] = p;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_ptr[dev];
   return VOILA_OK;

@@ -17,15 +17,15 @@ namespace voila {
 __device__ __forceinline__ void put_noise(float* buf, int ld, int col0, int dim, int nrows,
                                           long long row0, int N, bool rollout_map, uint32_t c2,
                                           uint32_t stream, uint32_t planner, uint32_t k0,
-                                          uint32_t k1) {
+                                          uint32_t k1, uint32_t n_off = 0, uint32_t k_off = 0) {
   const int nblk = (dim + 3) >> 2;
   for (int i = threadIdx.x; i < nrows * nblk; i += blockDim.x) {
     const int r = i / nblk, blk = i % nblk;
     const long long row = row0 + r;
     uint32_t c0, c1;
     if (rollout_map) {
-      c0 = (uint32_t)(row % N);
-      c1 = (uint32_t)(row / N);
+      c0 = (uint32_t)(row % N) + n_off;
+      c1 = (uint32_t)(row / N) + k_off;
     } else {
       c0 = (uint32_t)row;
       c1 = 0;
@@ -81,7 +81,7 @@ rollout_simt_kernel(RolloutArgs a) {
       }
       if (d_w > 0)
         put_noise(bufA, ld, d_s + d_a, d_w, nr, row0, a.N, true, (uint32_t)t,
-                  VOILA_STREAM_ROLLOUT_OMEGA, a.planner, a.key0, a.key1);
+                  VOILA_STREAM_ROLLOUT_OMEGA, a.planner, a.key0, a.key1, a.n_off, a.k_off);
       const float* y = simt_mlp<TW>(a.g, bufA, bufB, ld, nr);
       for (int i = threadIdx.x; i < nr * d_s; i += blockDim.x) {
         const int r = i / d_s, d = i % d_s;

@@ -93,7 +93,8 @@ struct TcPlanner {
   long long rows;          // N * K
   int N, H;
   uint32_t planner;        // noise stream id
-  int pad;
+  uint32_t n_off, k_off;   // the rows' particle and sequence indices in the unsharded problem
+                           // (noise counters (n + n_off, k + k_off, t))
 };
 
 struct TcParams {
@@ -869,6 +870,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       const uint32_t n = valid ? (uint32_t)(row % PL.N) : 0u;
       const uint32_t k = valid ? (uint32_t)(row / PL.N) : 0u;
       const float* act_row = PL.actions + (size_t)k * H * DA;
+      const uint32_t nc = n + PL.n_off, kc = k + PL.k_off;  // noise counters of the unsharded problem
       float s[DS], a[DA];  // sampler mode: x_t and the conditioning [s; a]
       // rollout mode: the row state as packed BF16 words (s_t, a_t and the
       // next step's tail [a_{t+1}; omega_T(n, k, t + 1)], drawn while the
@@ -890,7 +892,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
 #pragma unroll
         for (int i = 0; i < DS; ++i) s[i] = valid ? __ldg(PL.particles + (size_t)n * DS + i) : 0.0f;
         pack_state<DS>(s_pk, s);
-        draw_tail<DA, DW>(tn, act_row, p.key0, p.key1, n, k, 0u, PL.planner);
+        draw_tail<DA, DW>(tn, act_row, p.key0, p.key1, nc, kc, 0u, PL.planner);
         write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
         tail_actions<DA>(a_pk, tn);
       }
@@ -903,7 +905,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           const TcLayer& L = p.layers[l];
           if constexpr (!DDIM && !PAIRS) {
             if (owner && l == p.n_gen - 1 && t + 1 < H)
-              draw_tail<DA, DW>(tn, act_row + (t + 1) * DA, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
+              draw_tail<DA, DW>(tn, act_row + (t + 1) * DA, p.key0, p.key1, nc, kc, (uint32_t)(t + 1), PL.planner);
           }
           if (!bounded_wait(acc_bar, nacc & 1, abort_flag, p.hdr, 30 + g)) {
             ok = false;
@@ -1042,6 +1044,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       const uint32_t n = valid ? (uint32_t)(row % PL.N) : 0u;
       const uint32_t k = valid ? (uint32_t)(row / PL.N) : 0u;
       const float* act_row = PL.actions + (size_t)k * H * DA;
+      const uint32_t nc = n + PL.n_off, kc = k + PL.k_off;  // noise counters of the unsharded problem
       // row state of an owner, as packed BF16 words: s_t, a_t, and the tail
       // [a_{t+1}; omega_T(n, k, t + 1)] drawn ahead of the step's end
       uint32_t s_pk[DS / 2], a_pk[(DA + 1) / 2], tn[(DA + DW + 1) / 2];
@@ -1097,7 +1100,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         if constexpr (PROP)
           draw_tail<DA, DW>(tn, act_row, p.key0, p.key1, n, 0u, p.prop_step, PL.planner, VOILA_STREAM_BELIEF_OMEGA);
         else
-          draw_tail<DA, DW>(tn, act_row, p.key0, p.key1, n, k, 0u, PL.planner);
+          draw_tail<DA, DW>(tn, act_row, p.key0, p.key1, nc, kc, 0u, PL.planner);
         write_gen_row<DS, DA, DW>(Aown, r, s_pk, tn);
         tail_actions<DA>(a_pk, tn);
       }
@@ -1128,7 +1131,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 disc *= p.gamma;
               }
               if (t + 1 < H)
-                draw_tail<DA, DW>(tn, act_row + (t + 1) * DA, p.key0, p.key1, n, k, (uint32_t)(t + 1), PL.planner);
+                draw_tail<DA, DW>(tn, act_row + (t + 1) * DA, p.key0, p.key1, nc, kc, (uint32_t)(t + 1), PL.planner);
             }
             if (!bounded_wait(ptx::smem_u32(&accf[g]), nacc[g] & 1, abort_flag, p.hdr, 30 + g)) {
               ok = false;
@@ -1255,7 +1258,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                   Gacc += disc * (double)(-acc);
                   disc *= p.gamma;
                   if (t + 1 < H) {
-                    draw_tail<DA, DW>(tn, act_row + (t + 1) * DA, p.key0, p.key1, n, k, (uint32_t)(t + 1),
+                    draw_tail<DA, DW>(tn, act_row + (t + 1) * DA, p.key0, p.key1, nc, kc, (uint32_t)(t + 1),
                                       PL.planner);
                     write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
                   }
@@ -1621,6 +1624,8 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
     t.N = q.N;
     t.H = q.H;
     t.planner = q.planner;
+    t.n_off = q.n_off;
+    t.k_off = q.k_off;
     const long long item_rows = pl.wide ? 2 * kTileRows : kSuperRows;
     items += (t.rows + item_rows - 1) / item_rows;
     p.item_end[j] = items;
@@ -2059,6 +2064,8 @@ voila_status tc_rollout(const voila_mlp* g_T, const voila_reward* R, const Rollo
   q.K = a.K;
   q.H = a.H;
   q.planner = a.planner;
+  q.n_off = a.n_off;
+  q.k_off = a.k_off;
   return tc_rollout_batched(g_T, R, &q, 1, a.d_s, a.d_a, a.d_omega, a.gamma, a.key0, a.key1, 0, 0, hdr, scratch, s);
 }
 

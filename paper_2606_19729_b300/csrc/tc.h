@@ -20,6 +20,7 @@ struct TcProblem {
   double* G;               // [K][N]
   int N, K, H;
   uint32_t planner;
+  uint32_t n_off = 0, k_off = 0;  // offsets of a shard's particles and sequences in the whole problem
 };
 
 // Launches one persistent BF16 tcgen05 rollout over P problems sharing the

@@ -80,6 +80,9 @@ _lib_rollout_ws = _sig("voila_rollout_workspace_size", c_int32, POINTER(voila_ml
 _lib_rollout = _sig("voila_rollout", c_int32, POINTER(voila_mlp), POINTER(voila_reward), _P, _P, c_int32,
                     c_int32, _P, c_int32, c_int32, c_int32, c_int32, c_double, c_uint64, c_uint32, _P, _P,
                     _P, _P, c_size_t, _P)
+_lib_rollout_shard = _sig("voila_rollout_shard", c_int32, POINTER(voila_mlp), POINTER(voila_reward), _P, _P,
+                          c_int32, c_int32, c_int32, c_int32, _P, c_int32, c_int32, c_int32, c_int32, c_int32,
+                          c_double, c_uint64, c_uint32, _P, _P, _P, _P, c_size_t, _P)
 _lib_batched_ws = _sig("voila_rollout_batched_workspace_size", c_int32, POINTER(voila_mlp), POINTER(voila_reward),
                        POINTER(voila_planner), c_int32, POINTER(c_size_t))
 _lib_batched = _sig("voila_rollout_batched", c_int32, POINTER(voila_mlp), POINTER(voila_reward), POINTER(voila_planner),
@@ -260,6 +263,20 @@ def voila_rollout(g_T: DeviceMLP, R: voila_reward, particles: torch.Tensor, w: O
                         _ptr(G, torch.float64), _ptr(best_k, torch.int32), _ptr(workspace),
                         workspace.numel(), _stream(stream))
     _check(code, "voila_rollout")
+
+
+def voila_rollout_shard(g_T: DeviceMLP, R: voila_reward, particles: torch.Tensor, w: Optional[torch.Tensor],
+                        n_offset: int, N_total: int, actions: torch.Tensor, k_offset: int, d_omega: int,
+                        gamma: float, seed: int, planner_id: int, J: torch.Tensor, G: Optional[torch.Tensor],
+                        best_k: Optional[torch.Tensor], workspace: torch.Tensor, stream=None):
+    N, d_s = particles.shape
+    K, H, d_a = actions.shape
+    code = _lib_rollout_shard(ctypes.byref(g_T.desc), ctypes.byref(R), _ptr(particles, torch.float32),
+                              _ptr(w, torch.float64), N, n_offset, N_total, d_s, _ptr(actions, torch.float32), K,
+                              k_offset, H, d_a, d_omega, gamma, seed, planner_id, _ptr(J, torch.float64),
+                              _ptr(G, torch.float64), _ptr(best_k, torch.int32), _ptr(workspace),
+                              workspace.numel(), _stream(stream))
+    _check(code, "voila_rollout_shard")
 
 
 SCHED_LONGEST_FIRST = 1

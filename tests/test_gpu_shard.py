@@ -1,0 +1,97 @@
+"""voila_rollout_shard: a rollout split by sequences or by particles gives the
+unsharded call's results (Sec. 2.2: the simulations are independent).
+
+Split by sequences: J, G and best_k of the whole problem, bit for bit. Split by
+particles: every shard's G is the matching block of the whole G bit for bit,
+and the shards' partial J added in rank order equal the whole J within FP64
+rounding. Both precision forms that take different kernels (FP32 CUDA cores,
+BF16 tensor cores), ragged shard sizes, and the offsets checked against the
+oracle's counters (a shard is not the whole problem's first block)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import voila_oracle as O
+from paper_2606_19729_b300 import shard as S
+from paper_2606_19729_b300 import workloads as WL
+from tests.helpers import cuda, oracle_mlp, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_19729_b300 import voila
+    return voila
+
+
+def _setup(V, form):
+    if form == "bf16":
+        wl = WL.mid_bf16(N=700, K=37, H=4)
+        R = V.mlp_reward(V.DeviceMLP.from_spec(wl.reward_mlp))
+        Ro = O.Reward(O.REWARD_MLP, mlp=oracle_mlp(wl.reward_mlp))
+    else:
+        wl = WL.small_fp32(N=300, K=21, H=5)
+        R = V.goal_reward(list(wl.goal))
+        Ro = O.Reward(O.REWARD_GOAL, wl.goal)
+    return wl, V.DeviceMLP.from_spec(wl.g_T), R, Ro
+
+
+def _shard(V, wl, g, R, n0, n1, k0, k1):
+    N, K = n1 - n0, k1 - k0
+    J = torch.empty(K, dtype=torch.float64, device="cuda")
+    G = torch.empty((K, N), dtype=torch.float64, device="cuda")
+    best = torch.empty(1, dtype=torch.int32, device="cuda")
+    ws = V.alloc_workspace(V.voila_rollout_workspace_size(g, R, N, K, wl.H))
+    V.voila_rollout_shard(g, R, cuda(wl.particles[n0:n1]), None, n0, wl.N, cuda(wl.actions[k0:k1]), k0,
+                          wl.d_omega, wl.gamma, wl.seed, 2, J, G, best, ws)
+    assert V.workspace_status(ws) == V.OK
+    return J, G, int(best.item())
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16"])
+def test_sequence_split_is_bit_identical(V, form):
+    wl, g, R, _ = _setup(V, form)
+    Jf, Gf, bf = _shard(V, wl, g, R, 0, wl.N, 0, wl.K)
+    for cuts in ([0, 17, wl.K], [0, 1, 12, wl.K]):
+        parts = [_shard(V, wl, g, R, 0, wl.N, a, b) for a, b in zip(cuts[:-1], cuts[1:])]
+        J = S.combine_sequence_shards([p[0] for p in parts])
+        assert torch.equal(J, Jf)
+        assert torch.equal(torch.cat([p[1] for p in parts], dim=0), Gf)
+    assert bf == int(torch.argmax(Jf).item())
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16"])
+def test_particle_split_matches(V, form):
+    wl, g, R, Ro = _setup(V, form)
+    Jf, Gf, _ = _shard(V, wl, g, R, 0, wl.N, 0, wl.K)
+    cuts = [0, 129, wl.N - 3, wl.N]
+    parts = [_shard(V, wl, g, R, a, b, 0, wl.K) for a, b in zip(cuts[:-1], cuts[1:])]
+    assert torch.equal(torch.cat([p[1] for p in parts], dim=1), Gf)
+    J = S.combine_particle_shards([p[0] for p in parts])
+    np.testing.assert_allclose(J.cpu().numpy(), Jf.cpu().numpy(), rtol=1e-13, atol=1e-15)
+    # a shard in the middle of both axes, against the oracle's counters
+    n0, n1, k0, k1 = 129, 300, 5, 16
+    Js, Gs, _ = _shard(V, wl, g, R, n0, n1, k0, k1)
+    Jo, Go = O.rollout(oracle_mlp(wl.g_T), Ro, wl.particles[n0:n1], wl.actions, wl.d_omega, wl.gamma, wl.seed,
+                       planner=2, w=np.full(n1 - n0, 1.0 / wl.N), k_index=list(range(k0, k1)), n_offset=n0)
+    tol = 1e-5 if form == "fp32" else 2e-2
+    assert rel_err(Gs.cpu().numpy(), Go) < tol
+    assert rel_err(Js.cpu().numpy(), Jo) < tol
+
+
+def test_shard_arguments_checked(V):
+    wl, g, R, _ = _setup(V, "fp32")
+    J = torch.empty(wl.K, dtype=torch.float64, device="cuda")
+    ws = V.alloc_workspace(V.voila_rollout_workspace_size(g, R, 10, wl.K, wl.H))
+    for n_off, n_total in [(-1, wl.N), (wl.N - 5, wl.N), (0, 0)]:
+        with pytest.raises(V.VoilaError) as e:
+            V.voila_rollout_shard(g, R, cuda(wl.particles[:10]), None, n_off, n_total, cuda(wl.actions), 0,
+                                  wl.d_omega, wl.gamma, wl.seed, 0, J, None, None, ws)
+        assert e.value.code == V.ERR_ARG
+    with pytest.raises(V.VoilaError) as e:
+        V.voila_rollout_shard(g, R, cuda(wl.particles[:10]), None, 0, wl.N, cuda(wl.actions), -2,
+                              wl.d_omega, wl.gamma, wl.seed, 0, J, None, None, ws)
+    assert e.value.code == V.ERR_ARG

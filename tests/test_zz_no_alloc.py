@@ -104,3 +104,41 @@ def test_noalloc_reports_device_status_and_refuses_oversize(V):
         V.voila_belief_update_noalloc(g, lik, big, None, cuda(wl.actions[0, 0]), cuda(np.zeros(4)), wl.d_omega,
                                       1.0, 0, 0, 0, *outs, status)
     assert e.value.code == V.ERR_WORKSPACE
+
+
+def _largest_n(V, g, lik, cap):
+    """The largest particle count whose belief-update workspace fits `cap` bytes."""
+    lo, hi = 1, 1 << 20
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        if V.voila_belief_update_workspace_size(g, lik, mid) <= cap:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
+@pytest.mark.gpu
+def test_noalloc_bf16_tensor_core_proposal_up_to_the_limit(V):
+    # BF16 generator and likelihood of the tensor-core shapes: the packed weights
+    # share the fixed array with the particle scratch, and above 2048 particles
+    # the resampling runs in many CTAs; both run here through the fixed array,
+    # twice in a row, at the largest N it holds and one particle more
+    wl = WL.mid_bf16(N=80000, K=1, H=1)
+    g = V.DeviceMLP.from_spec(wl.g_T)
+    lik = V.mlp_likelihood(V.DeviceMLP.from_spec(wl.ell))
+    cap = 4 << 20  # VOILA_NOALLOC_SCRATCH_BYTES
+    n_max = _largest_n(V, g, lik, cap)
+    assert 50000 < n_max < 80000
+    for N, lam, step in ((4096, 1.0, 1), (n_max, 0.5, 2)):
+        ref, got = _case(V, wl, lik, N, lam, step)
+        _same(ref, got)
+        # indices: the systematic resampling of the device's own weights
+        u0 = O.resample_uniform(wl.seed, step, 0)
+        assert np.array_equal(got[1], O.systematic_resample(got[2], u0))
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    outs = _outputs(n_max + 1, wl.d_s)
+    with pytest.raises(V.VoilaError) as e:
+        V.voila_belief_update_noalloc(g, lik, cuda(wl.particles[:n_max + 1]), None, cuda(wl.actions[0, 0]),
+                                      cuda(np.zeros(wl.d_o)), wl.d_omega, 1.0, wl.seed, 3, 0, *outs, status)
+    assert e.value.code == V.ERR_WORKSPACE
