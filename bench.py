@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-seqs", type=int, default=16, help="sequences for the FP32-form comparison (0: skip)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32/FP8 form comparison")
+    ap.add_argument("--batched-schedules", action="store_true",
+                    help="batched workload: also time every candidate schedule of the autotuner")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the compact records of the other configurations in the default run")
     ap.add_argument("--sweep-err-seqs", type=int, default=64, help="sequences of the sweep's FP64 error subset")
@@ -475,7 +477,7 @@ def batched_record(args, rank, world, local):
         sequential()
         torch.cuda.synchronize()
         seq_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(max(1, args.steps // 2))]
+                  for _ in range(max(1, args.steps))]
         for a, b in seq_ev:
             flush.fill_(1)
             a.record(stream)
@@ -483,7 +485,29 @@ def batched_record(args, rank, world, local):
             b.record(stream)
         torch.cuda.synchronize()
         seq_s = sum(a.elapsed_time(b) for a, b in seq_ev) / 1e3
-    same = all(torch.equal(a, it["J"]) for a, it in zip(J_batched, items))
+        same = all(torch.equal(a, it["J"]) for a, it in zip(J_batched, items))
+        # every candidate schedule of the autotuner, timed alone on the same work
+        sched_ms = {}
+        if getattr(args, "batched_schedules", False):
+            full = torch.cuda.get_device_properties(local).multi_processor_count // 2
+            names = {"two-tile static LPT": 1, "two-tile static table order": 0, "two-tile queue LPT": 3,
+                     "two-tile queue table order": 2, f"two-tile queue LPT {full - 2} pairs": 3 | ((full - 2) << 8),
+                     f"two-tile static LPT {full * 7 // 8} pairs": 1 | ((full * 7 // 8) << 8),
+                     "one-tile queue LPT": 7, "one-tile static LPT": 5}
+            for nm, sc in names.items():
+                ts = []
+                for _ in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    flush.fill_(2)
+                    e0.record(stream)
+                    V.voila_rollout_batched(g, R, pl, wl.d_s, wl.d_a, wl.d_omega, wl.gamma, wl.seed, sc, ws,
+                                            stream=stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                sched_ms[nm] = {"schedule": sc, "ms_median_of_3": statistics.median(ts)}
+    b_ms = [a.elapsed_time(b) for a, b in ev]
+    s_ms = [a.elapsed_time(b) for a, b in seq_ev]
     peaks = load_peaks()
     clocks = clk.summary()
     fpt = flops_per_transition(wl)
@@ -497,11 +521,17 @@ def batched_record(args, rank, world, local):
                        "l2": "flushed (256 MB write) before every timed step",
                        "launch": "one autotuned batched launch captured in a CUDA graph"},
             "schedule": best, "autotune_ms": tune_ms,
-            "sequential_64_launches": {"value": E * len(seq_ev) / seq_s, "ms_per_step": 1e3 * seq_s / len(seq_ev)},
+            "batched_ms": {"repeats": len(b_ms), "min": min(b_ms), "median": statistics.median(b_ms),
+                           "max": max(b_ms), "stdev": statistics.pstdev(b_ms)},
+            "sequential_64_launches": {"value": E * len(seq_ev) / seq_s, "ms_per_step": 1e3 * seq_s / len(seq_ev),
+                                       "repeats": len(s_ms), "min": min(s_ms), "median": statistics.median(s_ms),
+                                       "max": max(s_ms), "stdev": statistics.pstdev(s_ms)},
             "batched_equals_sequential": same,
             "roofline": dict(tensor_roofline(achieved, peaks, clocks, "bf16"), traffic=None,
                              kernel="rollout_tc_kernel (batched)"),
             "gpu_launches": 4 * args.steps, "clocks": clocks}
+    if sched_ms:
+        line["schedules"] = sched_ms
     return line
 
 
@@ -1024,8 +1054,8 @@ def config_records(args, rank, world, local, fp8_peak):
     a.steps, a.warmup = 4, 1
     b = batched_record(a, rank, world, local)
     out["c5_batched"] = {k: b.get(k) for k in ("value", "unit", "ms_per_step", "schedule", "autotune_ms",
-                                               "sequential_64_launches", "batched_equals_sequential", "roofline",
-                                               "clocks")}
+                                               "batched_ms", "sequential_64_launches", "batched_equals_sequential",
+                                               "roofline", "clocks")}
     out["c5_batched"]["workload"] = b["config"]["workload"]
     return out
 

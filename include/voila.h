@@ -230,8 +230,17 @@ typedef struct {
 } voila_planner;
 
 /* Schedules of voila_rollout_batched: bit 0 = order work by descending
- * horizon (longest first); bits 8-15 = cap on CTA pairs (0 = all resident). */
+ * horizon (longest first); bit 1 = work items claimed from an atomic counter
+ * by whichever CTA pair is ready (else pair c takes items c, c + pairs, ...);
+ * bit 2 = the one-tile shape: one 128-row tile per CTA and work item, reward
+ * output as an MMA (else two tiles per CTA in flight and the scalar reward
+ * output computed in the epilogue; the two shapes round the reward
+ * differently, both within the BF16 tolerance; not available for FP8 MLPs of
+ * the mid-size dimensions: VOILA_ERR_UNSUPPORTED); bits 8-15 = cap on CTA
+ * pairs (0 = all resident). */
 #define VOILA_SCHED_LONGEST_FIRST 1
+#define VOILA_SCHED_QUEUE 2
+#define VOILA_SCHED_ONE_TILE 4
 #define VOILA_SCHED_CLUSTERS(n) ((n) << 8)
 
 /* Workspace bytes for voila_rollout_batched (host call, no device work). */
@@ -258,11 +267,17 @@ voila_status voila_rollout_batched(const voila_mlp* g_T, const voila_reward* R,
                                    voila_stream_t stream);
 
 /*
- * Autotuner for voila_rollout_batched: runs each candidate schedule (work
- * order x number of CTA pairs) on these inputs, times it with CUDA events and
- * writes the fastest to *best_schedule (host int32). Synchronises `stream`;
- * do not call it during stream capture. Outputs are left as the last
- * candidate's (all candidates compute the same values).
+ * Autotuner for voila_rollout_batched: runs each candidate schedule (tile
+ * shape: two tiles in flight with the fused reward output or one tile with the
+ * reward output as an MMA; work order: static longest-first, table order or
+ * the atomic queue; number of CTA pairs) on these inputs, times it with CUDA
+ * events and writes the fastest to *best_schedule (host int32) and its time to
+ * *best_ms (or NULL). Candidates a form has no kernel for are skipped.
+ * Synchronises `stream`; do not call it during stream capture. Outputs are
+ * left as the last candidate's: schedules of one tile shape compute the same
+ * bits; the two shapes differ in the reward output's rounding (within the
+ * BF16 tolerance), so pass the returned schedule to voila_rollout_batched to
+ * reproduce a result.
  */
 voila_status voila_rollout_batched_autotune(const voila_mlp* g_T, const voila_reward* R,
                                             const voila_planner* planners, int32_t P,

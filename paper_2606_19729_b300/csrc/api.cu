@@ -271,8 +271,10 @@ voila_status voila_rollout_batched(const voila_mlp* g_T, const voila_reward* R, 
       probs[i].H = planners[i].H;
       probs[i].planner = planners[i].planner_id;
     }
+    const int shape = ((schedule & VOILA_SCHED_QUEUE) ? kShapeQueue : 0) |
+                      ((schedule & VOILA_SCHED_ONE_TILE) ? kShapeOneTile : 0);
     st = tc_rollout_batched(g_T, R, probs, P, d_s, d_a, d_omega, gamma, k0, k1, schedule & 1,
-                            (schedule >> 8) & 0xff, (WsHeader*)ws, ws + align_up(kHeaderBytes, 1024), s);
+                            (schedule >> 8) & 0xff, shape, (WsHeader*)ws, ws + align_up(kHeaderBytes, 1024), s);
     if (st != VOILA_OK) return st;
   } else {
     for (int i = 0; i < P; ++i) {
@@ -335,30 +337,46 @@ voila_status voila_rollout_batched_autotune(const voila_mlp* g_T, const voila_re
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int full = nsm / 2;
-  const int32_t cands[6] = {VOILA_SCHED_LONGEST_FIRST,
-                            0,
-                            VOILA_SCHED_LONGEST_FIRST | VOILA_SCHED_CLUSTERS(full - 2),
-                            VOILA_SCHED_LONGEST_FIRST | VOILA_SCHED_CLUSTERS(full * 7 / 8),
-                            VOILA_SCHED_LONGEST_FIRST | VOILA_SCHED_CLUSTERS(full * 3 / 4),
-                            VOILA_SCHED_CLUSTERS(full * 3 / 4)};
+  // tile shape (two 128-row tiles per CTA in flight with fused scalar outputs,
+  // or one tile with the scalar outputs as MMAs) x work order (static
+  // longest-first, table order, or claimed from the queue) x CTA pairs
+  constexpr int kCands = 9;
+  const int32_t cands[kCands] = {VOILA_SCHED_LONGEST_FIRST,
+                                 0,
+                                 VOILA_SCHED_LONGEST_FIRST | VOILA_SCHED_QUEUE,
+                                 VOILA_SCHED_QUEUE,
+                                 VOILA_SCHED_LONGEST_FIRST | VOILA_SCHED_QUEUE | VOILA_SCHED_CLUSTERS(full - 2),
+                                 VOILA_SCHED_LONGEST_FIRST | VOILA_SCHED_CLUSTERS(full * 7 / 8),
+                                 VOILA_SCHED_LONGEST_FIRST | VOILA_SCHED_CLUSTERS(full * 3 / 4),
+                                 VOILA_SCHED_LONGEST_FIRST | VOILA_SCHED_QUEUE | VOILA_SCHED_ONE_TILE,
+                                 VOILA_SCHED_LONGEST_FIRST | VOILA_SCHED_ONE_TILE};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return VOILA_ERR_CUDA;
   float best = 1e30f;
   int32_t arg = cands[0];
   voila_status st = VOILA_OK;
-  for (int c = 0; c < 6 && st == VOILA_OK; ++c) {
-    st = voila_rollout_batched(g_T, R, planners, P, d_s, d_a, d_omega, gamma, seed, cands[c], workspace, ws_bytes,
-                               stream);  // warm-up
-    if (st != VOILA_OK) break;
-    cudaEventRecord(e0, s);
-    st = voila_rollout_batched(g_T, R, planners, P, d_s, d_a, d_omega, gamma, seed, cands[c], workspace, ws_bytes,
-                               stream);
-    cudaEventRecord(e1, s);
-    if (cudaEventSynchronize(e1) != cudaSuccess) st = VOILA_ERR_CUDA;
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (st == VOILA_OK && ms < best) {
-      best = ms;
+  for (int c = 0; c < kCands && st == VOILA_OK; ++c) {
+    // each candidate is timed once, and once more (keeping the faster) when a
+    // run is short enough for a first launch's set-up to show
+    float ms_c = 1e30f;
+    for (int rep = 0; rep < 2 && st == VOILA_OK; ++rep) {
+      cudaEventRecord(e0, s);
+      st = voila_rollout_batched(g_T, R, planners, P, d_s, d_a, d_omega, gamma, seed, cands[c], workspace,
+                                 ws_bytes, stream);
+      cudaEventRecord(e1, s);
+      if (st != VOILA_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = VOILA_ERR_CUDA;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < ms_c) ms_c = ms;
+      if (ms > 50.0f) break;
+    }
+    if (st == VOILA_ERR_UNSUPPORTED) {  // a tile shape this form has no kernel for
+      st = VOILA_OK;
+      continue;
+    }
+    if (st == VOILA_OK && ms_c < best) {
+      best = ms_c;
       arg = cands[c];
     }
   }

@@ -112,7 +112,10 @@ struct TcParams {
   WsHeader* hdr;
   // Work items are 512-row super-pairs, numbered planner by planner in table
   // order; cluster c takes items c, c + clusters, ... (with the table sorted
-  // by descending horizon this approximates longest-processing-time first).
+  // by descending horizon this approximates longest-processing-time first),
+  // or, in the queue instantiation, whichever item is next on the global
+  // counter `queue` (zeroed before the launch) when the cluster is ready.
+  unsigned long long* queue;
   int P;
   long long total_items;
   long long item_end[kMaxPlanners];  // inclusive prefix sum of items per planner
@@ -176,6 +179,67 @@ __device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, vola
       return false;
     }
   }
+}
+
+// ---- work-item queue (QUEUE instantiations) -------------------------------
+// The even CTA's producer thread claims items from the global counter and
+// posts each in slot j mod kItemRing of both CTAs' item rings (j = the
+// cluster's item number); every other role of the pair (the MMA thread, the
+// odd CTA's producer, each epilogue warp of both CTAs) takes item j from its
+// own ring and frees the slot on the even CTA's item_empty barrier, so all
+// roles walk the same items in the same order. -1 marks the end.
+constexpr int kItemRing = 4;
+constexpr int kItemTakers = 2 + 2 * (kTcThreads / 32 - 2);
+
+// bounded_wait with acquire semantics at cluster scope (the phase is completed
+// by release arrivals of the other CTA of the pair as well).
+__device__ __forceinline__ bool bounded_wait_cluster(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                                     WsHeader* hdr, int where) {
+  if (ptx::mbar_try_wait_acq_cluster(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (ptx::mbar_try_wait_acq_cluster(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kSpinLimit) {
+      *abort_flag = 1;
+      set_status(hdr, VOILA_ERR_TIMEOUT, where);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ long long claim_item(uint64_t* item_full, uint64_t* item_empty, long long* ring,
+                                                long long j, unsigned long long* counter, long long total,
+                                                volatile int* abort_flag, WsHeader* hdr) {
+  const int sl = (int)(j % kItemRing);
+  const uint32_t par = (uint32_t)((j / kItemRing) & 1);
+  if (!bounded_wait_cluster(ptx::smem_u32(&item_empty[sl]), par ^ 1, abort_flag, hdr, 13)) return -2;
+  const long long c = (long long)atomicAdd(counter, 1ull);
+  const long long it = c < total ? c : -1;
+  for (uint32_t r = 0; r < 2; ++r) {
+    ptx::st_shared_cluster_s64(ptx::mapa_shared(ptx::smem_u32(&ring[sl]), r), it);
+    ptx::mbar_arrive_release_cluster(ptx::mapa_shared(ptx::smem_u32(&item_full[sl]), r));
+  }
+  return it;
+}
+
+// Takes item j (-1: no more, -2: a wait expired). warp_wide: called by all 32
+// lanes of a warp, which then agree on the result, and lane 0 frees the slot.
+__device__ __forceinline__ long long take_item(uint64_t* item_full, uint64_t* item_empty, long long* ring,
+                                               long long j, bool warp_wide, volatile int* abort_flag,
+                                               WsHeader* hdr) {
+  const int sl = (int)(j % kItemRing);
+  const uint32_t par = (uint32_t)((j / kItemRing) & 1);
+  const bool got = bounded_wait_cluster(ptx::smem_u32(&item_full[sl]), par, abort_flag, hdr, 14);
+  long long it = got ? *reinterpret_cast<volatile long long*>(&ring[sl]) : -2;
+  if (warp_wide) {
+    if (!__all_sync(0xffffffffu, got)) return -2;
+    it = __shfl_sync(0xffffffffu, it, 0);
+  }
+  if (!got) return -2;
+  if (!warp_wide || (threadIdx.x & 31) == 0)
+    ptx::mbar_arrive_release_cluster(ptx::mapa_shared(ptx::smem_u32(&item_empty[sl]), 0));
+  return it;
 }
 
 // Activation of two accumulator values, packed to BF16x2 for the next layer.
@@ -603,7 +667,7 @@ __device__ __forceinline__ void write_pair_row(const TcParams& p, uint8_t* A, in
 // samples and the H steps are the sampler's steps; no reward, the output is x
 // per row. MODE kModePairs (DS = 8, DA = 2, DW = 6, not WIDE): the rows are
 // likelihood pairs; the MLP's scalar output is stored per row.
-template <int DS, int DA, int DW, bool F8, bool WIDE, int MODE = kModeRollout>
+template <int DS, int DA, int DW, bool F8, bool WIDE, int MODE = kModeRollout, bool QUEUE = false>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     rollout_tc_kernel(const __grid_constant__ TcParams p) {
   constexpr bool DDIM = MODE == kModeDdim;
@@ -614,6 +678,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
   static_assert(!OBS || (!WIDE && !F8), "observation rows use the two-tile kernel");
   constexpr bool PROP = MODE == kModePropose;
   static_assert(!PROP || (!WIDE && DS == 8 && DA == 2 && DW == 8), "belief proposal layout");
+  static_assert(!QUEUE || MODE == kModeRollout, "the work-item queue serves the rollout");
   // work items of the launch: the observation rows are counted on the device
   long long total_items = p.total_items;
   if constexpr (OBS) {
@@ -635,7 +700,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
   uint64_t* accf = bars + 2 * kStages;      // [2]
   uint64_t* ready = bars + 2 * kStages + 2;  // [2]
   uint64_t* drain = bars + 2 * kStages + 4;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 5);
+  uint64_t* item_full = bars + 2 * kStages + 5;               // [kItemRing]
+  uint64_t* item_empty = item_full + kItemRing;               // [kItemRing]
+  long long* item_ring = reinterpret_cast<long long*>(item_empty + kItemRing);  // [kItemRing]
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(item_ring + kItemRing);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -652,6 +720,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       ptx::mbar_init(ptx::smem_u32(&ready[g]), 4 * kEpiWarpsPerTile);
     }
     ptx::mbar_init(ptx::smem_u32(drain), 1);
+    for (int i = 0; i < kItemRing; ++i) {
+      ptx::mbar_init(ptx::smem_u32(&item_full[i]), 1);
+      ptx::mbar_init(ptx::smem_u32(&item_empty[i]), kItemTakers);
+    }
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
@@ -677,7 +749,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       bool ok = true;
       int last_round[kStages];
       for (int s = 0; s < kStages; ++s) last_round[s] = -1;
-      for (long long it = cl; it < total_items && ok; it += ncl) {
+      long long jq = 0;  // queue: the cluster's item number
+      for (long long it = QUEUE ? (rank == 0 ? claim_item(item_full, item_empty, item_ring, jq, p.queue, total_items,
+                                                          abort_flag, p.hdr)
+                                             : take_item(item_full, item_empty, item_ring, jq, false, abort_flag,
+                                                         p.hdr))
+                                : cl;
+           it >= 0 && it < total_items && ok;
+           it = QUEUE ? (rank == 0 ? claim_item(item_full, item_empty, item_ring, ++jq, p.queue, total_items,
+                                                abort_flag, p.hdr)
+                                   : take_item(item_full, item_empty, item_ring, ++jq, false, abort_flag, p.hdr))
+                      : it + ncl) {
         const int H = p.pl[item_planner(p, it)].H;
         for (int t = 0; t < H && ok; ++t)
           for (int l = 0; l < p.n_total && ok; ++l)
@@ -707,6 +789,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
               }
             }
       }
+      if (QUEUE && *abort_flag) ok = false;  // a claim or take that gave up ended the loop
       if (!ok && rank == 0) {  // drain loads still in flight before shared memory goes away
         for (int s = 0; s < kStages; ++s)
           if (last_round[s] >= 0) {
@@ -731,7 +814,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         const uint64_t adesc0 = ptx::smem_desc(ptx::smem_u32(Abuf[0]), 1024, ptx::kSwizzle128B);
         const uint64_t adesc1 = ptx::smem_desc(ptx::smem_u32(Abuf[1]), 1024, ptx::kSwizzle128B);
         const uint64_t bdesc0 = ptx::smem_desc(ring_addr, 1024, ptx::kSwizzle128B);
-        for (long long it = cl; it < total_items && ok; it += ncl) {
+        long long jq = 0;
+        for (long long it = QUEUE ? take_item(item_full, item_empty, item_ring, jq, false, abort_flag, p.hdr) : cl;
+             it >= 0 && it < total_items && ok;
+             it = QUEUE ? take_item(item_full, item_empty, item_ring, ++jq, false, abort_flag, p.hdr) : it + ncl) {
           const int H = p.pl[item_planner(p, it)].H;
           for (int t = 0; t < H && ok; ++t)
             for (int l = 0; l < p.n_total && ok; ++l) {
@@ -859,7 +945,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     const uint32_t acc_bar1 = ptx::smem_u32(&accf[1]);
     uint32_t nacc = 0, nacc1 = 0;
     bool ok = true;
-    for (long long it = cl; it < total_items && ok; it += ncl) {
+    long long jq = 0;
+    for (long long it = QUEUE ? take_item(item_full, item_empty, item_ring, jq, true, abort_flag, p.hdr) : cl;
+         it >= 0 && it < total_items && ok;
+         it = QUEUE ? take_item(item_full, item_empty, item_ring, ++jq, true, abort_flag, p.hdr) : it + ncl) {
       const int q = item_planner(p, it);
       const long long sp = it - (q ? p.item_end[q - 1] : 0);
       const TcPlanner& PL = p.pl[q];
@@ -1034,7 +1123,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     const uint32_t ready_remote1 = ptx::mapa_shared(ptx::smem_u32(&ready[1]), 0);
     uint32_t nacc[2] = {0u, 0u};
     bool ok = true;
-    for (long long it = cl; it < total_items && ok; it += ncl) {
+    long long jq = 0;
+    for (long long it = QUEUE ? take_item(item_full, item_empty, item_ring, jq, true, abort_flag, p.hdr) : cl;
+         it >= 0 && it < total_items && ok;
+         it = QUEUE ? take_item(item_full, item_empty, item_ring, ++jq, true, abort_flag, p.hdr) : it + ncl) {
       const int pq = item_planner(p, it);
       const long long sp = it - (pq ? p.item_end[pq - 1] : 0);
       const TcPlanner& PL = p.pl[pq];
@@ -1409,15 +1501,18 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 // ddim: g is the DDIM teacher [s (8); a (2); x (8); e (64)] -> ... -> 8; its
 // first layer is packed with 96 input columns in the order write_ddim_input
 // writes them.
-Plan make_plan(const voila_mlp* g, const voila_reward* R, bool ddim = false) {
+// one_tile: the one-tile shape (the wide kernel: one 128-row tile per CTA and
+// work item, the scalar output layers as MMAs) for MLPs of any width.
+Plan make_plan(const voila_mlp* g, const voila_reward* R, bool ddim = false, bool one_tile = false) {
   Plan pl;
   memset(&pl, 0, sizeof(pl));
   pl.ok = false;
   pl.pack.colmap_layer = -1;
+  pl.wide = one_tile;
   const voila_mlp* mlps[2] = {g, R && R->kind == VOILA_REWARD_MLP ? R->mlp : nullptr};
   int nl = 0, boff = 0, rows = 0, foff = 0;
   long long elems = 0;
-  bool any_wide = false;  // a layer wider than 256: the wide kernel, which has no fused outputs
+  bool any_wide = one_tile;  // a layer wider than 256: the wide kernel, which has no fused outputs
   for (int m = 0; m < 2; ++m)
     if (mlps[m])
       for (int l = 0; l <= mlps[m]->n_layers; ++l) any_wide = any_wide || mlps[m]->dims[l] > 256;
@@ -1520,14 +1615,16 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R, bool ddim = false) {
 }
 
 size_t tc_smem_bytes(int vec_floats) {
-  return 1024 + 2 * kABytes + kStages * kSlotBytes + (size_t)vec_floats * 4 + (2 * kStages + 5) * 8 + 16;
+  // barriers (weight ring, accumulators, ready, drain, item ring), item slots, TMEM address, abort flag
+  return 1024 + 2 * kABytes + kStages * kSlotBytes + (size_t)vec_floats * 4 + (2 * kStages + 5 + 3 * kItemRing) * 8 +
+         16;
 }
 
 // Launches one persistent CTA pair per co-resident cluster slot (at most
 // `max_clusters`, never more than there are super-pairs).
-template <int DS, int DA, int DW, bool F8, bool WIDE, int MODE = kModeRollout>
+template <int DS, int DA, int DW, bool F8, bool WIDE, int MODE = kModeRollout, bool QUEUE = false>
 cudaError_t launch_tc(const TcParams& p, size_t smem, long long max_clusters, cudaStream_t s) {
-  auto k = rollout_tc_kernel<DS, DA, DW, F8, WIDE, MODE>;
+  auto k = rollout_tc_kernel<DS, DA, DW, F8, WIDE, MODE, QUEUE>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
@@ -1577,20 +1674,30 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }  // namespace
 
 size_t tc_rollout_scratch_bytes(const voila_mlp* g_T, const voila_reward* R) {
+  // the larger of the two tile shapes' packed weights (the one-tile shape packs
+  // the scalar output layers as MMA operands)
   Plan pl = make_plan(g_T, R);
-  return pl.ok ? pl.total : 0;
+  Plan p1 = make_plan(g_T, R, false, true);
+  size_t b = pl.ok ? pl.total : 0;
+  if (p1.ok && p1.total > b) b = p1.total;
+  return b;
 }
 
 voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, const TcProblem* probs, int P,
                                 int d_s, int d_a, int d_omega, double gamma, uint32_t key0, uint32_t key1,
-                                int order, int max_clusters, WsHeader* hdr, void* scratch, cudaStream_t s) {
-  Plan pl = make_plan(g_T, R);
+                                int order, int max_clusters, int shape, WsHeader* hdr, void* scratch,
+                                cudaStream_t s) {
+  const bool queue = (shape & kShapeQueue) != 0;
+  const bool one_tile = (shape & kShapeOneTile) != 0;
+  Plan pl = make_plan(g_T, R, false, one_tile);
   if (!pl.ok) return VOILA_ERR_UNSUPPORTED;
   if (P < 1 || P > kMaxPlanners) return VOILA_ERR_ARG;
   const bool dims_a = d_s == 8 && d_a == 2 && d_omega == 8;
   const bool dims_b = d_s == 12 && d_a == 3 && d_omega == 16;
   if (!dims_a && !dims_b) return VOILA_ERR_UNSUPPORTED;
-  if (pl.wide && !dims_b) return VOILA_ERR_UNSUPPORTED;  // the wide kernel is built for the sweep dimensions
+  const bool f8 = g_T->prec == VOILA_FP8E4M3;
+  // the wide kernel is built for the sweep dimensions, and for the mid-size ones in BF16
+  if (pl.wide && !dims_b && (!dims_a || f8)) return VOILA_ERR_UNSUPPORTED;
   if ((uintptr_t)scratch % 16) return VOILA_ERR_WORKSPACE;  // TMA global base alignment
   TcParams& p = pl.p;
   // work table: planners with rows and steps, optionally longest horizon first
@@ -1679,16 +1786,30 @@ voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, con
   long long nclusters = items < nsm / 2 ? items : nsm / 2;
   if (max_clusters > 0 && nclusters > max_clusters) nclusters = max_clusters;
   const size_t smem = tc_smem_bytes(p.bias_total + p.scale_total + p.fuse_total + (p.fuse_total ? 1024 : 0));
-  const bool f8 = p.scale_total > 0;
+  if (queue) {  // the work-item counter, in the workspace header, starts at zero
+    p.queue = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(hdr) + kQueueCounterOffset);
+    if (cudaMemsetAsync(p.queue, 0, sizeof(unsigned long long), s) != cudaSuccess) return VOILA_ERR_CUDA;
+  }
+  constexpr int R0 = kModeRollout;
   cudaError_t e;
-  if (dims_a)
-    e = f8 ? launch_tc<8, 2, 8, true, false>(p, smem, nclusters, s) : launch_tc<8, 2, 8, false, false>(p, smem, nclusters, s);
+  if (dims_a && !pl.wide)
+    e = f8 ? (queue ? launch_tc<8, 2, 8, true, false, R0, true>(p, smem, nclusters, s)
+                    : launch_tc<8, 2, 8, true, false>(p, smem, nclusters, s))
+           : (queue ? launch_tc<8, 2, 8, false, false, R0, true>(p, smem, nclusters, s)
+                    : launch_tc<8, 2, 8, false, false>(p, smem, nclusters, s));
+  else if (dims_a)
+    e = queue ? launch_tc<8, 2, 8, false, true, R0, true>(p, smem, nclusters, s)
+              : launch_tc<8, 2, 8, false, true>(p, smem, nclusters, s);
   else if (!pl.wide)
-    e = f8 ? launch_tc<12, 3, 16, true, false>(p, smem, nclusters, s)
-           : launch_tc<12, 3, 16, false, false>(p, smem, nclusters, s);
+    e = f8 ? (queue ? launch_tc<12, 3, 16, true, false, R0, true>(p, smem, nclusters, s)
+                    : launch_tc<12, 3, 16, true, false>(p, smem, nclusters, s))
+           : (queue ? launch_tc<12, 3, 16, false, false, R0, true>(p, smem, nclusters, s)
+                    : launch_tc<12, 3, 16, false, false>(p, smem, nclusters, s));
   else
-    e = f8 ? launch_tc<12, 3, 16, true, true>(p, smem, nclusters, s)
-           : launch_tc<12, 3, 16, false, true>(p, smem, nclusters, s);
+    e = f8 ? (queue ? launch_tc<12, 3, 16, true, true, R0, true>(p, smem, nclusters, s)
+                    : launch_tc<12, 3, 16, true, true>(p, smem, nclusters, s))
+           : (queue ? launch_tc<12, 3, 16, false, true, R0, true>(p, smem, nclusters, s)
+                    : launch_tc<12, 3, 16, false, true>(p, smem, nclusters, s));
   return e == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
 
@@ -2066,7 +2187,8 @@ voila_status tc_rollout(const voila_mlp* g_T, const voila_reward* R, const Rollo
   q.planner = a.planner;
   q.n_off = a.n_off;
   q.k_off = a.k_off;
-  return tc_rollout_batched(g_T, R, &q, 1, a.d_s, a.d_a, a.d_omega, a.gamma, a.key0, a.key1, 0, 0, hdr, scratch, s);
+  return tc_rollout_batched(g_T, R, &q, 1, a.d_s, a.d_a, a.d_omega, a.gamma, a.key0, a.key1, 0, 0, 0, hdr, scratch,
+                            s);
 }
 
 namespace {

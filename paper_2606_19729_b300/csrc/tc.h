@@ -23,12 +23,20 @@ struct TcProblem {
   uint32_t n_off = 0, k_off = 0;  // offsets of a shard's particles and sequences in the whole problem
 };
 
+// Tile-shape and work-order flags of tc_rollout_batched.
+constexpr int kShapeQueue = 1;    // work items claimed from a global counter (else c, c + clusters, ...)
+constexpr int kShapeOneTile = 2;  // one 128-row tile per CTA and item, scalar outputs as MMAs (else two
+                                  // tiles per CTA in flight, scalar outputs fused into the epilogue)
+// The work-item counter's byte offset in the workspace header.
+constexpr size_t kQueueCounterOffset = 64;
+
 // Launches one persistent BF16 tcgen05 rollout over P problems sharing the
 // MLPs. order = 1 sorts the work by descending horizon (longest first);
-// max_clusters > 0 caps the number of CTA pairs.
+// max_clusters > 0 caps the number of CTA pairs; shape: kShape* flags.
 voila_status tc_rollout_batched(const voila_mlp* g_T, const voila_reward* R, const TcProblem* probs, int P,
                                 int d_s, int d_a, int d_omega, double gamma, uint32_t key0, uint32_t key1,
-                                int order, int max_clusters, WsHeader* hdr, void* scratch, cudaStream_t s);
+                                int order, int max_clusters, int shape, WsHeader* hdr, void* scratch,
+                                cudaStream_t s);
 
 // Launches the BF16 tcgen05 rollout; writes G [K][N]. Returns
 // VOILA_ERR_UNSUPPORTED for shapes the kernel does not cover.
