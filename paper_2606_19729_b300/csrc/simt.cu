@@ -264,12 +264,202 @@ static int simt_grid(long long ntiles, size_t smem) {
   return (int)(g < 1 ? 1 : g);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 rollout for small MLPs (generator and reward of two hidden layers at
+// most 64 wide, inputs at most 16 wide): one thread per row (particle,
+// sequence) through all H steps, the weights of both MLPs in shared memory,
+// zero padded to 64 hidden units and 16 inputs (padding adds exact zero
+// products). Each layer accumulates in input order from its bias, as the tiled
+// kernel does, so both give the same bits. The second hidden layer runs in
+// chunks of eight units whose activations go straight into the output layer's
+// sums, so only the first hidden layer's 64 activations live in registers.
+// ---------------------------------------------------------------------------
+constexpr int kRowHid = 64, kRowIn = 16, kRowOut = 8, kRowThreads = 128;
+// one MLP in shared memory: W0 [64][16], b0 [64], W1 [64][64], b1 [64], W2 [8][64], b2 [8]
+constexpr int kRowMlpFloats = kRowHid * kRowIn + kRowHid + kRowHid * kRowHid + kRowHid + kRowOut * kRowHid + kRowOut;
+
+__device__ void load_row_mlp(float* dst, const MlpDev& m) {
+  float* W0 = dst;
+  float* b0 = W0 + kRowHid * kRowIn;
+  float* W1 = b0 + kRowHid;
+  float* b1 = W1 + kRowHid * kRowHid;
+  float* W2 = b1 + kRowHid;
+  float* b2 = W2 + kRowOut * kRowHid;
+  const float* w0 = static_cast<const float*>(m.W[0]);
+  const float* w1 = static_cast<const float*>(m.W[1]);
+  const float* w2 = static_cast<const float*>(m.W[2]);
+  const int d0 = m.dims[0], d1 = m.dims[1], d2 = m.dims[2], d3 = m.dims[3];
+  for (int i = threadIdx.x; i < kRowHid * kRowIn; i += blockDim.x) {
+    const int j = i / kRowIn, k = i % kRowIn;
+    W0[i] = (j < d1 && k < d0) ? w0[j * d0 + k] : 0.0f;
+  }
+  for (int i = threadIdx.x; i < kRowHid * kRowHid; i += blockDim.x) {
+    const int j = i / kRowHid, k = i % kRowHid;
+    W1[i] = (j < d2 && k < d1) ? w1[j * d1 + k] : 0.0f;
+  }
+  for (int i = threadIdx.x; i < kRowOut * kRowHid; i += blockDim.x) {
+    const int j = i / kRowHid, k = i % kRowHid;
+    W2[i] = (j < d3 && k < d2) ? w2[j * d2 + k] : 0.0f;
+  }
+  for (int i = threadIdx.x; i < kRowHid; i += blockDim.x) {
+    b0[i] = i < d1 ? m.b[0][i] : 0.0f;
+    b1[i] = i < d2 ? m.b[1][i] : 0.0f;
+  }
+  for (int i = threadIdx.x; i < kRowOut; i += blockDim.x) b2[i] = i < d3 ? m.b[2][i] : 0.0f;
+}
+
+// y[NOUT] = mlp(x) for one row, the MLP's padded weights at `w` in shared memory.
+template <int NOUT>
+__device__ __forceinline__ void row_mlp(const float* __restrict__ w, const float* x, float* y, int act) {
+  const float* W0 = w;
+  const float* b0 = W0 + kRowHid * kRowIn;
+  const float* W1 = b0 + kRowHid;
+  const float* b1 = W1 + kRowHid * kRowHid;
+  const float* W2 = b1 + kRowHid;
+  const float* b2 = W2 + kRowOut * kRowHid;
+  float h[kRowHid];
+#pragma unroll
+  for (int j = 0; j < kRowHid; ++j) {
+    float acc = b0[j];
+#pragma unroll
+    for (int k = 0; k < kRowIn; k += 4) {
+      const float4 wv = *reinterpret_cast<const float4*>(W0 + j * kRowIn + k);
+      acc = fmaf(x[k], wv.x, acc);
+      acc = fmaf(x[k + 1], wv.y, acc);
+      acc = fmaf(x[k + 2], wv.z, acc);
+      acc = fmaf(x[k + 3], wv.w, acc);
+    }
+    h[j] = act_fp32(acc, act);
+  }
+#pragma unroll
+  for (int m = 0; m < NOUT; ++m) y[m] = b2[m];
+#pragma unroll 1
+  for (int j0 = 0; j0 < kRowHid; j0 += 8) {
+    float a8[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a8[i] = b1[j0 + i];
+#pragma unroll
+    for (int k = 0; k < kRowHid; k += 4) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float4 wv = *reinterpret_cast<const float4*>(W1 + (j0 + i) * kRowHid + k);
+        a8[i] = fmaf(h[k], wv.x, a8[i]);
+        a8[i] = fmaf(h[k + 1], wv.y, a8[i]);
+        a8[i] = fmaf(h[k + 2], wv.z, a8[i]);
+        a8[i] = fmaf(h[k + 3], wv.w, a8[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float hv = act_fp32(a8[i], act);
+#pragma unroll
+      for (int m = 0; m < NOUT; ++m) y[m] = fmaf(hv, W2[m * kRowHid + j0 + i], y[m]);
+    }
+  }
+}
+
+template <int DS, bool RMLP>
+__global__ void __launch_bounds__(kRowThreads) rollout_rows_kernel(RolloutArgs a) {
+  extern __shared__ __align__(16) float sw[];
+  float* gw = sw;
+  float* rw = sw + kRowMlpFloats;
+  load_row_mlp(gw, a.g);
+  if (RMLP) load_row_mlp(rw, a.r);
+  __syncthreads();
+  const long long rows = (long long)a.N * a.K;
+  const int d_a = a.d_a, d_w = a.d_omega;
+  for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
+       row += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(row % a.N), k = (int)(row / a.N);
+    float s[DS];
+#pragma unroll
+    for (int i = 0; i < DS; ++i) s[i] = a.particles[(size_t)n * DS + i];
+    double G = 0.0, disc = 1.0;
+    for (int t = 0; t < a.H; ++t) {
+      const float* at = a.actions + ((size_t)k * a.H + t) * d_a;
+      float x[kRowIn];
+#pragma unroll
+      for (int i = 0; i < kRowIn; ++i) x[i] = 0.0f;
+#pragma unroll
+      for (int i = 0; i < DS; ++i) x[i] = s[i];
+#pragma unroll
+      for (int i = 0; i < kRowIn - DS; ++i)
+        if (i < d_a) x[DS + i] = __ldg(at + i);
+#pragma unroll
+      for (int b = 0; b < (kRowIn + 3) / 4; ++b)
+        if (4 * b < d_w) {
+          const float4 z = normal4(a.key0, a.key1, (uint32_t)n + a.n_off, (uint32_t)k + a.k_off, (uint32_t)t,
+                                   VOILA_STREAM_ROLLOUT_OMEGA, a.planner, (uint32_t)b);
+          const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = DS + d_a + 4 * b + q;  // d_s + d_a + d_omega <= kRowIn
+            if (4 * b + q < d_w) {
+#pragma unroll
+              for (int cc = DS; cc < kRowIn; ++cc)
+                if (cc == c) x[cc] = zz[q];
+            }
+          }
+        }
+      row_mlp<DS>(gw, x, s, a.g.act);
+      float r;
+      if (RMLP) {
+        float xr[kRowIn];
+#pragma unroll
+        for (int i = 0; i < kRowIn; ++i) xr[i] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < DS; ++i) xr[i] = s[i];
+#pragma unroll
+        for (int i = 0; i < kRowIn - DS; ++i)
+          if (i < d_a) xr[DS + i] = __ldg(at + i);
+        float rv[1];
+        row_mlp<1>(rw, xr, rv, a.r.act);
+        r = rv[0];
+      } else {
+        float acc = 0.0f;
+#pragma unroll
+        for (int d = 0; d < DS; ++d)
+          if (d < a.goal_dims) {
+            const float e = s[d] - a.goal[d];
+            acc = fmaf(e, e, acc);
+          }
+        r = -acc;
+      }
+      G += disc * (double)r;
+      disc *= a.gamma;
+    }
+    a.G[row] = G;
+  }
+}
+
+// The row kernel takes FP32 generators (and reward MLPs) of two hidden layers
+// of at most 64 units, inputs of at most 16 and a state of 4 or 8.
+static bool rows_kernel_fits(const MlpDev& m, int out) {
+  return m.prec == VOILA_FP32 && m.n_layers == 3 && m.dims[0] <= kRowIn && m.dims[1] <= kRowHid &&
+         m.dims[2] <= kRowHid && m.dims[3] == out;
+}
+
 size_t rollout_simt_smem(int ld) {
   return (size_t)2 * kSimtRows * ld * sizeof(float) + kSimtRows * 32 * sizeof(float) +
          kSimtRows * sizeof(double);
 }
 
 cudaError_t launch_rollout_simt(const RolloutArgs& a, cudaStream_t s) {
+  const bool rmlp = a.reward_kind == VOILA_REWARD_MLP;
+  if ((a.d_s == 4 || a.d_s == 8) && rows_kernel_fits(a.g, a.d_s) && (!rmlp || rows_kernel_fits(a.r, 1)) &&
+      (rmlp || a.goal_dims <= a.d_s)) {
+    const size_t smem = (size_t)(rmlp ? 2 : 1) * kRowMlpFloats * sizeof(float);
+    void (*k)(RolloutArgs);
+    if (a.d_s == 4) k = rmlp ? rollout_rows_kernel<4, true> : rollout_rows_kernel<4, false>;
+    else k = rmlp ? rollout_rows_kernel<8, true> : rollout_rows_kernel<8, false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long rows = (long long)a.N * a.K;
+    long long grid = (rows + kRowThreads - 1) / kRowThreads;
+    if (grid > 148LL * 8) grid = 148LL * 8;
+    k<<<(int)grid, kRowThreads, smem, s>>>(a);
+    return cudaGetLastError();
+  }
   const size_t smem = rollout_simt_smem(a.ld);
   const long long ntiles = ((long long)a.N * a.K + kSimtRows - 1) / kSimtRows;
   const int grid = simt_grid(ntiles, smem);
