@@ -46,6 +46,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-seqs", type=int, default=16, help="sequences for the FP32-form comparison (0: skip)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32/FP8 form comparison")
+    ap.add_argument("--prec", choices=["bf16", "fp8"], default="bf16",
+                    help="mid_bf16 workload: the precision form of the timed step's MLPs (fp8: E4M3 hidden "
+                         "layers with per-channel scales)")
     ap.add_argument("--batched-schedules", action="store_true",
                     help="batched workload: also time every candidate schedule of the autotuner")
     ap.add_argument("--no-configs", action="store_true",
@@ -97,7 +100,8 @@ def make_workload(name, args=None):
         if v is not None:
             kw[key] = v
     if name == "mid_bf16":
-        return WL.mid_bf16(**kw)
+        prec = {"bf16": WL.PREC_BF16, "fp8": WL.PREC_FP8}[getattr(args, "prec", None) or "bf16"]
+        return WL.mid_bf16(prec=prec, **kw)
     if name == "mid_fp32":
         return WL.mid_bf16(prec=WL.PREC_FP32, **kw)
     return WL.small_fp32(**kw)
@@ -117,7 +121,8 @@ def workload_config(wl, args):
         "workload": f"{wl.name}: N={wl.N} particles x K={wl.K} sequences x H={wl.H}, "
                     f"d_s={wl.d_s} d_a={wl.d_a} d_o={wl.d_o} d_omega={wl.d_omega}, "
                     f"MLPs {'x'.join(str(d) for d in wl.g_T.dims)} "
-                    f"{'BF16' if wl.prec == 1 else 'FP32'}; belief update + rollout per step",
+                    f"{ {0: 'FP32', 1: 'BF16', 2: 'FP8 e4m3 (hidden layers, per-channel scales)'}[wl.prec] }; "
+                    "belief update + rollout per step",
         "N": wl.N, "K": wl.K, "H": wl.H,
         "l2": "flushed (256 MB write) before every timed step",
         "inputs": "synthetic, seeded; random-init weights",
@@ -219,7 +224,16 @@ def cpu_baseline(wl, seqs, particles=None):
                       f"sequences x {wl.N} particles x H={wl.H} ({trans} transitions) in {dt:.2f} s"}, J, res
 
 
-def device_belief_weights(V, g, ell_mlp, wl):
+def oracle_belief(wl, lam):
+    """The FP64 oracle's belief update on the error leg's inputs (prior particles,
+    a = actions[0, 0], o = 0, step 1, planner 0) at temperature `lam`."""
+    from oracle import voila_oracle as O
+    om = lambda spec: O.MLP(spec.W, spec.b, spec.act)  # noqa: E731
+    return O.belief_update(om(wl.g_T), O.Likelihood(O.LIK_MLP, mlp=om(wl.ell)), wl.particles, wl.actions[0, 0],
+                           np.zeros(wl.d_o), wl.d_omega, lam, wl.seed, 1)
+
+
+def device_belief_weights(V, g, ell_mlp, wl, lam=None):
     """The device belief update on the oracle leg's inputs (prior particles,
     a = actions[0, 0], o = 0, step 1, planner 0): its normalised weights and the
     median time of one call (ms)."""
@@ -233,8 +247,10 @@ def device_belief_weights(V, g, ell_mlp, wl):
     w = torch.empty(N, dtype=torch.float64, device="cuda")
     ws = V.alloc_workspace(V.voila_belief_update_workspace_size(g, lik, N))
 
+    lam = wl.lam if lam is None else lam
+
     def call():
-        V.voila_belief_update(g, lik, parts, None, a0, obs, wl.d_omega, wl.lam, wl.seed, 1, 0, out, None, w, None,
+        V.voila_belief_update(g, lik, parts, None, a0, obs, wl.d_omega, lam, wl.seed, 1, 0, out, None, w, None,
                               None, ws)
 
     warm_until(call, 0.3)
@@ -1116,10 +1132,16 @@ def main():
     from paper_2606_19729_b300 import workloads as WL
     s_true = torch.from_numpy(WL.true_state(wl.seed, wl.d_s, 1.0)).float().to(dev).reshape(1, -1)
     s_next = torch.empty((1, wl.d_s), device=dev)
-    V.voila_generator_fwd_seeded(g, s_true, action.reshape(1, -1), 0, wl.d_omega, wl.seed, 5, 0, planner, s_next)
+    # (the FP8 form draws the observation with the same weights in BF16: the seeded
+    # sampler forward runs FP32 and BF16 MLPs)
+    as_bf16 = lambda spec: V.DeviceMLP([torch.from_numpy(x) for x in spec.W],  # noqa: E731
+                                       [torch.from_numpy(x) for x in spec.b], spec.act, V.BF16)
+    g_draw, gz_draw = (g, gz) if wl.prec != 2 else (as_bf16(wl.g_T), as_bf16(wl.g_Z))
+    V.voila_generator_fwd_seeded(g_draw, s_true, action.reshape(1, -1), 0, wl.d_omega, wl.seed, 5, 0, planner,
+                                 s_next)
     obs2 = torch.empty((1, wl.d_o), device=dev)
-    V.voila_generator_fwd_seeded(gz, s_next, action.reshape(1, -1), 0, wl.d_omega, wl.seed, V.STREAM_OBS_OMEGA, 0,
-                                 planner, obs2)
+    V.voila_generator_fwd_seeded(gz_draw, s_next, action.reshape(1, -1), 0, wl.d_omega, wl.seed, V.STREAM_OBS_OMEGA,
+                                 0, planner, obs2)
     obs = obs2.reshape(-1).contiguous()
 
     p_new = torch.empty_like(particles)
@@ -1224,6 +1246,11 @@ def main():
         roof = dict(tensor_roofline(achieved, peaks, clocks, "bf16"), traffic=traffic,
                     kernel="rollout_tc_kernel (voila_rollout call: weight pack + rollout + return reduction)",
                     tensor_pipe_pct_ncu=tensor_pipe)
+    elif wl.prec == 2:
+        achieved = fpt * trans_per_step / roll_avg_s / 1e12
+        roof = dict(tensor_roofline(achieved, peaks, clocks, "fp8", measure_fp8_peak()), traffic=None,
+                    kernel="rollout_tc_kernel FP8 instantiation (voila_rollout call: scale + weight pack + rollout "
+                           "+ return reduction)")
     else:
         achieved = fpt * trans_per_step / roll_avg_s / 1e12
         roof = fp32_roofline(achieved, peaks, clocks, torch.cuda.get_device_properties(dev).multi_processor_count)
@@ -1231,7 +1258,8 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if wl.prec == 1 else "f32",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f32", 1: "bf16", 2: "e4m3 hidden layers, bf16 first/last"}[wl.prec],
             "data": "synthetic (seeded inputs, random-init weights)",
             "config": dict(workload_config(wl, args), parallelism=f"replicas x{world}"),
             "rollout_ms": statistics.median(roll_ms), "belief_update_ms": statistics.median(
@@ -1241,7 +1269,8 @@ def main():
             # BF16: weight pack, fused-output pack, tensor-core proposal, resampling (belief update); weight
             # pack, fused-output pack, rollout, reduce + argmax (rollout); backup. FP32: proposal, resampling,
             # rollout, reduce + argmax, backup. Resampling: one launch up to 2048 particles, four above.
-            "gpu_launches": ((9 if wl.prec == 1 else 5) + (1 if N <= 2048 else 4)) * args.steps,
+            # FP8: one channel-scale launch more in each of the two packs
+            "gpu_launches": ({0: 5, 1: 9, 2: 11}[wl.prec] + (1 if N <= 2048 else 4)) * args.steps,
             "clocks": clocks}
     J8 = None
     if wl.prec == 1 and rank == 0 and not args.no_forms:
@@ -1270,13 +1299,20 @@ def main():
         line["err_vs_fp64"] = {"J_normwise": float(np.max(np.abs(Jd - Jo)) / np.max(np.abs(Jo))),
                                "sample": f"J of {args.cpu_seqs} of {wl.K} sequences (all particles) vs the FP64 oracle "
                                          "from the same resampled particles",
-                               "tolerance": 2e-2 if wl.prec == 1 else 1e-5}
+                               "tolerance": {0: 1e-5, 1: 2e-2, 2: 6e-2}[wl.prec]}
         # belief-update weights of the device forms against the FP64 oracle's (same inputs)
         ell_lam = wl.lam / max(float(np.max(np.abs(bres.ell))), 1e-300)
         w_dev, ms_dev = device_belief_weights(V, g, V.DeviceMLP.from_spec(wl.ell), wl)
         line["err_vs_fp64"]["belief_logw_maxabs"] = logw_err(w_dev, bres.w)
         line["err_vs_fp64"]["belief_sample"] = (f"max |log w - log w*| over the {wl.N} particles' weights "
                                                 f"(lambda / max|l*| = {ell_lam:.3g})")
+        # and at a low temperature, where the weights are far from flat (ESS well below N)
+        lam_low = 0.02
+        bres_low = oracle_belief(wl, lam_low)
+        w_low, _ = device_belief_weights(V, g, V.DeviceMLP.from_spec(wl.ell), wl, lam=lam_low)
+        line["err_vs_fp64"]["belief_low_temperature"] = {
+            "lambda": lam_low, "logw_maxabs": logw_err(w_low, bres_low.w), "ess_over_N": bres_low.ess / wl.N,
+            "sample": "max |log w - log w*| over the weights above 1e-9, same inputs as belief_logw_maxabs"}
         if wl.prec == 1 and "forms" in line and "fp8_e4m3" in line["forms"]:
             mk8 = lambda spec: V.DeviceMLP([torch.from_numpy(x) for x in spec.W],  # noqa: E731
                                            [torch.from_numpy(x) for x in spec.b], spec.act, V.FP8E4M3)
