@@ -1306,8 +1306,10 @@ def main():
         line["err_vs_fp64"]["belief_logw_maxabs"] = logw_err(w_dev, bres.w)
         line["err_vs_fp64"]["belief_sample"] = (f"max |log w - log w*| over the {wl.N} particles' weights "
                                                 f"(lambda / max|l*| = {ell_lam:.3g})")
-        # and at a low temperature, where the weights are far from flat (ESS well below N)
-        lam_low = 0.02
+        # and at a low temperature, where the weights are far from flat: lambda = the
+        # spread of the oracle's likelihoods over the particles, so that the tempered
+        # log-weights spread by about one (ESS well below N)
+        lam_low = max(float(np.std(bres.ell)), 1e-6)
         bres_low = oracle_belief(wl, lam_low)
         w_low, _ = device_belief_weights(V, g, V.DeviceMLP.from_spec(wl.ell), wl, lam=lam_low)
         line["err_vs_fp64"]["belief_low_temperature"] = {

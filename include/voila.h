@@ -89,9 +89,11 @@ enum {
  * model shapes of Sec. 5.2 (widths up to VOILA_MAX_WIDTH).
  *   W[l]  device, row-major [dims[l+1]][dims[l]] ("[out][in]"), element type
  *         float for VOILA_FP32, __nv_bfloat16 for VOILA_BF16 and VOILA_FP8E4M3.
- *         The FP8 form (rollout only) quantises every hidden-to-hidden layer to
- *         E4M3 with per-output-channel FP32 scales max_k|W[n][k]| / 448 and runs it
- *         on E4M3 activations (FP32 accumulation); first and last layers stay BF16.
+ *         The FP8 form (rollout and tensor-core belief proposal) quantises every
+ *         hidden-to-hidden layer to E4M3 with per-output-channel FP32 scales
+ *         max_k|W[n][k]| / 448 and runs it on E4M3 activations (FP32
+ *         accumulation); first and last layers stay BF16. It takes SiLU MLPs
+ *         (act = VOILA_ACT_SILU); other activations return VOILA_ERR_UNSUPPORTED.
  *   b[l]  device, float [dims[l+1]].
  *   w_scale[l]  reserved, NULL (the FP8 form computes its channel scales).
  * The struct itself is read on the host during the call and may be freed
@@ -101,7 +103,7 @@ typedef struct {
   int32_t n_layers;                       /* 1 .. VOILA_MAX_LAYERS */
   int32_t dims[VOILA_MAX_LAYERS + 1];     /* dims[0] input width, dims[n_layers] output width */
   int32_t act;                            /* VOILA_ACT_*, applied after every layer but the last */
-  int32_t prec;                           /* VOILA_FP32 or VOILA_BF16 */
+  int32_t prec;                           /* VOILA_FP32, VOILA_BF16 or VOILA_FP8E4M3 */
   const void* W[VOILA_MAX_LAYERS];
   const float* b[VOILA_MAX_LAYERS];
   const float* w_scale[VOILA_MAX_LAYERS];

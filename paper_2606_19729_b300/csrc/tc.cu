@@ -307,7 +307,8 @@ __device__ __forceinline__ void epi_cols32(float* u, const float* bl, const floa
     return;
   }
   using ptx::f2_pack;
-  if (SCALE && !OUT_FP8 && act == VOILA_ACT_SILU) {  // E4M3 layer, BF16 output: one pass
+  // The E4M3 paths serve SiLU MLPs only (the FP8 form is refused for other activations).
+  if (SCALE && !OUT_FP8) {  // E4M3 layer, BF16 output: one pass
     uint8_t* slab = A + (c >> 1) * (128 * 128);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -326,7 +327,7 @@ __device__ __forceinline__ void epi_cols32(float* u, const float* bl, const floa
     }
     return;
   }
-  if (OUT_FP8 && act == VOILA_ACT_SILU) {
+  if (OUT_FP8) {
     // E4M3 output in one pass: (channel scale and) bias, SiLU, four values per
     // 32-bit word, sixteen per 16-byte chunk (128 K per 128-byte swizzled row)
     uint8_t* slab = A + (c >> 2) * (128 * 128);
@@ -355,58 +356,6 @@ __device__ __forceinline__ void epi_cols32(float* u, const float* bl, const floa
           make_uint4(wv[0], wv[1], wv[2], wv[3]);
     }
     return;
-  }
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {  // transformed in place (register pressure)
-    const float4 b = *reinterpret_cast<const float4*>(bl + 32 * c + 4 * j);
-    uint64_t x01, x23;
-    if (SCALE) {
-      const float4 sc = *reinterpret_cast<const float4*>(sl + 32 * c + 4 * j);
-      x01 = ptx::f2_fma(f2_pack(u[4 * j + 0], u[4 * j + 1]), f2_pack(sc.x, sc.y), f2_pack(b.x, b.y));
-      x23 = ptx::f2_fma(f2_pack(u[4 * j + 2], u[4 * j + 3]), f2_pack(sc.z, sc.w), f2_pack(b.z, b.w));
-    } else {
-      x01 = ptx::f2_add(f2_pack(u[4 * j + 0], u[4 * j + 1]), f2_pack(b.x, b.y));
-      x23 = ptx::f2_add(f2_pack(u[4 * j + 2], u[4 * j + 3]), f2_pack(b.z, b.w));
-    }
-    if (act == VOILA_ACT_SILU) {
-      x01 = silu2(x01);
-      x23 = silu2(x23);
-      ptx::f2_unpack(x01, u[4 * j + 0], u[4 * j + 1]);
-      ptx::f2_unpack(x23, u[4 * j + 2], u[4 * j + 3]);
-    } else {
-      float y0, y1, y2, y3;
-      ptx::f2_unpack(x01, y0, y1);
-      ptx::f2_unpack(x23, y2, y3);
-      u[4 * j + 0] = act_value(y0, act);
-      u[4 * j + 1] = act_value(y1, act);
-      u[4 * j + 2] = act_value(y2, act);
-      u[4 * j + 3] = act_value(y3, act);
-    }
-  }
-  // u now holds the activations
-  if (!OUT_FP8) {
-    uint8_t* slab = A + (c >> 1) * (128 * 128);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      uint4 o;
-      o.x = ptx::pack_bf16x2(u[8 * j + 0], u[8 * j + 1]);
-      o.y = ptx::pack_bf16x2(u[8 * j + 2], u[8 * j + 3]);
-      o.z = ptx::pack_bf16x2(u[8 * j + 4], u[8 * j + 5]);
-      o.w = ptx::pack_bf16x2(u[8 * j + 6], u[8 * j + 7]);
-      *reinterpret_cast<uint4*>(slab + r * 128 + ((((c & 1) * 4 + j) ^ (r & 7)) << 4)) = o;
-    }
-  } else {
-    uint8_t* slab = A + (c >> 2) * (128 * 128);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const float* y = u + 16 * j;
-      uint4 o;
-      o.x = ptx::pack_e4m3x4(y[0], y[1], y[2], y[3]);
-      o.y = ptx::pack_e4m3x4(y[4], y[5], y[6], y[7]);
-      o.z = ptx::pack_e4m3x4(y[8], y[9], y[10], y[11]);
-      o.w = ptx::pack_e4m3x4(y[12], y[13], y[14], y[15]);
-      *reinterpret_cast<uint4*>(slab + r * 128 + ((((c & 3) * 2 + j) ^ (r & 7)) << 4)) = o;
-    }
   }
 }
 
@@ -475,7 +424,7 @@ __device__ __forceinline__ uint64_t fuse_cols(const float* u, const float* bl, c
       x01 = ptx::f2_add(f2_pack(u[j], u[j + 1]), f2_pack(b.x, b.y));
       x23 = ptx::f2_add(f2_pack(u[j + 2], u[j + 3]), f2_pack(b.z, b.w));
     }
-    if (act == VOILA_ACT_SILU) {
+    if (SCALE || act == VOILA_ACT_SILU) {  // E4M3 layers: SiLU MLPs only
       x01 = silu2(x01);
       x23 = silu2(x23);
     } else {
@@ -1241,14 +1190,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
               const float* wf = fuse_s + L.fuse_off;
               const float* sl = scale_s + L.scale_off;
               uint64_t part2 = 0ull;  // (even, odd) column partial sums, both +0.0f
-              if (per >= 32) {
-                const int c0 = slice * (per >> 5);
-                for (int c = c0; c < c0 + (per >> 5); ++c) {
-                  float v[32];
-                  ptx::tmem_ld32(tm + 32 * c, v);
-                  ptx::tmem_wait_ld32(v);
-                  part2 = (F8 && L.fp8) ? fuse_cols<true, 32>(v, bl, sl, c, L.act, wf, part2)
-                                        : fuse_cols<false, 32>(v, bl, sl, c, L.act, wf, part2);
+              if (per >= 16) {
+                // 16 columns per TMEM load: the dot products hold fewer live values
+                // than the hidden epilogue, and 32-column loads here cost register spills
+                // that every other layer then pays for
+                const int c0 = slice * (per >> 4);
+                for (int c = c0; c < c0 + (per >> 4); ++c) {
+                  float v[16];
+                  ptx::tmem_ld16(tm + 16 * c, v);
+                  ptx::tmem_wait_ld();
+                  ptx::tie8(v);
+                  ptx::tie8(v + 8);
+                  part2 = (F8 && L.fp8) ? fuse_cols<true, 16>(v, bl, sl, c, L.act, wf, part2)
+                                        : fuse_cols<false, 16>(v, bl, sl, c, L.act, wf, part2);
                 }
               } else {
                 float v[16];
@@ -1520,6 +1474,7 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R, bool ddim = false, boo
     const voila_mlp* M = mlps[m];
     if (!M) continue;
     if ((M->prec != VOILA_BF16 && M->prec != VOILA_FP8E4M3) || M->n_layers < 2) return pl;
+    if (M->prec == VOILA_FP8E4M3 && M->act != VOILA_ACT_SILU) return pl;  // the E4M3 epilogues are SiLU's
     // a scalar output layer is computed in the previous layer's epilogue
     const bool fuse = !ddim && !any_wide && M->dims[M->n_layers] == 1;
     for (int l = 0; l < M->n_layers; ++l) {

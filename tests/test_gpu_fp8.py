@@ -60,3 +60,18 @@ def test_fp8_rollout_full_mid_size_sampled(V):
     J, G, Jo, Go = _run(V, wl, ks=ks)
     assert rel_err(J, Jo) < TOL_FP8
     assert rel_err(G, Go) < TOL_FP8
+
+
+def test_fp8_form_takes_silu_mlps_only(V):
+    # the E4M3 epilogues apply SiLU; an FP8 MLP with another activation is refused
+    rng = np.random.default_rng(7)
+    g = V.DeviceMLP.from_spec(WL.xavier_mlp(rng, [18, 256, 256, 256, 8], WL.ACT_TANH, WL.PREC_FP8))
+    rm = V.DeviceMLP.from_spec(WL.xavier_mlp(rng, [10, 256, 256, 256, 1], WL.ACT_TANH, WL.PREC_FP8))
+    R = V.mlp_reward(rm)
+    parts = torch.zeros((16, 8), dtype=torch.float32, device="cuda")
+    acts = torch.zeros((2, 3, 2), dtype=torch.float32, device="cuda")
+    J = torch.empty(2, dtype=torch.float64, device="cuda")
+    ws = V.alloc_workspace(V.voila_rollout_workspace_size(g, R, 16, 2, 3))
+    with pytest.raises(V.VoilaError) as e:
+        V.voila_rollout(g, R, parts, None, acts, 8, 0.98, 1, 0, J, None, None, ws)
+    assert e.value.code == V.ERR_UNSUPPORTED
