@@ -351,6 +351,24 @@ def tensor_roofline(achieved: float, peaks: dict, clocks: dict, kind: str = "bf1
     return out
 
 
+def profiled_traffic(form: str, wl):
+    """(DRAM bytes per launch, ncu tensor-pipe %) of the mid-size rollout kernel in
+    `form` ("bf16" or "fp8") from profiles/, or (None, None) when the capture was
+    taken on another kernel source or the workload is not the full mid-size one."""
+    try:
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", f"rollout_tc_mid_{form}_traffic.json")) as f:
+            prof = json.load(f)
+        src = b"".join(open(os.path.join(ROOT, "paper_2606_19729_b300", "csrc", n), "rb").read()
+                       for n in ("tc.cu", "tc_ptx.cuh"))
+        if (hashlib.sha256(src).hexdigest()[:16] == prof["source_sha16"] and wl.name == "mid_bf16"
+                and (wl.N, wl.K, wl.H) == (4096, 1024, 20)):
+            return prof["dram_read_bytes"] + prof["dram_write_bytes"], prof.get("tensor_pipe_pct")
+    except (OSError, KeyError, ValueError):
+        pass
+    return None, None
+
+
 def fp32_form(V, wl, seqs, planner, particles, stream):
     """The plain FP32 CUDA-core form on the same workload, timed on a slice of
     `seqs` action sequences (throughput per transition does not depend on K)."""
@@ -406,6 +424,7 @@ def fp8_form(V, wl, planner, particles, stream, peaks=None, fp8_peak=None):
     return {"value": wl.N * wl.K * wl.H / sec, "unit": UNIT, "dtype": "e4m3 hidden layers, bf16 first/last",
             "rollout_ms": 1e3 * sec, "sample": "full workload, same particles and weights",
             "roofline": dict(tensor_roofline(achieved, peaks or {}, clocks, "fp8", fp8_peak),
+                             traffic=profiled_traffic("fp8", wl)[0], tensor_pipe_pct_ncu=profiled_traffic("fp8", wl)[1],
                              kernel="rollout_tc_kernel FP8 instantiation (voila_rollout call)",
                              flops="algorithmic, as the BF16 line (543,232 per transition)"),
             "clocks": clocks}, J.cpu().numpy()
@@ -1227,20 +1246,7 @@ def main():
     clocks = clk.summary()
     fpt = flops_per_transition(wl)
     roll_avg_s = sum(roll_ms) / len(roll_ms) / 1e3
-    traffic = None
-    tensor_pipe = None
-    try:  # ncu DRAM bytes per launch, valid only for the kernel source they were taken on
-        import hashlib
-        with open(os.path.join(ROOT, "profiles", "rollout_tc_mid_bf16_traffic.json")) as f:
-            prof = json.load(f)
-        src = b"".join(open(os.path.join(ROOT, "paper_2606_19729_b300", "csrc", n), "rb").read()
-                       for n in ("tc.cu", "tc_ptx.cuh"))
-        if (hashlib.sha256(src).hexdigest()[:16] == prof["source_sha16"] and wl.name == "mid_bf16"
-                and (wl.N, wl.K, wl.H) == (4096, 1024, 20)):
-            traffic = prof["dram_read_bytes"] + prof["dram_write_bytes"]
-            tensor_pipe = prof.get("tensor_pipe_pct")
-    except (OSError, KeyError, ValueError):
-        traffic = None
+    traffic, tensor_pipe = profiled_traffic("fp8" if wl.prec == 2 else "bf16", wl)
     if wl.prec == 1:
         achieved = fpt * trans_per_step / roll_avg_s / 1e12
         roof = dict(tensor_roofline(achieved, peaks, clocks, "bf16"), traffic=traffic,
@@ -1248,9 +1254,9 @@ def main():
                     tensor_pipe_pct_ncu=tensor_pipe)
     elif wl.prec == 2:
         achieved = fpt * trans_per_step / roll_avg_s / 1e12
-        roof = dict(tensor_roofline(achieved, peaks, clocks, "fp8", measure_fp8_peak()), traffic=None,
+        roof = dict(tensor_roofline(achieved, peaks, clocks, "fp8", measure_fp8_peak()), traffic=traffic,
                     kernel="rollout_tc_kernel FP8 instantiation (voila_rollout call: scale + weight pack + rollout "
-                           "+ return reduction)")
+                           "+ return reduction)", tensor_pipe_pct_ncu=tensor_pipe)
     else:
         achieved = fpt * trans_per_step / roll_avg_s / 1e12
         roof = fp32_roofline(achieved, peaks, clocks, torch.cuda.get_device_properties(dev).multi_processor_count)

@@ -266,35 +266,40 @@ static int simt_grid(long long ntiles, size_t smem) {
 
 // ---------------------------------------------------------------------------
 // FP32 rollout for small MLPs (generator and reward of two hidden layers at
-// most 64 wide, inputs at most 16 wide): one thread per row (particle,
-// sequence) through all H steps, the weights of both MLPs in shared memory,
+// most 64 wide, inputs at most 16 wide): four threads (a quad of one warp) per
+// row (particle, sequence) through all H steps, thread `sub` of the quad
+// computing hidden units j = 4 i + sub (i < 16) of both hidden layers; the
+// units the next layer needs from the other three threads arrive by warp
+// shuffles, in input order. The weights of both MLPs sit in shared memory,
 // zero padded to 64 hidden units and 16 inputs (padding adds exact zero
-// products). Each layer accumulates in input order from its bias, as the tiled
-// kernel does, so both give the same bits. The second hidden layer runs in
-// chunks of eight units whose activations go straight into the output layer's
-// sums, so only the first hidden layer's 64 activations live in registers.
+// products), rows strided so that the four threads' rows fall in different
+// banks. Every layer accumulates in input order from its bias, like the tiled
+// kernel, so both give the same bits.
 // ---------------------------------------------------------------------------
 constexpr int kRowHid = 64, kRowIn = 16, kRowOut = 8, kRowThreads = 128;
-// one MLP in shared memory: W0 [64][16], b0 [64], W1 [64][64], b1 [64], W2 [8][64], b2 [8]
-constexpr int kRowMlpFloats = kRowHid * kRowIn + kRowHid + kRowHid * kRowHid + kRowHid + kRowOut * kRowHid + kRowOut;
+constexpr int kRowW0Ld = kRowIn + 4;   // 80-byte rows: the quad's rows j = 4 i + sub in distinct banks
+constexpr int kRowW1Ld = kRowHid + 4;  // 272-byte rows, likewise
+// one MLP in shared memory: W0 [64][20], b0 [64], W1 [64][68], b1 [64], W2 [8][64], b2 [8]
+constexpr int kRowMlpFloats =
+    kRowHid * kRowW0Ld + kRowHid + kRowHid * kRowW1Ld + kRowHid + kRowOut * kRowHid + kRowOut;
 
 __device__ void load_row_mlp(float* dst, const MlpDev& m) {
   float* W0 = dst;
-  float* b0 = W0 + kRowHid * kRowIn;
+  float* b0 = W0 + kRowHid * kRowW0Ld;
   float* W1 = b0 + kRowHid;
-  float* b1 = W1 + kRowHid * kRowHid;
+  float* b1 = W1 + kRowHid * kRowW1Ld;
   float* W2 = b1 + kRowHid;
   float* b2 = W2 + kRowOut * kRowHid;
   const float* w0 = static_cast<const float*>(m.W[0]);
   const float* w1 = static_cast<const float*>(m.W[1]);
   const float* w2 = static_cast<const float*>(m.W[2]);
   const int d0 = m.dims[0], d1 = m.dims[1], d2 = m.dims[2], d3 = m.dims[3];
-  for (int i = threadIdx.x; i < kRowHid * kRowIn; i += blockDim.x) {
-    const int j = i / kRowIn, k = i % kRowIn;
+  for (int i = threadIdx.x; i < kRowHid * kRowW0Ld; i += blockDim.x) {
+    const int j = i / kRowW0Ld, k = i % kRowW0Ld;
     W0[i] = (j < d1 && k < d0) ? w0[j * d0 + k] : 0.0f;
   }
-  for (int i = threadIdx.x; i < kRowHid * kRowHid; i += blockDim.x) {
-    const int j = i / kRowHid, k = i % kRowHid;
+  for (int i = threadIdx.x; i < kRowHid * kRowW1Ld; i += blockDim.x) {
+    const int j = i / kRowW1Ld, k = i % kRowW1Ld;
     W1[i] = (j < d2 && k < d1) ? w1[j * d1 + k] : 0.0f;
   }
   for (int i = threadIdx.x; i < kRowOut * kRowHid; i += blockDim.x) {
@@ -308,52 +313,64 @@ __device__ void load_row_mlp(float* dst, const MlpDev& m) {
   for (int i = threadIdx.x; i < kRowOut; i += blockDim.x) b2[i] = i < d3 ? m.b[2][i] : 0.0f;
 }
 
-// y[NOUT] = mlp(x) for one row, the MLP's padded weights at `w` in shared memory.
+// y[NOUT] = mlp(x) for one row, computed by its quad (every thread of the quad
+// passes the same x and gets the same y); the MLP's padded weights at `w`.
 template <int NOUT>
-__device__ __forceinline__ void row_mlp(const float* __restrict__ w, const float* x, float* y, int act) {
+__device__ __forceinline__ void quad_mlp(const float* __restrict__ w, const float* x, float* y, int act,
+                                         unsigned qmask, int qbase, int sub) {
   const float* W0 = w;
-  const float* b0 = W0 + kRowHid * kRowIn;
+  const float* b0 = W0 + kRowHid * kRowW0Ld;
   const float* W1 = b0 + kRowHid;
-  const float* b1 = W1 + kRowHid * kRowHid;
+  const float* b1 = W1 + kRowHid * kRowW1Ld;
   const float* W2 = b1 + kRowHid;
   const float* b2 = W2 + kRowOut * kRowHid;
-  float h[kRowHid];
+  constexpr int kPer = kRowHid / 4;  // hidden units per thread
+  float h[kPer];
 #pragma unroll
-  for (int j = 0; j < kRowHid; ++j) {
+  for (int i = 0; i < kPer; ++i) {  // first hidden layer: units 4 i + sub
+    const int j = 4 * i + sub;
     float acc = b0[j];
 #pragma unroll
     for (int k = 0; k < kRowIn; k += 4) {
-      const float4 wv = *reinterpret_cast<const float4*>(W0 + j * kRowIn + k);
+      const float4 wv = *reinterpret_cast<const float4*>(W0 + j * kRowW0Ld + k);
       acc = fmaf(x[k], wv.x, acc);
       acc = fmaf(x[k + 1], wv.y, acc);
       acc = fmaf(x[k + 2], wv.z, acc);
       acc = fmaf(x[k + 3], wv.w, acc);
     }
-    h[j] = act_fp32(acc, act);
+    h[i] = act_fp32(acc, act);
+  }
+  float a[kPer];  // second hidden layer, units 4 i + sub
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) a[i] = b1[4 * i + sub];
+#pragma unroll
+  for (int i2 = 0; i2 < kPer; ++i2) {  // inputs k = 4 i2 .. 4 i2 + 3, one from each thread of the quad
+    const float h0 = __shfl_sync(qmask, h[i2], qbase), h1 = __shfl_sync(qmask, h[i2], qbase + 1);
+    const float h2 = __shfl_sync(qmask, h[i2], qbase + 2), h3 = __shfl_sync(qmask, h[i2], qbase + 3);
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const float4 wv = *reinterpret_cast<const float4*>(W1 + (4 * i + sub) * kRowW1Ld + 4 * i2);
+      a[i] = fmaf(h0, wv.x, a[i]);
+      a[i] = fmaf(h1, wv.y, a[i]);
+      a[i] = fmaf(h2, wv.z, a[i]);
+      a[i] = fmaf(h3, wv.w, a[i]);
+    }
   }
 #pragma unroll
+  for (int i = 0; i < kPer; ++i) a[i] = act_fp32(a[i], act);
+#pragma unroll
   for (int m = 0; m < NOUT; ++m) y[m] = b2[m];
-#pragma unroll 1
-  for (int j0 = 0; j0 < kRowHid; j0 += 8) {
-    float a8[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) a8[i] = b1[j0 + i];
+  for (int i2 = 0; i2 < kPer; ++i2) {  // output layer over all 64 units, in order
+    const float g0 = __shfl_sync(qmask, a[i2], qbase), g1 = __shfl_sync(qmask, a[i2], qbase + 1);
+    const float g2 = __shfl_sync(qmask, a[i2], qbase + 2), g3 = __shfl_sync(qmask, a[i2], qbase + 3);
 #pragma unroll
-    for (int k = 0; k < kRowHid; k += 4) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float4 wv = *reinterpret_cast<const float4*>(W1 + (j0 + i) * kRowHid + k);
-        a8[i] = fmaf(h[k], wv.x, a8[i]);
-        a8[i] = fmaf(h[k + 1], wv.y, a8[i]);
-        a8[i] = fmaf(h[k + 2], wv.z, a8[i]);
-        a8[i] = fmaf(h[k + 3], wv.w, a8[i]);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float hv = act_fp32(a8[i], act);
-#pragma unroll
-      for (int m = 0; m < NOUT; ++m) y[m] = fmaf(hv, W2[m * kRowHid + j0 + i], y[m]);
+    for (int m = 0; m < NOUT; ++m) {
+      const float4 wv = *reinterpret_cast<const float4*>(W2 + m * kRowHid + 4 * i2);
+      y[m] = fmaf(g0, wv.x, y[m]);
+      y[m] = fmaf(g1, wv.y, y[m]);
+      y[m] = fmaf(g2, wv.z, y[m]);
+      y[m] = fmaf(g3, wv.w, y[m]);
     }
   }
 }
@@ -368,8 +385,10 @@ __global__ void __launch_bounds__(kRowThreads) rollout_rows_kernel(RolloutArgs a
   __syncthreads();
   const long long rows = (long long)a.N * a.K;
   const int d_a = a.d_a, d_w = a.d_omega;
-  for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
-       row += (long long)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31, sub = lane & 3, qbase = lane & ~3;
+  const unsigned qmask = 0xFu << qbase;
+  for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 2; row < rows;
+       row += ((long long)gridDim.x * blockDim.x) >> 2) {
     const int n = (int)(row % a.N), k = (int)(row / a.N);
     float s[DS];
 #pragma unroll
@@ -401,7 +420,7 @@ __global__ void __launch_bounds__(kRowThreads) rollout_rows_kernel(RolloutArgs a
             }
           }
         }
-      row_mlp<DS>(gw, x, s, a.g.act);
+      quad_mlp<DS>(gw, x, s, a.g.act, qmask, qbase, sub);
       float r;
       if (RMLP) {
         float xr[kRowIn];
@@ -413,7 +432,7 @@ __global__ void __launch_bounds__(kRowThreads) rollout_rows_kernel(RolloutArgs a
         for (int i = 0; i < kRowIn - DS; ++i)
           if (i < d_a) xr[DS + i] = __ldg(at + i);
         float rv[1];
-        row_mlp<1>(rw, xr, rv, a.r.act);
+        quad_mlp<1>(rw, xr, rv, a.r.act, qmask, qbase, sub);
         r = rv[0];
       } else {
         float acc = 0.0f;
@@ -428,7 +447,7 @@ __global__ void __launch_bounds__(kRowThreads) rollout_rows_kernel(RolloutArgs a
       G += disc * (double)r;
       disc *= a.gamma;
     }
-    a.G[row] = G;
+    if (sub == 0) a.G[row] = G;
   }
 }
 
@@ -455,7 +474,7 @@ cudaError_t launch_rollout_simt(const RolloutArgs& a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long rows = (long long)a.N * a.K;
-    long long grid = (rows + kRowThreads - 1) / kRowThreads;
+    long long grid = (4 * rows + kRowThreads - 1) / kRowThreads;  // a quad per row
     if (grid > 148LL * 8) grid = 148LL * 8;
     k<<<(int)grid, kRowThreads, smem, s>>>(a);
     return cudaGetLastError();
