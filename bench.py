@@ -454,6 +454,68 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def small_planners_record(V, WL, g, R, wl, rank, stream, reps=20):
+    """64 small planners (N log-uniform in [64, 1024], K in {8..64}, H in {5..30},
+    seed 5): the regime the batched launch is for, where one planner's rollout
+    is a fraction of a wave of CTA pairs. One autotuned batched launch captured in
+    a CUDA graph against 64 sequential voila_rollout calls, eager and captured in
+    a graph, each the median of `reps`; J must be identical."""
+    import torch
+    Ns, Ks, Hs = WL.batched_planners(seed=5, N_range=(64, 1024), K_range=(8, 64), H_range=(5, 30))
+    items = []
+    for i, (N, K, H) in enumerate(zip(Ns, Ks, Hs)):
+        parts, acts = WL.planner_inputs(2000 + i, int(N), int(K), int(H))
+        items.append({"particles": torch.from_numpy(parts).float().cuda(),
+                      "actions": torch.from_numpy(acts).float().cuda(), "planner_id": 64 * rank + i,
+                      "J": torch.empty(int(K), dtype=torch.float64, device="cuda"),
+                      "best_k": torch.empty(1, dtype=torch.int32, device="cuda")})
+    E = int(np.sum(Ns.astype(np.int64) * Ks * Hs))
+    pl = V.make_planners(items)
+    ws = V.alloc_workspace(V.voila_rollout_batched_workspace_size(g, R, pl))
+    big = max(V.voila_rollout_workspace_size(g, R, int(N), int(K), int(H)) for N, K, H in zip(Ns, Ks, Hs))
+    ws1 = V.alloc_workspace(big)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), statistics.pstdev(ts)
+
+    with torch.cuda.stream(stream):
+        best, _ = V.voila_rollout_batched_autotune(g, R, pl, wl.d_s, wl.d_a, wl.d_omega, wl.gamma, wl.seed, ws,
+                                                   stream=stream)
+        gb = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gb, stream=stream):
+            V.voila_rollout_batched(g, R, pl, wl.d_s, wl.d_a, wl.d_omega, wl.gamma, wl.seed, best, ws, stream=stream)
+        b_ms, b_sd = timed(gb.replay)
+        J_b = [it["J"].clone() for it in items]
+
+        def sequential():
+            for it in items:
+                V.voila_rollout(g, R, it["particles"], None, it["actions"], wl.d_omega, wl.gamma, wl.seed,
+                                it["planner_id"], it["J"], None, it["best_k"], ws1, stream=stream)
+        s_ms, s_sd = timed(sequential)
+        same = all(torch.equal(a, it["J"]) for a, it in zip(J_b, items))
+        gs = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gs, stream=stream):
+            sequential()
+        sg_ms, sg_sd = timed(gs.replay)
+    return {"workload": f"64 planners, N log-uniform [64, 1024], K in [8, 64], H in [5, 30] (seed 5); {E} transitions",
+            "schedule": best, "batched_graph_ms": b_ms, "batched_stdev_ms": b_sd,
+            "sequential_eager_ms": s_ms, "sequential_eager_stdev_ms": s_sd,
+            "sequential_graph_ms": sg_ms, "sequential_graph_stdev_ms": sg_sd,
+            "value_batched": E / (b_ms / 1e3), "value_sequential_graph": E / (sg_ms / 1e3),
+            "repeats": reps, "batched_equals_sequential": same}
+
+
 def batched_record(args, rank, world, local):
     """64 independent planners (uneven N, K, H from seed 4) sharing the mid-size BF16
     MLPs: one autotuned, graph-captured batched launch per step, against the same
@@ -567,6 +629,7 @@ def batched_record(args, rank, world, local):
             "gpu_launches": 4 * args.steps, "clocks": clocks}
     if sched_ms:
         line["schedules"] = sched_ms
+    line["small_planners"] = small_planners_record(V, WL, g, R, wl, rank, stream)
     return line
 
 
@@ -1090,7 +1153,7 @@ def config_records(args, rank, world, local, fp8_peak):
     b = batched_record(a, rank, world, local)
     out["c5_batched"] = {k: b.get(k) for k in ("value", "unit", "ms_per_step", "schedule", "autotune_ms",
                                                "batched_ms", "sequential_64_launches", "batched_equals_sequential",
-                                               "roofline", "clocks")}
+                                               "roofline", "clocks", "small_planners")}
     out["c5_batched"]["workload"] = b["config"]["workload"]
     return out
 

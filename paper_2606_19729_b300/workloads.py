@@ -262,13 +262,13 @@ def pw(seed: int = 6, M: int = 65536, n_nodes: int = 4096, C_max: int = 32, prec
                       obs0, node, s_next)
 
 
-def batched_planners(seed: int = 4, P: int = 64):
-    """Per-planner (N_p, K_p, H_p): N log-uniform in [512, 16384], K uniform in
-    {128..1024}, H uniform in {5..30}."""
+def batched_planners(seed: int = 4, P: int = 64, N_range=(512, 16384), K_range=(128, 1024), H_range=(5, 30)):
+    """Per-planner (N_p, K_p, H_p): N log-uniform in N_range (default [512, 16384]),
+    K uniform in K_range (default {128..1024}), H uniform in H_range (default {5..30})."""
     rng = np.random.default_rng(seed)
-    N = np.rint(np.exp(rng.uniform(math.log(512), math.log(16384), size=P))).astype(int)
-    K = rng.integers(128, 1025, size=P)
-    H = rng.integers(5, 31, size=P)
+    N = np.rint(np.exp(rng.uniform(math.log(N_range[0]), math.log(N_range[1]), size=P))).astype(int)
+    K = rng.integers(K_range[0], K_range[1] + 1, size=P)
+    H = rng.integers(H_range[0], H_range[1] + 1, size=P)
     return N, K, H
 
 
