@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_cons
   uint64_t* drain = bars + 2 * kGStages + 4;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kGStages + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  float* bias_s = reinterpret_cast<float*>(bars + 2 * kGStages + 6);  // [256]: the epilogue's bias reads
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles = (p.M + 127) / 128;
   const long long units = (long long)tiles * p.splits;
@@ -132,6 +133,8 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_cons
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
+  if (p.bias)
+    for (int i = threadIdx.x; i < p.N; i += blockDim.x) bias_s[i] = p.bias[i];
   if (warp == 1) {
     ptx::tmem_alloc(ptx::smem_u32(tmem_holder), 512);
     ptx::tmem_relinquish();
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_cons
             float h[16], d[16];
             if (p.mode == kGemmFwdHidden) {
 #pragma unroll
-              for (int j = 0; j < 16; ++j) act_and_grad(v[j] + p.bias[cb + j], p.act, h[j], d[j]);
+              for (int j = 0; j < 16; ++j) act_and_grad(v[j] + bias_s[cb + j], p.act, h[j], d[j]);
             } else {
               float a[16];
               if (valid) {
@@ -283,7 +286,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_cons
           } else if (p.mode == kGemmFwdOut) {
             if (valid)
               for (int j = 0; j < 16; ++j)
-                if (cb + j < p.n_real) p.Y[(size_t)m * p.ldY + cb + j] = v[j] + p.bias[cb + j];
+                if (cb + j < p.n_real) p.Y[(size_t)m * p.ldY + cb + j] = v[j] + bias_s[cb + j];
           } else {  // kGemmPartial
             if (valid) {
               float4* dst = reinterpret_cast<float4*>(p.P + ((size_t)split * p.M + m) * p.N + cb);
@@ -351,7 +354,7 @@ bool make_map(CUtensorMap* map, const __nv_bfloat16* base, long long K, long lon
 }  // namespace
 
 size_t tc_gemm_smem_bytes() {
-  return 1024 + kGStages * (kGABytes + kGBBytes) + kGStageBytes + (2 * kGStages + 5) * 8 + 16;
+  return 1024 + kGStages * (kGABytes + kGBBytes) + kGStageBytes + (2 * kGStages + 6) * 8 + 256 * 4;
 }
 
 cudaError_t tc_gemm(const TcGemm& g, cudaStream_t s) {

@@ -168,3 +168,22 @@ def test_batched_queue_fp8_and_sweep_dims(V):
     V.voila_rollout_batched(gs, Rg, pls, sw.d_s, sw.d_a, sw.d_omega, sw.gamma, sw.seed, QUEUE, wss)
     J, G = _single(V, sw, gs, Rg, its[0])
     assert torch.equal(its[0]["G"], G) and torch.equal(its[0]["J"], J)
+
+
+def test_batched_queue_many_tiny_planners(V):
+    # 64 planners of one work item or less each: fewer items than CTA pairs, so
+    # most pairs claim the end marker at once; every schedule gives each planner
+    # its single-call bits
+    rng = np.random.default_rng(11)
+    sizes = [(int(rng.integers(1, 40)), int(rng.integers(1, 4)), int(rng.integers(1, 4))) for _ in range(64)]
+    wl, g, rm, R, items, _ = _setup(V, sizes=sizes)
+    pl = V.make_planners(items)
+    ws = V.alloc_workspace(V.voila_rollout_batched_workspace_size(g, R, pl))
+    refs = [_single(V, wl, g, R, it) for it in items]
+    for schedule in (QUEUE, 1 | QUEUE, 1 | QUEUE | (2 << 8), 1):
+        for it in items:
+            it["J"].fill_(float("nan"))
+        V.voila_rollout_batched(g, R, pl, wl.d_s, wl.d_a, wl.d_omega, wl.gamma, wl.seed, schedule, ws)
+        assert V.workspace_status(ws) == V.OK
+        for it, (J, G) in zip(items, refs):
+            assert torch.equal(it["G"], G) and torch.equal(it["J"], J)

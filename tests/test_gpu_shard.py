@@ -95,3 +95,20 @@ def test_shard_arguments_checked(V):
         V.voila_rollout_shard(g, R, cuda(wl.particles[:10]), None, 0, wl.N, cuda(wl.actions), -2,
                               wl.d_omega, wl.gamma, wl.seed, 0, J, None, None, ws)
     assert e.value.code == V.ERR_ARG
+
+
+def test_shard_zero_horizon_and_empty_blocks(V):
+    wl, g, R, _ = _setup(V, "bf16")
+    # an empty sequence block is a no-op; a zero horizon gives zero returns
+    J = torch.full((1,), 7.0, dtype=torch.float64, device="cuda")
+    ws = V.alloc_workspace(V.voila_rollout_workspace_size(g, R, wl.N, 1, wl.H))
+    V.voila_rollout_shard(g, R, cuda(wl.particles), None, 0, wl.N, cuda(wl.actions[:0]), 3, wl.d_omega, wl.gamma,
+                          wl.seed, 0, torch.empty(0, dtype=torch.float64, device="cuda"), None, None, ws)
+    acts0 = torch.empty((2, 0, wl.d_a), dtype=torch.float32, device="cuda")
+    J2 = torch.full((2,), 7.0, dtype=torch.float64, device="cuda")
+    G2 = torch.full((2, 64), 7.0, dtype=torch.float64, device="cuda")
+    V.voila_rollout_shard(g, R, cuda(wl.particles[64:128]), None, 64, wl.N, acts0, 5, wl.d_omega, wl.gamma,
+                          wl.seed, 0, J2, G2, None, ws)
+    torch.cuda.synchronize()
+    assert torch.all(G2 == 0) and torch.all(J2 == 0)
+    assert J.item() == 7.0
