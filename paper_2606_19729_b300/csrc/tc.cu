@@ -611,7 +611,8 @@ __device__ __forceinline__ void write_pair_row(const TcParams& p, uint8_t* A, in
 // WIDE: layers up to 512 wide. Each CTA owns one 128-row tile per work item
 // (256 rows per pair); the two 256-column TMEM halves and the two 64 KB A
 // buffers hold the two column halves of a layer (K up to 512); the epilogue
-// starts when both halves' MMAs are done (the next input overwrites A).
+// drains half 0 while the MMAs of half 1 run, and the next layer's MMAs on
+// K < 256 start while it drains half 1.
 // MODE kModeDdim (with WIDE, DS = 8, DA = 10, DW = 0): the rows are teacher
 // samples and the H steps are the sampler's steps; no reward, the output is x
 // per row. MODE kModePairs (DS = 8, DA = 2, DW = 6, not WIDE): the rows are
@@ -652,7 +653,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
   uint64_t* item_full = bars + 2 * kStages + 5;               // [kItemRing]
   uint64_t* item_empty = item_full + kItemRing;               // [kItemRing]
   long long* item_ring = reinterpret_cast<long long*>(item_empty + kItemRing);  // [kItemRing]
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(item_ring + kItemRing);
+  uint64_t* alo_free = reinterpret_cast<uint64_t*>(item_ring + kItemRing);  // wide: A columns 0..255 read
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(alo_free + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -669,6 +671,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       ptx::mbar_init(ptx::smem_u32(&ready[g]), 4 * kEpiWarpsPerTile);
     }
     ptx::mbar_init(ptx::smem_u32(drain), 1);
+    ptx::mbar_init(ptx::smem_u32(alo_free), 1);
     for (int i = 0; i < kItemRing; ++i) {
       ptx::mbar_init(ptx::smem_u32(&item_full[i]), 1);
       ptx::mbar_init(ptx::smem_u32(&item_empty[i]), kItemTakers);
@@ -780,34 +783,35 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
               // complete), so every weight chunk crosses from L2 once per layer
               const int slot0 = slot;
               const uint32_t phase0 = phase;
+              // wide kernel: ready[0] says the previous layer's epilogue has written A
+              // columns 0..255 and read TMEM half 0, ready[1] the same of columns
+              // 256..511 and half 1; the MMAs on K < 256 start on ready[0] alone
+              bool hi_done = !WIDE;
+              const int kchunk = p.layers[l].spc * (f8 ? 128 : 64);  // K of one chunk
+              const int last_lo = (256 / kchunk < nch ? 256 / kchunk : nch) - 1;  // last chunk of K < 256
               for (int g = 0; g < (WIDE ? p.layers[l].ngroups : 2) && ok; ++g) {
                 if (!WIDE) {
                   slot = slot0;
                   phase = phase0;
                 }
                 // both CTAs' A operands of tile g are written and their accumulators read
-                // (wide: the whole layer input, once per layer)
-                const uint32_t nr = g ? nready1 : nready0;
-                const uint32_t rb = ptx::smem_u32(&ready[g]);
-                bool got = (WIDE && g == 1) ? true : ptx::mbar_try_wait(rb, nr & 1);
-                if (!got) {
-                  const long long t0 = clock64();
-                  while (!(got = ptx::mbar_try_wait(rb, nr & 1))) {
-                    if (*abort_flag) break;
-                    if (clock64() - t0 > kSpinLimit) {
-                      *abort_flag = 1;
-                      set_status(p.hdr, VOILA_ERR_TIMEOUT, 21 + g);
-                      break;
-                    }
-                  }
-                }
-                if (!got) {
-                  ok = false;
-                  break;
-                }
+                // (wide: A columns 0..255 and TMEM half 0 before group 0, TMEM half 1
+                // before group 1)
                 if (!WIDE || g == 0) {
+                  if (!bounded_wait(ptx::smem_u32(&ready[g]), (g ? nready1 : nready0) & 1, abort_flag, p.hdr, 21 + g)) {
+                    ok = false;
+                    break;
+                  }
                   if (g) ++nready1;
                   else ++nready0;
+                  ptx::tc_fence_after();
+                } else if (!hi_done) {
+                  if (!bounded_wait(ptx::smem_u32(&ready[1]), nready1 & 1, abort_flag, p.hdr, 22)) {
+                    ok = false;
+                    break;
+                  }
+                  ++nready1;
+                  hi_done = true;
                   ptx::tc_fence_after();
                 }
                 const uint64_t ad_tile = (!WIDE && g) ? adesc1 : adesc0;
@@ -832,6 +836,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                   if (!landed) {
                     ok = false;
                     break;
+                  }
+                  if (WIDE && !hi_done && c > last_lo) {  // K >= 256: A columns 256..511
+                    if (!bounded_wait(ptx::smem_u32(&ready[1]), nready1 & 1, abort_flag, p.hdr, 22)) {
+                      ok = false;
+                      break;
+                    }
+                    ++nready1;
+                    hi_done = true;
+                    ptx::tc_fence_after();
                   }
                   // chunk c = K steps [kpc c, kpc c + kpc): K step j sits in A slab j / 4 and in B
                   // slab (j mod kpc) / 4 of the slot; each K step is +32 bytes (+2 in the
@@ -859,12 +872,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                                          (c | kk) ? 1u : 0u);
                   }
                   if (WIDE || g == 1) ptx::mma_commit_pair(ptx::smem_u32(&empty[slot]), 0x3);
+                  // wide: the layer's MMAs on A columns 0..255 are issued; the
+                  // epilogue may overwrite them once these complete
+                  if (WIDE && g == p.layers[l].ngroups - 1 && c == last_lo)
+                    ptx::mma_commit_pair(ptx::smem_u32(alo_free), 0x3);
                   if (c == nch - 1) ptx::mma_commit_pair(ptx::smem_u32(&accf[g]), 0x3);
                   if (++slot == kStages) {
                     slot = 0;
                     phase ^= 1;
                   }
                 }
+              }
+              if (WIDE && ok && !hi_done) {  // one ready[1] phase per layer
+                if (!bounded_wait(ptx::smem_u32(&ready[1]), nready1 & 1, abort_flag, p.hdr, 22)) {
+                  ok = false;
+                  break;
+                }
+                ++nready1;
+                ptx::tc_fence_after();
               }
             }
         }
@@ -877,22 +902,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     }
   } else if constexpr (WIDE) {
     // ------------------------------------------------------------ epilogue (wide)
-    // One tile per CTA and work item: the sixteen warps form two column groups
-    // of eight; warp w may read TMEM lanes 32*(w % 4) .. +31 (its rows); the two
-    // warps of a lane quadrant split a group's columns. The group-0 "sub 0"
-    // warps also own the row state.
+    // One tile per CTA and work item. A layer's output is drained in two
+    // phases, each by all sixteen warps: TMEM half 0 (columns 0..255) as soon
+    // as its MMAs complete, while the MMAs of half 1 run, then half 1. Phase 0
+    // stores into A columns 0..255 once the MMAs reading them have completed
+    // (alo_free) and announces them on ready[0], so the next layer's MMAs on K
+    // < 256 start while phase 1 runs; phase 1 announces columns 256..511 on
+    // ready[1]. Warp w may read TMEM lanes 32*(w % 4) .. +31 (its rows); the
+    // four warps of a lane quadrant take 32-column batches in turn. The
+    // slice-0 warps also own the row state.
     const int e = warp - 2;
-    const int g = e >> 3;                   // tile of this warp (wide kernel: column group)
-    const int sub = (e >> 2) & 1;           // column half of the hidden layers
+    const int slice = e >> 2;               // batches slice, slice + 4, ... of a TMEM half
     const int q = warp & 3;                 // TMEM lane quadrant this warp may access
     const int r = 32 * q + lane;            // row within the tile
-    const bool owner = sub == 0 && (!WIDE || g == 0);  // holds the row state
-    uint8_t* A = WIDE ? Abuf[0] : Abuf[g];
-    const uint32_t tm = tmem_base + (uint32_t)(g * 256) + ((uint32_t)(32 * q) << 16);
-    const uint32_t ready_remote = ptx::mapa_shared(ptx::smem_u32(&ready[WIDE ? 0 : g]), 0);  // even CTA's
-    const uint32_t acc_bar = ptx::smem_u32(&accf[WIDE ? 0 : g]);
+    const bool owner = slice == 0;          // holds the row state
+    uint8_t* A = Abuf[0];                   // with Abuf[1]: one K = 512 operand
+    const uint32_t tm = tmem_base + ((uint32_t)(32 * q) << 16);
+    const uint32_t ready_lo = ptx::mapa_shared(ptx::smem_u32(&ready[0]), 0);  // even CTA's
+    const uint32_t ready_hi = ptx::mapa_shared(ptx::smem_u32(&ready[1]), 0);
+    const uint32_t acc_bar = ptx::smem_u32(&accf[0]);
     const uint32_t acc_bar1 = ptx::smem_u32(&accf[1]);
-    uint32_t nacc = 0, nacc1 = 0;
+    const uint32_t alo_bar = ptx::smem_u32(alo_free);
+    uint32_t nacc = 0, nacc1 = 0, nalo = 0;
     bool ok = true;
     long long jq = 0;
     for (long long it = QUEUE ? take_item(item_full, item_empty, item_ring, jq, true, abort_flag, p.hdr) : cl;
@@ -902,8 +933,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       const long long sp = it - (q ? p.item_end[q - 1] : 0);
       const TcPlanner& PL = p.pl[q];
       const int H = PL.H;
-      const long long row = WIDE ? sp * (2 * kTileRows) + (long long)rank * kTileRows + r
-                                 : sp * kSuperRows + g * (2 * kTileRows) + (long long)rank * kTileRows + r;
+      const long long row = sp * (2 * kTileRows) + (long long)rank * kTileRows + r;
       const bool valid = row < PL.rows;
       const uint32_t n = valid ? (uint32_t)(row % PL.N) : 0u;
       const uint32_t k = valid ? (uint32_t)(row / PL.N) : 0u;
@@ -936,7 +966,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
       }
       ptx::fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) ptx::mbar_arrive_cluster(ready_remote);
+      if (lane == 0) {
+        ptx::mbar_arrive_cluster(ready_lo);
+        ptx::mbar_arrive_cluster(ready_hi);
+      }
       double Gacc = 0.0, disc = 1.0;
       for (int t = 0; t < H && ok; ++t) {
         for (int l = 0; l < p.n_total; ++l) {
@@ -945,99 +978,119 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
             if (owner && l == p.n_gen - 1 && t + 1 < H)
               draw_tail<DA, DW>(tn, act_row + (t + 1) * DA, p.key0, p.key1, nc, kc, (uint32_t)(t + 1), PL.planner);
           }
-          if (!bounded_wait(acc_bar, nacc & 1, abort_flag, p.hdr, 30 + g)) {
-            ok = false;
-            break;
-          }
-          ++nacc;
-          const bool mine = !WIDE || g < L.ngroups;  // wide kernel: does this layer have column group g
-          // Wide layers: both column groups wait for both halves' MMAs, because
-          // the next layer's input overwrites the A slabs the second half reads.
-          if (WIDE && L.ngroups == 2) {
-            if (!bounded_wait(acc_bar1, nacc1 & 1, abort_flag, p.hdr, 32)) {
-              ok = false;
-              break;
-            }
-            ++nacc1;
-          }
-          ptx::tc_fence_after();
           const float* bl = bias_s + L.bias_off;  // shared memory (L1 loads measured slower)
           // no A operand follows the final layer of the final step
           const bool arrive = !(t == H - 1 && l == p.n_total - 1);
-          if (L.act >= 0) {
-            // hidden layer: bias + activation -> BF16 A operand of the next layer,
-            // 32 columns per TMEM load (measured faster than larger batches)
-            const int gcols = (L.Npad > 256 ? 256 : L.Npad);  // columns of this warp's group
-            const int nc = gcols >> 6;                          // 32-column batches per warp
-            const int cbase = WIDE ? g * 8 : 0;                 // first batch of the group in the layer
-            for (int c = cbase + sub * nc; mine && c < cbase + (sub + 1) * nc; ++c) {
-              float v[32];
-              ptx::tmem_ld32(tm + 32 * (c - cbase), v);
-              ptx::tmem_wait_ld32(v);
-              if (!F8) {
-                epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
-              } else if (L.out_fp8) {
-                if (L.fp8) epi_cols32<true, true>(v, bl, scale_s + L.scale_off, c, L.act, A, r);
-                else epi_cols32<false, true>(v, bl, nullptr, c, L.act, A, r);
-              } else {
-                if (L.fp8) epi_cols32<true, false>(v, bl, scale_s + L.scale_off, c, L.act, A, r);
-                else epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
+          bool lo_free = false;  // the MMAs reading A columns 0..255 have completed
+          for (int h = 0; h < L.ngroups && ok; ++h) {
+            if (!bounded_wait(h ? acc_bar1 : acc_bar, (h ? nacc1 : nacc) & 1, abort_flag, p.hdr, 30 + h)) {
+              ok = false;
+              break;
+            }
+            if (h) ++nacc1;
+            else ++nacc;
+            ptx::tc_fence_after();
+            if (L.act >= 0) {
+              // hidden layer: bias + activation -> A operand of the next layer,
+              // 32 columns per TMEM load (measured faster than larger batches)
+              const int nb = (L.Npad > 256 ? 256 : L.Npad) >> 5;  // 32-column batches of a TMEM half
+              for (int bt = slice; bt < nb; bt += 4) {
+                float v[32];
+                ptx::tmem_ld32(tm + (uint32_t)(256 * h + 32 * bt), v);
+                ptx::tmem_wait_ld32(v);
+                if (!lo_free) {
+                  if (!bounded_wait(alo_bar, nalo & 1, abort_flag, p.hdr, 33)) {
+                    ok = false;
+                    break;
+                  }
+                  ++nalo;
+                  lo_free = true;
+                }
+                const int c = 8 * h + bt;  // 32-column batch of the layer
+                if (!F8) {
+                  epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
+                } else if (L.out_fp8) {
+                  if (L.fp8) epi_cols32<true, true>(v, bl, scale_s + L.scale_off, c, L.act, A, r);
+                  else epi_cols32<false, true>(v, bl, nullptr, c, L.act, A, r);
+                } else {
+                  if (L.fp8) epi_cols32<true, false>(v, bl, scale_s + L.scale_off, c, L.act, A, r);
+                  else epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
+                }
               }
             }
-          } else if (PAIRS && owner) {
-            float v[16];
-            ptx::tmem_ld16(tm, v);
-            ptx::tmem_wait_ld();
-            if (valid) p.pair_out[row] = v[0] + bl[0];
-          } else if (DDIM && owner) {
-            // teacher output v: x <- cx[t] x + cv[t] (v + b), then the next step's input
-            float v[16];
-            ptx::tmem_ld16(tm, v);
-            ptx::tmem_wait_ld();
-            const float cx = p.ddim_cx[t], cv = p.ddim_cv[t];
+            if (h == 1 || !ok) break;
+            if (!lo_free) {  // one alo_free phase per layer
+              if (!bounded_wait(alo_bar, nalo & 1, abort_flag, p.hdr, 33)) {
+                ok = false;
+                break;
+              }
+              ++nalo;
+              lo_free = true;
+            }
+            if (L.act >= 0) {
+              // hidden layer: stored above
+            } else if (PAIRS && owner) {
+              float v[16];
+              ptx::tmem_ld16(tm, v);
+              ptx::tmem_wait_ld();
+              if (valid) p.pair_out[row] = v[0] + bl[0];
+            } else if (DDIM && owner) {
+              // teacher output v: x <- cx[t] x + cv[t] (v + b), then the next step's input
+              float v[16];
+              ptx::tmem_ld16(tm, v);
+              ptx::tmem_wait_ld();
+              const float cx = p.ddim_cx[t], cv = p.ddim_cv[t];
 #pragma unroll
-            for (int i = 0; i < DS; ++i) s[i] = fmaf(cx, s[i], cv * (v[i] + bl[i]));
-            if (t + 1 < H) write_ddim_input(A, r, s, a, p.ddim_emb + (size_t)(t + 1) * 8);
-          } else if (owner && l == p.n_gen - 1) {
-            // generator output: s_{t+1} (FP32 here; BF16 words from here on)
-            float v[32];
-            ptx::tmem_ld16(tm, v);
-            if (DS > 16) ptx::tmem_ld16(tm + 16, v + 16);
-            ptx::tmem_wait_ld();
+              for (int i = 0; i < DS; ++i) s[i] = fmaf(cx, s[i], cv * (v[i] + bl[i]));
+              if (t + 1 < H) write_ddim_input(A, r, s, a, p.ddim_emb + (size_t)(t + 1) * 8);
+            } else if (owner && l == p.n_gen - 1) {
+              // generator output: s_{t+1} (FP32 here; BF16 words from here on)
+              float v[32];
+              ptx::tmem_ld16(tm, v);
+              if (DS > 16) ptx::tmem_ld16(tm + 16, v + 16);
+              ptx::tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < DS; ++i) s[i] = v[i] + bl[i];
-            pack_state<DS>(s_pk, s);
-            if (p.reward_kind == VOILA_REWARD_GOAL) {
-              if (t + 1 < H) write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
-              float acc = 0.0f;
+              for (int i = 0; i < DS; ++i) s[i] = v[i] + bl[i];
+              pack_state<DS>(s_pk, s);
+              if (p.reward_kind == VOILA_REWARD_GOAL) {
+                if (t + 1 < H) write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
+                float acc = 0.0f;
 #pragma unroll
-              for (int i = 0; i < VOILA_MAX_GOAL; ++i)
-                if (i < p.goal_dims && i < DS) {
-                  const float d = s[i] - p.goal[i];
-                  acc = fmaf(d, d, acc);
-                }
-              Gacc += disc * (double)(-acc);
+                for (int i = 0; i < VOILA_MAX_GOAL; ++i)
+                  if (i < p.goal_dims && i < DS) {
+                    const float d = s[i] - p.goal[i];
+                    acc = fmaf(d, d, acc);
+                  }
+                Gacc += disc * (double)(-acc);
+                disc *= p.gamma;
+              } else {
+                write_rew_row<DS, DA>(A, r, s_pk, a_pk);
+              }
+            } else if (owner) {
+              // reward output r_t: G += gamma^t r_t in FP64
+              float v[16];
+              ptx::tmem_ld16(tm, v);
+              ptx::tmem_wait_ld();
+              if (t + 1 < H) {
+                write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
+                tail_actions<DA>(a_pk, tn);
+              }
+              Gacc += disc * (double)(v[0] + bl[0]);
               disc *= p.gamma;
-            } else {
-              write_rew_row<DS, DA>(A, r, s_pk, a_pk);
             }
-          } else if (owner) {
-            // reward output r_t: G += gamma^t r_t in FP64
-            float v[16];
-            ptx::tmem_ld16(tm, v);
-            ptx::tmem_wait_ld();
-            if (t + 1 < H) {
-              write_gen_row<DS, DA, DW>(A, r, s_pk, tn);
-              tail_actions<DA>(a_pk, tn);
+            ptx::tc_fence_before();
+            if (arrive) {  // A columns 0..255 written, TMEM half 0 read
+              ptx::fence_proxy_async_smem();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive_cluster(ready_lo);
             }
-            Gacc += disc * (double)(v[0] + bl[0]);
-            disc *= p.gamma;
           }
+          if (!ok) break;
           ptx::tc_fence_before();
-          if (arrive) {
+          if (arrive) {  // A columns 256..511 written, TMEM half 1 read
             ptx::fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive_cluster(ready_remote);
+            if (lane == 0) ptx::mbar_arrive_cluster(ready_hi);
           }
         }
       }
@@ -1570,8 +1623,9 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R, bool ddim = false, boo
 }
 
 size_t tc_smem_bytes(int vec_floats) {
-  // barriers (weight ring, accumulators, ready, drain, item ring), item slots, TMEM address, abort flag
-  return 1024 + 2 * kABytes + kStages * kSlotBytes + (size_t)vec_floats * 4 + (2 * kStages + 5 + 3 * kItemRing) * 8 +
+  // barriers (weight ring, accumulators, ready, drain, item ring), item slots, A-free barrier, TMEM
+  // address, abort flag
+  return 1024 + 2 * kABytes + kStages * kSlotBytes + (size_t)vec_floats * 4 + (2 * kStages + 6 + 3 * kItemRing) * 8 +
          16;
 }
 
