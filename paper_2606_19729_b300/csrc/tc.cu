@@ -83,6 +83,7 @@ struct TcLayer {
   int fuse_out;     // 1: a scalar output layer follows, computed in this layer's epilogue on CUDA cores
   int fuse_off;     // its weights (fuse_K floats) and bias in the fused-output vector
   int fuse_K;
+  int rot;          // wide kernel: 1 when this layer's K < 256 sits in the upper A half (see make_plan)
 };
 
 // One independent planning problem of a (batched) launch.
@@ -789,6 +790,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
               bool hi_done = !WIDE;
               const int kchunk = p.layers[l].spc * (f8 ? 128 : 64);  // K of one chunk
               const int last_lo = (256 / kchunk < nch ? 256 / kchunk : nch) - 1;  // last chunk of K < 256
+              // A half of K < 256 (16-byte units: 64 KB of BF16 or 32 KB of E4M3 per half)
+              const uint32_t amask = (WIDE && p.layers[l].rot) ? (f8 ? 2048u : 4096u) : 0u;
               for (int g = 0; g < (WIDE ? p.layers[l].ngroups : 2) && ok; ++g) {
                 if (!WIDE) {
                   slot = slot0;
@@ -850,7 +853,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                   // slab (j mod kpc) / 4 of the slot; each K step is +32 bytes (+2 in the
                   // descriptor's address field) inside a slab
                   const int kb = kpc * c;
-                  const uint32_t a_lo = ad_lo + (uint32_t)(kb >> 2) * 1024u;
+                  const uint32_t a_lo = ad_lo + (((uint32_t)(kb >> 2) * 1024u) ^ amask);
                   const uint32_t b_lo = bd_lo + (uint32_t)slot * (uint32_t)(kSlotBytes >> 4);
                   const int ks = ksteps - kb < kpc ? ksteps - kb : kpc;
                   if (F8 && kpc == 4 && f8) {
@@ -982,6 +985,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
           // no A operand follows the final layer of the final step
           const bool arrive = !(t == H - 1 && l == p.n_total - 1);
           bool lo_free = false;  // the MMAs reading A columns 0..255 have completed
+          // The next layer reads its K < 256 from A half rot_next; half h of this
+          // output goes to A half h ^ rot_next. When that differs from this layer's
+          // own rot (a layer with K <= 256 reads one A half only), phase 0 writes the
+          // half this layer does not read and need not wait for alo_free.
+          const int rot_next = (L.act >= 0 && l + 1 < p.n_total) ? p.layers[l + 1].rot : 0;
+          const bool lo_need = L.act < 0 || rot_next == L.rot;
           for (int h = 0; h < L.ngroups && ok; ++h) {
             if (!bounded_wait(h ? acc_bar1 : acc_bar, (h ? nacc1 : nacc) & 1, abort_flag, p.hdr, 30 + h)) {
               ok = false;
@@ -998,7 +1007,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                 float v[32];
                 ptx::tmem_ld32(tm + (uint32_t)(256 * h + 32 * bt), v);
                 ptx::tmem_wait_ld32(v);
-                if (!lo_free) {
+                if (!lo_free && lo_need) {
                   if (!bounded_wait(alo_bar, nalo & 1, abort_flag, p.hdr, 33)) {
                     ok = false;
                     break;
@@ -1006,20 +1015,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
                   ++nalo;
                   lo_free = true;
                 }
-                const int c = 8 * h + bt;  // 32-column batch of the layer
+                // batch c of the layer (its biases and scales) is stored as A batch
+                // ca; epi_cols32 addresses both through its batch argument
+                const int c = 8 * h + bt, ca = c ^ (8 * rot_next);
+                const float* blc = bl + 32 * (c - ca);
+                const float* slc = scale_s + L.scale_off + 32 * (c - ca);
                 if (!F8) {
-                  epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
+                  epi_cols32<false, false>(v, blc, nullptr, ca, L.act, A, r);
                 } else if (L.out_fp8) {
-                  if (L.fp8) epi_cols32<true, true>(v, bl, scale_s + L.scale_off, c, L.act, A, r);
-                  else epi_cols32<false, true>(v, bl, nullptr, c, L.act, A, r);
+                  if (L.fp8) epi_cols32<true, true>(v, blc, slc, ca, L.act, A, r);
+                  else epi_cols32<false, true>(v, blc, nullptr, ca, L.act, A, r);
                 } else {
-                  if (L.fp8) epi_cols32<true, false>(v, bl, scale_s + L.scale_off, c, L.act, A, r);
-                  else epi_cols32<false, false>(v, bl, nullptr, c, L.act, A, r);
+                  if (L.fp8) epi_cols32<true, false>(v, blc, slc, ca, L.act, A, r);
+                  else epi_cols32<false, false>(v, blc, nullptr, ca, L.act, A, r);
                 }
               }
             }
             if (h == 1 || !ok) break;
-            if (!lo_free) {  // one alo_free phase per layer
+            if (!lo_free && lo_need) {
               if (!bounded_wait(alo_bar, nalo & 1, abort_flag, p.hdr, 33)) {
                 ok = false;
                 break;
@@ -1084,6 +1097,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
               __syncwarp();
               if (lane == 0) ptx::mbar_arrive_cluster(ready_lo);
             }
+          }
+          if (ok && !lo_free) {  // one alo_free phase per layer
+            if (!bounded_wait(alo_bar, nalo & 1, abort_flag, p.hdr, 33)) ok = false;
+            ++nalo;
           }
           if (!ok) break;
           ptx::tc_fence_before();
@@ -1599,6 +1616,19 @@ Plan make_plan(const voila_mlp* g, const voila_reward* R, bool ddim = false, boo
                         : (c >= 32 && c < 96) ? (short)(c - 14) : (short)-1;
   }
   pl.p.n_total = nl;
+  // Wide kernel: a 512-wide layer with K <= 256 reads one A half, so its
+  // epilogue can write its first output half into the other A half at once,
+  // and the next layer takes its K < 256 from there (rot = 1); a layer whose
+  // input the row owner writes (after an output layer, or the first) has
+  // rot = 0. Used for the DDIM teacher (sampler 2.96 -> 2.75 ms at 65,536
+  // samples); the sweep generator measured 1-3 % slower with it and keeps
+  // rot = 0.
+  for (int l = 0, r = 0; l < nl; ++l) {
+    TcLayer& L = pl.p.layers[l];
+    L.rot = r;
+    const bool flip = ddim && pl.wide && L.ngroups == 2 && L.Kp <= 256;
+    r = L.act >= 0 ? (r ^ (flip ? 1 : 0)) : 0;
+  }
   // the two-tile kernel keeps a layer's chunks in the ring for both tiles
   if (!pl.wide)
     for (int l = 0; l < nl; ++l)

@@ -71,16 +71,26 @@ TrainLayout train_layout(const voila_mlp* m, long long M) {
   return T;
 }
 
-// X (FP32 [M][d0]) -> Xb [M][K0p] and X^T [K0p][ldT], BF16, zero padded.
-__global__ void prep_x_kernel(const float* __restrict__ X, long long M, int d0, int K0p, long long ldT,
-                              __nv_bfloat16* __restrict__ xb, __nv_bfloat16* __restrict__ xt) {
-  const long long n = M * K0p;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const long long m = e / K0p;
-    const int c = (int)(e % K0p);
-    const __nv_bfloat16 v = __float2bfloat16_rn(c < d0 ? X[m * d0 + c] : 0.0f);
-    xb[e] = v;
-    xt[(size_t)c * ldT + m] = v;
+// X (FP32 [M][d]) -> Xb [M][Kp] and X^T [Kp][ldT], BF16, zero padded (Kp a
+// multiple of 8). One row per thread: the row goes out in 16-byte stores, and
+// a warp's transposed stores of one column are 32 consecutive rows.
+__global__ void pad_rows_kernel(const float* __restrict__ X, long long M, int d, int Kp, long long ldT,
+                                __nv_bfloat16* __restrict__ xb, __nv_bfloat16* __restrict__ xt) {
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x) {
+    const float* x = X + m * d;
+    for (int c0 = 0; c0 < Kp; c0 += 8) {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        const int c = c0 + j;
+        const __nv_bfloat16 lo = __float2bfloat16_rn(c < d ? x[c] : 0.0f);
+        const __nv_bfloat16 hi = __float2bfloat16_rn(c + 1 < d ? x[c + 1] : 0.0f);
+        xt[(size_t)c * ldT + m] = lo;
+        xt[(size_t)(c + 1) * ldT + m] = hi;
+        w[j >> 1] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+      }
+      *reinterpret_cast<uint4*>(xb + m * Kp + c0) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
   }
 }
 
@@ -102,26 +112,24 @@ __global__ void pad_transpose_kernel(const __nv_bfloat16* __restrict__ src, int 
   }
 }
 
-// dY (FP32 [M][dL]) -> delta_L [M][NLp] and its transpose [NLp][ldT], BF16.
-__global__ void prep_dy_kernel(const float* __restrict__ dY, long long M, int dL, int NLp, long long ldT,
-                               __nv_bfloat16* __restrict__ dl, __nv_bfloat16* __restrict__ dlt) {
-  const long long n = M * NLp;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const long long m = e / NLp;
-    const int c = (int)(e % NLp);
-    const __nv_bfloat16 v = __float2bfloat16_rn(c < dL ? dY[m * dL + c] : 0.0f);
-    dl[e] = v;
-    dlt[(size_t)c * ldT + m] = v;
-  }
-}
-
 // out[r][c] = sum_s P[s][r][c] (s in order), r < R, c < C; P is [S][Rg][Cg].
+// Eight partials are loaded ahead of their (ordered) additions.
 __global__ void reduce_partials_kernel(const float* __restrict__ P, int S, int Rg, int Cg, int R, int C,
                                        float* __restrict__ out) {
+  const size_t step = (size_t)Rg * Cg;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < R * C; e += gridDim.x * blockDim.x) {
     const int r = e / C, c = e % C;
+    const float* src = P + (size_t)r * Cg + c;
     float acc = 0.0f;
-    for (int s = 0; s < S; ++s) acc += P[((size_t)s * Rg + r) * Cg + c];
+    int s = 0;
+    for (; s + 8 <= S; s += 8) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = __ldg(src + (size_t)(s + j) * step);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc += v[j];
+    }
+    for (; s < S; ++s) acc += __ldg(src + (size_t)s * step);
     out[e] = acc;
   }
 }
@@ -134,8 +142,20 @@ __global__ void __launch_bounds__(256) rowsum_bf16_kernel(const __nv_bfloat16* _
   const __nv_bfloat16* row = DT + (size_t)blockIdx.x * ldT;
   const long long groups = M / 8;
   float a = 0.0f;
-  for (long long gi = threadIdx.x; gi < groups; gi += blockDim.x) {
-    const uint4 w = *reinterpret_cast<const uint4*>(row + 8 * gi);
+  long long gi = threadIdx.x;
+  for (; gi + 3 * blockDim.x < groups; gi += 4 * blockDim.x) {  // four loads ahead, added in order
+    uint4 w4[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w4[u] = __ldg(reinterpret_cast<const uint4*>(row + 8 * (gi + u * blockDim.x)));
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t ws[4] = {w4[u].x, w4[u].y, w4[u].z, w4[u].w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a += __uint_as_float(ws[j] << 16) + __uint_as_float(ws[j] & 0xffff0000u);
+    }
+  }
+  for (; gi < groups; gi += blockDim.x) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(row + 8 * gi));
     const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) a += __uint_as_float(ws[j] << 16) + __uint_as_float(ws[j] & 0xffff0000u);
@@ -146,26 +166,40 @@ __global__ void __launch_bounds__(256) rowsum_bf16_kernel(const __nv_bfloat16* _
 }
 
 // part[b][c] = sum over the rows of block b of dY[m][c] (contiguous row ranges,
-// fixed order), then out[c] = sum_b part[b][c] in block order.
+// fixed order), then out[c] = sum_b part[b][c] in a fixed order. Thread t of a
+// block (dL <= blockDim.x) adds column t mod dL of rows t / dL, + blockDim.x / dL,
+// ... (consecutive threads read consecutive floats); the block then adds the
+// threads of a column in thread order.
 __global__ void __launch_bounds__(256) colsum_partial_kernel(const float* __restrict__ dY, long long M, int dL,
                                                              double* __restrict__ part) {
-  __shared__ double red[33];
+  __shared__ double red[256];
+  const int rpi = blockDim.x / dL;  // rows per pass
+  const int c = threadIdx.x % dL, r0 = threadIdx.x / dL;
   const long long per = (M + gridDim.x - 1) / gridDim.x;
   const long long m0 = blockIdx.x * per, m1 = m0 + per < M ? m0 + per : M;
-  for (int c = 0; c < dL; ++c) {
-    double a = 0.0;
-    for (long long m = m0 + threadIdx.x; m < m1; m += blockDim.x) a += (double)dY[m * dL + c];
-    a = block_sum(a, red);
-    if (threadIdx.x == 0) part[(size_t)blockIdx.x * dL + c] = a;
+  double a = 0.0;
+  if (r0 < rpi)
+    for (long long m = m0 + r0; m < m1; m += rpi) a += (double)__ldg(dY + m * dL + c);
+  red[threadIdx.x] = a;
+  __syncthreads();
+  if ((int)threadIdx.x < dL) {
+    double t = 0.0;
+    for (int i = 0; i < rpi; ++i) t += red[i * dL + threadIdx.x];
+    part[(size_t)blockIdx.x * dL + threadIdx.x] = t;
   }
 }
 
+// warp w sums columns w, w + 8, ...: lane j adds blocks j, j + 32, ..., then a
+// fixed butterfly over the lanes
 __global__ void colsum_final_kernel(const double* __restrict__ part, int nb, int dL, float* __restrict__ out) {
-  const int c = threadIdx.x;
-  if (c >= dL) return;
-  double a = 0.0;
-  for (int b = 0; b < nb; ++b) a += part[(size_t)b * dL + c];
-  out[c] = (float)a;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = w; c < dL; c += blockDim.x >> 5) {
+    double a = 0.0;
+    for (int b = lane; b < nb; b += 32) a += part[(size_t)b * dL + c];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) out[c] = (float)a;
+  }
 }
 
 int grid_of(long long n) {
@@ -199,8 +233,8 @@ voila_status tc_train_forward(const voila_mlp* m, const float* X, long long M, f
   const int L = T.L;
   typedef __nv_bfloat16 bf;
   // operands: padded input and first/last weights, transposed weights for the backward
-  prep_x_kernel<<<grid_of(M * T.K0p), 256, 0, s>>>(X, M, T.d[0], T.K0p, T.ldT, at<bf>(scratch, T.xb),
-                                                   at<bf>(scratch, T.xt));
+  pad_rows_kernel<<<grid_of(M), 256, 0, s>>>(X, M, T.d[0], T.K0p, T.ldT, at<bf>(scratch, T.xb),
+                                             at<bf>(scratch, T.xt));
   pad_copy_kernel<<<grid_of((long long)T.d[1] * T.K0p), 256, 0, s>>>((const bf*)m->W[0], T.d[1], T.d[0], T.d[1],
                                                                       T.K0p, at<bf>(scratch, T.w1p));
   pad_copy_kernel<<<grid_of((long long)T.NLp * T.d[L - 1]), 256, 0, s>>>(
@@ -260,8 +294,8 @@ voila_status tc_train_backward(const voila_mlp* m, const float* dY, long long M,
     goff[l][1] = o;
     o += T.d[l];
   }
-  prep_dy_kernel<<<grid_of(M * T.NLp), 256, 0, s>>>(dY, M, T.d[L], T.NLp, T.ldT, at<bf>(scratch, T.dl),
-                                                    at<bf>(scratch, T.dlt));
+  pad_rows_kernel<<<grid_of(M), 256, 0, s>>>(dY, M, T.d[L], T.NLp, T.ldT, at<bf>(scratch, T.dl),
+                                             at<bf>(scratch, T.dlt));
   colsum_partial_kernel<<<kColsumBlocks, 256, 0, s>>>(dY, M, T.d[L], at<double>(scratch, T.colpart));
   colsum_final_kernel<<<1, 256, 0, s>>>(at<double>(scratch, T.colpart), kColsumBlocks, T.d[L], grads + goff[L][1]);
   if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
