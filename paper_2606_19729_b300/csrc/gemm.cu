@@ -9,11 +9,14 @@
 // the accumulator (warp w owns TMEM lanes 32 (w mod 4) .. +31, one row per
 // thread; the four warps of a lane quadrant split the columns) and run one of
 // the epilogues:
-//   kFwdHidden  z = acc + b;  H = act(z), AD = act'(z) row-major, H^T via
-//               a shared-memory transpose (BF16);
+//   kFwdHidden  z = acc + b;  H = act(z), AD = act'(z) row-major and H^T (BF16);
 //   kFwdOut     Y = acc + b (FP32, the first n_real columns);
 //   kBwd        delta = acc * AD_in;  D row-major and D^T (BF16);
 //   kPartial    P[split][m][n] = acc (FP32), summed later in split order.
+// The BF16 outputs leave by TMA: each warp stages its 32 rows x 16 columns
+// (row-major, and transposed) in its own shared-memory slots and one lane
+// stores them as tensor tiles, so no store instruction scatters over 32
+// rows and no warp waits for another.
 // Every wait is bounded; on expiry the kernel records VOILA_ERR_TIMEOUT,
 // waits (bounded) for its copies, frees TMEM and returns.
 #include <cuda.h>
@@ -34,11 +37,12 @@ constexpr int kGEpiThreads = 512;
 constexpr int kGStages = 3;
 constexpr int kGABytes = 128 * 128;  // 128 rows x 64 BF16
 constexpr int kGBBytes = 256 * 128;  // up to 256 rows x 64 BF16
-constexpr int kGStageBytes = 256 * 128 * 2;  // transposed staging: [N <= 256][128 rows] BF16
+constexpr int kGWarpStage = 3 * 32 * 16;   // BF16 per epilogue warp: [32][16] row-major x2, [16][32] transposed
 constexpr long long kGSpin = 4000000000LL;
 
 struct GemmParams {
   CUtensorMap ta, tb;
+  CUtensorMap tH, tAD, tHT;  // store maps: H / AD [M][N] (box 16 x 32), HT [N][M] (box 32 x 16)
   int M, N;           // rows of A (valid rows), columns of D (MMA N, multiple of 16, <= 256)
   int n_real;         // columns stored by kFwdOut / kPartial-transposed users
   int kchunks;        // K chunks of 64 per unit (K split)
@@ -100,14 +104,14 @@ __device__ __forceinline__ uint32_t bf2(float lo, float hi) { return ptx::pack_b
 // 128-row tile x K split). Two FP32 accumulators in TMEM (columns [0, 256) and
 // [256, 512)) let the MMAs of a CTA's next unit run while the epilogue warps
 // drain the previous one; the producer streams the next unit's chunks into the
-// ring meanwhile. The transposed outputs go through their own staging buffer.
+// ring meanwhile.
 __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_constant__ GemmParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* ringA = smem;
   uint8_t* ringB = smem + kGStages * kGABytes;
-  __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(ringB + kGStages * kGBBytes);  // [N][128]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(stage) + kGStageBytes);
+  __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(ringB + kGStages * kGBBytes);  // per epilogue warp
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stage + 16 * kGWarpStage);
   uint64_t* full = bars;
   uint64_t* empty = bars + kGStages;
   uint64_t* accf = bars + 2 * kGStages;      // [2] accumulator b holds a finished unit
@@ -225,7 +229,11 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_cons
     const int r = 32 * q + lane;
     const int cps = p.N >= 64 ? p.N / 4 : 16;  // columns per slice (multiples of 16)
     const int c_lo = slice * cps, c_hi = c_lo + cps < p.N ? c_lo + cps : p.N;
-    const bool transpose = p.mode == kGemmFwdHidden || p.mode == kGemmBwd;
+    const bool tstore = p.mode == kGemmFwdHidden || p.mode == kGemmBwd;
+    __nv_bfloat16* stH = stage + (warp - 2) * kGWarpStage;  // [32 rows][16] : H (or D)
+    __nv_bfloat16* stA = stH + 512;                          // [32 rows][16] : AD
+    __nv_bfloat16* stT = stH + 1024;                         // [16][32 rows] : H^T (or D^T)
+    bool pending = false;  // lane 0: bulk stores of this warp whose reads may be in flight
     bool ok = true;
     int k = 0;
     for (long long u = blockIdx.x; u < units; u += gridDim.x, ++k) {
@@ -233,14 +241,29 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_cons
       const int m0 = (int)(u % tiles) * 128, split = (int)(u / tiles);
       const int m = m0 + r;
       const bool valid = m < p.M;
+      const int mq = m0 + 32 * q;  // first row of this warp's lane quadrant
       if (ok) ok = gwait(ptx::smem_u32(&accf[b]), (uint32_t)(k >> 1) & 1u, abort_flag, p.hdr, 72);
       ptx::tc_fence_after();
       const uint32_t tq = tmem + (uint32_t)(b * 256) + ((uint32_t)(32 * q) << 16);
       bool released = false;  // this warp has arrived on acce[b] for this unit
       if (ok) {
+        // backward: the activation derivatives of the next 16 columns are
+        // loaded one batch ahead of their use
+        uint4 an0 = make_uint4(0u, 0u, 0u, 0u), an1 = an0;
+        if (p.mode == kGemmBwd && valid && c_lo < c_hi) {
+          const uint4* src = reinterpret_cast<const uint4*>(p.AD_in + (size_t)m * p.N + c_lo);
+          an0 = __ldg(src);
+          an1 = __ldg(src + 1);
+        }
         for (int cb = c_lo; cb < c_hi; cb += 16) {
           float v[16];
           ptx::tmem_ld16(tq + cb, v);
+          const uint4 a0 = an0, a1 = an1;
+          if (p.mode == kGemmBwd && valid && cb + 16 < c_hi) {
+            const uint4* src = reinterpret_cast<const uint4*>(p.AD_in + (size_t)m * p.N + cb + 16);
+            an0 = __ldg(src);
+            an1 = __ldg(src + 1);
+          }
           ptx::tmem_wait_ld();
           if (cb + 16 >= c_hi) {  // this warp's last read of the accumulator
             ptx::tc_fence_before();
@@ -248,41 +271,49 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_cons
             if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&acce[b]));
             released = true;
           }
-          if (transpose) {
-            float h[16], d[16];
+          if (tstore) {
+            uint32_t hp[8], dp[8];
             if (p.mode == kGemmFwdHidden) {
 #pragma unroll
-              for (int j = 0; j < 16; ++j) act_and_grad(v[j] + bias_s[cb + j], p.act, h[j], d[j]);
+              for (int j = 0; j < 8; ++j) {
+                float h0, d0, h1, d1;
+                act_and_grad(v[2 * j] + bias_s[cb + 2 * j], p.act, h0, d0);
+                act_and_grad(v[2 * j + 1] + bias_s[cb + 2 * j + 1], p.act, h1, d1);
+                hp[j] = bf2(h0, h1);
+                dp[j] = bf2(d0, d1);
+              }
             } else {
-              float a[16];
-              if (valid) {
-                const uint4* src = reinterpret_cast<const uint4*>(p.AD_in + (size_t)m * p.N + cb);
-                const uint4 w0 = src[0], w1 = src[1];
-                const uint32_t ws[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+              const uint32_t ws[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                  a[2 * j] = __uint_as_float(ws[j] << 16);
-                  a[2 * j + 1] = __uint_as_float(ws[j] & 0xffff0000u);
-                }
-              } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) a[j] = 0.0f;
-              }
-#pragma unroll
-              for (int j = 0; j < 16; ++j) h[j] = v[j] * a[j];
+              for (int j = 0; j < 8; ++j)
+                hp[j] = bf2(v[2 * j] * __uint_as_float(ws[j] << 16), v[2 * j + 1] * __uint_as_float(ws[j] & 0xffff0000u));
             }
-            if (valid) {
-              uint4* dst = reinterpret_cast<uint4*>(p.H + (size_t)m * p.N + cb);
-              dst[0] = make_uint4(bf2(h[0], h[1]), bf2(h[2], h[3]), bf2(h[4], h[5]), bf2(h[6], h[7]));
-              dst[1] = make_uint4(bf2(h[8], h[9]), bf2(h[10], h[11]), bf2(h[12], h[13]), bf2(h[14], h[15]));
-              if (p.mode == kGemmFwdHidden) {
-                uint4* dd = reinterpret_cast<uint4*>(p.AD + (size_t)m * p.N + cb);
-                dd[0] = make_uint4(bf2(d[0], d[1]), bf2(d[2], d[3]), bf2(d[4], d[5]), bf2(d[6], d[7]));
-                dd[1] = make_uint4(bf2(d[8], d[9]), bf2(d[10], d[11]), bf2(d[12], d[13]), bf2(d[14], d[15]));
-              }
+            // the slots are free once the previous batch's stores have read them
+            if (lane == 0 && pending) ptx::bulk_wait_read_all();
+            __syncwarp();
+            uint4* rowH = reinterpret_cast<uint4*>(stH + lane * 16);
+            rowH[0] = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+            rowH[1] = make_uint4(hp[4], hp[5], hp[6], hp[7]);
+            if (p.mode == kGemmFwdHidden) {
+              uint4* rowA = reinterpret_cast<uint4*>(stA + lane * 16);
+              rowA[0] = make_uint4(dp[0], dp[1], dp[2], dp[3]);
+              rowA[1] = make_uint4(dp[4], dp[5], dp[6], dp[7]);
             }
 #pragma unroll
-            for (int j = 0; j < 16; ++j) stage[(cb + j) * 128 + r] = __float2bfloat16_rn(valid ? h[j] : 0.0f);
+            for (int j = 0; j < 8; ++j) {
+              stT[(2 * j) * 32 + lane] = __ushort_as_bfloat16((unsigned short)(hp[j] & 0xffffu));
+              stT[(2 * j + 1) * 32 + lane] = __ushort_as_bfloat16((unsigned short)(hp[j] >> 16));
+            }
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            // rows from M on (a ragged last tile) fall outside the tensors and are not written
+            if (lane == 0 && mq < p.M) {
+              ptx::tma_store_2d(&p.tH, cb, mq, ptx::smem_u32(stH));
+              if (p.mode == kGemmFwdHidden) ptx::tma_store_2d(&p.tAD, cb, mq, ptx::smem_u32(stA));
+              ptx::tma_store_2d(&p.tHT, mq, cb, ptx::smem_u32(stT));
+              ptx::bulk_commit();
+              pending = true;
+            }
           } else if (p.mode == kGemmFwdOut) {
             if (valid)
               for (int j = 0; j < 16; ++j)
@@ -301,22 +332,10 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_cons
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&acce[b]));
       }
-      if (transpose) {
-        // transposed copy: stage [N][128] -> HT[n][m0 .. m0 + 127], 16 bytes per store
-        asm volatile("bar.sync 1, 512;" ::: "memory");
-        if (ok) {
-          const int per_row = 16;  // 128 BF16 = 16 x 16 bytes
-          for (int e = threadIdx.x - 64; e < p.N * per_row; e += kGEpiThreads) {
-            const int n = e / per_row, j = e % per_row;
-            const int mm = m0 + 8 * j;
-            if (mm + 8 <= p.ldT)
-              *reinterpret_cast<uint4*>(p.HT + (size_t)n * p.ldT + mm) =
-                  *reinterpret_cast<const uint4*>(stage + n * 128 + 8 * j);
-          }
-        }
-        asm volatile("bar.sync 1, 512;" ::: "memory");  // the stage is free for the next unit
-      }
     }
+    // the bulk stores complete (their shared-memory reads and global writes)
+    // before the kernel ends
+    if (lane == 0 && pending) ptx::bulk_wait_all();
   }
 
   ptx::tc_fence_before();
@@ -351,10 +370,25 @@ bool make_map(CUtensorMap* map, const __nv_bfloat16* base, long long K, long lon
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Store map of a row-major [rows][cols] BF16 tensor (row stride ld elements), box
+// box_c columns x box_r rows, no swizzle: the shared-memory tile is dense row-major.
+bool make_store_map(CUtensorMap* map, const __nv_bfloat16* base, long long cols, long long rows, long long ld,
+                    int box_c, int box_r) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+  if (!enc || ((uintptr_t)base & 15) || (ld * 2) % 16 || cols < 1 || rows < 1) return false;
+  const cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)(ld * 2)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_c, (cuuint32_t)box_r};
+  const cuuint32_t estride[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, gdim, gstride, box, estride,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 size_t tc_gemm_smem_bytes() {
-  return 1024 + kGStages * (kGABytes + kGBBytes) + kGStageBytes + (2 * kGStages + 6) * 8 + 256 * 4;
+  return 1024 + kGStages * (kGABytes + kGBBytes) + 16 * kGWarpStage * 2 + (2 * kGStages + 6) * 8 + 256 * 4;
 }
 
 cudaError_t tc_gemm(const TcGemm& g, cudaStream_t s) {
@@ -363,6 +397,13 @@ cudaError_t tc_gemm(const TcGemm& g, cudaStream_t s) {
   memset(&p, 0, sizeof(p));
   if (!make_map(&p.ta, g.A, g.K, g.M, g.lda, 128)) return cudaErrorInvalidValue;
   if (!make_map(&p.tb, g.B, g.K, g.N, g.ldb, g.N)) return cudaErrorInvalidValue;
+  if (g.mode == kGemmFwdHidden || g.mode == kGemmBwd) {
+    if (!g.H || !g.HT || (g.mode == kGemmFwdHidden && !g.AD) || (g.mode == kGemmBwd && !g.AD_in) || g.ldT < g.M)
+      return cudaErrorInvalidValue;
+    if (!make_store_map(&p.tH, g.H, g.N, g.M, g.N, 16, 32)) return cudaErrorInvalidValue;
+    if (g.mode == kGemmFwdHidden && !make_store_map(&p.tAD, g.AD, g.N, g.M, g.N, 16, 32)) return cudaErrorInvalidValue;
+    if (!make_store_map(&p.tHT, g.HT, g.M, g.N, g.ldT, 32, 16)) return cudaErrorInvalidValue;
+  }
   const int kchunks_total = (int)((g.K + 63) / 64);
   p.M = g.M;
   p.N = g.N;

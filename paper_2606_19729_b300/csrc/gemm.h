@@ -14,7 +14,8 @@ enum { kGemmFwdHidden = 0, kGemmFwdOut = 1, kGemmBwd = 2, kGemmPartial = 3 };
 // D[M][N] = A[M][K] . B[N][K]^T (BF16 row-major operands, leading dimensions
 // lda, ldb in elements, multiples of 8; N a multiple of 16, <= 256).
 //   kGemmFwdHidden: z = D + bias; H = act(z), AD = act'(z) ([M][N], BF16),
-//                   HT = H^T ([N][ldT], BF16; ldT >= M, a multiple of 8).
+//                   HT = H^T ([N][ldT], BF16; ldT >= M, a multiple of 8;
+//                   columns from M on are not written).
 //   kGemmFwdOut:    Y[m][n] = D + bias for n < n_real (FP32, row stride ldY).
 //   kGemmBwd:       H = D * AD_in ([M][N], BF16, the backpropagated delta)
 //                   and HT = its transpose.
