@@ -583,6 +583,21 @@ def batched_record(args, rank, world, local):
         torch.cuda.synchronize()
         seq_s = sum(a.elapsed_time(b) for a, b in seq_ev) / 1e3
         same = all(torch.equal(a, it["J"]) for a, it in zip(J_batched, items))
+        # paired: the two forms alternate, so slow drifts of the clock affect both alike
+        pairs = []
+        for i in range(max(1, args.steps)):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            flush.fill_(3)
+            e[0].record(stream)
+            graph.replay()
+            e[1].record(stream)
+            flush.fill_(4)
+            e[2].record(stream)
+            sequential()
+            e[3].record(stream)
+            pairs.append(e)
+        torch.cuda.synchronize()
+        paired = [(e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])) for e in pairs]
         # every candidate schedule of the autotuner, timed alone on the same work
         sched_ms = {}
         if getattr(args, "batched_schedules", False):
@@ -624,6 +639,11 @@ def batched_record(args, rank, world, local):
                                        "repeats": len(s_ms), "min": min(s_ms), "median": statistics.median(s_ms),
                                        "max": max(s_ms), "stdev": statistics.pstdev(s_ms)},
             "batched_equals_sequential": same,
+            "paired": {"pairs": len(paired), "batched_ms": [round(b, 3) for b, _ in paired],
+                       "sequential_ms": [round(q, 3) for _, q in paired],
+                       "sequential_minus_batched_ms_median": statistics.median(q - b for b, q in paired),
+                       "sequential_minus_batched_ms_min": min(q - b for b, q in paired),
+                       "batched_faster_in": sum(1 for b, q in paired if q > b)},
             "roofline": dict(tensor_roofline(achieved, peaks, clocks, "bf16"), traffic=None,
                              kernel="rollout_tc_kernel (batched)"),
             "gpu_launches": 4 * args.steps, "clocks": clocks}
@@ -1153,6 +1173,7 @@ def config_records(args, rank, world, local, fp8_peak):
     b = batched_record(a, rank, world, local)
     out["c5_batched"] = {k: b.get(k) for k in ("value", "unit", "ms_per_step", "schedule", "autotune_ms",
                                                "batched_ms", "sequential_64_launches", "batched_equals_sequential",
+                                               "paired",
                                                "roofline", "clocks", "small_planners")}
     out["c5_batched"]["workload"] = b["config"]["workload"]
     return out
