@@ -84,18 +84,44 @@ __device__ __forceinline__ bool gwait(uint32_t bar, uint32_t parity, volatile in
   }
 }
 
-__device__ __forceinline__ void act_and_grad(float z, int act, float& h, float& d) {
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// act(z) and act'(z) of a pair z = (z0, z1) in packed FP32x2 arithmetic, one
+// MUFU op per value. SiLU: s = sigmoid(z) = (1 + tanh(z/2)) / 2, act = z s,
+// act' = s (1 + z (1 - s)) = s + act (1 - s); tanh: t = tanh z, act' = 1 - t^2.
+// (tanh.approx.f32: relative error about 2^-11, below the BF16 rounding of
+// the stored values.)
+__device__ __forceinline__ void act_and_grad2(uint64_t z, int act, uint32_t& hp, uint32_t& dp) {
+  using ptx::f2_fma;
+  using ptx::f2_pack;
+  using ptx::f2_unpack;
+  using ptx::tanh_approx;
+  float h0, h1, d0, d1;
   if (act == VOILA_ACT_SILU) {
-    const float sg = __fdividef(1.0f, 1.0f + __expf(-z));
-    h = z * sg;
-    d = sg * (1.0f + z * (1.0f - sg));
+    const uint64_t half = f2_pack(0.5f, 0.5f), nhalf = f2_pack(-0.5f, -0.5f);
+    float a0, a1;
+    f2_unpack(f2_mul(z, half), a0, a1);
+    const uint64_t t = f2_pack(tanh_approx(a0), tanh_approx(a1));
+    const uint64_t s = f2_fma(t, half, half), om = f2_fma(t, nhalf, half);
+    const uint64_t h = f2_mul(z, s);
+    f2_unpack(h, h0, h1);
+    f2_unpack(f2_fma(h, om, s), d0, d1);
   } else if (act == VOILA_ACT_TANH) {
-    h = tanhf(z);
-    d = 1.0f - h * h;
+    float z0, z1;
+    f2_unpack(z, z0, z1);
+    const uint64_t t = f2_pack(tanh_approx(z0), tanh_approx(z1));
+    f2_unpack(t, h0, h1);
+    f2_unpack(f2_fma(t, f2_pack(-h0, -h1), f2_pack(1.0f, 1.0f)), d0, d1);
   } else {
-    h = z;
-    d = 1.0f;
+    f2_unpack(z, h0, h1);
+    d0 = d1 = 1.0f;
   }
+  hp = ptx::pack_bf16x2(h0, h1);
+  dp = ptx::pack_bf16x2(d0, d1);
 }
 
 __device__ __forceinline__ uint32_t bf2(float lo, float hi) { return ptx::pack_bf16x2(lo, hi); }
@@ -265,6 +291,8 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_cons
             an1 = __ldg(src + 1);
           }
           ptx::tmem_wait_ld();
+          ptx::tie8(v);  // no use of v is scheduled before the wait
+          ptx::tie8(v + 8);
           if (cb + 16 >= c_hi) {  // this warp's last read of the accumulator
             ptx::tc_fence_before();
             __syncwarp();
@@ -274,13 +302,14 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_cons
           if (tstore) {
             uint32_t hp[8], dp[8];
             if (p.mode == kGemmFwdHidden) {
+              const float4* b4 = reinterpret_cast<const float4*>(bias_s + cb);
 #pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                float h0, d0, h1, d1;
-                act_and_grad(v[2 * j] + bias_s[cb + 2 * j], p.act, h0, d0);
-                act_and_grad(v[2 * j + 1] + bias_s[cb + 2 * j + 1], p.act, h1, d1);
-                hp[j] = bf2(h0, h1);
-                dp[j] = bf2(d0, d1);
+              for (int j = 0; j < 4; ++j) {
+                const float4 bb = b4[j];
+                act_and_grad2(ptx::f2_add(ptx::f2_pack(v[4 * j], v[4 * j + 1]), ptx::f2_pack(bb.x, bb.y)), p.act,
+                              hp[2 * j], dp[2 * j]);
+                act_and_grad2(ptx::f2_add(ptx::f2_pack(v[4 * j + 2], v[4 * j + 3]), ptx::f2_pack(bb.z, bb.w)), p.act,
+                              hp[2 * j + 1], dp[2 * j + 1]);
               }
             } else {
               const uint32_t ws[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
