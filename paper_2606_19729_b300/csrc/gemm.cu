@@ -314,8 +314,13 @@ __global__ void __launch_bounds__(kGThreads, 1) gemm_tc_kernel(const __grid_cons
             } else {
               const uint32_t ws[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
 #pragma unroll
-              for (int j = 0; j < 8; ++j)
-                hp[j] = bf2(v[2 * j] * __uint_as_float(ws[j] << 16), v[2 * j + 1] * __uint_as_float(ws[j] & 0xffff0000u));
+              for (int j = 0; j < 8; ++j) {
+                float d0, d1;
+                ptx::f2_unpack(f2_mul(ptx::f2_pack(v[2 * j], v[2 * j + 1]),
+                                      ptx::f2_pack(__uint_as_float(ws[j] << 16), __uint_as_float(ws[j] & 0xffff0000u))),
+                               d0, d1);
+                hp[j] = bf2(d0, d1);
+              }
             }
             // the slots are free once the previous batch's stores have read them
             if (lane == 0 && pending) ptx::bulk_wait_read_all();
