@@ -192,6 +192,14 @@ __device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, vola
 constexpr int kItemRing = 4;
 constexpr int kItemTakers = 2 + 2 * (kTcThreads / 32 - 2);
 
+// Static order: cluster c of n takes item j n + c in even rounds j and
+// j n + (n - 1 - c) in odd ones when `serp` is set (a serpentine deal: with the
+// items sorted by decreasing horizon, no cluster takes the largest item of
+// every round), else j n + c.
+__device__ __forceinline__ long long static_item(long long j, long long c, long long n, bool serp) {
+  return j * n + ((serp && (j & 1)) ? n - 1 - c : c);
+}
+
 // bounded_wait with acquire semantics at cluster scope (the phase is completed
 // by release arrivals of the other CTA of the pair as well).
 __device__ __forceinline__ bool bounded_wait_cluster(uint32_t bar, uint32_t parity, volatile int* abort_flag,
@@ -630,6 +638,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
   constexpr bool PROP = MODE == kModePropose;
   static_assert(!PROP || (!WIDE && DS == 8 && DA == 2 && DW == 8), "belief proposal layout");
   static_assert(!QUEUE || MODE == kModeRollout, "the work-item queue serves the rollout");
+  // the static order is dealt serpentine for rollouts (items of uneven cost in
+  // a batched launch); the pair mode's look-ahead assumes the plain order
+  constexpr bool SERP = MODE == kModeRollout;
   // work items of the launch: the observation rows are counted on the device
   long long total_items = p.total_items;
   if constexpr (OBS) {
@@ -712,7 +723,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
            it = QUEUE ? (rank == 0 ? claim_item(item_full, item_empty, item_ring, ++jq, p.queue, total_items,
                                                 abort_flag, p.hdr)
                                    : take_item(item_full, item_empty, item_ring, ++jq, false, abort_flag, p.hdr))
-                      : it + ncl) {
+                      : (SERP ? static_item(++jq, cl, ncl, true) : it + ncl)) {
         const int H = p.pl[item_planner(p, it)].H;
         for (int t = 0; t < H && ok; ++t)
           for (int l = 0; l < p.n_total && ok; ++l)
@@ -768,9 +779,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
         const uint64_t adesc1 = ptx::smem_desc(ptx::smem_u32(Abuf[1]), 1024, ptx::kSwizzle128B);
         const uint64_t bdesc0 = ptx::smem_desc(ring_addr, 1024, ptx::kSwizzle128B);
         long long jq = 0;
-        for (long long it = QUEUE ? take_item(item_full, item_empty, item_ring, jq, false, abort_flag, p.hdr) : cl;
+        for (long long it = QUEUE ? take_item(item_full, item_empty, item_ring, jq, false, abort_flag, p.hdr)
+                                  : cl;
              it >= 0 && it < total_items && ok;
-             it = QUEUE ? take_item(item_full, item_empty, item_ring, ++jq, false, abort_flag, p.hdr) : it + ncl) {
+             it = QUEUE ? take_item(item_full, item_empty, item_ring, ++jq, false, abort_flag, p.hdr)
+                        : (SERP ? static_item(++jq, cl, ncl, true) : it + ncl)) {
           const int H = p.pl[item_planner(p, it)].H;
           for (int t = 0; t < H && ok; ++t)
             for (int l = 0; l < p.n_total && ok; ++l) {
@@ -929,9 +942,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     uint32_t nacc = 0, nacc1 = 0, nalo = 0;
     bool ok = true;
     long long jq = 0;
-    for (long long it = QUEUE ? take_item(item_full, item_empty, item_ring, jq, true, abort_flag, p.hdr) : cl;
+    for (long long it = QUEUE ? take_item(item_full, item_empty, item_ring, jq, true, abort_flag, p.hdr)
+                              : cl;
          it >= 0 && it < total_items && ok;
-         it = QUEUE ? take_item(item_full, item_empty, item_ring, ++jq, true, abort_flag, p.hdr) : it + ncl) {
+         it = QUEUE ? take_item(item_full, item_empty, item_ring, ++jq, true, abort_flag, p.hdr)
+                    : (SERP ? static_item(++jq, cl, ncl, true) : it + ncl)) {
       const int q = item_planner(p, it);
       const long long sp = it - (q ? p.item_end[q - 1] : 0);
       const TcPlanner& PL = p.pl[q];
@@ -1143,9 +1158,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
     uint32_t nacc[2] = {0u, 0u};
     bool ok = true;
     long long jq = 0;
-    for (long long it = QUEUE ? take_item(item_full, item_empty, item_ring, jq, true, abort_flag, p.hdr) : cl;
+    for (long long it = QUEUE ? take_item(item_full, item_empty, item_ring, jq, true, abort_flag, p.hdr)
+                              : cl;
          it >= 0 && it < total_items && ok;
-         it = QUEUE ? take_item(item_full, item_empty, item_ring, ++jq, true, abort_flag, p.hdr) : it + ncl) {
+         it = QUEUE ? take_item(item_full, item_empty, item_ring, ++jq, true, abort_flag, p.hdr)
+                    : (SERP ? static_item(++jq, cl, ncl, true) : it + ncl)) {
       const int pq = item_planner(p, it);
       const long long sp = it - (pq ? p.item_end[pq - 1] : 0);
       const TcPlanner& PL = p.pl[pq];
