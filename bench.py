@@ -787,26 +787,39 @@ def distill_record(args, rank, world, local):
     d = Distiller(teacher, [torch.from_numpy(w) for w in wl.student.W], [torch.from_numpy(b) for b in wl.student.b],
                   wl.student.act, V.BF16, B, wl.T, wl.beta0, wl.beta1, wl.emb_dim, lr=wl.lr)
     S, A, om = (torch.from_numpy(x).float().cuda() for x in (wl.S, wl.A, wl.omega))
+    # each step trains on the batch and samples the teacher targets of the next
+    # batch (here the same synthetic batch) on a second stream meanwhile
+    # (Distiller.step_overlapped; the same results as the plain step)
     losses = torch.empty(args.warmup + args.steps, dtype=torch.float64, device="cuda")
     for i in range(args.warmup):
-        d.step(S, A, om, loss_out=losses[i:i + 1])
+        d.step_overlapped(S, A, om, S, A, om, loss_out=losses[i:i + 1])
+    d.join()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with Clocks(local) as clk:
         t_all0 = torch.cuda.Event(enable_timing=True)
         t_all1 = torch.cuda.Event(enable_timing=True)
         t_all0.record(stream)
-        for i, (e0, e1) in enumerate(ev):
-            e0.record(stream)
-            d.step(S, A, om, loss_out=losses[args.warmup + i:args.warmup + i + 1])
-            e1.record(stream)
+        for i in range(args.steps):
+            d.step_overlapped(S, A, om, S, A, om, loss_out=losses[args.warmup + i:args.warmup + i + 1])
+        d.join()  # the last step's sampler is inside the timed region
         t_all1.record(stream)
         torch.cuda.synchronize()
     sec = max_over_ranks(t_all0.elapsed_time(t_all1) / 1e3, world, torch.device("cuda", local))
     value = aggregate_rate(B * args.steps, world, sec)
     lo = losses.cpu().numpy()
+    # the plain step (sampler, then the student's step, on one stream) beside it
+    pl0 = torch.cuda.Event(enable_timing=True)
+    pl1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        d.step(S, A, om)
+    pl0.record(stream)
+    for _ in range(args.steps):
+        d.step(S, A, om)
+    pl1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = pl0.elapsed_time(pl1) / args.steps
     # the dominant kernel alone: the teacher sampler, same inputs, CUDA events on its
     # stream, back to back for long enough to run under the power cap
     Y = torch.empty(B, wl.d_x, device="cuda")
@@ -824,16 +837,27 @@ def distill_record(args, rank, world, local):
     achieved = f_teacher * B / ddim_s / 1e12
     peaks = load_peaks()
     clocks = clk.summary()
-    # end to end: inputs copied from pinned host memory each step, the loss read back
+    # end to end: each step copies the next batch's inputs from pinned host memory
+    # into one of two device buffers and reads the loss back (the training
+    # stream synchronised; the sampler of the next batch keeps running)
     hS, hA, hO = (x.cpu().pin_memory() for x in (S, A, om))
     hl = torch.empty(1, dtype=torch.float64).pin_memory()
+    bufs = [tuple(torch.empty_like(x) for x in (S, A, om)) for _ in range(2)]
+    d.join()
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_steps = max(1, args.steps)
-    for _ in range(e2e_steps):
-        dS, dA, dO = (x.to("cuda", non_blocking=True) for x in (hS, hA, hO))
-        l = d.step(dS, dA, dO)
+    for x, h in zip(bufs[0], (hS, hA, hO)):
+        x.copy_(h, non_blocking=True)
+    for i in range(e2e_steps):
+        cur_b, nxt_b = bufs[i % 2], bufs[(i + 1) % 2]
+        for x, h in zip(nxt_b, (hS, hA, hO)):
+            x.copy_(h, non_blocking=True)
+        l = d.step_overlapped(*cur_b, *nxt_b)
         hl.copy_(l, non_blocking=True)
-        torch.cuda.synchronize()
+        torch.cuda.current_stream().synchronize()
+    d.join()
+    torch.cuda.synchronize()
     e2e_sec = max_over_ranks((time.perf_counter() - t0), world, torch.device("cuda", local))
     line = {"metric": "distillation samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
@@ -843,8 +867,13 @@ def distill_record(args, rank, world, local):
                                    f"(BF16, tensor cores), {wl.T} DDIM steps, linear beta 1e-4..0.02; student "
                                    "18x256x256x256x8 SiLU, BF16 forward copy (FP32 arithmetic), FP32 master, Adam",
                        "l2": "inputs resident; the step's working set (teacher activations, saved "
-                             "pre-activations, gradients) exceeds L2"},
+                             "pre-activations, gradients) exceeds L2",
+                       "launch": "the teacher sampler of the next batch on a second, high-priority stream "
+                                 "while the student trains (its GEMMs one CTA per tile); every step is one "
+                                 "sampler pass and one student step"},
             "loss": {"first": float(lo[0]), "last": float(lo[-1])},
+            "plain_step": {"ms_per_step": plain_ms, "value": aggregate_rate(B, world, plain_ms / 1e3),
+                           "note": "sampler, then the student's step, on one stream"},
             "teacher_ms": 1e3 * ddim_s,
             "roofline": dict(tensor_roofline(achieved, peaks, clocks, "bf16"), traffic=None,
                              kernel="rollout_tc_kernel (DDIM sampler mode)",
@@ -1166,8 +1195,9 @@ def config_records(args, rank, world, local, fp8_peak):
     a.steps, a.warmup = 10, 3
     d = distill_record(a, rank, world, local)
     out["c4_distill"] = {k: d.get(k) for k in ("metric", "value", "unit", "ms_per_step", "teacher_ms", "roofline",
-                                               "loss", "e2e", "cpu_baseline", "clocks")}
+                                               "loss", "e2e", "cpu_baseline", "clocks", "plain_step")}
     out["c4_distill"]["workload"] = d["config"]["workload"]
+    out["c4_distill"]["launch"] = d["config"]["launch"]
     a = copy.copy(args)
     a.steps, a.warmup = 4, 1
     b = batched_record(a, rank, world, local)

@@ -509,6 +509,42 @@ voila_status voila_distill_step(const voila_mlp* teacher, const voila_mlp* stude
                                 int32_t d_a, int32_t d_x, double* loss_out, float* grad_out,
                                 void* workspace, size_t ws_bytes, voila_stream_t stream);
 
+/* voila_distill_train_step flags. SPREAD: the tensor-core GEMMs launch one CTA
+ * per 128-row tile instead of one persistent CTA per SM, so that they start on
+ * the SMs that other work running concurrently on the device (the teacher
+ * sampler of the next batch) releases; without it they wait for whole SMs.
+ * Results do not depend on the flag. */
+#define VOILA_TRAIN_SPREAD 1
+
+/* Workspace of voila_distill_train_step for B rows and output width d_x, in
+ * bytes. */
+voila_status voila_distill_train_step_workspace_size(const voila_mlp* student, int32_t B, int32_t d_x,
+                                                     size_t* bytes);
+
+/*
+ * Steps 2-5 of voila_distill_step (the student's forward, the loss, the
+ * gradients and the Adam update, Eq. 3) with the teacher targets given:
+ *   s_hat  device float [B][d_x], the targets voila_ddim_sample wrote for the
+ *          same S, A, omega (read only, stream-ordered: the caller orders the
+ *          sampler before this call).
+ * The other arguments are those of voila_distill_step; flags is 0 or
+ * VOILA_TRAIN_SPREAD. The workspace (1024-byte aligned,
+ * voila_distill_train_step_workspace_size bytes) is this call's alone, so a
+ * sampler run for the next batch on another stream, with its own workspace,
+ * can overlap it; its first bytes are the status word of the tensor-core
+ * kernels (zeroed by the call; voila_workspace_status). A voila_ddim_sample
+ * followed by this call gives exactly the results of voila_distill_step.
+ * Errors: VOILA_ERR_ARG (null pointer, negative B, unknown flags),
+ * VOILA_ERR_SHAPE (student widths), VOILA_ERR_UNSUPPORTED (precision),
+ * VOILA_ERR_WORKSPACE, VOILA_ERR_CUDA.
+ */
+voila_status voila_distill_train_step(const voila_mlp* student, float* master, float* adam_m,
+                                      float* adam_v, const voila_adam* opt, const float* S,
+                                      const float* A, const float* omega, const float* s_hat,
+                                      int32_t B, int32_t d_s, int32_t d_a, int32_t d_x,
+                                      int32_t flags, double* loss_out, float* grad_out,
+                                      void* workspace, size_t ws_bytes, voila_stream_t stream);
+
 /*
  * Writes an MLP's weights from a flat FP32 vector [W_0, b_0, W_1, b_1, ...]
  * (W_l [dims[l+1]][dims[l]] row-major): W in the MLP's precision (BF16 by

@@ -465,7 +465,8 @@ cudaError_t tc_gemm(const TcGemm& g, cudaStream_t s) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const long long units = (long long)((g.M + 127) / 128) * splits;
-  const int grid = (int)(units < nsm ? units : nsm);  // persistent: one CTA per SM
+  // persistent: one CTA per SM; spread: one CTA per unit
+  const int grid = (int)(g.spread || units < nsm ? units : nsm);
   gemm_tc_kernel<<<grid, kGThreads, smem, s>>>(p);
   return cudaGetLastError();
 }

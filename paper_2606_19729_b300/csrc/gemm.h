@@ -40,6 +40,8 @@ struct TcGemm {
   int ldY, n_real;
   float* P;
   WsHeader* hdr;
+  bool spread;  // one CTA per unit instead of one persistent CTA per SM: the
+                // units start on SMs as other work on the device releases them
 };
 
 size_t tc_gemm_smem_bytes();

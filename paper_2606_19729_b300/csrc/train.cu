@@ -485,18 +485,19 @@ size_t ddim_ws_bytes(const voila_mlp* teacher, int T) {
 // teacher-sampler workspace, s_hat [B][d_x], X [B][din], Y [B][d_x],
 // dY [B][d_x], saved [B][hidden], grads [n_params], loss partials
 // [kLossBlocks] (FP64), scratch (bwd).
-struct DistillLayout {
-  size_t ddim, s_hat, x, y, dy, saved, grads, part, scratch, total;
+// The student's part of a distillation step (forward, loss, backward, Adam),
+// offsets from the start of its region; the first kDdimHeader bytes are a
+// status header when the region is a workspace of its own.
+struct TrainRegion {
+  size_t x, y, dy, saved, grads, part, scratch, total;
   bool tc;  // BF16 student: the training forward/backward run on the tensor cores (scratch)
 };
 
-DistillLayout distill_layout(const voila_mlp* teacher, const voila_mlp* st, int B, int d_x, int T) {
-  DistillLayout L;
+TrainRegion train_region(const voila_mlp* st, int B, int d_x) {
+  TrainRegion L;
   long long off[2 * VOILA_MAX_LAYERS + 1];
   const long long np = param_layout(st, off);
-  size_t o = 0;
-  L.ddim = o;  o += align256(ddim_ws_bytes(teacher, T));
-  L.s_hat = o; o += align256((size_t)B * d_x * 4);
+  size_t o = kDdimHeader;
   L.x = o;     o += align256((size_t)B * st->dims[0] * 4);
   L.y = o;     o += align256((size_t)B * d_x * 4);
   L.dy = o;    o += align256((size_t)B * d_x * 4);
@@ -509,10 +510,95 @@ DistillLayout distill_layout(const voila_mlp* teacher, const voila_mlp* st, int 
   L.total = o;
   return L;
 }
+
+struct DistillLayout {
+  size_t ddim, s_hat, train, total;  // sampler workspace, targets, the student's region (1024-aligned)
+  TrainRegion t;
+};
+
+DistillLayout distill_layout(const voila_mlp* teacher, const voila_mlp* st, int B, int d_x, int T) {
+  DistillLayout L;
+  size_t o = 0;
+  L.ddim = o;  o += align256(ddim_ws_bytes(teacher, T));
+  L.s_hat = o; o += align256((size_t)B * d_x * 4);
+  o = (o + 1023) & ~(size_t)1023;
+  L.train = o;
+  L.t = train_region(st, B, d_x);
+  L.total = o + L.t.total;
+  return L;
+}
+
+bool student_ok(const voila_mlp* student, int d_s, int d_a, int d_x, voila_status* err) {
+  if (student->n_layers < 1 || student->n_layers > VOILA_MAX_LAYERS) return *err = VOILA_ERR_ARG, false;
+  if (student->prec != VOILA_FP32 && student->prec != VOILA_BF16) return *err = VOILA_ERR_UNSUPPORTED, false;
+  if (student->dims[0] != d_s + d_a + d_x || student->dims[student->n_layers] != d_x)
+    return *err = VOILA_ERR_SHAPE, false;
+  for (int l = 0; l < student->n_layers; ++l)
+    if (!student->W[l] || !student->b[l]) return *err = VOILA_ERR_ARG, false;
+  return true;
+}
+
+// Steps 2-5 of a distillation step with the targets s_hat given; `base` is the
+// student's region (TrainRegion offsets), `hdr` the status word the
+// tensor-core kernels write.
+voila_status distill_train(const voila_mlp* student, float* master, float* adam_m, float* adam_v,
+                           const voila_adam* opt, const float* S, const float* A, const float* omega,
+                           const float* s_hat, int32_t B, int32_t d_s, int32_t d_a, int32_t d_x, bool spread,
+                           double* loss_out, float* grad_out, char* base, const TrainRegion& L, WsHeader* hdr,
+                           cudaStream_t s);
 }  // namespace
 }  // namespace voila
 
 using namespace voila;
+namespace voila {
+namespace {
+voila_status distill_train(const voila_mlp* student, float* master, float* adam_m, float* adam_v,
+                           const voila_adam* opt, const float* S, const float* A, const float* omega,
+                           const float* s_hat, int32_t B, int32_t d_s, int32_t d_a, int32_t d_x, bool spread,
+                           double* loss_out, float* grad_out, char* base, const TrainRegion& L, WsHeader* hdr,
+                           cudaStream_t s) {
+  float* X = (float*)(base + L.x);
+  float* Y = (float*)(base + L.y);
+  float* dY = (float*)(base + L.dy);
+  float* saved = (float*)(base + L.saved);
+  float* grads = grad_out ? grad_out : (float*)(base + L.grads);
+  double* part = (double*)(base + L.part);
+  float* scratch = (float*)(base + L.scratch);
+  const size_t scratch_bytes = L.total - L.scratch;
+  const voila_stream_t stream = (voila_stream_t)s;
+  // 2. student forward f_T(s, a, omega), pre-activations saved
+  concat_input_kernel<<<grid_for((long long)B * student->dims[0], 256), 256, 0, s>>>(S, A, omega, B, d_s, d_a,
+                                                                                     d_x, X);
+  if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
+  voila_status st;
+  if (L.tc) st = tc_train_forward(student, X, B, Y, scratch, hdr, s, spread);
+  else st = voila_generator_fwd_train(student, X, B, Y, saved, scratch, scratch_bytes, stream);
+  if (st != VOILA_OK) return st;
+  // 3. loss (1/B) sum ||f - s_hat||^2 and dL/dY = 2 (f - s_hat) / B
+  mse_kernel<<<kLossBlocks, 256, 0, s>>>(Y, s_hat, (long long)B * d_x, 2.0f / (float)B, dY, part);
+  loss_final_kernel<<<1, 512, 0, s>>>(part, kLossBlocks, 1.0 / (double)B, loss_out);
+  if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
+  // 4. gradients into the flat layout of `master`
+  long long off[2 * VOILA_MAX_LAYERS + 1];
+  const long long np = param_layout(student, off);
+  float* dW[VOILA_MAX_LAYERS];
+  float* db[VOILA_MAX_LAYERS];
+  for (int l = 0; l < student->n_layers; ++l) {
+    dW[l] = grads + off[2 * l];
+    db[l] = grads + off[2 * l + 1];
+  }
+  if (L.tc) st = tc_train_backward(student, dY, B, grads, scratch, hdr, s, spread);
+  else st = voila_generator_bwd(student, X, saved, dY, B, nullptr, dW, db, scratch, scratch_bytes, stream);
+  if (st != VOILA_OK) return st;
+  // 5. Adam on the FP32 master weights, then the forward copy
+  st = voila_adam_step(master, grads, adam_m, adam_v, np, opt->lr, opt->beta1, opt->beta2, opt->eps, opt->step,
+                       stream);
+  if (st != VOILA_OK) return st;
+  return voila_mlp_load_flat(student, master, stream);
+}
+}  // namespace
+}  // namespace voila
+
 
 extern "C" {
 
@@ -674,59 +760,49 @@ voila_status voila_distill_step(const voila_mlp* teacher, const voila_mlp* stude
                                 size_t ws_bytes, voila_stream_t stream) {
   if (!teacher || !student || !ddim || !opt || !master || !adam_m || !adam_v || !loss_out || B < 0)
     return VOILA_ERR_ARG;
-  if (student->n_layers < 1 || student->n_layers > VOILA_MAX_LAYERS) return VOILA_ERR_ARG;
-  if (student->prec != VOILA_FP32 && student->prec != VOILA_BF16) return VOILA_ERR_UNSUPPORTED;
-  if (student->dims[0] != d_s + d_a + d_x || student->dims[student->n_layers] != d_x) return VOILA_ERR_SHAPE;
-  for (int l = 0; l < student->n_layers; ++l)
-    if (!student->W[l] || !student->b[l]) return VOILA_ERR_ARG;
+  voila_status err = VOILA_OK;
+  if (!student_ok(student, d_s, d_a, d_x, &err)) return err;
   if (ddim->T < 1 || ddim->T > 64) return VOILA_ERR_ARG;
   if (B == 0) return VOILA_OK;
   const DistillLayout L = distill_layout(teacher, student, B, d_x, ddim->T);
   if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 1023)) return VOILA_ERR_WORKSPACE;
-  cudaStream_t s = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   float* s_hat = (float*)(ws + L.s_hat);
-  float* X = (float*)(ws + L.x);
-  float* Y = (float*)(ws + L.y);
-  float* dY = (float*)(ws + L.dy);
-  float* saved = (float*)(ws + L.saved);
-  float* grads = grad_out ? grad_out : (float*)(ws + L.grads);
-  double* part = (double*)(ws + L.part);
-  float* scratch = (float*)(ws + L.scratch);
-  const size_t scratch_bytes = L.total - L.scratch;
-
   // 1. teacher targets s_hat' (the ODE sampler of Eq. 3)
   voila_status st = voila_ddim_sample(teacher, S, A, omega, B, d_s, d_a, d_x, ddim->T, ddim->beta0, ddim->beta1,
                                       ddim->emb_dim, s_hat, ws + L.ddim, L.s_hat - L.ddim, stream);
   if (st != VOILA_OK) return st;
-  // 2. student forward f_T(s, a, omega), pre-activations saved
-  concat_input_kernel<<<grid_for((long long)B * student->dims[0], 256), 256, 0, s>>>(S, A, omega, B, d_s, d_a,
-                                                                                     d_x, X);
-  if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
-  if (L.tc) st = tc_train_forward(student, X, B, Y, scratch, (WsHeader*)ws, s);
-  else st = voila_generator_fwd_train(student, X, B, Y, saved, scratch, scratch_bytes, stream);
-  if (st != VOILA_OK) return st;
-  // 3. loss (1/B) sum ||f - s_hat||^2 and dL/dY = 2 (f - s_hat) / B
-  mse_kernel<<<kLossBlocks, 256, 0, s>>>(Y, s_hat, (long long)B * d_x, 2.0f / (float)B, dY, part);
-  loss_final_kernel<<<1, 512, 0, s>>>(part, kLossBlocks, 1.0 / (double)B, loss_out);
-  if (cudaGetLastError() != cudaSuccess) return VOILA_ERR_CUDA;
-  // 4. gradients into the flat layout of `master`
-  long long off[2 * VOILA_MAX_LAYERS + 1];
-  const long long np = param_layout(student, off);
-  float* dW[VOILA_MAX_LAYERS];
-  float* db[VOILA_MAX_LAYERS];
-  for (int l = 0; l < student->n_layers; ++l) {
-    dW[l] = grads + off[2 * l];
-    db[l] = grads + off[2 * l + 1];
-  }
-  if (L.tc) st = tc_train_backward(student, dY, B, grads, scratch, (WsHeader*)ws, s);
-  else st = voila_generator_bwd(student, X, saved, dY, B, nullptr, dW, db, scratch, scratch_bytes, stream);
-  if (st != VOILA_OK) return st;
-  // 5. Adam on the FP32 master weights, then the forward copy
-  st = voila_adam_step(master, grads, adam_m, adam_v, np, opt->lr, opt->beta1, opt->beta2, opt->eps, opt->step,
-                       stream);
-  if (st != VOILA_OK) return st;
-  return voila_mlp_load_flat(student, master, stream);
+  // 2-5. the student's step; its kernels report into the sampler's status word
+  return distill_train(student, master, adam_m, adam_v, opt, S, A, omega, s_hat, B, d_s, d_a, d_x, false,
+                       loss_out, grad_out, ws + L.train, L.t, (WsHeader*)ws, (cudaStream_t)stream);
+}
+
+voila_status voila_distill_train_step_workspace_size(const voila_mlp* student, int32_t B, int32_t d_x,
+                                                     size_t* bytes) {
+  if (!student || !bytes || student->n_layers < 1 || student->n_layers > VOILA_MAX_LAYERS || B < 0 || d_x < 1)
+    return VOILA_ERR_ARG;
+  *bytes = train_region(student, B, d_x).total;
+  return VOILA_OK;
+}
+
+voila_status voila_distill_train_step(const voila_mlp* student, float* master, float* adam_m, float* adam_v,
+                                      const voila_adam* opt, const float* S, const float* A, const float* omega,
+                                      const float* s_hat, int32_t B, int32_t d_s, int32_t d_a, int32_t d_x,
+                                      int32_t flags, double* loss_out, float* grad_out, void* workspace,
+                                      size_t ws_bytes, voila_stream_t stream) {
+  if (!student || !opt || !master || !adam_m || !adam_v || !loss_out || B < 0 || (flags & ~VOILA_TRAIN_SPREAD))
+    return VOILA_ERR_ARG;
+  voila_status err = VOILA_OK;
+  if (!student_ok(student, d_s, d_a, d_x, &err)) return err;
+  if (B == 0) return VOILA_OK;
+  if (!S || !A || !omega || !s_hat) return VOILA_ERR_ARG;
+  const TrainRegion L = train_region(student, B, d_x);
+  if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 1023)) return VOILA_ERR_WORKSPACE;
+  WsHeader* hdr = (WsHeader*)workspace;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s) != cudaSuccess) return VOILA_ERR_CUDA;
+  return distill_train(student, master, adam_m, adam_v, opt, S, A, omega, s_hat, B, d_s, d_a, d_x,
+                       (flags & VOILA_TRAIN_SPREAD) != 0, loss_out, grad_out, (char*)workspace, L, hdr, s);
 }
 
 voila_status voila_mlp_load_flat(const voila_mlp* mlp, const float* flat, voila_stream_t stream) {

@@ -227,7 +227,7 @@ bool tc_train_supported(const voila_mlp* m) {
 size_t tc_train_bytes(const voila_mlp* m, long long M) { return train_layout(m, M).total; }
 
 voila_status tc_train_forward(const voila_mlp* m, const float* X, long long M, float* Y, void* scratch,
-                              WsHeader* hdr, cudaStream_t s) {
+                              WsHeader* hdr, cudaStream_t s, bool spread) {
   if (!tc_train_supported(m) || ((uintptr_t)scratch & 1023)) return VOILA_ERR_UNSUPPORTED;
   const TrainLayout T = train_layout(m, M);
   const int L = T.L;
@@ -256,6 +256,7 @@ voila_status tc_train_forward(const voila_mlp* m, const float* X, long long M, f
     g.bias = m->b[l - 1];
     g.act = m->act;
     g.hdr = hdr;
+    g.spread = spread;
     if (l < L) {
       g.B = l == 1 ? at<bf>(scratch, T.w1p) : (const bf*)m->W[l - 1];
       g.ldb = g.lda;
@@ -280,7 +281,7 @@ voila_status tc_train_forward(const voila_mlp* m, const float* X, long long M, f
 }
 
 voila_status tc_train_backward(const voila_mlp* m, const float* dY, long long M, float* grads, void* scratch,
-                               WsHeader* hdr, cudaStream_t s) {
+                               WsHeader* hdr, cudaStream_t s, bool spread) {
   if (!tc_train_supported(m) || ((uintptr_t)scratch & 1023)) return VOILA_ERR_UNSUPPORTED;
   const TrainLayout T = train_layout(m, M);
   const int L = T.L;
@@ -317,6 +318,7 @@ voila_status tc_train_backward(const voila_mlp* m, const float* dY, long long M,
     g.HT = at<bf>(scratch, T.ddt[l - 1]);
     g.ldT = (int)T.ldT;
     g.hdr = hdr;
+    g.spread = spread;
     if (tc_gemm(g, s) != cudaSuccess) return VOILA_ERR_CUDA;
   }
   // weight gradients: split-K over the batch, partials summed in split order
@@ -344,6 +346,7 @@ voila_status tc_train_backward(const voila_mlp* m, const float* dY, long long M,
     g.mode = kGemmPartial;
     g.P = part;
     g.hdr = hdr;
+    g.spread = spread;
     if (tc_gemm(g, s) != cudaSuccess) return VOILA_ERR_CUDA;
     reduce_partials_kernel<<<grid_of((long long)T.d[l] * T.d[l - 1]), 256, 0, s>>>(
         part, splits, Mg, Ng, T.d[l], T.d[l - 1], grads + goff[l][0]);

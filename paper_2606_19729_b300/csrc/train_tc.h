@@ -17,11 +17,12 @@ bool tc_train_supported(const voila_mlp* m);
 // deltas, transposes and split-K partials.
 size_t tc_train_bytes(const voila_mlp* m, long long M);
 // Y [M][d_L] FP32 = mlp(X), X [M][d_0] FP32; keeps what the backward needs in scratch.
+// spread: the GEMMs launch one CTA per 128-row unit (see TcGemm::spread).
 voila_status tc_train_forward(const voila_mlp* m, const float* X, long long M, float* Y, void* scratch,
-                              WsHeader* hdr, cudaStream_t s);
+                              WsHeader* hdr, cudaStream_t s, bool spread = false);
 // grads (flat [W_0, b_0, W_1, b_1, ...], FP32) of the loss with dL/dY = dY [M][d_L]
 // after tc_train_forward on the same scratch.
 voila_status tc_train_backward(const voila_mlp* m, const float* dY, long long M, float* grads, void* scratch,
-                               WsHeader* hdr, cudaStream_t s);
+                               WsHeader* hdr, cudaStream_t s, bool spread = false);
 
 }  // namespace voila

@@ -114,3 +114,84 @@ class Distiller:
         V.voila_distill_step(self.teacher, self.student, self.ddim, self.master, self.m, self.v, opt, S, A, omega,
                              out, grad_out, self.ws, stream)
         return out
+
+    # ---- overlapped steps --------------------------------------------------
+    # The teacher does not depend on the student, so the targets of the next
+    # batch can be sampled while the student trains on the current one. The
+    # sampler runs on a high-priority stream and takes every SM first; the
+    # student's kernels (their GEMMs launched one CTA per tile) fill the SMs
+    # the sampler's last round of work items leaves idle. Two target buffers
+    # alternate; events order each sampler after the training that last read
+    # its buffer, and each training after the sampler that filled its buffer.
+
+    def _overlap_state(self):
+        if getattr(self, "_ov", None) is None:
+            T = self.ddim.T
+            self._ov = {
+                "stream": torch.cuda.Stream(priority=-100),
+                "targets": [torch.empty(self.B, self.d_x, device="cuda") for _ in range(2)],
+                "ddim_ws": V.alloc_workspace(V.voila_ddim_sample_workspace_size(self.teacher, T)),
+                "train_ws": V.alloc_workspace(V.voila_distill_train_step_workspace_size(self.student, self.B,
+                                                                                        self.d_x)),
+                "sampled": [torch.cuda.Event(), torch.cuda.Event()],
+                "trained": [torch.cuda.Event(), torch.cuda.Event()],
+                "used": [False, False],  # the slot's buffer has been read by a training
+                "pending": None,         # (slot, key) of targets sampled for a batch not yet trained on
+                "slot": 0,
+            }
+        return self._ov
+
+    @staticmethod
+    def _key(S, A, omega):
+        return tuple((t.data_ptr(), tuple(t.shape)) for t in (S, A, omega))
+
+    def _sample(self, ov, slot, S, A, omega):
+        st = ov["stream"]
+        if ov["used"][slot]:
+            st.wait_event(ov["trained"][slot])
+        V.voila_ddim_sample(self.teacher, S, A, omega, self.ddim.T, self.ddim.beta0, self.ddim.beta1,
+                            self.ddim.emb_dim, ov["targets"][slot], ov["ddim_ws"], stream=st)
+        ov["sampled"][slot].record(st)
+
+    def step_overlapped(self, S: torch.Tensor, A: torch.Tensor, omega: torch.Tensor,
+                        S_next: Optional[torch.Tensor] = None, A_next: Optional[torch.Tensor] = None,
+                        omega_next: Optional[torch.Tensor] = None, grad_out: Optional[torch.Tensor] = None,
+                        loss_out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """One step on (S, A, omega), the same results as `step`, with the
+        teacher targets of (S_next, A_next, omega_next), when given, sampled
+        meanwhile for the following call. Runs on the current stream (the
+        training) and an internal high-priority stream (the sampler); the
+        returned loss is ordered on the current stream."""
+        if omega.shape[0] > self.B:
+            raise ValueError("batch larger than the workspace was sized for")
+        ov = self._overlap_state()
+        cur = torch.cuda.current_stream()
+        key = self._key(S, A, omega)
+        if ov["pending"] is not None and ov["pending"][1] == key:
+            slot = ov["pending"][0]
+        else:  # nothing sampled for this batch yet
+            slot = ov["slot"]
+            ov["stream"].wait_stream(cur)
+            self._sample(ov, slot, S, A, omega)
+        ov["pending"] = None
+        if S_next is not None:
+            nxt = 1 - slot
+            ov["stream"].wait_stream(cur)  # the next batch's inputs as the caller wrote them
+            self._sample(ov, nxt, S_next, A_next, omega_next)
+            ov["pending"] = (nxt, self._key(S_next, A_next, omega_next))
+            ov["slot"] = slot
+        self.t += 1
+        opt = V.voila_adam(self.lr, self.betas[0], self.betas[1], self.eps, self.t)
+        out = self.loss if loss_out is None else loss_out
+        cur.wait_event(ov["sampled"][slot])
+        V.voila_distill_train_step(self.student, self.master, self.m, self.v, opt, S, A, omega, ov["targets"][slot],
+                                   V.TRAIN_SPREAD, out, grad_out, ov["train_ws"], stream=cur)
+        ov["trained"][slot].record(cur)
+        ov["used"][slot] = True
+        return out
+
+    def join(self):
+        """Orders the current stream after every overlapped sampler issued so far."""
+        ov = getattr(self, "_ov", None)
+        if ov is not None:
+            torch.cuda.current_stream().wait_stream(ov["stream"])

@@ -114,6 +114,10 @@ _lib_distill_ws = _sig("voila_distill_step_workspace_size", c_int32, POINTER(voi
                        c_int32, c_int32, POINTER(c_size_t))
 _lib_distill = _sig("voila_distill_step", c_int32, POINTER(voila_mlp), POINTER(voila_mlp), POINTER(voila_ddim), _P, _P,
                     _P, POINTER(voila_adam), _P, _P, _P, c_int32, c_int32, c_int32, c_int32, _P, _P, _P, c_size_t, _P)
+_lib_dtrain_ws = _sig("voila_distill_train_step_workspace_size", c_int32, POINTER(voila_mlp), c_int32, c_int32,
+                      POINTER(c_size_t))
+_lib_dtrain = _sig("voila_distill_train_step", c_int32, POINTER(voila_mlp), _P, _P, _P, POINTER(voila_adam), _P, _P,
+                   _P, _P, c_int32, c_int32, c_int32, c_int32, c_int32, _P, _P, _P, c_size_t, _P)
 _lib_load_flat = _sig("voila_mlp_load_flat", c_int32, POINTER(voila_mlp), _P, _P)
 _lib_backup = _sig("voila_preference_backup", c_int32, _P, _P, c_int32, c_double, _P, _P, _P)
 _lib_nce_ws = _sig("voila_infonce_workspace_size", c_int32, POINTER(voila_mlp), c_int32, POINTER(c_size_t))
@@ -465,6 +469,29 @@ def voila_distill_step(teacher: DeviceMLP, student: DeviceMLP, ddim: voila_ddim,
                         _ptr(omega, torch.float32), B, S.shape[1], A.shape[1], d_x, _ptr(loss_out, torch.float64),
                         _ptr(grad_out, torch.float32), _ptr(workspace), workspace.numel(), _stream(stream)),
            "voila_distill_step")
+
+
+TRAIN_SPREAD = 1  # VOILA_TRAIN_SPREAD
+
+
+def voila_distill_train_step_workspace_size(student: DeviceMLP, B: int, d_x: int) -> int:
+    n = c_size_t(0)
+    _check(_lib_dtrain_ws(ctypes.byref(student.desc), B, d_x, ctypes.byref(n)),
+           "voila_distill_train_step_workspace_size")
+    return n.value
+
+
+def voila_distill_train_step(student: DeviceMLP, master: torch.Tensor, adam_m: torch.Tensor, adam_v: torch.Tensor,
+                             opt: voila_adam, S: torch.Tensor, A: torch.Tensor, omega: torch.Tensor,
+                             s_hat: torch.Tensor, flags: int, loss_out: torch.Tensor,
+                             grad_out: Optional[torch.Tensor], workspace: torch.Tensor, stream=None):
+    B, d_x = omega.shape
+    _check(_lib_dtrain(ctypes.byref(student.desc), _ptr(master, torch.float32), _ptr(adam_m, torch.float32),
+                       _ptr(adam_v, torch.float32), ctypes.byref(opt), _ptr(S, torch.float32),
+                       _ptr(A, torch.float32), _ptr(omega, torch.float32), _ptr(s_hat, torch.float32), B,
+                       S.shape[1], A.shape[1], d_x, flags, _ptr(loss_out, torch.float64),
+                       _ptr(grad_out, torch.float32), _ptr(workspace), workspace.numel(), _stream(stream)),
+           "voila_distill_train_step")
 
 
 def voila_mlp_load_flat(mlp: DeviceMLP, flat: torch.Tensor, stream=None):

@@ -315,3 +315,44 @@ def test_autograd_function_matches_oracle(V):
     for l in range(len(gW)):
         assert rel_err(params[2 * l].grad.cpu().numpy(), gW[l]) < TOL
         assert rel_err(params[2 * l + 1].grad.cpu().numpy(), gb[l]) < TOL
+
+
+@pytest.mark.parametrize("prec", [WL.PREC_BF16, WL.PREC_FP32])
+def test_overlapped_steps_equal_plain_steps(V, prec):
+    # the sampler of the next batch on its own stream while the student trains
+    # (tensor-core GEMMs spread one CTA per tile): the same losses, gradients
+    # and weights, bit for bit, as the plain steps; four batches, then one
+    # batch again without a look-ahead
+    from paper_2606_19729_b300.distill import Distiller
+    B, nb = 1000, 4
+    wl = WL.distill(B=B * nb, teacher_prec=WL.PREC_BF16)
+    teacher = V.DeviceMLP.from_spec(wl.teacher)
+    S, A, om = cuda(wl.S), cuda(wl.A), cuda(wl.omega)
+    batches = [(S[i * B:(i + 1) * B], A[i * B:(i + 1) * B], om[i * B:(i + 1) * B]) for i in range(nb)]
+    batches.append(batches[1])
+
+    def make():
+        return Distiller(teacher, [torch.from_numpy(w) for w in wl.student.W],
+                         [torch.from_numpy(b) for b in wl.student.b], wl.student.act, prec, B, wl.T, wl.beta0,
+                         wl.beta1, wl.emb_dim, lr=wl.lr)
+
+    plain, ovl = make(), make()
+    n = len(batches)
+    lp = torch.empty(n, dtype=torch.float64, device="cuda")
+    lo = torch.empty(n, dtype=torch.float64, device="cuda")
+    gp = [torch.empty_like(plain.master) for _ in range(n)]
+    go = [torch.empty_like(plain.master) for _ in range(n)]
+    for i, b in enumerate(batches):
+        plain.step(*b, loss_out=lp[i:i + 1], grad_out=gp[i])
+    for i, b in enumerate(batches):
+        nxt = batches[i + 1] if i + 1 < nb else (None, None, None)
+        ovl.step_overlapped(*b, *nxt, loss_out=lo[i:i + 1], grad_out=go[i])
+    ovl.join()
+    torch.cuda.synchronize()
+    assert V.workspace_status(ovl._ov["train_ws"]) == V.OK
+    assert torch.equal(lp, lo)
+    for a, b in zip(gp, go):
+        assert torch.equal(a, b)
+    assert torch.equal(plain.master, ovl.master)
+    for wa, wb in zip(plain.student.W, ovl.student.W):
+        assert torch.equal(wa, wb)
