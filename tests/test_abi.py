@@ -63,3 +63,32 @@ def test_workspace_sizes_are_host_computable():
     lik = V.gaussian_likelihood(0.5)
     assert V._lib_belief_ws(ctypes.byref(m), ctypes.byref(lik), 256, ctypes.byref(n)) == V.OK
     assert n.value >= 256 * (4 * 4 + 16)
+
+
+def test_distill_train_step_host_validation():
+    # the student's half of a distillation step: workspace size computable on the
+    # host, unknown flags and missing pointers refused before any device work
+    from paper_2606_19729_b300 import voila as V
+    m = V.voila_mlp()
+    m.n_layers = 4
+    for i, d in enumerate([18, 256, 256, 256, 8]):
+        m.dims[i] = d
+    m.act, m.prec = V.ACT_SILU, V.BF16
+    for l in range(4):
+        m.W[l] = 16  # never dereferenced on the host
+        m.b[l] = 16
+    n = ctypes.c_size_t(0)
+    assert V._lib_dtrain_ws(ctypes.byref(m), 65536, 8, ctypes.byref(n)) == V.OK
+    small = n.value
+    assert V._lib_dtrain_ws(ctypes.byref(m), 131072, 8, ctypes.byref(n)) == V.OK and n.value > small
+    assert V._lib_dtrain_ws(ctypes.byref(m), -1, 8, ctypes.byref(n)) == V.ERR_ARG
+    opt = V.voila_adam(1e-3, 0.9, 0.999, 1e-8, 1)
+    p = ctypes.c_void_p(16)
+    args = [ctypes.byref(m), p, p, p, ctypes.byref(opt), p, p, p, p, 64, 8, 2, 8]
+    # unknown flag bits
+    assert V._lib_dtrain(*args, 2, p, None, p, small, None) == V.ERR_ARG
+    # no loss output
+    assert V._lib_dtrain(*args, V.TRAIN_SPREAD, None, None, p, small, None) == V.ERR_ARG
+    # widths that do not match the student
+    bad = [ctypes.byref(m), p, p, p, ctypes.byref(opt), p, p, p, p, 64, 8, 3, 8]
+    assert V._lib_dtrain(*bad, 0, p, None, p, small, None) == V.ERR_SHAPE
