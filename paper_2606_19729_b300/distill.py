@@ -147,6 +147,8 @@ class Distiller:
 
     def _sample(self, ov, slot, S, A, omega):
         st = ov["stream"]
+        for t in (S, A, omega):  # the caching allocator keeps them until the sampler has read them
+            t.record_stream(st)
         if ov["used"][slot]:
             st.wait_event(ov["trained"][slot])
         V.voila_ddim_sample(self.teacher, S, A, omega, self.ddim.T, self.ddim.beta0, self.ddim.beta1,
