@@ -1199,7 +1199,7 @@ def config_records(args, rank, world, local, fp8_peak):
     out["c4_distill"]["workload"] = d["config"]["workload"]
     out["c4_distill"]["launch"] = d["config"]["launch"]
     a = copy.copy(args)
-    a.steps, a.warmup = 8, 1  # 8 repeats and 8 alternating pairs: the forms differ by a fraction of a percent
+    a.steps, a.warmup = 10, 1  # 10 repeats and 10 alternating pairs: the forms differ by a fraction of a percent
     b = batched_record(a, rank, world, local)
     out["c5_batched"] = {k: b.get(k) for k in ("value", "unit", "ms_per_step", "schedule", "autotune_ms",
                                                "batched_ms", "sequential_64_launches", "batched_equals_sequential",
