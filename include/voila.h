@@ -274,7 +274,10 @@ voila_status voila_rollout_batched(const voila_mlp* g_T, const voila_reward* R,
  * reward output as an MMA; work order: static longest-first, table order or
  * the atomic queue; number of CTA pairs) on these inputs, times it with CUDA
  * events and writes the fastest to *best_schedule (host int32) and its time to
- * *best_ms (or NULL). Candidates a form has no kernel for are skipped.
+ * *best_ms (or NULL); a queue schedule within 0.5 % of its faster static twin
+ * is taken instead (it balances CTA pairs that run at slightly different
+ * speeds, which one timing per candidate cannot resolve). Candidates a form
+ * has no kernel for are skipped.
  * Synchronises `stream`; do not call it during stream capture. Outputs are
  * left as the last candidate's: schedules of one tile shape compute the same
  * bits; the two shapes differ in the reward output's rounding (within the
