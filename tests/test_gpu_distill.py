@@ -356,3 +356,30 @@ def test_overlapped_steps_equal_plain_steps(V, prec):
     assert torch.equal(plain.master, ovl.master)
     for wa, wb in zip(plain.student.W, ovl.student.W):
         assert torch.equal(wa, wb)
+
+
+@pytest.mark.parametrize("act", [WL.ACT_TANH, WL.ACT_IDENTITY])
+def test_tensor_core_training_gradient_other_activations(V, act):
+    # the training GEMM's tanh and identity epilogues (act and act' of the
+    # forward, the delta of the backward) against the FP64 gradient
+    from paper_2606_19729_b300.distill import Distiller
+    B = 1000
+    wl = WL.distill(B=B)
+    teacher = V.DeviceMLP.from_spec(wl.teacher)
+    d = Distiller(teacher, [torch.from_numpy(w) for w in wl.student.W], [torch.from_numpy(b) for b in wl.student.b],
+                  act, WL.PREC_BF16, B, wl.T, wl.beta0, wl.beta1, wl.emb_dim, lr=wl.lr)
+    grad = torch.empty_like(d.master)
+    loss = d.step(cuda(wl.S), cuda(wl.A), cuda(wl.omega), grad_out=grad)
+    torch.cuda.synchronize()
+    assert V.workspace_status(d.ws) == V.OK
+    fwd = O.MLP([WL.round_bf16(w) for w in wl.student.W], [np.asarray(b, np.float64) for b in wl.student.b], act)
+    s_hat = O.distill_targets(oracle_mlp(wl.teacher), wl.S, wl.A, wl.omega, wl.T, wl.beta0, wl.beta1, wl.emb_dim)
+    L, gW, gb = O.distill_loss_and_grad(fwd, wl.S, wl.A, wl.omega, s_hat)
+    assert abs(loss.item() - L) <= TOL_BF16 * L
+    o = 0
+    for l in range(len(gW)):
+        n = gW[l].size
+        assert rel_err(grad.cpu().numpy()[o:o + n], gW[l].ravel()) < TOL_BF16, l
+        o += n
+        assert rel_err(grad.cpu().numpy()[o:o + gb[l].size], gb[l]) < TOL_BF16, l
+        o += gb[l].size
