@@ -1165,9 +1165,32 @@ def small_fp32_record(args, local):
     Jo, _ = O.rollout(O.MLP(wl.g_T.W, wl.g_T.b, wl.g_T.act), O.Reward(O.REWARD_GOAL, wl.goal),
                       p_new.cpu().double().numpy(), wl.actions, wl.d_omega, wl.gamma, wl.seed)
     Jd = J.cpu().numpy()
+    # the same step captured once in a CUDA graph and replayed: the calls issue
+    # no host synchronisation, so the graph holds the same launches without the
+    # gaps between them
+    gs = torch.cuda.Stream()
+    gs.wait_stream(stream)
+    with torch.cuda.stream(gs):
+        step()
+        gs.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gs):
+            step()
+        for _ in range(20):
+            graph.replay()
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in gev:
+            e0.record(gs)
+            graph.replay()
+            e1.record(gs)
+        gs.synchronize()
+    assert V.workspace_status(ws_b) == V.OK and V.workspace_status(ws_r) == V.OK
+    graph_ms = statistics.median(e0.elapsed_time(e1) for e0, e1 in gev)
     return {"workload": "small_fp32: N=256 x K=64 x H=10, d_s=4 d_a=2 d_o=4 d_omega=4, 2x64 tanh FP32, GOAL "
                         "reward; belief update + rollout per step",
             "value": trans / (step_ms / 1e3), "unit": UNIT, "ms_per_step": step_ms, "rollout_ms": roll_ms,
+            "graph_step": {"ms_per_step": graph_ms, "value": trans / (graph_ms / 1e3),
+                           "note": "the same calls captured once in a CUDA graph and replayed"},
             "belief_update_ms": statistics.median(e[0].elapsed_time(e[1]) for e in ev), "dtype": "f32",
             "roofline": dict(fp32_roofline(achieved, load_peaks(), clocks, nsm), kernel="rollout_simt_kernel",
                              note="launch-latency bound: 163,840 transitions per launch"),
