@@ -54,3 +54,17 @@ def test_sweep_full_size_sampled(V, prec):
     J, G, Jo, Go = _run(V, wl, ks=ks)
     assert rel_err(J, Jo) < TOL[prec]
     assert rel_err(G, Go) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [WL.PREC_BF16, WL.PREC_FP8])
+def test_mixed_width_wide_generator(V, prec):
+    # 31 -> 512 -> 256 -> 512 -> 12: a 256-wide layer between 512-wide ones runs
+    # the wide kernel's other half-layer cases (one column group reading K = 512,
+    # and K = 256 feeding two groups) against the oracle
+    import dataclasses
+    wl = WL.sweep(N=300, K=2, H=3, prec=prec)
+    rng = np.random.default_rng(21)
+    wl = dataclasses.replace(wl, g_T=WL.xavier_mlp(rng, [31, 512, 256, 512, 12], WL.ACT_SILU, prec))
+    J, G, Jo, Go = _run(V, wl)
+    assert rel_err(G, Go) < TOL[prec]
+    np.testing.assert_allclose(J, Jo, rtol=TOL[prec])
