@@ -383,3 +383,22 @@ def test_tensor_core_training_gradient_other_activations(V, act):
         o += n
         assert rel_err(grad.cpu().numpy()[o:o + gb[l].size], gb[l]) < TOL_BF16, l
         o += gb[l].size
+
+
+def test_ddim_tensor_core_mixed_width_teacher(V):
+    # 82 -> 512 -> 256 -> 512 -> 8: the sampler's swapped A halves (a layer with
+    # K <= 256 writes its first output half into the A half it does not read)
+    # across a 256-wide layer, which flips the swap back, against the oracle
+    import dataclasses
+    B, T = 600, 8
+    wl = WL.distill(B=B, teacher_prec=WL.PREC_BF16)
+    rng = np.random.default_rng(31)
+    wl = dataclasses.replace(wl, teacher=WL.xavier_mlp(rng, [82, 512, 256, 512, 8], WL.ACT_SILU, WL.PREC_BF16))
+    teacher = V.DeviceMLP.from_spec(wl.teacher)
+    ws = V.alloc_workspace(V.voila_ddim_sample_workspace_size(teacher, T))
+    Y = torch.empty(B, wl.d_x, device="cuda")
+    V.voila_ddim_sample(teacher, cuda(wl.S), cuda(wl.A), cuda(wl.omega), T, wl.beta0, wl.beta1, wl.emb_dim, Y, ws)
+    torch.cuda.synchronize()
+    assert V.workspace_status(ws) == V.OK
+    want = O.distill_targets(oracle_mlp(wl.teacher), wl.S, wl.A, wl.omega, T, wl.beta0, wl.beta1, wl.emb_dim)
+    assert rel_err(Y.cpu().numpy(), want) < TOL_BF16
