@@ -846,7 +846,9 @@ def distill_record(args, rank, world, local):
     d.join()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_steps = max(1, args.steps)
+    # the first step also samples its own batch's targets: 30 steps or more keep that one extra
+    # sampler pass a small share of the loop
+    e2e_steps = max(30, args.steps)
     for x, h in zip(bufs[0], (hS, hA, hO)):
         x.copy_(h, non_blocking=True)
     for i in range(e2e_steps):
