@@ -402,3 +402,31 @@ def test_ddim_tensor_core_mixed_width_teacher(V):
     assert V.workspace_status(ws) == V.OK
     want = O.distill_targets(oracle_mlp(wl.teacher), wl.S, wl.A, wl.omega, T, wl.beta0, wl.beta1, wl.emb_dim)
     assert rel_err(Y.cpu().numpy(), want) < TOL_BF16
+
+
+def test_overlapped_steps_equal_plain_steps_full_batch(V):
+    # the bench's configuration (65,536 samples, tensor-core teacher and student):
+    # six overlapped steps on the same batch give the plain steps' losses and
+    # weights bit for bit (the spread GEMMs run 512 one-tile CTAs per launch)
+    from paper_2606_19729_b300.distill import Distiller
+    wl = WL.distill(teacher_prec=WL.PREC_BF16)
+    teacher = V.DeviceMLP.from_spec(wl.teacher)
+    S, A, om = cuda(wl.S), cuda(wl.A), cuda(wl.omega)
+
+    def make():
+        return Distiller(teacher, [torch.from_numpy(w) for w in wl.student.W],
+                         [torch.from_numpy(b) for b in wl.student.b], wl.student.act, WL.PREC_BF16, wl.B, wl.T,
+                         wl.beta0, wl.beta1, wl.emb_dim, lr=wl.lr)
+
+    plain, ovl = make(), make()
+    n = 6
+    lp = torch.empty(n, dtype=torch.float64, device="cuda")
+    lo = torch.empty(n, dtype=torch.float64, device="cuda")
+    for i in range(n):
+        plain.step(S, A, om, loss_out=lp[i:i + 1])
+        ovl.step_overlapped(S, A, om, S, A, om, loss_out=lo[i:i + 1])
+    ovl.join()
+    torch.cuda.synchronize()
+    assert V.workspace_status(ovl._ov["train_ws"]) == V.OK and V.workspace_status(plain.ws) == V.OK
+    assert torch.equal(lp, lo)
+    assert torch.equal(plain.master, ovl.master)
