@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include "trace.h"
 #include "../../include/voila.h"
 #include "kernels.h"
 #include "simt_mlp.cuh"
@@ -118,6 +119,7 @@ const char* voila_status_string(voila_status s) {
 }
 
 voila_status voila_workspace_status(const void* workspace, voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (!workspace) return VOILA_ERR_ARG;
   WsHeader h;
   cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost,
@@ -128,6 +130,7 @@ voila_status voila_workspace_status(const void* workspace, voila_stream_t stream
 }
 
 voila_status voila_selftest_wait_timeout(void* workspace, int64_t limit_cycles, voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (!workspace || ((uintptr_t)workspace % kAlign) || limit_cycles < 0 || limit_cycles > 4000000000LL)
     return VOILA_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -137,6 +140,7 @@ voila_status voila_selftest_wait_timeout(void* workspace, int64_t limit_cycles, 
 
 voila_status voila_rollout_workspace_size(const voila_mlp* g_T, const voila_reward* R, int32_t N,
                                           int32_t K, int32_t H, size_t* bytes) {
+  VOILA_NVTX_RANGE();
   if (!bytes || !valid_mlp(g_T) || !R || N < 0 || K < 0 || H < 0) return VOILA_ERR_ARG;
   // G scratch is always reserved so callers may pass G == NULL.
   *bytes = rollout_layout(g_T, R, N, K, H, true).total;
@@ -149,6 +153,7 @@ voila_status voila_rollout(const voila_mlp* g_T, const voila_reward* R, const fl
                            uint64_t seed, uint32_t planner_id, double* J, double* G,
                            int32_t* best_k, void* workspace, size_t ws_bytes,
                            voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   return voila_rollout_shard(g_T, R, particles, w, N, 0, N, d_s, actions, K, 0, H, d_a, d_omega, gamma, seed,
                              planner_id, J, G, best_k, workspace, ws_bytes, stream);
 }
@@ -159,6 +164,7 @@ voila_status voila_rollout_shard(const voila_mlp* g_T, const voila_reward* R, co
                                  int32_t d_omega, double gamma, uint64_t seed, uint32_t planner_id, double* J,
                                  double* G, int32_t* best_k, void* workspace, size_t ws_bytes,
                                  voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   voila_status st = check_rollout(g_T, R, N, d_s, K, H, d_a, d_omega);
   if (st != VOILA_OK) return st;
   if (planner_id >= 65536u) return VOILA_ERR_ARG;
@@ -237,6 +243,7 @@ static voila_status check_batched(const voila_mlp* g_T, const voila_reward* R, c
 
 voila_status voila_rollout_batched_workspace_size(const voila_mlp* g_T, const voila_reward* R,
                                                   const voila_planner* planners, int32_t P, size_t* bytes) {
+  VOILA_NVTX_RANGE();
   if (!bytes || !valid_mlp(g_T) || !R || !planners || P < 1 || P > VOILA_MAX_PLANNERS) return VOILA_ERR_ARG;
   for (int i = 0; i < P; ++i)
     if (planners[i].N < 0 || planners[i].K < 0 || planners[i].H < 0) return VOILA_ERR_ARG;
@@ -248,6 +255,7 @@ voila_status voila_rollout_batched(const voila_mlp* g_T, const voila_reward* R, 
                                    int32_t P, int32_t d_s, int32_t d_a, int32_t d_omega, double gamma,
                                    uint64_t seed, int32_t schedule, void* workspace, size_t ws_bytes,
                                    voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   voila_status st = check_batched(g_T, R, planners, P, d_s, d_a, d_omega);
   if (st != VOILA_OK) return st;
   if (!workspace || ((uintptr_t)workspace % kAlign)) return VOILA_ERR_WORKSPACE;
@@ -331,6 +339,7 @@ voila_status voila_rollout_batched_autotune(const voila_mlp* g_T, const voila_re
                                             int32_t d_omega, double gamma, uint64_t seed, void* workspace,
                                             size_t ws_bytes, int32_t* best_schedule, float* best_ms,
                                             voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (!best_schedule) return VOILA_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int nsm = 148, dev = 0;
@@ -403,6 +412,7 @@ voila_status voila_rollout_batched_autotune(const voila_mlp* g_T, const voila_re
 
 voila_status voila_belief_update_workspace_size(const voila_mlp* g_T, const voila_likelihood* ell,
                                                 int32_t N, size_t* bytes) {
+  VOILA_NVTX_RANGE();
   if (!bytes || !valid_mlp(g_T) || N < 0) return VOILA_ERR_ARG;
   const int d_s = g_T->dims[g_T->n_layers];
   size_t off = kHeaderBytes;
@@ -428,6 +438,7 @@ voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* e
                                  int32_t* idx_out, double* w_out, double* logZ_out,
                                  double* ess_out, void* workspace, size_t ws_bytes,
                                  voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (!valid_mlp(g_T) || !ell) return VOILA_ERR_ARG;
   if (N < 0 || d_s < 1 || d_a < 0 || d_o < 0 || d_omega < 0) return VOILA_ERR_ARG;
   if (d_s > 32 || d_a > 32 || d_o > 64 || d_omega > 64 || N > 262144) return VOILA_ERR_SHAPE;
@@ -531,6 +542,7 @@ voila_status voila_belief_update(const voila_mlp* g_T, const voila_likelihood* e
 
 voila_status voila_generator_fwd(const voila_mlp* mlp, const float* X, int32_t B, float* Y,
                                  voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (!valid_mlp(mlp) || B < 0) return VOILA_ERR_ARG;
   if (mlp->prec == VOILA_FP8E4M3) return VOILA_ERR_UNSUPPORTED;
   if (B == 0) return VOILA_OK;
@@ -550,6 +562,7 @@ voila_status voila_generator_fwd_seeded(const voila_mlp* mlp, const float* S, co
                                         int32_t d_omega, uint64_t seed, uint32_t stream_id,
                                         uint32_t step, uint32_t planner_id, float* Y,
                                         voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (!valid_mlp(mlp) || B < 0 || d_s < 1 || d_a < 0 || d_omega < 0 || a_stride < 0)
     return VOILA_ERR_ARG;
   if (mlp->dims[0] != d_s + d_a + d_omega || d_omega > 64 || stream_id > 15 ||
@@ -579,6 +592,7 @@ voila_status voila_generator_fwd_seeded(const voila_mlp* mlp, const float* S, co
 
 voila_status voila_philox_fill(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3,
                                uint32_t* out, int64_t n, voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (n < 0 || (n > 0 && !out) || n > (1LL << 32)) return VOILA_ERR_ARG;
   if (n == 0) return VOILA_OK;
   uint32_t k0, k1;
@@ -589,6 +603,7 @@ voila_status voila_philox_fill(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t
 voila_status voila_normal_fill(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t stream_id,
                                uint32_t planner_id, int32_t dim, float* out, int64_t n,
                                voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (n < 0 || dim < 1 || dim > 64 || stream_id > 15 || planner_id >= 65536u ||
       (n > 0 && !out) || n > (1LL << 32))
     return VOILA_ERR_ARG;

@@ -16,6 +16,7 @@
 #include <string.h>
 
 #include "../../include/voila.h"
+#include "trace.h"
 #include "common.cuh"
 #include "kernels.h"
 #include "reduce.cuh"
@@ -185,12 +186,14 @@ extern "C" {
 
 voila_status voila_preference_backup(const double* J, const double* log_pi0, int32_t K, double eta, double* V_out,
                                      double* pi_out, voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (K < 1 || !J || !V_out || !(eta > 0.0) || !isfinite(eta)) return VOILA_ERR_ARG;
   backup_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(J, log_pi0, K, eta, V_out, pi_out);
   return cudaGetLastError() == cudaSuccess ? VOILA_OK : VOILA_ERR_CUDA;
 }
 
 voila_status voila_infonce_workspace_size(const voila_mlp* ell, int32_t B, size_t* bytes) {
+  VOILA_NVTX_RANGE();
   if (!mlp_ok(ell) || !bytes || B < 0 || B > 46340) return VOILA_ERR_ARG;
   *bytes = fwd_layout(ell, B).total;
   return VOILA_OK;
@@ -200,6 +203,7 @@ voila_status voila_infonce_forward(const voila_mlp* ell, const float* S, const f
                                    int32_t d_s, int32_t d_a, int32_t d_o, float* L_out, double* lse_out,
                                    double* loss_out, float* G_out, void* workspace, size_t ws_bytes,
                                    voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   voila_status st = check_infonce(ell, B, d_s, d_a, d_o);
   if (st != VOILA_OK) return st;
   if (!loss_out) return VOILA_ERR_ARG;
@@ -284,6 +288,7 @@ static StepLayout step_layout(const voila_mlp* ell, int B) {
 }
 
 voila_status voila_infonce_step_workspace_size(const voila_mlp* ell, int32_t B, size_t* bytes) {
+  VOILA_NVTX_RANGE();
   if (!mlp_ok(ell) || !bytes || B < 0 || B > 46340) return VOILA_ERR_ARG;
   *bytes = step_layout(ell, B).total;
   return VOILA_OK;
@@ -293,6 +298,7 @@ voila_status voila_infonce_step(const voila_mlp* ell, float* master, float* adam
                                 const voila_adam* opt, const float* S, const float* A, const float* Ob, int32_t B,
                                 int32_t d_s, int32_t d_a, int32_t d_o, double* loss_out, float* grad_out,
                                 void* workspace, size_t ws_bytes, voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   voila_status st = check_infonce(ell, B, d_s, d_a, d_o);
   if (st != VOILA_OK) return st;
   if (!master || !adam_m || !adam_v || !opt || !loss_out) return VOILA_ERR_ARG;

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include "../../include/voila.h"
+#include "trace.h"
 #include "common.cuh"
 #include "kernels.h"
 #include "simt_mlp.cuh"
@@ -604,6 +605,7 @@ extern "C" {
 
 voila_status voila_generator_fwd_train(const voila_mlp* mlp, const float* X, int32_t B, float* Y, float* saved,
                                        void* workspace, size_t ws_bytes, voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (!mlp || mlp->n_layers < 1 || mlp->n_layers > VOILA_MAX_LAYERS || B < 0) return VOILA_ERR_ARG;
   if (mlp->prec != VOILA_FP32 && mlp->prec != VOILA_BF16) return VOILA_ERR_UNSUPPORTED;
   if (B == 0) return VOILA_OK;
@@ -617,6 +619,7 @@ voila_status voila_generator_fwd_train(const voila_mlp* mlp, const float* X, int
 }
 
 voila_status voila_generator_bwd_workspace_size(const voila_mlp* mlp, int32_t B, size_t* bytes) {
+  VOILA_NVTX_RANGE();
   if (!mlp || !bytes || mlp->n_layers < 1 || mlp->n_layers > VOILA_MAX_LAYERS || B < 0) return VOILA_ERR_ARG;
   *bytes = bwd_ws_bytes(mlp, B);
   return VOILA_OK;
@@ -625,6 +628,7 @@ voila_status voila_generator_bwd_workspace_size(const voila_mlp* mlp, int32_t B,
 voila_status voila_generator_bwd(const voila_mlp* mlp, const float* X, const float* saved, const float* dY,
                                  int32_t B, float* dX, float* const* dW, float* const* db, void* workspace,
                                  size_t ws_bytes, voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (!mlp || mlp->n_layers < 1 || mlp->n_layers > VOILA_MAX_LAYERS || B < 0 || !dW || !db) return VOILA_ERR_ARG;
   if (mlp->prec != VOILA_FP32 && mlp->prec != VOILA_BF16) return VOILA_ERR_UNSUPPORTED;
   for (int l = 0; l < mlp->n_layers; ++l)
@@ -642,6 +646,7 @@ voila_status voila_generator_bwd(const voila_mlp* mlp, const float* X, const flo
 }
 
 voila_status voila_ddim_sample_workspace_size(const voila_mlp* teacher, int32_t T, size_t* bytes) {
+  VOILA_NVTX_RANGE();
   if (!teacher || !bytes || teacher->n_layers < 1 || teacher->n_layers > VOILA_MAX_LAYERS || T < 1 || T > 64)
     return VOILA_ERR_ARG;
   *bytes = ddim_ws_bytes(teacher, T);
@@ -652,6 +657,7 @@ voila_status voila_ddim_sample(const voila_mlp* teacher, const float* S, const f
                                int32_t B, int32_t d_s, int32_t d_a, int32_t d_x, int32_t T, double beta0,
                                double beta1, int32_t emb_dim, float* Y, void* workspace, size_t ws_bytes,
                                voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (!teacher || teacher->n_layers < 1 || teacher->n_layers > VOILA_MAX_LAYERS || B < 0) return VOILA_ERR_ARG;
   if (teacher->prec != VOILA_FP32 && teacher->prec != VOILA_BF16) return VOILA_ERR_UNSUPPORTED;
   if (T < 1 || T > 64 || d_x < 1 || d_x > 16 || emb_dim < 0 || emb_dim > 64 || (emb_dim & 1) || d_s < 0 ||
@@ -733,6 +739,7 @@ voila_status voila_ddim_sample(const voila_mlp* teacher, const float* S, const f
 
 voila_status voila_adam_step(float* params, const float* grads, float* m, float* v, int64_t n, float lr,
                              float beta1, float beta2, float eps, int32_t step, voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (n < 0 || step < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
       !(eps > 0.0f))
     return VOILA_ERR_ARG;
@@ -746,6 +753,7 @@ voila_status voila_adam_step(float* params, const float* grads, float* m, float*
 
 voila_status voila_distill_step_workspace_size(const voila_mlp* teacher, const voila_mlp* student, int32_t B,
                                                int32_t d_x, int32_t T, size_t* bytes) {
+  VOILA_NVTX_RANGE();
   if (!teacher || !student || !bytes || student->n_layers < 1 || student->n_layers > VOILA_MAX_LAYERS || B < 0 ||
       d_x < 1 || teacher->n_layers < 1 || teacher->n_layers > VOILA_MAX_LAYERS || T < 1 || T > 64)
     return VOILA_ERR_ARG;
@@ -758,6 +766,7 @@ voila_status voila_distill_step(const voila_mlp* teacher, const voila_mlp* stude
                                 const float* S, const float* A, const float* omega, int32_t B, int32_t d_s,
                                 int32_t d_a, int32_t d_x, double* loss_out, float* grad_out, void* workspace,
                                 size_t ws_bytes, voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (!teacher || !student || !ddim || !opt || !master || !adam_m || !adam_v || !loss_out || B < 0)
     return VOILA_ERR_ARG;
   voila_status err = VOILA_OK;
@@ -779,6 +788,7 @@ voila_status voila_distill_step(const voila_mlp* teacher, const voila_mlp* stude
 
 voila_status voila_distill_train_step_workspace_size(const voila_mlp* student, int32_t B, int32_t d_x,
                                                      size_t* bytes) {
+  VOILA_NVTX_RANGE();
   if (!student || !bytes || student->n_layers < 1 || student->n_layers > VOILA_MAX_LAYERS || B < 0 || d_x < 1)
     return VOILA_ERR_ARG;
   *bytes = train_region(student, B, d_x).total;
@@ -790,6 +800,7 @@ voila_status voila_distill_train_step(const voila_mlp* student, float* master, f
                                       const float* s_hat, int32_t B, int32_t d_s, int32_t d_a, int32_t d_x,
                                       int32_t flags, double* loss_out, float* grad_out, void* workspace,
                                       size_t ws_bytes, voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (!student || !opt || !master || !adam_m || !adam_v || !loss_out || B < 0 || (flags & ~VOILA_TRAIN_SPREAD))
     return VOILA_ERR_ARG;
   voila_status err = VOILA_OK;
@@ -806,6 +817,7 @@ voila_status voila_distill_train_step(const voila_mlp* student, float* master, f
 }
 
 voila_status voila_mlp_load_flat(const voila_mlp* mlp, const float* flat, voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (!mlp || !flat || mlp->n_layers < 1 || mlp->n_layers > VOILA_MAX_LAYERS) return VOILA_ERR_ARG;
   if (mlp->prec != VOILA_FP32 && mlp->prec != VOILA_BF16) return VOILA_ERR_UNSUPPORTED;
   for (int l = 0; l < mlp->n_layers; ++l)

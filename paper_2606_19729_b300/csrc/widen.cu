@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include "../../include/voila.h"
+#include "trace.h"
 #include "common.cuh"
 #include "kernels.h"
 #include "simt_mlp.cuh"
@@ -743,6 +744,7 @@ extern "C" {
 voila_status voila_progressive_widening_workspace_size(const voila_pw_tree* tree, const voila_mlp* g_Z,
                                                        const voila_likelihood* ell,
                                                        int32_t M, size_t* bytes) {
+  VOILA_NVTX_RANGE();
   if (!tree || !ell || M < 0 || M > (1 << 24) || !bytes || tree->n_nodes < 1 || tree->n_nodes >= (1 << 24) ||
       tree->C_max < 1 || tree->C_max > 65535)
     return VOILA_ERR_ARG;
@@ -756,6 +758,7 @@ voila_status voila_progressive_widening(const voila_pw_tree* tree, const int32_t
                                         uint32_t step, uint32_t planner_id, int32_t* branch_out,
                                         uint8_t* widened_out, float* ell_out, double* w_out, int32_t* idx_out,
                                         float* s_out, void* workspace, size_t ws_bytes, voila_stream_t stream) {
+  VOILA_NVTX_RANGE();
   if (!tree || !g_Z || !ell || M < 0 || M > (1 << 24) || d_s < 1 || d_omega < 0 || !(k_o > 0.0) ||
       !(alpha_o > 0.0) || !(lambda > 0.0f) || planner_id >= 65536)
     return VOILA_ERR_ARG;
