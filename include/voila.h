@@ -177,6 +177,10 @@ voila_status voila_rollout_workspace_size(const voila_mlp* g_T, const voila_rewa
  * per-channel scales (see voila_mlp).
  * Returns are accumulated in FP64 in both forms.
  * N == 0 or K == 0 is a no-op; H == 0 gives zero returns.
+ * Device status (voila_workspace_status(workspace), cleared by the call):
+ * VOILA_ERR_NONFINITE if some J[k] is NaN or infinite (a non-finite weight,
+ * particle, action or model value reached it; J and G are still written),
+ * VOILA_ERR_TIMEOUT if a bounded wait of the tensor-core kernel ran out.
  */
 voila_status voila_rollout(const voila_mlp* g_T, const voila_reward* R,
                            const float* particles, const double* w, int32_t N, int32_t d_s,
@@ -260,7 +264,9 @@ voila_status voila_rollout_batched_workspace_size(const voila_mlp* g_T, const vo
  * the device. P <= VOILA_MAX_PLANNERS. BF16 runs batched; FP32 runs the
  * planners one after another on CUDA cores.
  * Batched execution of VOPP's many simulations (Sec. 2.2, Sec. 4.3), with the
- * per-planner semantics of voila_rollout.
+ * per-planner semantics of voila_rollout. One device status word for the
+ * call: VOILA_ERR_NONFINITE if any planner's J has a NaN or infinite entry,
+ * VOILA_ERR_TIMEOUT as for voila_rollout.
  */
 voila_status voila_rollout_batched(const voila_mlp* g_T, const voila_reward* R,
                                    const voila_planner* planners, int32_t P, int32_t d_s,

@@ -210,7 +210,7 @@ voila_status voila_rollout_shard(const voila_mlp* g_T, const voila_reward* R, co
     a.ld = simt_ld(maxw);
     if (cudaError_t e = launch_rollout_simt(a, s)) return cuda_status(e);
   }
-  return cuda_status(launch_reduce_returns(Gbuf, w, N, N_total, K, J, best_k, s));
+  return cuda_status(launch_reduce_returns(Gbuf, w, N, N_total, K, J, best_k, (WsHeader*)ws, s));
 }
 
 // Batched rollout workspace: [header | tensor-core scratch | G of every planner
@@ -316,6 +316,7 @@ voila_status voila_rollout_batched(const voila_mlp* g_T, const voila_reward* R, 
   }
   BatchedReduceArgs r;
   memset(&r, 0, sizeof(r));
+  r.hdr = (WsHeader*)ws;
   long long kacc = 0;
   for (int i = 0; i < P; ++i) {
     const voila_planner& q = planners[i];

@@ -300,10 +300,13 @@ cudaError_t launch_belief_resample(const ResampleArgs& a, cudaStream_t s) {
 
 // J_k = sum_n w_n G[k][n]: one CTA per sequence, fixed summation order;
 // without w every particle weighs 1 / N_total (N_total = N unless the call is
-// one particle shard of a larger problem).
+// one particle shard of a larger problem). A J_k that is NaN or infinite (a
+// non-finite weight, particle, action or model output reached it) latches
+// VOILA_ERR_NONFINITE in the workspace status word.
 __global__ void __launch_bounds__(256) reduce_returns_kernel(const double* __restrict__ G,
                                                              const double* __restrict__ w, int N,
-                                                             int N_total, int K, double* __restrict__ J) {
+                                                             int N_total, int K, double* __restrict__ J,
+                                                             WsHeader* hdr) {
   __shared__ double red[33];
   const int k = blockIdx.x;
   const double invN = 1.0 / (double)N_total;
@@ -311,7 +314,10 @@ __global__ void __launch_bounds__(256) reduce_returns_kernel(const double* __res
   const double* g = G + (size_t)k * N;
   for (int n = threadIdx.x; n < N; n += blockDim.x) acc += g[n] * (w ? w[n] : invN);
   const double tot = block_sum(acc, red);
-  if (threadIdx.x == 0) J[k] = tot;
+  if (threadIdx.x == 0) {
+    J[k] = tot;
+    if (!isfinite(tot)) set_status(hdr, VOILA_ERR_NONFINITE, kWhereReturns);
+  }
 }
 
 // argmax_k J_k, lowest index on ties (NaN never wins).
@@ -375,7 +381,10 @@ __global__ void __launch_bounds__(256) reduce_returns_batched_kernel(const __gri
   double acc = 0.0;
   for (int n = threadIdx.x; n < N; n += blockDim.x) acc += g[n] * (w ? w[n] : invN);
   const double tot = block_sum(acc, red);
-  if (threadIdx.x == 0) a.J[q][k] = tot;
+  if (threadIdx.x == 0) {
+    a.J[q][k] = tot;
+    if (!isfinite(tot)) set_status(a.hdr, VOILA_ERR_NONFINITE, kWhereReturns);
+  }
 }
 
 __global__ void __launch_bounds__(1024) argmax_batched_kernel(const __grid_constant__ BatchedReduceArgs a) {
@@ -437,8 +446,8 @@ cudaError_t launch_reduce_returns_batched(const BatchedReduceArgs& a, cudaStream
 }
 
 cudaError_t launch_reduce_returns(const double* G, const double* w, int N, int N_total, int K, double* J,
-                                  int32_t* best_k, cudaStream_t s) {
-  reduce_returns_kernel<<<K, 256, 0, s>>>(G, w, N, N_total, K, J);
+                                  int32_t* best_k, WsHeader* hdr, cudaStream_t s) {
+  reduce_returns_kernel<<<K, 256, 0, s>>>(G, w, N, N_total, K, J, hdr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !best_k) return e;
   argmax_kernel<<<1, 1024, 0, s>>>(J, K, best_k);

@@ -84,9 +84,11 @@ cudaError_t launch_rollout_simt(const RolloutArgs& a, cudaStream_t s);
 cudaError_t launch_belief_propose(const BeliefArgs& a, cudaStream_t s);
 cudaError_t launch_belief_resample(const ResampleArgs& a, cudaStream_t s);
 cudaError_t launch_mlp_fwd(const FwdArgs& a, cudaStream_t s);
-// J_k = sum_n w_n G[k][n] (w == NULL: the uniform weight 1 / N_total).
+// J_k = sum_n w_n G[k][n] (w == NULL: the uniform weight 1 / N_total); a
+// non-finite J_k sets VOILA_ERR_NONFINITE in *hdr (where = kWhereReturns).
+constexpr int32_t kWhereReturns = 70;
 cudaError_t launch_reduce_returns(const double* G, const double* w, int N, int N_total, int K, double* J,
-                                  int32_t* best_k, cudaStream_t s);
+                                  int32_t* best_k, WsHeader* hdr, cudaStream_t s);
 // Returns of P planners in one launch: J_q[k] = sum_n w_q[n] G_q[k][n], then argmax per planner.
 struct BatchedReduceArgs {
   const double* G[kMaxPlanners];
@@ -96,6 +98,7 @@ struct BatchedReduceArgs {
   int N[kMaxPlanners], K[kMaxPlanners];
   long long k_end[kMaxPlanners];  // inclusive prefix sum of K
   int P;
+  WsHeader* hdr;  // status word of the call's workspace (non-finite J_k)
 };
 cudaError_t launch_reduce_returns_batched(const BatchedReduceArgs& a, cudaStream_t s);
 

@@ -29,6 +29,11 @@ def flat_views(flat: torch.Tensor, dims: Sequence[int]) -> List[Tuple[torch.Tens
     return out
 
 
+def _aliases(t: torch.Tensor, base: torch.Tensor) -> bool:
+    """Whether t is a view into base's storage (an FP32 student's weights are)."""
+    return t.untyped_storage().data_ptr() == base.untyped_storage().data_ptr()
+
+
 def n_params(dims: Sequence[int]) -> int:
     return sum(din * dout + dout for din, dout in zip(dims[:-1], dims[1:]))
 
@@ -114,6 +119,44 @@ class Distiller:
         V.voila_distill_step(self.teacher, self.student, self.ddim, self.master, self.m, self.v, opt, S, A, omega,
                              out, grad_out, self.ws, stream)
         return out
+
+    # ---- checkpoint and resume ----------------------------------------------
+    # The training state is the FP32 master weights, Adam's two moment vectors
+    # and its step count, and (BF16 students) the forward copy the next step's
+    # forward pass reads. Restoring all of them exactly makes a resumed run
+    # continue bit for bit; the dictionary holds host tensors and plain values,
+    # so torch.save / torch.load store it.
+
+    def state_dict(self) -> dict:
+        """The training state as host tensors and plain values."""
+        self.join()
+        return {
+            "dims": list(self.dims), "act": self.student.act, "prec": self.student.prec,
+            "master": self.master.cpu(), "m": self.m.cpu(), "v": self.v.cpu(), "t": self.t,
+            "lr": self.lr, "betas": tuple(self.betas), "eps": self.eps,
+            "forward_W": [w.cpu() for w in self.student.W],
+        }
+
+    def load_state_dict(self, sd: dict) -> None:
+        """Restores a state_dict() of a Distiller of the same student shape.
+
+        Samples an overlapped step prepared for a following batch are
+        dropped (that batch is sampled again)."""
+        if list(sd["dims"]) != list(self.dims) or sd["act"] != self.student.act or sd["prec"] != self.student.prec:
+            raise ValueError("checkpoint of a different student")
+        self.join()
+        # in place: the device descriptors keep pointing at these buffers
+        self.master.copy_(sd["master"])
+        self.m.copy_(sd["m"])
+        self.v.copy_(sd["v"])
+        for w, src in zip(self.student.W, sd["forward_W"]):
+            if not _aliases(w, self.master):  # a BF16 forward copy; FP32 weights are views of master
+                w.copy_(src)
+        self.t = int(sd["t"])
+        self.lr, self.betas, self.eps = sd["lr"], tuple(sd["betas"]), sd["eps"]
+        ov = getattr(self, "_ov", None)
+        if ov is not None:
+            ov["pending"] = None
 
     # ---- overlapped steps --------------------------------------------------
     # The teacher does not depend on the student, so the targets of the next

@@ -430,3 +430,56 @@ def test_overlapped_steps_equal_plain_steps_full_batch(V):
     assert V.workspace_status(ovl._ov["train_ws"]) == V.OK and V.workspace_status(plain.ws) == V.OK
     assert torch.equal(lp, lo)
     assert torch.equal(plain.master, ovl.master)
+
+
+@pytest.mark.parametrize("prec", [WL.PREC_BF16, WL.PREC_FP32])
+def test_checkpoint_resume_continues_bit_for_bit(V, prec):
+    # three steps, a checkpoint through torch.save / torch.load, then two more
+    # steps: a fresh Distiller (other initial weights) restored from the
+    # checkpoint reproduces the last two steps' losses, gradients, weights and
+    # moments exactly
+    import io
+    from paper_2606_19729_b300.distill import Distiller
+    B, nb = 2048, 5
+    wl = WL.distill(B=B * nb)
+    teacher = V.DeviceMLP.from_spec(wl.teacher)
+    S, A, om = cuda(wl.S), cuda(wl.A), cuda(wl.omega)
+    batches = [(S[i * B:(i + 1) * B], A[i * B:(i + 1) * B], om[i * B:(i + 1) * B]) for i in range(nb)]
+
+    def make(scale):
+        return Distiller(teacher, [torch.from_numpy(w * scale) for w in wl.student.W],
+                         [torch.from_numpy(b) for b in wl.student.b], wl.student.act, prec, B, wl.T, wl.beta0,
+                         wl.beta1, wl.emb_dim, lr=wl.lr)
+
+    run = make(1.0)
+    for b in batches[:3]:
+        run.step(*b)
+    buf = io.BytesIO()
+    torch.save(run.state_dict(), buf)
+    la = torch.empty(2, dtype=torch.float64, device="cuda")
+    ga = [torch.empty_like(run.master) for _ in range(2)]
+    for i, b in enumerate(batches[3:]):
+        run.step(*b, loss_out=la[i:i + 1], grad_out=ga[i])
+
+    res = make(0.5)
+    res.step(*batches[4])  # a different history, overwritten by the checkpoint
+    buf.seek(0)
+    res.load_state_dict(torch.load(buf))
+    assert res.t == 3
+    lb = torch.empty(2, dtype=torch.float64, device="cuda")
+    gb = [torch.empty_like(res.master) for _ in range(2)]
+    for i, b in enumerate(batches[3:]):
+        res.step(*b, loss_out=lb[i:i + 1], grad_out=gb[i])
+    torch.cuda.synchronize()
+    assert V.workspace_status(res.ws) == V.OK
+    assert torch.equal(la, lb)
+    for a, b in zip(ga, gb):
+        assert torch.equal(a, b)
+    for x, y in ((run.master, res.master), (run.m, res.m), (run.v, res.v)):
+        assert torch.equal(x, y)
+    for wa, wb in zip(run.student.W, res.student.W):
+        assert torch.equal(wa, wb)
+    with pytest.raises(ValueError):
+        bad = run.state_dict()
+        bad["dims"] = bad["dims"][:-1] + [bad["dims"][-1] + 1]
+        res.load_state_dict(bad)
