@@ -62,7 +62,7 @@ typedef enum {
   VOILA_ERR_NONFINITE = -4,    /* device status: a log-weight was NaN or +inf */
   VOILA_ERR_DEGENERATE = -5,   /* device status: every log-weight was -inf */
   VOILA_ERR_TIMEOUT = -6,      /* device status: a bounded wait ran out */
-  VOILA_ERR_UNSUPPORTED = -7,  /* valid request this build has no kernel for */
+  VOILA_ERR_UNSUPPORTED = -7,  /* valid request the library has no kernel for */
   VOILA_ERR_WORKSPACE = -8     /* workspace missing, misaligned or too small */
 } voila_status;
 

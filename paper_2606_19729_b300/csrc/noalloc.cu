@@ -21,7 +21,7 @@ std::mutex g_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
 CUcontext g_scratch_ctx[kMaxDevices] = {};  // the context the address above belongs to
 
-// The driver's cuCtxGetCurrent through the runtime's entry-point query (the
+// The CUDA driver API's cuCtxGetCurrent through the runtime's entry-point query (the
 // library does not link libcuda itself).
 typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
 CtxGetCurrentFn ctx_get_current() {
