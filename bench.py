@@ -1146,7 +1146,15 @@ def small_fp32_record(args, local):
         V.voila_rollout(g, R, p_new, None, A, wl.d_omega, wl.gamma, wl.seed, 0, J, None, best, ws_r)
 
     warm_until(step, 0.3)
-    reps = 200
+    # enough steps for ~1.5 s of timed region, so that the clock sampler (one
+    # nvidia-smi sample per 200 ms) sees it
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(20):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    reps = int(min(20000, max(200, 1500.0 / (e0.elapsed_time(e1) / 20))))
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(reps)]
     with Clocks(local) as clk:
         for e in ev:
@@ -1194,8 +1202,9 @@ def small_fp32_record(args, local):
             "graph_step": {"ms_per_step": graph_ms, "value": trans / (graph_ms / 1e3),
                            "note": "the same calls captured once in a CUDA graph and replayed"},
             "belief_update_ms": statistics.median(e[0].elapsed_time(e[1]) for e in ev), "dtype": "f32",
-            "roofline": dict(fp32_roofline(achieved, load_peaks(), clocks, nsm), kernel="rollout_simt_kernel",
-                             note="launch-latency bound: 163,840 transitions per launch"),
+            "roofline": dict(fp32_roofline(achieved, load_peaks(), clocks, nsm),
+                             kernel="rollout_rows_kernel (8 threads per row)",
+                             note="latency bound: 16,384 rows, 163,840 transitions per launch"),
             "err_vs_fp64": {"J_normwise": float(np.max(np.abs(Jd - Jo)) / np.max(np.abs(Jo))), "tolerance": 1e-5,
                             "sample": "all 64 sequences, from the device's resampled particles"},
             "steps_timed": reps, "clocks": clocks}
@@ -1399,7 +1408,9 @@ def main():
     else:
         achieved = fpt * trans_per_step / roll_avg_s / 1e12
         roof = fp32_roofline(achieved, peaks, clocks, torch.cuda.get_device_properties(dev).multi_processor_count)
-        roof["kernel"] = "rollout_simt_kernel"
+        # MLPs of at most two 64-unit hidden layers run on the row kernel, wider ones tiled
+        small = max(max(w.shape) for w in wl.g_T.W) <= 64 and len(wl.g_T.W) == 3
+        roof["kernel"] = "rollout_rows_kernel" if small else "rollout_simt_kernel"
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,

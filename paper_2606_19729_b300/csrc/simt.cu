@@ -266,18 +266,21 @@ static int simt_grid(long long ntiles, size_t smem) {
 
 // ---------------------------------------------------------------------------
 // FP32 rollout for small MLPs (generator and reward of two hidden layers at
-// most 64 wide, inputs at most 16 wide): four threads (a quad of one warp) per
-// row (particle, sequence) through all H steps, thread `sub` of the quad
-// computing hidden units j = 4 i + sub (i < 16) of both hidden layers; the
-// units the next layer needs from the other three threads arrive by warp
-// shuffles, in input order. The weights of both MLPs sit in shared memory,
-// zero padded to 64 hidden units and 16 inputs (padding adds exact zero
-// products), rows strided so that the four threads' rows fall in different
-// banks. Every layer accumulates in input order from its bias, like the tiled
-// kernel, so both give the same bits.
+// most 64 wide, inputs at most 16 wide): a group of TPR = 4 or 8 threads of
+// one warp per row (particle, sequence) through all H steps, thread `sub` of
+// the group computing hidden units j = TPR i + sub of both hidden layers; the
+// units the next layer needs from the other threads arrive by warp shuffles,
+// in input order. The weights of both MLPs sit in shared memory, zero padded
+// to 64 hidden units and 16 inputs (padding adds exact zero products), rows
+// strided so that the group's rows fall in different banks. Every layer
+// accumulates in input order from its bias, like the tiled kernel, so both
+// group sizes and the tiled kernel give the same bits.
 // ---------------------------------------------------------------------------
-constexpr int kRowHid = 64, kRowIn = 16, kRowOut = 8, kRowThreads = 128;
-constexpr int kRowW0Ld = kRowIn + 4;   // 80-byte rows: the quad's rows j = 4 i + sub in distinct banks
+constexpr int kRowHid = 64, kRowIn = 16, kRowOut = 8;
+// Rows a launch of the row kernel holds at once: 4 CTAs of 32 rows per SM (the
+// two MLPs' 50 KB of shared memory per CTA allow four).
+constexpr long long kRowsOneWave = 148LL * 4 * 32;
+constexpr int kRowW0Ld = kRowIn + 4;   // 80-byte rows: a group's rows j = TPR i + sub in distinct banks
 constexpr int kRowW1Ld = kRowHid + 4;  // 272-byte rows, likewise
 // one MLP in shared memory: W0 [64][20], b0 [64], W1 [64][68], b1 [64], W2 [8][64], b2 [8]
 constexpr int kRowMlpFloats =
@@ -313,22 +316,24 @@ __device__ void load_row_mlp(float* dst, const MlpDev& m) {
   for (int i = threadIdx.x; i < kRowOut; i += blockDim.x) b2[i] = i < d3 ? m.b[2][i] : 0.0f;
 }
 
-// y[NOUT] = mlp(x) for one row, computed by its quad (every thread of the quad
-// passes the same x and gets the same y); the MLP's padded weights at `w`.
-template <int NOUT>
-__device__ __forceinline__ void quad_mlp(const float* __restrict__ w, const float* x, float* y, int act,
-                                         unsigned qmask, int qbase, int sub) {
+// y[NOUT] = mlp(x) for one row, computed by its group of TPR threads (every
+// thread of the group passes the same x and gets the same y); the MLP's
+// padded weights at `w`. Thread `sub` of the group computes hidden units
+// TPR i + sub; every unit and output accumulates from its bias in input order.
+template <int NOUT, int TPR>
+__device__ __forceinline__ void group_mlp(const float* __restrict__ w, const float* x, float* y, int act,
+                                          unsigned gmask, int gbase, int sub) {
   const float* W0 = w;
   const float* b0 = W0 + kRowHid * kRowW0Ld;
   const float* W1 = b0 + kRowHid;
   const float* b1 = W1 + kRowHid * kRowW1Ld;
   const float* W2 = b1 + kRowHid;
   const float* b2 = W2 + kRowOut * kRowHid;
-  constexpr int kPer = kRowHid / 4;  // hidden units per thread
+  constexpr int kPer = kRowHid / TPR;  // hidden units per thread
   float h[kPer];
 #pragma unroll
-  for (int i = 0; i < kPer; ++i) {  // first hidden layer: units 4 i + sub
-    const int j = 4 * i + sub;
+  for (int i = 0; i < kPer; ++i) {  // first hidden layer: units TPR i + sub
+    const int j = TPR * i + sub;
     float acc = b0[j];
 #pragma unroll
     for (int k = 0; k < kRowIn; k += 4) {
@@ -340,20 +345,24 @@ __device__ __forceinline__ void quad_mlp(const float* __restrict__ w, const floa
     }
     h[i] = act_fp32(acc, act);
   }
-  float a[kPer];  // second hidden layer, units 4 i + sub
+  float a[kPer];  // second hidden layer, units TPR i + sub
 #pragma unroll
-  for (int i = 0; i < kPer; ++i) a[i] = b1[4 * i + sub];
+  for (int i = 0; i < kPer; ++i) a[i] = b1[TPR * i + sub];
 #pragma unroll
-  for (int i2 = 0; i2 < kPer; ++i2) {  // inputs k = 4 i2 .. 4 i2 + 3, one from each thread of the quad
-    const float h0 = __shfl_sync(qmask, h[i2], qbase), h1 = __shfl_sync(qmask, h[i2], qbase + 1);
-    const float h2 = __shfl_sync(qmask, h[i2], qbase + 2), h3 = __shfl_sync(qmask, h[i2], qbase + 3);
+  for (int i2 = 0; i2 < kPer; ++i2) {  // inputs TPR i2 .. TPR i2 + TPR - 1, one from each thread of the group
+    float hv[TPR];
+#pragma unroll
+    for (int q = 0; q < TPR; ++q) hv[q] = __shfl_sync(gmask, h[i2], gbase + q);
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
-      const float4 wv = *reinterpret_cast<const float4*>(W1 + (4 * i + sub) * kRowW1Ld + 4 * i2);
-      a[i] = fmaf(h0, wv.x, a[i]);
-      a[i] = fmaf(h1, wv.y, a[i]);
-      a[i] = fmaf(h2, wv.z, a[i]);
-      a[i] = fmaf(h3, wv.w, a[i]);
+#pragma unroll
+      for (int q = 0; q < TPR; q += 4) {
+        const float4 wv = *reinterpret_cast<const float4*>(W1 + (TPR * i + sub) * kRowW1Ld + TPR * i2 + q);
+        a[i] = fmaf(hv[q], wv.x, a[i]);
+        a[i] = fmaf(hv[q + 1], wv.y, a[i]);
+        a[i] = fmaf(hv[q + 2], wv.z, a[i]);
+        a[i] = fmaf(hv[q + 3], wv.w, a[i]);
+      }
     }
   }
 #pragma unroll
@@ -362,21 +371,29 @@ __device__ __forceinline__ void quad_mlp(const float* __restrict__ w, const floa
   for (int m = 0; m < NOUT; ++m) y[m] = b2[m];
 #pragma unroll
   for (int i2 = 0; i2 < kPer; ++i2) {  // output layer over all 64 units, in order
-    const float g0 = __shfl_sync(qmask, a[i2], qbase), g1 = __shfl_sync(qmask, a[i2], qbase + 1);
-    const float g2 = __shfl_sync(qmask, a[i2], qbase + 2), g3 = __shfl_sync(qmask, a[i2], qbase + 3);
+    float gv[TPR];
+#pragma unroll
+    for (int q = 0; q < TPR; ++q) gv[q] = __shfl_sync(gmask, a[i2], gbase + q);
 #pragma unroll
     for (int m = 0; m < NOUT; ++m) {
-      const float4 wv = *reinterpret_cast<const float4*>(W2 + m * kRowHid + 4 * i2);
-      y[m] = fmaf(g0, wv.x, y[m]);
-      y[m] = fmaf(g1, wv.y, y[m]);
-      y[m] = fmaf(g2, wv.z, y[m]);
-      y[m] = fmaf(g3, wv.w, y[m]);
+#pragma unroll
+      for (int q = 0; q < TPR; q += 4) {
+        const float4 wv = *reinterpret_cast<const float4*>(W2 + m * kRowHid + TPR * i2 + q);
+        y[m] = fmaf(gv[q], wv.x, y[m]);
+        y[m] = fmaf(gv[q + 1], wv.y, y[m]);
+        y[m] = fmaf(gv[q + 2], wv.z, y[m]);
+        y[m] = fmaf(gv[q + 3], wv.w, y[m]);
+      }
     }
   }
 }
 
-template <int DS, bool RMLP>
-__global__ void __launch_bounds__(kRowThreads) rollout_rows_kernel(RolloutArgs a) {
+// TPR threads per row (4 or 8), 32 rows per CTA. Eight threads per row (four
+// CTAs per SM, 64 registers) double the warps of a launch whose rows fit in one
+// wave; with more rows four threads per row do less work in total (each thread
+// of a group computes the output layer in full).
+template <int DS, bool RMLP, int TPR>
+__global__ void __launch_bounds__(32 * TPR, TPR == 8 ? 4 : 1) rollout_rows_kernel(RolloutArgs a) {
   extern __shared__ __align__(16) float sw[];
   float* gw = sw;
   float* rw = sw + kRowMlpFloats;
@@ -385,10 +402,10 @@ __global__ void __launch_bounds__(kRowThreads) rollout_rows_kernel(RolloutArgs a
   __syncthreads();
   const long long rows = (long long)a.N * a.K;
   const int d_a = a.d_a, d_w = a.d_omega;
-  const int lane = threadIdx.x & 31, sub = lane & 3, qbase = lane & ~3;
-  const unsigned qmask = 0xFu << qbase;
-  for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 2; row < rows;
-       row += ((long long)gridDim.x * blockDim.x) >> 2) {
+  const int lane = threadIdx.x & 31, sub = lane & (TPR - 1), gbase = lane & ~(TPR - 1);
+  const unsigned gmask = (TPR == 8 ? 0xFFu : 0xFu) << gbase;
+  for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / TPR; row < rows;
+       row += ((long long)gridDim.x * blockDim.x) / TPR) {
     const int n = (int)(row % a.N), k = (int)(row / a.N);
     float s[DS];
 #pragma unroll
@@ -420,7 +437,7 @@ __global__ void __launch_bounds__(kRowThreads) rollout_rows_kernel(RolloutArgs a
             }
           }
         }
-      quad_mlp<DS>(gw, x, s, a.g.act, qmask, qbase, sub);
+      group_mlp<DS, TPR>(gw, x, s, a.g.act, gmask, gbase, sub);
       float r;
       if (RMLP) {
         float xr[kRowIn];
@@ -432,7 +449,7 @@ __global__ void __launch_bounds__(kRowThreads) rollout_rows_kernel(RolloutArgs a
         for (int i = 0; i < kRowIn - DS; ++i)
           if (i < d_a) xr[DS + i] = __ldg(at + i);
         float rv[1];
-        quad_mlp<1>(rw, xr, rv, a.r.act, qmask, qbase, sub);
+        group_mlp<1, TPR>(rw, xr, rv, a.r.act, gmask, gbase, sub);
         r = rv[0];
       } else {
         float acc = 0.0f;
@@ -469,14 +486,20 @@ cudaError_t launch_rollout_simt(const RolloutArgs& a, cudaStream_t s) {
       (rmlp || a.goal_dims <= a.d_s)) {
     const size_t smem = (size_t)(rmlp ? 2 : 1) * kRowMlpFloats * sizeof(float);
     void (*k)(RolloutArgs);
-    if (a.d_s == 4) k = rmlp ? rollout_rows_kernel<4, true> : rollout_rows_kernel<4, false>;
-    else k = rmlp ? rollout_rows_kernel<8, true> : rollout_rows_kernel<8, false>;
+    const long long rows = (long long)a.N * a.K;
+    const int tpr = rows <= kRowsOneWave ? 8 : 4;
+    if (tpr == 8) {
+      if (a.d_s == 4) k = rmlp ? rollout_rows_kernel<4, true, 8> : rollout_rows_kernel<4, false, 8>;
+      else k = rmlp ? rollout_rows_kernel<8, true, 8> : rollout_rows_kernel<8, false, 8>;
+    } else {
+      if (a.d_s == 4) k = rmlp ? rollout_rows_kernel<4, true, 4> : rollout_rows_kernel<4, false, 4>;
+      else k = rmlp ? rollout_rows_kernel<8, true, 4> : rollout_rows_kernel<8, false, 4>;
+    }
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const long long rows = (long long)a.N * a.K;
-    long long grid = (4 * rows + kRowThreads - 1) / kRowThreads;  // a quad per row
+    long long grid = (rows + 31) / 32;  // 32 rows per CTA
     if (grid > 148LL * 8) grid = 148LL * 8;
-    k<<<(int)grid, kRowThreads, smem, s>>>(a);
+    k<<<(int)grid, 32 * tpr, smem, s>>>(a);
     return cudaGetLastError();
   }
   const size_t smem = rollout_simt_smem(a.ld);

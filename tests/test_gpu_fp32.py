@@ -235,3 +235,36 @@ def test_argument_errors_raise(V):
         V.voila_rollout(g, V.goal_reward(wl.goal), cuda(wl.particles), None, cuda(wl.actions), 3,
                         wl.gamma, 0, 0, J, None, None, ws)
     assert e.value.code == V.ERR_SHAPE
+
+
+@pytest.mark.parametrize("mlp_reward", [False, True])
+def test_row_kernel_group_sizes_give_the_same_bits(V, mlp_reward):
+    # the small-MLP FP32 kernel takes 8 threads per row when a launch's rows fit
+    # in one wave (here the two 40-sequence shards, 10,240 rows each) and 4
+    # threads per row above (the whole 80-sequence problem, 20,480 rows); both
+    # accumulate every layer in input order, so the returns agree bit for bit,
+    # and both match the FP64 oracle
+    wl = WL.small_fp32(N=256, K=80, H=6)
+    g = V.DeviceMLP.from_spec(wl.g_T)
+    if mlp_reward:
+        R, Ro = V.mlp_reward(V.DeviceMLP.from_spec(wl.reward_mlp)), O.Reward(O.REWARD_MLP, mlp=oracle_mlp(wl.reward_mlp))
+    else:
+        R, Ro = V.goal_reward(wl.goal), O.Reward(O.REWARD_GOAL, wl.goal)
+    P, A = cuda(wl.particles), cuda(wl.actions)
+    N, K, H = 256, 80, 6
+    J = torch.empty(K, dtype=torch.float64, device="cuda")
+    G = torch.empty((K, N), dtype=torch.float64, device="cuda")
+    ws = V.alloc_workspace(V.voila_rollout_workspace_size(g, R, N, K, H))
+    V.voila_rollout(g, R, P, None, A, wl.d_omega, wl.gamma, wl.seed, 0, J, G, None, ws)
+    Gs = torch.empty((K, N), dtype=torch.float64, device="cuda")
+    Js = torch.empty(K, dtype=torch.float64, device="cuda")
+    wss = V.alloc_workspace(V.voila_rollout_workspace_size(g, R, N, K // 2, H))
+    for k0 in (0, K // 2):
+        V.voila_rollout_shard(g, R, P, None, 0, N, A[k0:k0 + K // 2].contiguous(), k0, wl.d_omega, wl.gamma,
+                              wl.seed, 0, Js[k0:k0 + K // 2], Gs[k0:k0 + K // 2], None, wss)
+        assert V.workspace_status(wss) == V.OK
+    assert V.workspace_status(ws) == V.OK
+    assert torch.equal(G, Gs) and torch.equal(J, Js)
+    Jo, Go = O.rollout(oracle_mlp(wl.g_T), Ro, wl.particles, wl.actions, wl.d_omega, wl.gamma, wl.seed)
+    assert rel_err(G.cpu().numpy(), Go) < TOL_FP32
+    assert rel_err(J.cpu().numpy(), Jo) < TOL_FP32
