@@ -224,6 +224,23 @@ def cpu_baseline(wl, seqs, particles=None):
                       f"sequences x {wl.N} particles x H={wl.H} ({trans} transitions) in {dt:.2f} s"}, J, res
 
 
+def one_core_oracle(wl, particles, seqs: int = 1):
+    """The oracle's rollout of `seqs` sequences x all particles with numpy's
+    BLAS held to one thread: the single-core figure beside the all-core one."""
+    from oracle import voila_oracle as O
+    import threadpoolctl
+    om = lambda spec: O.MLP(spec.W, spec.b, spec.act)  # noqa: E731
+    R = O.Reward(O.REWARD_MLP, mlp=om(wl.reward_mlp)) if wl.goal is None else O.Reward(O.REWARD_GOAL, wl.goal)
+    with threadpoolctl.threadpool_limits(limits=1):
+        t0 = time.perf_counter()
+        O.rollout(om(wl.g_T), R, particles, wl.actions, wl.d_omega, wl.gamma, wl.seed, k_index=list(range(seqs)))
+        dt = time.perf_counter() - t0
+    trans = seqs * wl.N * wl.H
+    return {"value": trans / dt, "unit": UNIT, "cores": 1,
+            "sample": f"rollout of {seqs} of {wl.K} sequences x {wl.N} particles x H={wl.H} ({trans} transitions) "
+                      f"in {dt:.2f} s, BLAS limited to one thread"}
+
+
 def oracle_belief(wl, lam):
     """The FP64 oracle's belief update on the error leg's inputs (prior particles,
     a = actions[0, 0], o = 0, step 1, planner 0) at temperature `lam`."""
@@ -1447,6 +1464,7 @@ def main():
         V.voila_rollout(g, R, p_new, None, actions, wl.d_omega, wl.gamma, wl.seed, planner, J, None, best, ws_r)
         torch.cuda.synchronize()
         cb, Jo, bres = cpu_baseline(wl, args.cpu_seqs, p_new.cpu().double().numpy())
+        cb["one_core"] = one_core_oracle(wl, p_new.cpu().double().numpy())
         line["cpu_baseline"] = cb
         Jd = J[: args.cpu_seqs].cpu().numpy()
         if J8 is not None:
