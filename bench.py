@@ -224,21 +224,43 @@ def cpu_baseline(wl, seqs, particles=None):
                       f"sequences x {wl.N} particles x H={wl.H} ({trans} transitions) in {dt:.2f} s"}, J, res
 
 
+_ONE_CORE_CHILD = """
+import json, sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2606_19729_b300 import workloads as WL
+from oracle import voila_oracle as O
+kind, prec, N, K, H, seqs = sys.argv[3], int(sys.argv[4]), *map(int, sys.argv[5:9])
+wl = WL.mid_bf16(prec=prec, N=N, K=K, H=H) if kind == "mid" else WL.small_fp32(N=N, K=K, H=H)
+om = lambda spec: O.MLP(spec.W, spec.b, spec.act)
+R = O.Reward(O.REWARD_MLP, mlp=om(wl.reward_mlp)) if wl.goal is None else O.Reward(O.REWARD_GOAL, wl.goal)
+p = np.load(sys.argv[2])
+t0 = time.perf_counter()
+O.rollout(om(wl.g_T), R, p, wl.actions, wl.d_omega, wl.gamma, wl.seed, k_index=list(range(seqs)))
+print(json.dumps({"dt": time.perf_counter() - t0}))
+"""
+
+
 def one_core_oracle(wl, particles, seqs: int = 1):
-    """The oracle's rollout of `seqs` sequences x all particles with numpy's
-    BLAS held to one thread: the single-core figure beside the all-core one."""
-    from oracle import voila_oracle as O
-    import threadpoolctl
-    om = lambda spec: O.MLP(spec.W, spec.b, spec.act)  # noqa: E731
-    R = O.Reward(O.REWARD_MLP, mlp=om(wl.reward_mlp)) if wl.goal is None else O.Reward(O.REWARD_GOAL, wl.goal)
-    with threadpoolctl.threadpool_limits(limits=1):
-        t0 = time.perf_counter()
-        O.rollout(om(wl.g_T), R, particles, wl.actions, wl.d_omega, wl.gamma, wl.seed, k_index=list(range(seqs)))
-        dt = time.perf_counter() - t0
+    """The oracle's rollout of `seqs` sequences x all particles in a fresh
+    interpreter whose BLAS runs one thread: the single-core figure beside the
+    all-core one."""
+    import tempfile
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    kind = "mid" if wl.name.startswith("mid") else "small"
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "particles.npy")
+        np.save(path, np.asarray(particles, dtype=np.float64))
+        r = subprocess.run([sys.executable, "-c", _ONE_CORE_CHILD, os.path.dirname(os.path.abspath(__file__)), path,
+                            kind, str(wl.prec), str(wl.N), str(wl.K), str(wl.H), str(seqs)],
+                           env=env, capture_output=True, text=True, timeout=300)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "error": (r.stderr.strip().splitlines() or ["?"])[-1]}
+    dt = json.loads(r.stdout.strip().splitlines()[-1])["dt"]
     trans = seqs * wl.N * wl.H
     return {"value": trans / dt, "unit": UNIT, "cores": 1,
             "sample": f"rollout of {seqs} of {wl.K} sequences x {wl.N} particles x H={wl.H} ({trans} transitions) "
-                      f"in {dt:.2f} s, BLAS limited to one thread"}
+                      f"in {dt:.2f} s, one BLAS thread (a fresh interpreter)"}
 
 
 def oracle_belief(wl, lam):
